@@ -1,0 +1,172 @@
+"""Ewald-split evaluation of the periodic sum (ground truth), FP64.
+TEST INFRASTRUCTURE ONLY.
+
+This is not one of the paper's algorithms: it evaluates the plain definition,
+Eq. 1 with the image sum of Eq. 2 (self term n = m, i = 0 dropped, every other
+image of every source kept), by the classical Ewald splitting so that both
+halves converge exponentially.  For a splitting parameter E:
+
+  spatial  f_E(R) = [e^{-jkR} erfc(RE - jk/2E) + e^{jkR} erfc(RE + jk/2E)] / (8 pi R)
+           (k = 0: erfc(RE)/(4 pi R))
+  3D lattice spectral part (Poisson summation, k_G = k0 + G, V = cell volume):
+           (1/V) sum_G exp((k^2-|k_G|^2)/4E^2)/(|k_G|^2-k^2) exp(-j k_G.r)
+  2D lattice (periodic x, y; z free; A = cell area, kz from Eq. pgf's branch):
+           sum_{m,n} exp(-j kt.rho)/(4 j kz A)
+                 * [e^{-j kz z} erfc(j kz/2E - zE) + e^{j kz z} erfc(j kz/2E + zE)]
+  self     lim_{R->0} [f_E(R) - G0(R)] = jk erfc(jk/2E)/(4 pi) - E e^{k^2/4E^2}/(2 pi^{3/2})
+
+As E -> infinity the 2D spectral part reduces term by term to Eq. pgf_2 and
+the 3D one to the Fourier series of Eq. 2; the tests check independence of E
+and agreement with brute-force image sums for a lossy wavenumber.
+
+For k = k0 = 0 on a 3D lattice the G = 0 term is dropped: this is the
+"tin-foil" periodic Green's function, which solves -lap G = delta - 1/V with
+zero cell mean.  Eq. lgf_3 solves the same equation, so the two differ by a
+constant that cancels for neutral charges (Eq. neutral).
+"""
+import numpy as np
+from scipy import special
+
+from .greens import csqrt_neg_imag
+
+FOUR_PI = 4.0 * np.pi
+SQRT_PI = np.sqrt(np.pi)
+
+
+def exp_erfc(A, B):
+    """exp(A) * erfc(B) for complex A, B without overflow of either factor."""
+    A = np.asarray(A, np.complex128)
+    B = np.asarray(B, np.complex128)
+    out = np.empty(np.broadcast(A, B).shape, np.complex128)
+    Ab, Bb = np.broadcast_arrays(A, B)
+    pos = Bb.real > 0
+    out[pos] = special.erfcx(Bb[pos]) * np.exp(Ab[pos] - Bb[pos] ** 2)
+    out[~pos] = np.exp(Ab[~pos]) * special.erfc(Bb[~pos])
+    return out
+
+
+def spatial_kernel(R, k, E):
+    """f_E(R) (see module docstring); R > 0."""
+    R = np.asarray(R, np.float64)
+    if k == 0:
+        return special.erfc(R * E) / (FOUR_PI * R)
+    a = 1j * k / (2.0 * E)
+    return (exp_erfc(-1j * k * R, R * E - a) + exp_erfc(1j * k * R, R * E + a)) / (2.0 * FOUR_PI * R)
+
+
+def self_term(k, E):
+    """lim_{R->0} [f_E(R) - G0(R)]."""
+    if k == 0:
+        return -E / (2.0 * np.pi * SQRT_PI)
+    return 1j * k * special.erfc(1j * k / (2.0 * E)) / FOUR_PI - E * np.exp(k * k / (4.0 * E * E)) / (2.0 * np.pi * SQRT_PI)
+
+
+def _spatial_images(L, pdims, rcut):
+    rng = []
+    for d in range(3):
+        if d in pdims:
+            M = int(np.ceil(rcut / L[d])) + 1
+            rng.append(np.arange(-M, M + 1))
+        else:
+            rng.append(np.zeros(1, np.int64))
+    return np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, 3)
+
+
+def potential(points, q, tgt, L, pdims, k, k0, E, tol=1e-15, chunk=2048):
+    """u at the points with indices tgt (Eq. 1, self term excluded), by Ewald
+    splitting on a 3D or 2D lattice.  points (N,3), q (N,) complex.
+    For the 2D lattice the periodic axes are relabelled to x, y."""
+    points = np.asarray(points, np.float64)
+    q = np.asarray(q, np.complex128)
+    tgt = np.asarray(tgt, np.int64)
+    L = np.asarray(L, np.float64)
+    k0 = np.asarray(k0, np.complex128)
+    pd = sorted(pdims)
+    order = pd + [d for d in range(3) if d not in pd]
+    points, L, k0 = points[:, order], L[order], k0[order]
+    pdc = tuple(range(len(pd)))
+    X = np.sqrt(-np.log(tol)) + 0.5           # erfc(X) ~ tol
+    rcut = X / E
+    u = np.zeros(len(tgt), np.complex128)
+    # ---------------- spatial part -----------------------------------
+    imgs = _spatial_images(L, pdc, rcut + np.linalg.norm(L[list(pdc)]))
+    for t, m in enumerate(tgt):
+        acc = 0.0 + 0.0j
+        for i in imgs:
+            sh = i * L
+            d = points[m] - points - sh
+            R = np.linalg.norm(d, axis=1)
+            sel = R < rcut
+            if not i.any():
+                sel[m] = False
+            if not sel.any():
+                continue
+            ph = np.exp(-1j * np.dot(k0, sh))
+            acc += ph * np.sum(q[sel] * spatial_kernel(R[sel], k, E))
+        u[t] = acc + q[m] * self_term(k, E)
+    # ---------------- spectral part ----------------------------------
+    Gc = 2.0 * E * X + abs(k) + 1.0
+    if len(pd) == 3:
+        V = np.prod(L)
+        ms = [np.arange(-int(np.ceil(Gc * L[d] / (2 * np.pi))) - 1, int(np.ceil(Gc * L[d] / (2 * np.pi))) + 2) for d in range(3)]
+        kx = k0[0] + 2 * np.pi * ms[0] / L[0]
+        ky = k0[1] + 2 * np.pi * ms[1] / L[1]
+        kz = k0[2] + 2 * np.pi * ms[2] / L[2]
+        # structure factor T(kG) = sum_n q_n exp(+j kG . r_n), separable in x, y, z
+        ex = np.exp(1j * np.outer(points[:, 0], kx))
+        ey = np.exp(1j * np.outer(points[:, 1], ky))
+        ez = np.exp(1j * np.outer(points[:, 2], kz))
+        K2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+        with np.errstate(divide="ignore", invalid="ignore"):
+            f = np.exp((k * k - K2) / (4 * E * E)) / (K2 - k * k)
+        if k == 0 and not np.any(k0 != 0):
+            f[np.abs(K2) == 0] = 0.0
+        f[np.abs(K2) ** 0.5 > Gc + 2 * np.pi / L.min()] = 0.0
+        T = np.zeros(K2.shape, np.complex128)
+        for s0 in range(0, len(points), chunk):
+            s1 = min(len(points), s0 + chunk)
+            qa = q[s0:s1, None] * ex[s0:s1]
+            yz = (ey[s0:s1, :, None] * ez[s0:s1, None, :]).reshape(s1 - s0, -1)
+            T += (qa.T @ yz).reshape(K2.shape)
+        W = f * T / V
+        for t, m in enumerate(tgt):
+            px = np.exp(-1j * kx * points[m, 0])
+            py = np.exp(-1j * ky * points[m, 1])
+            pz = np.exp(-1j * kz * points[m, 2])
+            u[t] += np.einsum("abc,a,b,c->", W, px, py, pz)
+        if k == 0 and not np.any(k0 != 0):
+            u += -np.sum(q) / (4 * E * E * V)
+    elif len(pd) == 2:
+        A = L[0] * L[1]
+        Mx = int(np.ceil(Gc * L[0] / (2 * np.pi))) + 1
+        My = int(np.ceil(Gc * L[1] / (2 * np.pi))) + 1
+        kx = k0[0] + 2 * np.pi * np.arange(-Mx, Mx + 1) / L[0]
+        ky = k0[1] + 2 * np.pi * np.arange(-My, My + 1) / L[1]
+        KX, KY = np.meshgrid(kx, ky, indexing="ij")
+        sel = np.hypot(np.abs(KX), np.abs(KY)) <= Gc + 2 * np.pi / min(L[0], L[1])
+        KX, KY = KX[sel], KY[sel]
+        kz = csqrt_neg_imag(k * k - KX ** 2 - KY ** 2)
+        jkz = 1j * kz
+        for t, m in enumerate(tgt):
+            d = points[m] - points
+            z = d[:, 2][:, None]
+            tph = np.exp(-1j * (np.outer(d[:, 0], KX) + np.outer(d[:, 1], KY)))
+            br = exp_erfc(-1j * kz[None, :] * z, jkz[None, :] / (2 * E) - z * E) \
+                + exp_erfc(1j * kz[None, :] * z, jkz[None, :] / (2 * E) + z * E)
+            u[t] += np.sum(q[:, None] * tph * br / (4j * kz[None, :] * A))
+    else:
+        raise ValueError("Ewald ground truth implemented for 2D and 3D lattices")
+    return u
+
+
+def greens_function(r, L, pdims, k, k0, E):
+    """Single-source periodic Green's function G^p(r) by Ewald splitting
+    (for r not on the lattice).  Implemented as the potential at r of a unit
+    source at the origin."""
+    r = np.atleast_2d(np.asarray(r, np.float64))
+    out = np.empty(len(r), np.complex128)
+    for i, rr in enumerate(r):
+        pts = np.stack([rr, np.zeros(3)])
+        qq = np.array([0.0, 1.0], np.complex128)
+        out[i] = potential(pts, qq, [0], L, pdims, k, k0, E)[0]
+    return out

@@ -1,0 +1,137 @@
+"""Seeded synthetic workloads (points, source strengths and problem sizes).
+
+This module holds no arithmetic of the method: it only draws points and
+source strengths with numpy's PCG64 generator and lists the problem
+parameters of each workload.  The CUDA library and the FP64 oracles both take
+their inputs from here.
+
+The paper's own workloads are tetrahedral meshes of cubes and of a coaxial
+cable (Sec. 4), which are not published; these synthetic point sets stand in
+for them.  Each workload below is named by what it is.
+
+  coulomb3d_4k      3D-periodic static Coulomb, unit cube, N = 4096 uniform,
+                    charges +-1 in equal numbers (net zero), grid 32^3, p = 4,
+                    one near-image layer, FP64.
+  helmholtz2d_262k  2D-periodic (x, y) Helmholtz with a Bloch phase shift,
+                    cell 1 x 1 x 0.5, k = 2 pi 0.8, k0 = (0.3k, 0.1k, 0),
+                    N = 262144: half uniform, half on a sphere of radius 0.2
+                    at the cell centre; sources CN(0, 1); grid 128 x 128 x 64,
+                    p = 4; complex64 bulk, FP64 far series and correction.
+  helmholtz1d_batch 16 sets, 1D-periodic along z Helmholtz, cell
+                    1 x 0.25 x 0.25, k = 2 pi 0.5, N log-uniform in
+                    [1e4, 5e5] (half uniform, half in 8 Gaussian clusters of
+                    sigma 0.02), 64 complex64 right-hand sides.
+  coulomb3d_1m      3D static Coulomb, N = 10^6 uniform, charges N(0,1) minus
+                    their mean, grid 256^3, p = 4, FP32 bulk; energy gradient.
+  helmholtz3d_16m   3D-periodic Helmholtz with Bloch phase, k = 2 pi 2,
+                    k0 = (0.2k, 0.2k, 0), N = 1.6e7 (3/4 uniform, 1/4 on 8
+                    spheres of radius 0.05), grid 512^3, p = 4.
+
+"Twins" are the same recipes at a smaller N and grid (for tests whose
+oracle must finish in seconds).
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2312_02376
+
+
+@dataclass
+class Workload:
+    name: str
+    D: tuple
+    pdims: tuple
+    k: float
+    k0: tuple
+    n: tuple                 # near grid nodes per axis (spanning [0, D])
+    p: int
+    layers: int
+    b: int                   # correction radius (grid steps)
+    nf: tuple                # far grid nodes per axis
+    pf: int
+    precision: str           # "fp64" or "fp32"
+    N: int
+    nrhs: int = 1
+    points: np.ndarray = field(default=None, repr=False)
+    q: np.ndarray = field(default=None, repr=False)
+
+
+def _rng(index, salt=0):
+    return np.random.Generator(np.random.PCG64(SEED_BASE + index + 1000 * salt))
+
+
+def _sphere(rng, n, centre, radius):
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return centre + radius * v
+
+
+def _cn(rng, shape):
+    """Circular complex normal CN(0,1): real and imaginary parts N(0, 1/2)."""
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * np.sqrt(0.5)
+
+
+def coulomb3d(N=4096, n=32, index=0, salt=0, b=5, nf=10):
+    rng = _rng(index, salt)
+    pts = rng.random((N, 3))
+    q = np.concatenate([np.ones(N // 2), -np.ones(N - N // 2)])
+    rng.shuffle(q)
+    return Workload("coulomb3d_%d" % N, (1.0, 1.0, 1.0), (0, 1, 2), 0.0, (0.0, 0.0, 0.0),
+                    (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp64", N, 1, pts, q.astype(np.float64))
+
+
+def helmholtz2d(N=262144, n=(128, 128, 64), index=1, salt=0, b=5, nf=(12, 12, 8)):
+    rng = _rng(index, salt)
+    D = np.array([1.0, 1.0, 0.5])
+    nu = N // 2
+    uni = rng.random((nu, 3)) * D
+    sph = _sphere(rng, N - nu, np.array([0.5, 0.5, 0.25]), 0.2)
+    pts = np.concatenate([uni, sph])
+    q = _cn(rng, N)
+    k = 2 * np.pi * 0.8
+    return Workload("helmholtz2d_%d" % N, tuple(D), (0, 1), k, (0.3 * k, 0.1 * k, 0.0),
+                    tuple(n), 4, 1, b, tuple(nf), 4, "fp32", N, 1, pts, q.astype(np.complex64))
+
+
+def coulomb3d_big(N=1_000_000, n=256, index=3, salt=0, b=5, nf=10):
+    rng = _rng(index, salt)
+    pts = rng.random((N, 3))
+    q = rng.standard_normal(N)
+    q = q - np.mean(q)
+    return Workload("coulomb3d_%d" % N, (1.0, 1.0, 1.0), (0, 1, 2), 0.0, (0.0, 0.0, 0.0),
+                    (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp32", N, 1, pts, q.astype(np.float32))
+
+
+def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=20):
+    rng = _rng(index, salt)
+    nu = (3 * N) // 4
+    uni = rng.random((nu, 3))
+    rest = N - nu
+    centres = 0.05 + 0.9 * rng.random((8, 3))
+    per = np.full(8, rest // 8)
+    per[: rest - per.sum()] += 1
+    sph = np.concatenate([_sphere(rng, c, centres[i], 0.05) for i, c in enumerate(per)])
+    pts = np.concatenate([uni, sph])
+    k = 2 * np.pi * 2.0
+    q = _cn(rng, N)
+    return Workload("helmholtz3d_%d" % N, (1.0, 1.0, 1.0), (0, 1, 2), k, (0.2 * k, 0.2 * k, 0.0),
+                    (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp32", N, 1, pts, q.astype(np.complex64))
+
+
+def random_case(N, D, pdims, k, k0, n, p=4, layers=1, b=5, nf=(10, 10, 10), pf=4, seed=0,
+                complex_q=True, neutral=False, precision="fp64", nrhs=1):
+    """A small uniform case with arbitrary parameters (for parity tests)."""
+    rng = _rng(100 + seed)
+    D = np.asarray(D, np.float64)
+    pts = rng.random((N, 3)) * D
+    if complex_q:
+        q = _cn(rng, (N, nrhs))
+    else:
+        q = rng.standard_normal((N, nrhs))
+    if neutral:
+        q = q - q.mean(axis=0, keepdims=True)
+    if nrhs == 1:
+        q = q[:, 0]
+    return Workload("random_%d" % N, tuple(D), tuple(pdims), k, tuple(k0), tuple(n), p, layers, b,
+                    tuple(nf), pf, precision, N, nrhs, pts, q)

@@ -1,0 +1,213 @@
+"""Pins for oracle.pim, the FFT-PIM operator of Sec. 3 with a direct grid
+convolution.  Each test checks the oracle against something other than
+itself: the plain O(N^2) definition (Eq. 1-2), Ewald ground truth, the exact
+near-zone sum that the correction must reproduce when every pair is
+corrected (Eq. er), a dense conjugate transpose, an FFT convolution, and the
+method's error trend in the interpolation order (Sec. 4.1)."""
+import numpy as np
+import pytest
+
+from oracle import ewald, greens, pim
+from paper_2312_02376_gb300 import inputs
+
+
+def _dense_exact(pts, k, D=None, pdims=(), k0=(0, 0, 0), images=None):
+    """sum over the given images of exp(-jk0.iL) G0(r_m - r_n - iL), self term dropped."""
+    N = len(pts)
+    if images is None:
+        images = np.zeros((1, 3), np.int64)
+    A = np.zeros((N, N), np.complex128)
+    for i in images:
+        sh = i * np.asarray(D if D is not None else np.ones(3))
+        d = pts[:, None, :] - pts[None, :, :] - sh
+        R = np.linalg.norm(d, axis=-1)
+        if not i.any():
+            np.fill_diagonal(R, 1.0)
+        G = np.exp(-1j * np.dot(np.asarray(k0, complex), sh)) * greens.G0(R, k)
+        if not i.any():
+            np.fill_diagonal(G, 0.0)
+        A += G
+    return A
+
+
+@pytest.mark.parametrize("k", [0.0, 4.0])
+def test_all_pairs_corrected_equals_exact_sum_nonperiodic(k):
+    # With every pair corrected, Eq. er replaces the whole grid interaction
+    # by the exact kernel: the result is Eq. 1 with G0, to round-off.
+    rng = np.random.default_rng(1)
+    pts = rng.random((90, 3)) * np.array([1, 1, 0.5])
+    q = rng.standard_normal(90) + 1j * rng.standard_normal(90)
+    P = pim.Params(D=(1, 1, 0.5), pdims=(), k=k, k0=(0, 0, 0), n=(12, 12, 7), p=4, layers=0, b=100)
+    u = pim.Plan(P, pts).apply(q)
+    ex = _dense_exact(pts, k) @ q
+    assert np.linalg.norm(u - ex) / np.linalg.norm(ex) < 1e-12
+
+
+def test_all_pairs_corrected_periodic_near_part_exact():
+    # 2D-periodic, Bloch phase: with every (pair, near image) corrected, the
+    # near part is the exact truncated image sum of Eq. 4.
+    rng = np.random.default_rng(2)
+    pts = rng.random((70, 3)) * np.array([1, 1, 0.5])
+    q = rng.standard_normal(70) + 1j * rng.standard_normal(70)
+    k = 2 * np.pi * 0.8
+    k0 = (0.3 * k, 0.1 * k, 0.0)
+    P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=k, k0=k0, n=(10, 10, 6), p=4, layers=1, b=100,
+                   nf=(8, 8, 6), pf=4)
+    pl = pim.Plan(P, pts)
+    u = pl.apply(q)
+    far = pim.far_apply(P, pl.F, pl.ss, pl.ws, pl.so, pl.wo, q)
+    ex = _dense_exact(pts, k, P.D, P.pdims, k0, P.images()) @ q
+    assert np.linalg.norm(u - far - ex) / np.linalg.norm(ex) < 1e-12
+
+
+def test_separable_correction_equals_explicit_double_sum():
+    rng = np.random.default_rng(3)
+    pts = rng.random((120, 3))
+    P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=3.0, k0=(1.0, 0.5, 0.2), n=(12, 12, 12), p=4, layers=1, b=4)
+    s, w, B = pim.near_stencils(P, pts)
+    m, n, ii = pim.correction_pairs(P, B)
+    sel = np.random.default_rng(0).choice(len(m), 1500, replace=False)
+    a = pim.correction_values_explicit(P, pts, s, w, m[sel], n[sel], ii[sel])
+    b = pim.correction_values(P, pts, s, w, m[sel], n[sel], ii[sel])
+    assert np.max(np.abs(a - b)) < 1e-14 * np.max(np.abs(a))
+
+
+def test_direct_convolution_matches_fft_convolution():
+    P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=2.0, k0=(0.5, 0.0, 0.3), n=(9, 7, 6), p=2, layers=1)
+    K = pim.near_table(P)
+    rng = np.random.default_rng(4)
+    Q = rng.standard_normal(tuple(P.n)) + 1j * rng.standard_normal(tuple(P.n))
+    U = pim.conv_direct_full(P, K, Q)
+    # linear convolution by zero-padded FFT, sizes 3n-2
+    sh = tuple(3 * P.n - 2)
+    full = np.fft.ifftn(np.fft.fftn(K, sh, axes=(0, 1, 2)) * np.fft.fftn(Q, sh, axes=(0, 1, 2)))
+    n = P.n
+    assert np.allclose(U, full[n[0] - 1:2 * n[0] - 1, n[1] - 1:2 * n[1] - 1, n[2] - 1:2 * n[2] - 1], atol=1e-12)
+    nodes = np.array([[0, 0, 0], [8, 6, 5], [3, 2, 4]])
+    assert np.allclose(pim.conv_direct_at(P, K, Q, nodes), U[nodes[:, 0], nodes[:, 1], nodes[:, 2]], atol=1e-12)
+
+
+def test_apply_rows_equals_apply():
+    W = inputs.random_case(150, (1, 1, 0.5), (0, 1), 5.0, (1.0, 0.5, 0.0), (10, 10, 6), b=3, nf=(8, 8, 6))
+    P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=1, b=W.b, nf=W.nf, pf=4)
+    pl = pim.Plan(P, W.points)
+    u = pl.apply(W.q)
+    rows = np.array([0, 17, 99, 149])
+    assert np.allclose(pl.apply_rows(W.q, rows), u[rows], rtol=1e-12, atol=1e-12 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("case", ["helmholtz2d", "npsp3d", "helmholtz1d"])
+def test_adjoint_is_conjugate_transpose(case):
+    rng = np.random.default_rng(5)
+    N = 30
+    if case == "helmholtz2d":
+        P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=4.0, k0=(1.2, 0.4, 0.0), n=(8, 8, 6), p=3, layers=1, b=2,
+                       nf=(6, 6, 5), pf=3)
+    elif case == "helmholtz1d":
+        P = pim.Params(D=(0.5, 0.5, 1.0), pdims=(2,), k=3.0, k0=(0, 0, 0.0), n=(6, 6, 8), p=2, layers=1, b=2,
+                       nf=(5, 5, 6), pf=2)
+    else:
+        P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=0.0, k0=(0, 0, 0), n=(8, 8, 8), p=2, layers=1, b=2,
+                       nf=(5, 5, 5), pf=2)
+    pts = rng.random((N, 3)) * P.D
+    pl = pim.Plan(P, pts)
+    E = np.eye(N, dtype=complex)
+    if P.npsp:
+        # the forward operator is defined on neutral inputs: use the basis of
+        # the neutral subspace e_j - mean
+        cols = [pl.apply(E[:, j] - 1.0 / N) for j in range(N)]
+    else:
+        cols = [pl.apply(E[:, j]) for j in range(N)]
+    A = np.array(cols).T
+    AH = np.array([pl.apply_adjoint(E[:, j]) for j in range(N)]).T
+    if P.npsp:
+        Pm = np.eye(N) - 1.0 / N
+        assert np.allclose(AH, Pm @ A.conj().T, atol=1e-12 * np.abs(A).max())
+    else:
+        assert np.allclose(AH, A.conj().T, atol=1e-12 * np.abs(A).max())
+
+
+def test_method_error_falls_with_order_lossy_periodic():
+    # Sec. 4.1: the error falls with interpolation order; reference = Eq. 2
+    # summed by brute force (converges for Im k < 0).
+    rng = np.random.default_rng(6)
+    N = 220
+    D = np.array([1.0, 1.0, 0.5])
+    pts = rng.random((N, 3)) * D
+    q = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    k = 6.0 - 2.5j
+    k0 = (0.8, -0.5, 0.0)
+    imgs = greens.image_offsets((0, 1), 14)
+    ref = _dense_exact(pts, k, D, (0, 1), k0, imgs) @ q
+    errs = []
+    for p in (2, 4):
+        P = pim.Params(D=D, pdims=(0, 1), k=k, k0=k0, n=(17, 17, 9), p=p, layers=1, b=p + 1,
+                       nf=(14, 14, 8), pf=p)
+        u = pim.Plan(P, pts).apply(q)
+        errs.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    assert errs[1] < 0.2 * errs[0]
+    assert errs[1] < 3e-4
+
+
+def test_npsp3d_vs_ewald_within_method_error():
+    W = inputs.coulomb3d(N=512, n=16)
+    P = pim.Params(D=W.D, pdims=W.pdims, k=0.0, k0=W.k0, n=W.n, p=4, layers=1, b=5, nf=W.nf, pf=4)
+    u = pim.Plan(P, W.points).apply(W.q)
+    ref = ewald.potential(W.points, W.q.astype(complex), np.arange(W.N), W.D, W.pdims, 0.0, np.zeros(3), 6.0)
+    e = u - ref
+    e -= e.mean()          # Eq. lgf and the Ewald sum differ by a constant
+    assert np.linalg.norm(e) / np.linalg.norm(ref - ref.mean()) < 2e-4
+
+
+def test_far_table_against_ewald():
+    # F(delta) = G^p - G_near at delta*Delta + Delta/2, checked pointwise
+    # against the Ewald sum minus the same near images.
+    P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=2 * np.pi * 0.8, k0=(1.5, 0.5, 0.0), n=(8, 8, 6), p=4,
+                   layers=1, nf=(6, 6, 4), pf=3)
+    F = pim.far_table(P)
+    dF = P.delta_f
+    for dl in [(0, 0, 0), (-5, 3, -3), (5, -5, 3), (2, 1, -1)]:
+        r = np.array(dl) * dF + 0.5 * dF
+        e = ewald.greens_function(r, P.D, P.pdims, P.k, P.k0, 3.0)[0]
+        e -= greens.image_sum(r[None], P.D, P.pdims, P.k, P.k0, P.images())[0]
+        got = F[tuple(np.array(dl) + P.nf - 1)]
+        assert abs(got - e) < 1e-12 * max(1.0, abs(e))
+
+
+def test_npsp_neutrality_and_constant_invariance():
+    W = inputs.coulomb3d(N=64, n=8)
+    P = pim.Params(D=W.D, pdims=W.pdims, k=0.0, k0=W.k0, n=W.n, p=2, layers=1, b=3, nf=(5, 5, 5), pf=2)
+    pl = pim.Plan(P, W.points)
+    u = pl.apply(W.q)
+    with pytest.raises(ValueError):
+        pl.apply(W.q + 0.01)
+    # Eq. lgf is defined up to a constant: shifting the far table by one does
+    # not change the potential of a neutral source set.
+    pl2 = pim.Plan(P, W.points, F=pl.F + 7.25)
+    assert np.allclose(pl2.apply(W.q), u, atol=1e-12 * np.abs(u).max())
+
+
+def test_bloch_phase_when_a_source_crosses_the_cell():
+    # Eq. 2: moving a source by a lattice vector a with its amplitude scaled
+    # by exp(-j k0.a) leaves every other potential unchanged, and the
+    # potential at the moved point scales by exp(-j k0.a); exact for the
+    # definition, at method-error level for FFT-PIM.
+    rng = np.random.default_rng(8)
+    N = 200
+    D = np.array([1.0, 1.0, 0.5])
+    pts = rng.random((N, 3)) * D
+    pts[0, 0] = 0.0
+    q = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    k = 2 * np.pi * 0.8
+    k0 = np.array([0.3 * k, 0.1 * k, 0.0])
+    P = pim.Params(D=D, pdims=(0, 1), k=k, k0=k0, n=(17, 17, 9), p=4, layers=1, b=5, nf=(14, 14, 8), pf=4)
+    u1 = pim.Plan(P, pts).apply(q)
+    pts2 = pts.copy()
+    pts2[0, 0] = 1.0
+    q2 = q.copy()
+    ph = np.exp(-1j * k0[0] * 1.0)
+    q2[0] *= ph
+    u2 = pim.Plan(P, pts2).apply(q2)
+    scale = np.linalg.norm(u1)
+    assert np.linalg.norm(u2[1:] - u1[1:]) / scale < 3e-4
+    assert abs(u2[0] - ph * u1[0]) / np.abs(u1).mean() < 3e-3
