@@ -141,9 +141,13 @@ def pgf3_canon_grid(xs, ys, z, Lx, Ly, Lz, k, kx0, ky0, kz0):
     kx, ky, kz = _pgf2_modes(dlen, Lx, Ly, k, kx0, ky0)
     em = np.exp(-1j * (kz - kz0) * Lz)
     ep = np.exp(-1j * (kz + kz0) * Lz)
+    # the bracket of Eq. pgf_3 with each numerator's exponentials combined,
+    # e^{-j(kz-kz0)Lz} e^{-j kz z} = e^{-j kz (Lz+z)} e^{j kz0 Lz} and
+    # e^{-j(kz+kz0)Lz} e^{+j kz z} = e^{-j kz (Lz-z)} e^{-j kz0 Lz},
+    # so that no factor overflows for strongly evanescent modes
     zfac = (np.exp(-1j * kz * abs(z))
-            + em * np.exp(-1j * kz * z) / (1.0 - em)
-            + ep * np.exp(1j * kz * z) / (1.0 - ep))
+            + np.exp(-1j * kz * (Lz + z) + 1j * kz0 * Lz) / (1.0 - em)
+            + np.exp(-1j * kz * (Lz - z) - 1j * kz0 * Lz) / (1.0 - ep))
     F = zfac / (2j * kz * Lx * Ly)
     Ex = np.exp(-1j * np.outer(np.asarray(xs, np.float64), kx))
     Ey = np.exp(-1j * np.outer(np.asarray(ys, np.float64), ky))
