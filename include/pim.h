@@ -1,0 +1,217 @@
+/*
+ * pim.h -- C ABI of the GB300 FFT-PIM library (libpim.so).
+ *
+ * FFT periodic interpolation method of Ai & Lomakin, arXiv 2312.02376:
+ * the periodic scalar potential
+ *
+ *     u(r_m) = sum_n G^p(r_m - r_n) q_n                         (Eq. 1)
+ *     G^p(r) = sum_i exp(-j k0.(i o L)) G0(r - i o L),
+ *     G0(r)  = exp(-j k |r|) / (4 pi |r|)                       (Eq. 2)
+ *
+ * at N points that are both sources and observers in one cell of a 1D, 2D
+ * or 3D periodic array (Sec. 2), evaluated as u = u_near + u_far (Eq. 4-5):
+ * the near zone (images |i_d| <= i_d) by Lagrange anterpolation onto a
+ * uniform grid, a zero-padded FFT convolution with the tabulated near-zone
+ * kernel, interpolation back to the points and a sparse near-pair
+ * correction (Sec. 3.3, steps 1-4, Eq. er); the far zone (all other images)
+ * by projection onto a sparse grid, a grid-to-grid sum with the series form
+ * of the periodic Green's function (Eq. pgf; Eq. lgf in the neutral static
+ * case) and interpolation from a grid shifted by half a step (Sec. 3.2,
+ * Eq. grid, projection, 8, interpolation).
+ *
+ * Conventions
+ *   - The paper's engineering convention: j = sqrt(-1), time factor e^{jwt},
+ *     so the Bloch condition is u(r + a) = exp(-j k0.a) u(r) for a lattice
+ *     vector a (the physics form exp(i k0.a) with i = -j).
+ *   - The self term n = m is dropped only for the image i = 0; self images
+ *     (n = m, i != 0) are kept.
+ *   - Complex data are interleaved (re, im).  q and u are [N][nrhs], the
+ *     right-hand-side index fastest.  PIM_FP64 plans use complex128 data,
+ *     PIM_FP32_MIXED plans complex64.  In the neutral static case
+ *     (k = 0 and k0 = 0) the data are real (float64 / float32).
+ *   - Pointers may be device or host memory; host buffers are staged
+ *     through the plan's device buffers on the given stream (the call then
+ *     returns after the result has been copied back).
+ *   - Threading: a plan is not thread safe.  All device work of a call is
+ *     ordered on the stream passed to that call (0 = the legacy default
+ *     stream); the plan's internal second stream is joined back to it.
+ *
+ * Errors are returned as pim_status codes; no call aborts the process, and
+ * no device fault is used for control flow.  Device-side conditions (a
+ * non-neutral input in the neutral static case, an internal bounds check)
+ * set a flag that pim_last_device_status() reads after synchronising.
+ */
+#ifndef PIM_H
+#define PIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pim_plan_s* pim_plan;
+
+typedef enum {
+    PIM_OK = 0,
+    PIM_ERR_ARG = 1,          /* invalid argument (null pointer, size, grid) */
+    PIM_ERR_UNSUPPORTED = 2,  /* non-rectangular lattice, complex k or k0, p out of range */
+    PIM_ERR_ANOMALY = 3,      /* Rayleigh-Wood anomaly: k_z or k_rho of a Floquet mode ~ 0 (Sec. 2) */
+    PIM_ERR_NOT_NEUTRAL = 4,  /* k = k0 = 0 and |sum q| > neutral_tol * sum |q| (Eq. neutral) */
+    PIM_ERR_OUT_OF_CELL = 5,  /* a point outside the closed cell [0, D] */
+    PIM_ERR_STATE = 6,        /* apply before pim_set_points */
+    PIM_ERR_OOM = 7,          /* device allocation failed or mem_cap exceeded */
+    PIM_ERR_CUDA = 8,         /* a CUDA runtime call failed */
+    PIM_ERR_TIMEOUT = 9,      /* a bounded device wait ran out */
+    PIM_ERR_DEVICE = 10       /* a device-side bounds check tripped */
+} pim_status;
+
+typedef enum {
+    PIM_FP64 = 0,             /* every stage in FP64 */
+    PIM_FP32_MIXED = 1        /* spread, FFT, gather in FP32 / complex64; far series,
+                                 far grid sum, near-pair correction and the neutral
+                                 regularisation in FP64 */
+} pim_precision;
+
+typedef enum {
+    PIM_CORR_FP64 = 0,        /* correction values FP64, FP64 accumulation */
+    PIM_CORR_DOUBLE_FLOAT = 1,/* values as FP64 split into two floats, compensated
+                                 (double-float) accumulation on the FP32 pipes */
+    PIM_CORR_FP32 = 2         /* values rounded to complex64 after the FP64
+                                 cancellation, FP32 accumulation */
+} pim_corr_mode;
+
+typedef struct {
+    int far_n[3];        /* far grid nodes per axis; 0 -> max(10, ceil(4 k D_d))      */
+    int far_p;           /* far Lagrange degree; -1 -> p                               */
+    int corr_radius;     /* b, error-correction radius D^ER in grid steps; -1 -> p+1   */
+    int corr_cube;       /* 0: boxes within D^ER of the observer box (|r - r_m| <=
+                            D^ER, Sec. 3.3 step 4); 1: Chebyshev box distance <= b     */
+    int corr_mode;       /* pim_corr_mode; ignored (FP64) for PIM_FP64 plans           */
+    int tile[3];         /* spread node tile; 0 -> autotuned default                   */
+    double neutral_tol;  /* tau of the neutrality check; default 1e-6                  */
+    double series_tol;   /* relative truncation of the far series; default 1e-16      */
+    size_t mem_cap;      /* bytes; 0 = no cap.  Exceeding it -> PIM_ERR_OOM            */
+} pim_options;
+
+typedef struct {
+    int n[3];            /* near grid nodes per axis (spanning [0, D_d])               */
+    int nf[3];           /* far grid nodes per axis                                    */
+    int p, pf, corr_radius, precision, corr_mode, periodic_mask, near_layers;
+    int64_t N;           /* points (0 before pim_set_points)                           */
+    int64_t nnz;         /* near-pair correction entries                               */
+    size_t device_bytes; /* bytes the plan holds on the device                         */
+    double plan_ms;      /* wall time of pim_plan_create                               */
+    double points_ms;    /* wall time of the last pim_set_points                       */
+} pim_info;
+
+/* Fills *opt with the defaults documented above. */
+void pim_options_default(pim_options* opt);
+
+/* Human-readable name of a status code (static string). */
+const char* pim_status_string(pim_status s);
+
+/* Message of the last error raised by a call on this thread ("" if none);
+ * valid until the next call. */
+const char* pim_last_error(void);
+
+/*
+ * pim_plan_create -- pre-processing of Sec. 3.2-3.3 that does not depend on
+ * the points: near grid, near-zone kernel table (G_near of Eq. 4 on the
+ * grid, Sec. 3.3 step 2) and its spectrum on the zero-padded grid, far grids
+ * (Eq. grid) and the far table G_far = G^p - G_near (Sec. 3.2) from the
+ * series of Eq. pgf / Eq. lgf.
+ *
+ *   out            receives the plan (NULL on error).
+ *   lattice        3x3 row-major, rows a1, a2, a3.  Must be diagonal
+ *                  (rectangular cell, PIM_ERR_UNSUPPORTED otherwise).  The
+ *                  diagonal gives the cell extents D_d; on periodic axes the
+ *                  period is L_d = D_d.
+ *   periodic_mask  bit d set: periodic along axis d (0 = free space, near
+ *                  zone only).
+ *   k              wavenumber (k_0 of the paper), real, >= 0.
+ *   k0             phase shift per axis (k_x0, k_y0, k_z0), real; must be 0 on
+ *                  non-periodic axes.
+ *   h              grid spacing per axis: D_d / h_d must be an integer; the
+ *                  grid has n_d = D_d / h_d + 1 nodes spanning [0, D_d].
+ *   p              near Lagrange degree (p+1 nodes per axis), 2..4.
+ *   near_layers    i_d >= 0, near-zone image layers per periodic axis (Eq. 4).
+ *   prec           pim_precision.
+ *   opt            options (NULL = defaults); copied.
+ *   stream         cudaStream_t (NULL = legacy default stream) for the
+ *                  table kernels; the call synchronises before returning.
+ * Returns PIM_OK, PIM_ERR_ARG, PIM_ERR_UNSUPPORTED, PIM_ERR_ANOMALY,
+ * PIM_ERR_OOM or PIM_ERR_CUDA.  The plan owns every device buffer it makes.
+ */
+pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned periodic_mask, double k,
+                           const double k0[3], const double h[3], int p, int near_layers,
+                           pim_precision prec, const pim_options* opt, void* stream);
+
+/*
+ * pim_set_points -- the point-dependent pre-processing (Sec. 3.2 and 3.3):
+ * bins the points into the grid's boxes (counting sort), stores their
+ * stencils and interpolation coordinates, and builds the near-pair
+ * correction list of Sec. 3.3 step 4 (Eq. er, single-extra-image rule) with
+ * its values exp(-j k0.(i o L)) [G0(r_m - r_n - i o L) - G_grid] in FP64.
+ *
+ *   xyz   N x 3 row-major FP64 positions, device or host pointer; copied.
+ *         Every point must lie in the closed cell [0, D] (else
+ *         PIM_ERR_OUT_OF_CELL).
+ * Replaces the points of an earlier call.  Synchronises before returning.
+ */
+pim_status pim_set_points(pim_plan plan, int64_t N, const double* xyz);
+
+/*
+ * pim_apply -- u = A q (Eq. 1 through Eq. 5): near spread, FFT
+ * convolution, gather and correction, plus the far-zone projection, grid
+ * sum and interpolation (run on a second stream and joined).
+ *   q     [N][nrhs] source strengths in the caller's point order.
+ *   u     [N][nrhs] potentials, written (not accumulated).  May not alias q.
+ *   nrhs  >= 1.
+ * Neutral static plans remove the FP64 mean of q first; a non-neutral q
+ * sets the device flag PIM_ERR_NOT_NEUTRAL (see pim_last_device_status).
+ * Asynchronous on `stream` for device pointers; synchronous for host ones.
+ */
+pim_status pim_apply(pim_plan plan, const void* q, void* u, int nrhs, void* stream);
+
+/*
+ * pim_apply_adjoint -- w = A^H v, the exact conjugate transpose of the
+ * discrete operator of pim_apply (same weights, conjugated spectrum and
+ * correction values, far grids with their roles swapped).  Not part of the
+ * paper; needed for gradients.  Same layout and semantics as pim_apply.
+ * Neutral static plans remove the mean of w (the projector is self-adjoint).
+ */
+pim_status pim_apply_adjoint(pim_plan plan, const void* v, void* w, int nrhs, void* stream);
+
+/* Device-side status of the calls issued so far: synchronises the plan's
+ * streams, returns the first flag raised (PIM_OK if none) and clears it. */
+pim_status pim_last_device_status(pim_plan plan);
+
+/* Sizes and timings of a plan. */
+pim_status pim_plan_info(pim_plan plan, pim_info* info);
+
+/*
+ * pim_debug_copy -- copies an internal table to host memory, for tests of
+ * individual stages.  `what`:
+ *   0 far table G_far(delta o Delta + Delta/2), (2nf_x-1)(2nf_y-1)(2nf_z-1)
+ *     complex128, x fastest;
+ *   1 grid charges Q of the last apply (step 1), n_x n_y n_z, x fastest,
+ *     complex of the plan precision (the last right-hand side);
+ *   2 grid potential U of the last apply (step 2), same layout;
+ *   3 sort permutation (int32, sorted slot -> caller index), N entries;
+ *   4 correction row pointers (int64, N+1) in sorted order;
+ *   5 correction columns (uint32, nnz): sorted column | image index << 25;
+ *   6 correction values (complex128 FP64, nnz): G0 - G_grid before the phase.
+ * `bytes` must be at least the size of the table; PIM_ERR_ARG otherwise.
+ */
+pim_status pim_debug_copy(pim_plan plan, int what, void* host_out, size_t bytes);
+
+/* Frees every resource of the plan (NULL is ignored). */
+void pim_destroy(pim_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIM_H */

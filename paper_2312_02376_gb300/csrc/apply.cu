@@ -1,0 +1,577 @@
+// The apply u = A q and its adjoint (Sec. 3.2 steps 1-3, Sec. 3.3 steps 1-4).
+#include <cmath>
+
+#include "pim_internal.cuh"
+
+namespace {
+
+// ------------------------------- reductions --------------------------------
+constexpr int RED_NT = 256, RED_BLOCKS = PIM_RED_BLOCKS;
+
+template <typename T, bool REAL>
+__device__ __forceinline__ double2 load_val(const void* q, long long i) {
+    if (REAL) return make_double2((double)((const T*)q)[i], 0.0);
+    const cplx<T> v = ((const cplx<T>*)q)[i];
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// partial[b] = (sum re, sum im, sum |q|) over a grid-stride slice, FP64
+template <typename T, bool REAL>
+__global__ void sum_partials_kernel(const void* q, long long N, int nrhs, int r, double* partial) {
+    __shared__ double sh[3][RED_NT];
+    double a = 0, b = 0, c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = load_val<T, REAL>(q, i * nrhs + r);
+        a += v.x;
+        b += v.y;
+        c += sqrt(v.x * v.x + v.y * v.y);
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int s = RED_NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) partial[3 * blockIdx.x + k] = sh[k][0];
+}
+
+// out = (mean re, mean im); raises the not-neutral flag if check and
+// |sum q| > tol * sum |q| (Eq. neutral)
+__global__ void sum_final_kernel(const double* partial, int nb, long long N, double tol, int check, double* out,
+                                 int* status) {
+    __shared__ double sh[3][RED_NT];
+    double a = 0, b = 0, c = 0;
+    for (int i = threadIdx.x; i < nb; i += RED_NT) {
+        a += partial[3 * i];
+        b += partial[3 * i + 1];
+        c += partial[3 * i + 2];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    sh[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int s = RED_NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0] / (double)N;
+        out[1] = sh[1][0] / (double)N;
+        if (check && sqrt(sh[0][0] * sh[0][0] + sh[1][0] * sh[1][0]) > tol * sh[2][0]) atomicOr(status, PIM_DEV_NOT_NEUTRAL);
+    }
+}
+
+// qs[m] = q[perm[m]] - mean (sorted order, plan precision)
+template <typename T, bool REAL>
+__global__ void permute_kernel(const void* q, const int* perm, long long N, int nrhs, int r, const double* mean,
+                               cplx<T>* qs) {
+    const double mr = mean ? mean[0] : 0.0, mi = mean ? mean[1] : 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const double2 v = load_val<T, REAL>(q, (long long)perm[m] * nrhs + r);
+        qs[m] = mk<T>((T)(v.x - mr), (T)(v.y - mi));
+    }
+}
+
+// ------------------------------- near spread -------------------------------
+struct SpreadArgs {
+    int n[3], nb[3];
+    int tile[3];
+    int ntiles[3];
+    const int* box_ptr;
+    const uint32_t* ns;
+    const float* nt;
+    const double* ntd;
+};
+
+// Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1).  One CTA owns a tile of grid
+// nodes and accumulates every point whose stencil reaches it in shared
+// memory, then writes the tile once: no global atomics, every node written
+// by exactly one CTA.  Candidate points are read box row by box row (boxes
+// are contiguous along x in the sorted order).
+template <typename T, int P>
+__global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>* __restrict__ qs, cplx<T>* Q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);  // 2 * TX*TY*TZ
+    const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
+    const int ntile = TX * TY * TZ;
+    int t = blockIdx.x;
+    const int tx = t % a.ntiles[0];
+    t /= a.ntiles[0];
+    const int ty = t % a.ntiles[1];
+    const int tz = t / a.ntiles[1];
+    const int a0[3] = {tx * TX, ty * TY, tz * TZ};
+    for (int i = threadIdx.x; i < 2 * ntile; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
+    int blo[3], bhi[3];
+    const int T3[3] = {TX, TY, TZ};
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = max(0, a0[d] - P - 1);
+        bhi[d] = min(a.nb[d] - 1, a0[d] + T3[d] + P);
+    }
+    const int nry = bhi[1] - blo[1] + 1, nrz = bhi[2] - blo[2] + 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int row = wid; row < nry * nrz; row += nw) {
+        const int by = blo[1] + row % nry, bz = blo[2] + row / nry;
+        const long long rb = ((long long)bz * a.nb[1] + by) * a.nb[0];
+        const int lo = a.box_ptr[rb + blo[0]], hi = a.box_ptr[rb + bhi[0] + 1];
+        for (int m = lo + lane; m < hi; m += 32) {
+            int s[3];
+            unpack3(a.ns[m], s[0], s[1], s[2]);
+            int j0[3], j1[3];
+            bool hit = true;
+            for (int d = 0; d < 3; ++d) {
+                j0[d] = max(0, a0[d] - s[d]);
+                j1[d] = min(P, a0[d] + T3[d] - 1 - s[d]);
+                if (j0[d] > j1[d]) hit = false;
+            }
+            if (!hit) continue;
+            T w[3][P + 1];
+            for (int d = 0; d < 3; ++d) {
+                const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+                lagrange_weights<T>(P, tt, w[d]);
+            }
+            const cplx<T> qv = qs[m];
+            for (int jz = j0[2]; jz <= j1[2]; ++jz) {
+                const int lz = s[2] + jz - a0[2];
+                for (int jy = j0[1]; jy <= j1[1]; ++jy) {
+                    const int ly = s[1] + jy - a0[1];
+                    const T wzy = w[2][jz] * w[1][jy];
+                    T* rowp = acc + 2 * ((lz * TY + ly) * TX + (s[0] - a0[0]));
+                    for (int jx = j0[0]; jx <= j1[0]; ++jx) {
+                        const T ww = wzy * w[0][jx];
+                        atomicAdd(rowp + 2 * jx, ww * qv.x);
+                        atomicAdd(rowp + 2 * jx + 1, ww * qv.y);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
+        const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
+        const int x = a0[0] + lx, y = a0[1] + ly, z = a0[2] + lz;
+        if (x < a.n[0] && y < a.n[1] && z < a.n[2])
+            Q[((long long)z * a.n[1] + y) * a.n[0] + x] = mk<T>(acc[2 * i], acc[2 * i + 1]);
+    }
+}
+
+// ------------------------------- far spread --------------------------------
+struct FarSpreadArgs {
+    int nf[3], pf;
+    long long N;
+    int chunk;             // points per CTA
+    const uint32_t* fst;   // stencil starts of the grid spread onto
+    const float* ft;       // local coordinates (stride 6, offset toff)
+    const double* ftd;
+    int toff;
+};
+
+// Per-CTA partial far-grid charges (Eq. projection) in shared memory.
+template <typename T>
+__global__ void far_spread_kernel(FarSpreadArgs a, const cplx<T>* __restrict__ qs, cplx<T>* part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    const int G = a.nf[0] * a.nf[1] * a.nf[2];
+    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
+    const long long m0 = (long long)blockIdx.x * a.chunk;
+    const long long m1 = min(a.N, m0 + a.chunk);
+    const int pf = a.pf, np = pf + 1;
+    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+        int s[3];
+        unpack3(a.fst[m], s[0], s[1], s[2]);
+        T w[3][PIM_MAX_P + 1];
+        for (int d = 0; d < 3; ++d) {
+            const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
+            lagrange_weights<T>(pf, tt, w[d]);
+        }
+        const cplx<T> qv = qs[m];
+        for (int jz = 0; jz < np; ++jz)
+            for (int jy = 0; jy < np; ++jy) {
+                const T wzy = w[2][jz] * w[1][jy];
+                T* rowp = acc + 2 * (((s[2] + jz) * a.nf[1] + (s[1] + jy)) * a.nf[0] + s[0]);
+                for (int jx = 0; jx < np; ++jx) {
+                    const T ww = wzy * w[0][jx];
+                    atomicAdd(rowp + 2 * jx, ww * qv.x);
+                    atomicAdd(rowp + 2 * jx + 1, ww * qv.y);
+                }
+            }
+    }
+    __syncthreads();
+    cplx<T>* out = part + (long long)blockIdx.x * G;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) out[i] = mk<T>(acc[2 * i], acc[2 * i + 1]);
+}
+
+// qf[g] = sum over CTAs of the partials, in FP64, fixed order
+template <typename T>
+__global__ void far_reduce_kernel(const cplx<T>* part, int nchunks, int G, double2* qf) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int c = 0; c < nchunks; ++c) {
+            const cplx<T> v = part[(long long)c * G + g];
+            s.x += (double)v.x;
+            s.y += (double)v.y;
+        }
+        qf[g] = s;
+    }
+}
+
+template <typename T>
+__global__ void far_convert_kernel(const double2* in, cplx<T>* out, int G) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+        out[g] = mk<T>((T)in[g].x, (T)in[g].y);
+}
+
+// ------------------------------- gather + correction -----------------------
+struct GatherArgs {
+    int n[3], nf[3], pf;
+    long long N;
+    int nrhs, r;
+    int cmode, adj, has_far, real_out, sorted_out, self_img;
+    const int* perm;
+    const uint32_t* ns;
+    const float* nt;
+    const double* ntd;
+    const uint32_t* fst;   // far stencils of the grid gathered from
+    const float* ft;
+    const double* ftd;
+    int toff;
+    const int64_t* row_ptr;
+    const uint32_t* col;
+    const double2* val;
+    const float4* valdf;
+    const float2* valf;
+    const double2* phase;
+};
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
+// One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
+// correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
+// written in the caller's order.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
+                                                     const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
+                                                     void* out) {
+    const int lane = threadIdx.x & 31;
+    const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (m >= a.N) return;
+    // near gather
+    int s[3];
+    unpack3(a.ns[m], s[0], s[1], s[2]);
+    T w[3][P + 1];
+    for (int d = 0; d < 3; ++d) {
+        const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+        lagrange_weights<T>(P, tt, w[d]);
+    }
+    constexpr int NP = P + 1, NP3 = NP * NP * NP;
+    cplx<T> acc = mk<T>(T(0), T(0));
+    for (int idx = lane; idx < NP3; idx += 32) {
+        const int jx = idx % NP, jy = (idx / NP) % NP, jz = idx / (NP * NP);
+        const T ww = w[0][jx] * w[1][jy] * w[2][jz];
+        const cplx<T> v = U[((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + (s[0] + jx)];
+        acc.x += ww * v.x;
+        acc.y += ww * v.y;
+    }
+    // far gather
+    if (a.has_far) {
+        int f[3];
+        unpack3(a.fst[m], f[0], f[1], f[2]);
+        T wf[3][PIM_MAX_P + 1];
+        for (int d = 0; d < 3; ++d) {
+            const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
+            lagrange_weights<T>(a.pf, tt, wf[d]);
+        }
+        const int np = a.pf + 1, np3 = np * np * np;
+        for (int idx = lane; idx < np3; idx += 32) {
+            const int jx = idx % np, jy = (idx / np) % np, jz = idx / (np * np);
+            const T ww = wf[0][jx] * wf[1][jy] * wf[2][jz];
+            const cplx<T> v = uf[((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + (f[0] + jx)];
+            acc.x += ww * v.x;
+            acc.y += ww * v.y;
+        }
+    }
+    // near-pair correction: exp(-j k0.(i o L)) d q_n (forward) or
+    // exp(-j k0.(i o L)) conj(d) v_n (adjoint)
+    const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
+    const double cs = a.adj ? -1.0 : 1.0;
+    double2 accd = make_double2(0.0, 0.0);
+    if (a.cmode == PIM_CORR_FP64) {
+        for (long long q = r0 + lane; q < r1; q += 32) {
+            const uint32_t c = a.col[q];
+            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+            double2 d = a.val[q];
+            d.y *= cs;
+            const cplx<T> x = qs[n];
+            double2 t = make_double2(d.x * (double)x.x - d.y * (double)x.y, d.x * (double)x.y + d.y * (double)x.x);
+            if (ii != a.self_img) t = cmul(a.phase[ii], t);
+            accd = cadd(accd, t);
+        }
+    } else if (a.cmode == PIM_CORR_DOUBLE_FLOAT) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        const float fs = (float)cs;
+        for (long long q = r0 + lane; q < r1; q += 32) {
+            const uint32_t c = a.col[q];
+            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+            const float4 d = a.valdf[q];  // re_hi, re_lo, im_hi, im_lo
+            const cplx<T> xv = qs[n];
+            const float xr = (float)xv.x, xi = (float)xv.y;
+            const float dih = fs * d.z, dil = fs * d.w;
+            if (ii == a.self_img) {
+                // re += dr*xr - di*xi ; im += dr*xi + di*xr, products split exactly
+                const float p1 = d.x * xr, e1 = fmaf(d.x, xr, -p1);
+                const float p2 = dih * xi, e2 = fmaf(dih, xi, -p2);
+                const float p3 = d.x * xi, e3 = fmaf(d.x, xi, -p3);
+                const float p4 = dih * xr, e4 = fmaf(dih, xr, -p4);
+                two_sum_acc(rh, rl, p1);
+                two_sum_acc(rh, rl, -p2);
+                two_sum_acc(ih, il, p3);
+                two_sum_acc(ih, il, p4);
+                rl += (e1 - e2) + (d.y * xr - dil * xi);
+                il += (e3 + e4) + (d.y * xi + dil * xr);
+            } else {
+                const double dr = (double)d.x + (double)d.y, di = (double)dih + (double)dil;
+                double2 t = make_double2(dr * xr - di * xi, dr * xi + di * xr);
+                accd = cadd(accd, cmul(a.phase[ii], t));
+            }
+        }
+        accd.x += (double)rh + (double)rl;
+        accd.y += (double)ih + (double)il;
+    } else {
+        cplx<T> af = mk<T>(T(0), T(0));
+        for (long long q = r0 + lane; q < r1; q += 32) {
+            const uint32_t c = a.col[q];
+            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+            float2 d = a.valf[q];
+            d.y *= (float)cs;
+            const cplx<T> x = qs[n];
+            float2 t = make_float2(d.x * (float)x.x - d.y * (float)x.y, d.x * (float)x.y + d.y * (float)x.x);
+            if (ii != a.self_img) {
+                const double2 ph = a.phase[ii];
+                t = make_float2((float)ph.x * t.x - (float)ph.y * t.y, (float)ph.x * t.y + (float)ph.y * t.x);
+            }
+            af.x += (T)t.x;
+            af.y += (T)t.y;
+        }
+        acc.x += af.x;
+        acc.y += af.y;
+    }
+    // warp reduction
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        accd.x += __shfl_xor_sync(0xffffffffu, accd.x, o);
+        accd.y += __shfl_xor_sync(0xffffffffu, accd.y, o);
+    }
+    if (lane == 0) {
+        const double re = (double)acc.x + accd.x, im = (double)acc.y + accd.y;
+        if (a.sorted_out) {
+            ((cplx<T>*)out)[m] = mk<T>((T)re, (T)im);
+        } else {
+            const long long o = (long long)a.perm[m] * a.nrhs + a.r;
+            if (a.real_out) ((T*)out)[o] = (T)re;
+            else ((cplx<T>*)out)[o] = mk<T>((T)re, (T)im);
+        }
+    }
+}
+
+// u[perm[m]] = us[m] - mean  (the adjoint of the neutral static case)
+template <typename T>
+__global__ void unpermute_kernel(const cplx<T>* us, const int* perm, long long N, int nrhs, int r, const double* mean,
+                                 int real_out, void* out) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const double re = (double)us[m].x - mean[0], im = (double)us[m].y - mean[1];
+        const long long o = (long long)perm[m] * nrhs + r;
+        if (real_out) ((T*)out)[o] = (T)re;
+        else ((cplx<T>*)out)[o] = mk<T>((T)re, (T)im);
+    }
+}
+
+// ------------------------------- driver ------------------------------------
+template <typename T>
+pim_status mean_of(pim_plan P, const void* q, bool sorted_complex, long long N, int nrhs, int r, bool check,
+                   cudaStream_t s) {
+    double* partial = P->dsum + 4;
+    if (sorted_complex) sum_partials_kernel<T, false><<<RED_BLOCKS, RED_NT, 0, s>>>(q, N, 1, 0, partial);
+    else if (P->real_data) sum_partials_kernel<T, true><<<RED_BLOCKS, RED_NT, 0, s>>>(q, N, nrhs, r, partial);
+    else sum_partials_kernel<T, false><<<RED_BLOCKS, RED_NT, 0, s>>>(q, N, nrhs, r, partial);
+    sum_final_kernel<<<1, RED_NT, 0, s>>>(partial, RED_BLOCKS, N, P->neutral_tol, check ? 1 : 0, P->dsum,
+                                          P->dstatus);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <typename T, int PP>
+pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    const long long N = d.N;
+    cplx<T>* qs = (cplx<T>*)P->qs;
+    cplx<T>* gA = (cplx<T>*)P->gA;
+    pim_status st;
+    for (int r = 0; r < nrhs; ++r) {
+        // 1. sorted, regularised sources (Eq. neutral)
+        const double* mean = nullptr;
+        if (P->npsp && !adj) {
+            if ((st = mean_of<T>(P, q, false, N, nrhs, r, true, s)) != PIM_OK) return st;
+            mean = P->dsum;
+        }
+        if (P->real_data) permute_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
+        else permute_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
+        PIM_CK(cudaGetLastError());
+        // 2. far zone on the second stream
+        if (P->has_far) {
+            PIM_CK(cudaEventRecord(P->ev_fork, s));
+            PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
+            FarSpreadArgs fa{};
+            for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
+            fa.pf = P->pf;
+            fa.N = N;
+            fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);
+            fa.fst = adj ? d.fo : d.fs;
+            fa.ft = d.ft;
+            fa.ftd = d.ftd;
+            fa.toff = adj ? 3 : 0;
+            const int G = P->nf[0] * P->nf[1] * P->nf[2];
+            const size_t sm = 2 * sizeof(T) * G;
+            PIM_CK(cudaFuncSetAttribute(far_spread_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            if (N > 0) far_spread_kernel<T><<<P->far_chunks, 256, sm, P->s_far>>>(fa, qs, (cplx<T>*)P->fpart);
+            else PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, P->s_far));
+            far_reduce_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks, G,
+                                                                        P->fA);
+            PIM_CK(cudaGetLastError());
+            if ((st = fft3_conv<double>(P, P->fg, P->fA, P->fB, P->fC, P->fspec, adj, P->s_far)) != PIM_OK) return st;
+            if (sizeof(T) == 4) {
+                far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)P->fB, G);
+                PIM_CK(cudaGetLastError());
+            }
+            PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
+        }
+        // 3. near spread, 4. FFT convolution
+        SpreadArgs sa{};
+        for (int i = 0; i < 3; ++i) {
+            sa.n[i] = P->n[i];
+            sa.nb[i] = P->nb[i];
+            sa.tile[i] = P->tile[i];
+            sa.ntiles[i] = (P->n[i] + P->tile[i] - 1) / P->tile[i];
+        }
+        sa.box_ptr = d.box_ptr;
+        sa.ns = d.ns;
+        sa.nt = d.nt;
+        sa.ntd = d.ntd;
+        const int ntiles = sa.ntiles[0] * sa.ntiles[1] * sa.ntiles[2];
+        const size_t sm = 2 * sizeof(T) * P->tile[0] * P->tile[1] * P->tile[2];
+        PIM_CK(cudaFuncSetAttribute(spread_kernel<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        spread_kernel<T, PP><<<ntiles, 256, sm, s>>>(sa, qs, gA);
+        PIM_CK(cudaGetLastError());
+        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, s)) != PIM_OK)
+            return st;
+        // 5. gather + correction + far gather
+        if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
+        GatherArgs ga{};
+        for (int i = 0; i < 3; ++i) { ga.n[i] = P->n[i]; ga.nf[i] = P->nf[i]; }
+        ga.pf = P->pf;
+        ga.N = N;
+        ga.nrhs = nrhs;
+        ga.r = r;
+        ga.cmode = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
+        ga.adj = adj ? 1 : 0;
+        ga.has_far = P->has_far ? 1 : 0;
+        ga.real_out = P->real_data ? 1 : 0;
+        const bool post_mean = P->npsp && adj;
+        ga.sorted_out = post_mean ? 1 : 0;
+        ga.self_img = -1;
+        for (int i = 0; i < P->nimg; ++i)
+            if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) ga.self_img = i;
+        ga.perm = d.perm;
+        ga.ns = d.ns;
+        ga.nt = d.nt;
+        ga.ntd = d.ntd;
+        ga.fst = adj ? d.fs : d.fo;
+        ga.ft = d.ft;
+        ga.ftd = d.ftd;
+        ga.toff = adj ? 0 : 3;
+        ga.row_ptr = d.row_ptr;
+        ga.col = d.col;
+        ga.val = d.val;
+        ga.valdf = d.valdf;
+        ga.valf = d.valf;
+        ga.phase = P->dphase;
+        const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
+        void* dst = post_mean ? P->us : u;
+        const long long threads = N * 32;
+        if (N > 0)
+            gather_kernel<T, PP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ga, gA, ufar, qs, dst);
+        PIM_CK(cudaGetLastError());
+        if (post_mean) {
+            if ((st = mean_of<T>(P, P->us, true, N, 1, 0, false, s)) != PIM_OK) return st;
+            unpermute_kernel<T><<<1024, 256, 0, s>>>((const cplx<T>*)P->us, d.perm, N, nrhs, r, P->dsum,
+                                                     P->real_data ? 1 : 0, u);
+            PIM_CK(cudaGetLastError());
+        }
+    }
+    return PIM_OK;
+}
+
+template <typename T>
+pim_status run_p(pim_plan P, const void* q, void* u, int nrhs, bool adj, cudaStream_t s) {
+    switch (P->p) {
+        case 2: return run_typed<T, 2>(P, q, u, nrhs, adj, s);
+        case 3: return run_typed<T, 3>(P, q, u, nrhs, adj, s);
+        case 4: return run_typed<T, 4>(P, q, u, nrhs, adj, s);
+        default: pim_set_error("GPU path supports p = 2, 3, 4"); return PIM_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename T, int PP>
+pim_status debug_spread_typed(pim_plan P, void* out, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    SpreadArgs sa{};
+    for (int i = 0; i < 3; ++i) {
+        sa.n[i] = P->n[i];
+        sa.nb[i] = P->nb[i];
+        sa.tile[i] = P->tile[i];
+        sa.ntiles[i] = (P->n[i] + P->tile[i] - 1) / P->tile[i];
+    }
+    sa.box_ptr = d.box_ptr;
+    sa.ns = d.ns;
+    sa.nt = d.nt;
+    sa.ntd = d.ntd;
+    const int ntiles = sa.ntiles[0] * sa.ntiles[1] * sa.ntiles[2];
+    const size_t sm = 2 * sizeof(T) * P->tile[0] * P->tile[1] * P->tile[2];
+    PIM_CK(cudaFuncSetAttribute(spread_kernel<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    spread_kernel<T, PP><<<ntiles, 256, sm, s>>>(sa, (const cplx<T>*)P->qs, (cplx<T>*)out);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <typename T>
+pim_status debug_spread_p(pim_plan P, void* out, cudaStream_t s) {
+    switch (P->p) {
+        case 2: return debug_spread_typed<T, 2>(P, out, s);
+        case 3: return debug_spread_typed<T, 3>(P, out, s);
+        case 4: return debug_spread_typed<T, 4>(P, out, s);
+        default: return PIM_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace
+
+pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {
+    if (P->prec == PIM_FP64) return debug_spread_p<double>(P, out, s);
+    return debug_spread_p<float>(P, out, s);
+}
+
+pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s) {
+    if (P->prec == PIM_FP64) return run_p<double>(P, q, u, nrhs, adjoint, s);
+    return run_p<float>(P, q, u, nrhs, adjoint, s);
+}

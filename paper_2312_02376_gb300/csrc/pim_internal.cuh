@@ -1,0 +1,198 @@
+// Internal declarations of libpim: the plan, device helpers, kernel entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pim.h"
+
+#define PIM_CK(call)                                                    \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            pim_set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return PIM_ERR_CUDA;                                        \
+        }                                                               \
+    } while (0)
+
+void pim_set_error(const std::string& msg);
+
+// Column word of the correction list: sorted source index in the low bits,
+// near-image code above it.
+constexpr int PIM_COL_BITS = 25;
+constexpr uint32_t PIM_COL_MASK = (1u << PIM_COL_BITS) - 1u;
+constexpr int PIM_MAX_IMAGES = 125;
+constexpr int PIM_MAX_P = 6;
+
+// device-side status flags (bit set)
+enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2 };
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T re, T im) {
+    cplx<T> c; c.x = re; c.y = im; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C c; c.x = a.x * b.x - a.y * b.y; c.y = a.x * b.y + a.y * b.x; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+
+// ---------------------------------------------------------------------------
+// Lagrange weights (Sec. 3.2): w_j(t) = prod_{l != j} (t - l) / (j - l),
+// j = 0..p, from prefix and suffix products of (t - l).
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ __forceinline__ void lagrange_weights(int p, T t, T* w) {
+    T pre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1];
+    pre[0] = T(1);
+    for (int j = 1; j <= p; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
+    suf[p] = T(1);
+    for (int j = p - 1; j >= 0; --j) suf[j] = suf[j + 1] * (t - T(j + 1));
+    // denominator prod_{l != j} (j - l) = (-1)^{p-j} j! (p-j)!
+    T fact[PIM_MAX_P + 1];
+    fact[0] = T(1);
+    for (int j = 1; j <= p; ++j) fact[j] = fact[j - 1] * T(j);
+    for (int j = 0; j <= p; ++j) {
+        T den = fact[j] * fact[p - j];
+        if ((p - j) & 1) den = -den;
+        w[j] = pre[j] * suf[j] / den;
+    }
+}
+
+// Stencil rule: even p: floor(u + 1/2) - p/2; odd p: floor(u) - (p-1)/2;
+// clamped to [0, n-1-p].  Decided in FP64.
+__host__ __device__ __forceinline__ int stencil_start(double u, int n, int p) {
+    int s = (p & 1) ? (int)floor(u) - (p - 1) / 2 : (int)floor(u + 0.5) - p / 2;
+    if (s < 0) s = 0;
+    if (s > n - 1 - p) s = n - 1 - p;
+    return s;
+}
+
+__host__ __device__ __forceinline__ uint32_t pack3(int a, int b, int c) {
+    return (uint32_t)a | ((uint32_t)b << 10) | ((uint32_t)c << 20);
+}
+__host__ __device__ __forceinline__ void unpack3(uint32_t v, int& a, int& b, int& c) {
+    a = v & 1023; b = (v >> 10) & 1023; c = (v >> 20) & 1023;
+}
+
+// ---------------------------------------------------------------------------
+// FFT plan for one padded 3D grid: lengths L[d] (powers of two), the data
+// lengths n[d] (<= L[d]) that are nonzero on input / kept on output.
+// ---------------------------------------------------------------------------
+struct FftGeom {
+    int n[3];   // data nodes per axis
+    int L[3];   // padded FFT length per axis
+};
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct PointsData {
+    int64_t N = 0;
+    int* perm = nullptr;          // sorted slot -> caller index
+    double* pos = nullptr;        // sorted positions, 3N (x, y, z interleaved)
+    uint32_t* ns = nullptr;       // near stencil starts, packed
+    float* nt = nullptr;          // near local coordinates (FP32), 3N
+    double* ntd = nullptr;        // near local coordinates (FP64), 3N
+    uint32_t* fs = nullptr;       // far source-grid stencil starts, packed
+    uint32_t* fo = nullptr;       // far observer-grid stencil starts, packed
+    float* ft = nullptr;          // far local coordinates, source grid then observer grid (6N)
+    double* ftd = nullptr;        // same in FP64 (FP64 plans)
+    int* box_ptr = nullptr;       // nboxes + 1
+    int64_t* row_ptr = nullptr;   // N + 1
+    uint32_t* col = nullptr;      // nnz
+    double2* val = nullptr;       // nnz: G0 - G_grid (FP64)
+    float4* valdf = nullptr;      // nnz: double-float split (re_hi, re_lo, im_hi, im_lo)
+    float2* valf = nullptr;       // nnz: complex64
+    int64_t nnz = 0;
+};
+
+struct pim_plan_s {
+    // geometry and method parameters
+    double D[3], h[3], k, k0[3], df[3];
+    unsigned pmask = 0;
+    int npd = 0;                  // number of periodic axes
+    int n[3], nb[3], p, layers, b, cube, nf[3], pf, prec, corr_mode;
+    int tile[3];
+    bool npsp = false;
+    bool real_data = false;
+    double neutral_tol, series_tol;
+    size_t mem_cap = 0, bytes = 0;
+    int nimg = 0;
+    int img[PIM_MAX_IMAGES][3];
+    double2 phase[PIM_MAX_IMAGES];    // exp(-j k0.(i o L))
+    // near spectrum and work grids
+    FftGeom ng;
+    void* spec = nullptr;         // [Lz][Ly][Lx] complex<T>, scaled by 1/(Lx Ly Lz)
+    void* gA = nullptr;           // [nz][ny][nx]
+    void* gB = nullptr;           // [nz][ny][Lx]
+    void* gC = nullptr;           // [nz][Ly][Lx]
+    // far zone
+    bool has_far = false;
+    FftGeom fg;
+    double2* ftab = nullptr;      // (2nf-1)^3 table, x fastest
+    double2* fspec = nullptr;     // [Lz][Ly][Lx] FP64 spectrum of the far table, scaled
+    double2* fA = nullptr;        // far grid charges / potentials [nfz][nfy][nfx]
+    double2* fB = nullptr;        // [nfz][nfy][Lx]
+    double2* fC = nullptr;        // [nfz][Ly][Lx]
+    void* fpart = nullptr;        // far spread partials [nchunk][nf^3] complex<T>
+    int far_chunks = 0;
+    // twiddles (cos, sin of 2 pi j / L) per padded length, FP32 and FP64 copies
+    float2* tw32 = nullptr;       // concatenated tables, offsets per power of two
+    double2* tw64 = nullptr;
+    int tw_off[12];
+    // points
+    PointsData pts;
+    void* qs = nullptr;           // sorted sources, complex<T>, N
+    void* us = nullptr;           // staging for host pointers
+    size_t stage_bytes = 0;
+    void* hq = nullptr;           // device staging of caller buffers (host pointers)
+    void* hu = nullptr;
+    double* dsum = nullptr;       // FP64 scratch: [0..1] mean, [4..) reduction partials
+    double2* dphase = nullptr;    // device copy of phase[]
+    int* dstatus = nullptr;
+    // streams and events
+    cudaStream_t s_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double plan_ms = 0, points_ms = 0;
+};
+
+// ---------------------------------------------------------------------------
+// internal entry points (defined in the .cu files)
+// ---------------------------------------------------------------------------
+pim_status pim_alloc(pim_plan P, void** ptr, size_t bytes);
+void pim_free(pim_plan P, void* ptr, size_t bytes);
+
+// fft.cu
+pim_status fft_make_twiddles(pim_plan P);
+template <typename T>
+pim_status fft3_conv(pim_plan P, const FftGeom& g, cplx<T>* A, cplx<T>* B, cplx<T>* C, const cplx<T>* spec,
+                     bool conj_spec, cudaStream_t s);
+template <typename T>
+pim_status fft3_forward_full(pim_plan P, const FftGeom& g, cplx<T>* X, cplx<T>* tmp, cudaStream_t s);
+
+// tables.cu
+pim_status build_near_spectrum(pim_plan P, cudaStream_t s);
+pim_status build_far_table(pim_plan P, cudaStream_t s);
+
+// points.cu
+pim_status points_build(pim_plan P, int64_t N, const double* xyz_dev, cudaStream_t s);
+void points_free(pim_plan P);
+
+// apply.cu
+constexpr int PIM_RED_BLOCKS = 608;
+pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s);
+pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
+int pim_fft_len(int n);

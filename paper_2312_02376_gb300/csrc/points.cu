@@ -1,0 +1,514 @@
+// Point-dependent pre-processing (Sec. 3.2 and 3.3): binning into the grid's
+// boxes by counting sort, per-point stencil data, and the near-pair
+// correction list of Sec. 3.3 step 4 with its FP64 values.
+#include <cmath>
+#include <vector>
+
+#include "pim_internal.cuh"
+
+namespace {
+
+constexpr double PI = 3.141592653589793238462643383279502884;
+
+__device__ __forceinline__ double2 G0(double R, double k) {
+    double s, c;
+    sincos(k * R, &s, &c);
+    const double a = 1.0 / (4.0 * PI * R);
+    return make_double2(c * a, -s * a);
+}
+
+// ------------------------------- exclusive scan ----------------------------
+constexpr int SCAN_NT = 1024, SCAN_IPT = 4, SCAN_TILE = SCAN_NT * SCAN_IPT;
+
+__device__ __forceinline__ long long block_scan_excl(long long v, long long* warp_tot, long long& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        long long t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        long long u = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        warp_tot[lane] = u - t;  // exclusive warp offsets
+        if (lane == 31) warp_tot[32] = u;
+    }
+    __syncthreads();
+    total = warp_tot[32];
+    const long long r = warp_tot[wid] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_block_sums(const int* in, long long n, long long* partial) {
+    __shared__ long long wt[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_IPT;
+    long long s = 0;
+    for (int i = 0; i < SCAN_IPT; ++i)
+        if (base + i < n) s += in[base + i];
+    long long tot;
+    block_scan_excl(s, wt, tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void scan_partials(long long* partial, long long nb, long long* total_out) {
+    __shared__ long long wt[33];
+    long long carry = 0;
+    for (long long b0 = 0; b0 < nb; b0 += SCAN_NT) {
+        const long long i = b0 + threadIdx.x;
+        const long long v = i < nb ? partial[i] : 0;
+        long long tot;
+        const long long ex = block_scan_excl(v, wt, tot);
+        if (i < nb) partial[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+template <typename OutT>
+__global__ void scan_write(const int* in, long long n, const long long* partial, const long long* total, OutT* out) {
+    __shared__ long long wt[33];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_IPT;
+    long long v[SCAN_IPT];
+    long long s = 0;
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    long long tot;
+    long long off = block_scan_excl(s, wt, tot) + partial[blockIdx.x];
+    for (int i = 0; i < SCAN_IPT; ++i) {
+        if (base + i < n) out[base + i] = (OutT)off;
+        off += v[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (OutT)(*total);
+}
+
+// ------------------------------- binning -----------------------------------
+struct BinArgs {
+    double D[3], h[3];
+    int nb[3];
+};
+
+__global__ void keys_kernel(const double* xyz, long long N, BinArgs a, int* key, int* counts, int* status) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        int b[3];
+        bool ok = true;
+        for (int d = 0; d < 3; ++d) {
+            const double x = xyz[3 * i + d];
+            if (!(x >= 0.0 && x <= a.D[d])) ok = false;
+            int v = (int)floor(x / a.h[d]);
+            v = v < 0 ? 0 : (v > a.nb[d] - 1 ? a.nb[d] - 1 : v);
+            b[d] = v;
+        }
+        if (!ok) atomicOr(status, 1);
+        const int k = (b[2] * a.nb[1] + b[1]) * a.nb[0] + b[0];
+        key[i] = k;
+        atomicAdd(&counts[k], 1);
+    }
+}
+
+__global__ void scatter_kernel(const int* key, long long N, const int* box_ptr, int* cursor, int* slot) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int k = key[i];
+        const int pos = box_ptr[k] + atomicAdd(&cursor[k], 1);
+        slot[pos] = (int)i;
+    }
+}
+
+// order each box's points by caller index (deterministic layout)
+__global__ void sort_boxes_kernel(const int* box_ptr, long long nboxes, int* slot) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nboxes;
+         b += (long long)gridDim.x * blockDim.x) {
+        const int lo = box_ptr[b], hi = box_ptr[b + 1];
+        for (int i = lo + 1; i < hi; ++i) {
+            const int v = slot[i];
+            int j = i - 1;
+            while (j >= lo && slot[j] > v) {
+                slot[j + 1] = slot[j];
+                --j;
+            }
+            slot[j + 1] = v;
+        }
+    }
+}
+
+struct PtArgs {
+    double h[3], df[3];
+    int n[3], nf[3], p, pf;
+    int has_far;
+};
+
+__global__ void point_data_kernel(const double* xyz, const int* perm, long long N, PtArgs a, double* pos,
+                                  uint32_t* ns, float* nt, double* ntd, uint32_t* fs, uint32_t* fo, float* ft,
+                                  double* ftd) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const long long i = perm[m];
+        int s[3], ss[3], so[3];
+        for (int d = 0; d < 3; ++d) {
+            const double x = xyz[3 * i + d];
+            pos[3 * m + d] = x;
+            const double u = x / a.h[d];
+            s[d] = stencil_start(u, a.n[d], a.p);
+            const double t = u - s[d];
+            nt[3 * m + d] = (float)t;
+            ntd[3 * m + d] = t;
+            if (a.has_far) {
+                const double uf = x / a.df[d];
+                ss[d] = stencil_start(uf, a.nf[d], a.pf);
+                const double uo = (x - 0.5 * a.df[d]) / a.df[d];
+                so[d] = stencil_start(uo, a.nf[d], a.pf);
+                ft[6 * m + d] = (float)(uf - ss[d]);
+                ft[6 * m + 3 + d] = (float)(uo - so[d]);
+                ftd[6 * m + d] = uf - ss[d];
+                ftd[6 * m + 3 + d] = uo - so[d];
+            }
+        }
+        ns[m] = pack3(s[0], s[1], s[2]);
+        if (a.has_far) {
+            fs[m] = pack3(ss[0], ss[1], ss[2]);
+            fo[m] = pack3(so[0], so[1], so[2]);
+        }
+    }
+}
+
+// ------------------------------- near pairs --------------------------------
+struct PairArgs {
+    int nb[3], nL[3];
+    int b, cube;
+    int nimg;
+    const int* img;     // nimg x 3
+};
+
+__device__ __forceinline__ int isqrt_floor(int r) {
+    int g = (int)sqrt((double)r);
+    while ((g + 1) * (g + 1) <= r) ++g;
+    while (g * g > r) --g;
+    return g;
+}
+
+// Visits every (image, source box row) of the correction region of the
+// point in box B: calls f(image, first sorted slot, end slot).
+template <typename F>
+__device__ __forceinline__ void for_each_region_row(const PairArgs& a, const int* box_ptr, const int B[3], F f) {
+    const int R = a.b + 1;
+    for (int ii = 0; ii < a.nimg; ++ii) {
+        int cb[3];
+        for (int d = 0; d < 3; ++d) cb[d] = B[d] - a.img[3 * ii + d] * a.nL[d];
+        for (int dz = -R; dz <= R; ++dz) {
+            const int bz = cb[2] - dz;
+            if (bz < 0 || bz >= a.nb[2]) continue;
+            const int gz = abs(dz) > 1 ? abs(dz) - 1 : 0;
+            for (int dy = -R; dy <= R; ++dy) {
+                const int by = cb[1] - dy;
+                if (by < 0 || by >= a.nb[1]) continue;
+                const int gy = abs(dy) > 1 ? abs(dy) - 1 : 0;
+                int xr;
+                if (a.cube) {
+                    if (abs(dz) > a.b || abs(dy) > a.b) continue;
+                    xr = a.b;
+                } else {
+                    const int rem = a.b * a.b - gz * gz - gy * gy;
+                    if (rem < 0) continue;
+                    xr = isqrt_floor(rem) + 1;
+                }
+                int x0 = cb[0] - xr, x1 = cb[0] + xr;
+                x0 = x0 < 0 ? 0 : x0;
+                x1 = x1 > a.nb[0] - 1 ? a.nb[0] - 1 : x1;
+                if (x0 > x1) continue;
+                const long long row = ((long long)bz * a.nb[1] + by) * a.nb[0];
+                const int lo = box_ptr[row + x0], hi = box_ptr[row + x1 + 1];
+                if (hi > lo) f(ii, lo, hi);
+            }
+        }
+    }
+}
+
+__global__ void pair_count_kernel(const double* pos, long long N, const double* hh, PairArgs a, const int* box_ptr,
+                                  int* rowlen) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        int B[3];
+        for (int d = 0; d < 3; ++d) {
+            int v = (int)floor(pos[3 * m + d] / hh[d]);
+            B[d] = v < 0 ? 0 : (v > a.nb[d] - 1 ? a.nb[d] - 1 : v);
+        }
+        long long cnt = 0;
+        for_each_region_row(a, box_ptr, B, [&](int, int lo, int hi) { cnt += hi - lo; });
+        rowlen[m] = (int)cnt;
+    }
+}
+
+struct FillArgs {
+    PairArgs pa;
+    double h[3], D[3], k;
+    int p, R, W, self_img;
+    const double2* gtab;   // g(e), e in [-R, R]^3, x fastest
+    int corr_mode;
+};
+
+// Correction value (Eq. er) for observer m, source n, image ii, before the
+// phase: G0(r_m - r_n - i o L) [not for m = n, i = 0] minus the grid
+// interaction sum_a sum_c w_m(a) w_n(c) g(a - c - i o (n-1)), the latter via
+//   sum_e g(s_m - s_n - i o (n-1) + e) Cx(e_x) Cy(e_y) Cz(e_z),
+//   Cd(e) = sum_{j - l = e} w_{m,d}[j] w_{n,d}[l].
+__device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32_t* ns, const double* ntd, long long m,
+                              long long n, int ii, int* status) {
+    const int p = a.p;
+    int sm[3], sn[3];
+    unpack3(ns[m], sm[0], sm[1], sm[2]);
+    unpack3(ns[n], sn[0], sn[1], sn[2]);
+    double C[3][2 * PIM_MAX_P + 1];
+    int base[3];
+    for (int d = 0; d < 3; ++d) {
+        double wm[PIM_MAX_P + 1], wn[PIM_MAX_P + 1];
+        lagrange_weights<double>(p, ntd[3 * m + d], wm);
+        lagrange_weights<double>(p, ntd[3 * n + d], wn);
+        for (int e = 0; e <= 2 * p; ++e) C[d][e] = 0.0;
+        for (int j = 0; j <= p; ++j)
+            for (int l = 0; l <= p; ++l) C[d][j - l + p] += wm[j] * wn[l];
+        base[d] = sm[d] - sn[d] - a.pa.img[3 * ii + d] * a.pa.nL[d];
+        if (abs(base[d]) + p > a.R) {
+            atomicOr(status, PIM_DEV_BOUNDS);
+            return make_double2(0.0, 0.0);
+        }
+    }
+    double2 grid = make_double2(0.0, 0.0);
+    for (int ez = 0; ez <= 2 * p; ++ez) {
+        double2 sy = make_double2(0.0, 0.0);
+        for (int ey = 0; ey <= 2 * p; ++ey) {
+            const double2* row =
+                a.gtab + ((long long)(base[2] + ez - p + a.R) * a.W + (base[1] + ey - p + a.R)) * a.W + (base[0] - p + a.R);
+            double2 sx = make_double2(0.0, 0.0);
+            for (int ex = 0; ex <= 2 * p; ++ex) {
+                const double2 g = row[ex];
+                sx.x += C[0][ex] * g.x;
+                sx.y += C[0][ex] * g.y;
+            }
+            sy.x += C[1][ey] * sx.x;
+            sy.y += C[1][ey] * sx.y;
+        }
+        grid.x += C[2][ez] * sy.x;
+        grid.y += C[2][ez] * sy.y;
+    }
+    double2 exact = make_double2(0.0, 0.0);
+    if (!(m == n && ii == a.self_img)) {
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double x = pos[3 * m + d] - pos[3 * n + d] - a.pa.img[3 * ii + d] * a.D[d];
+            r2 += x * x;
+        }
+        exact = G0(sqrt(r2), a.k);
+    }
+    return csub(exact, grid);
+}
+
+__global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
+                                 const int* box_ptr, const int64_t* row_ptr, uint32_t* col, double2* val,
+                                 float4* valdf, float2* valf, int* status) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long m = warp; m < N; m += nwarps) {
+        int B[3];
+        for (int d = 0; d < 3; ++d) {
+            int v = (int)floor(pos[3 * m + d] / a.h[d]);
+            B[d] = v < 0 ? 0 : (v > a.pa.nb[d] - 1 ? a.pa.nb[d] - 1 : v);
+        }
+        long long off = row_ptr[m];
+        for_each_region_row(a.pa, box_ptr, B, [&](int ii, int lo, int hi) {
+            for (int n = lo + lane; n < hi; n += 32) {
+                const long long q = off + (n - lo);
+                const double2 d = corr_value(a, pos, ns, ntd, m, n, ii, status);
+                col[q] = (uint32_t)n | ((uint32_t)ii << PIM_COL_BITS);
+                val[q] = d;
+                if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
+                    const float rh = (float)d.x, ih = (float)d.y;
+                    valdf[q] = make_float4(rh, (float)(d.x - (double)rh), ih, (float)(d.y - (double)ih));
+                } else if (a.corr_mode == PIM_CORR_FP32) {
+                    valf[q] = make_float2((float)d.x, (float)d.y);
+                }
+            }
+            off += hi - lo;
+        });
+    }
+}
+
+__global__ void gtab_kernel(double2* gtab, int R, double h0, double h1, double h2, double k) {
+    const int W = 2 * R + 1;
+    const long long tot = (long long)W * W * W;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e % W) - R, y = (int)((e / W) % W) - R, z = (int)(e / ((long long)W * W)) - R;
+        const double r = sqrt((x * h0) * (x * h0) + (y * h1) * (y * h1) + (z * h2) * (z * h2));
+        gtab[e] = r > 0.0 ? G0(r, k) : make_double2(0.0, 0.0);
+    }
+}
+
+template <typename OutT>
+pim_status scan(pim_plan P, const int* in, OutT* out, long long n, cudaStream_t s) {
+    const long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    long long* part = nullptr;
+    pim_status st;
+    if ((st = pim_alloc(P, (void**)&part, sizeof(long long) * (nb + 1))) != PIM_OK) return st;
+    if (nb > 0) scan_block_sums<<<(unsigned)nb, SCAN_NT, 0, s>>>(in, n, part);
+    scan_partials<<<1, SCAN_NT, 0, s>>>(part, nb, part + nb);
+    if (nb > 0) scan_write<OutT><<<(unsigned)nb, SCAN_NT, 0, s>>>(in, n, part, part + nb, out);
+    else {
+        OutT z = 0;
+        PIM_CK(cudaMemcpyAsync(out, &z, sizeof(OutT), cudaMemcpyHostToDevice, s));
+    }
+    PIM_CK(cudaGetLastError());
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, part, sizeof(long long) * (nb + 1));
+    return PIM_OK;
+}
+
+}  // namespace
+
+void points_free(pim_plan P) {
+    PointsData& d = P->pts;
+    const size_t N = (size_t)d.N;
+    pim_free(P, d.perm, N * sizeof(int));
+    pim_free(P, d.pos, 3 * N * sizeof(double));
+    pim_free(P, d.ns, N * sizeof(uint32_t));
+    pim_free(P, d.nt, 3 * N * sizeof(float));
+    pim_free(P, d.ntd, 3 * N * sizeof(double));
+    pim_free(P, d.fs, N * sizeof(uint32_t));
+    pim_free(P, d.fo, N * sizeof(uint32_t));
+    pim_free(P, d.ft, 6 * N * sizeof(float));
+    pim_free(P, d.ftd, 6 * N * sizeof(double));
+    const size_t nboxes = (size_t)P->nb[0] * P->nb[1] * P->nb[2];
+    pim_free(P, d.box_ptr, (nboxes + 1) * sizeof(int));
+    pim_free(P, d.row_ptr, (N + 1) * sizeof(int64_t));
+    pim_free(P, d.col, d.nnz * sizeof(uint32_t));
+    pim_free(P, d.val, d.nnz * sizeof(double2));
+    pim_free(P, d.valdf, d.nnz * sizeof(float4));
+    pim_free(P, d.valf, d.nnz * sizeof(float2));
+    d = PointsData{};
+}
+
+pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s) {
+    PointsData& d = P->pts;
+    pim_status st;
+    const long long nboxes = (long long)P->nb[0] * P->nb[1] * P->nb[2];
+    int *key = nullptr, *counts = nullptr, *cursor = nullptr;
+    if ((st = pim_alloc(P, (void**)&key, N * sizeof(int))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&counts, nboxes * sizeof(int))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&cursor, nboxes * sizeof(int))) != PIM_OK) return st;
+    PIM_CK(cudaMemsetAsync(counts, 0, nboxes * sizeof(int), s));
+    PIM_CK(cudaMemsetAsync(cursor, 0, nboxes * sizeof(int), s));
+    PIM_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
+    BinArgs ba{};
+    for (int i = 0; i < 3; ++i) { ba.D[i] = P->D[i]; ba.h[i] = P->h[i]; ba.nb[i] = P->nb[i]; }
+    d.N = N;
+    if (N > 0) keys_kernel<<<1024, 256, 0, s>>>(xyz, N, ba, key, counts, P->dstatus);
+    PIM_CK(cudaGetLastError());
+    int hstat = 0;
+    PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIM_CK(cudaStreamSynchronize(s));
+    if (hstat) {
+        pim_free(P, key, N * sizeof(int));
+        pim_free(P, counts, nboxes * sizeof(int));
+        pim_free(P, cursor, nboxes * sizeof(int));
+        d.N = 0;
+        pim_set_error("a point lies outside the closed cell [0, D]");
+        return PIM_ERR_OUT_OF_CELL;
+    }
+    if ((st = pim_alloc(P, (void**)&d.box_ptr, (nboxes + 1) * sizeof(int))) != PIM_OK) return st;
+    if ((st = scan<int>(P, counts, d.box_ptr, nboxes, s)) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.perm, N * sizeof(int))) != PIM_OK) return st;
+    if (N > 0) {
+        scatter_kernel<<<1024, 256, 0, s>>>(key, N, d.box_ptr, cursor, d.perm);
+        sort_boxes_kernel<<<(unsigned)((nboxes + 255) / 256), 256, 0, s>>>(d.box_ptr, nboxes, d.perm);
+    }
+    PIM_CK(cudaGetLastError());
+    // per-point data in sorted order
+    if ((st = pim_alloc(P, (void**)&d.pos, 3 * N * sizeof(double))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.ns, N * sizeof(uint32_t))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.nt, 3 * N * sizeof(float))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.ntd, 3 * N * sizeof(double))) != PIM_OK) return st;
+    if (P->has_far) {
+        if ((st = pim_alloc(P, (void**)&d.fs, N * sizeof(uint32_t))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.fo, N * sizeof(uint32_t))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.ft, 6 * N * sizeof(float))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.ftd, 6 * N * sizeof(double))) != PIM_OK) return st;
+    }
+    PtArgs pa{};
+    for (int i = 0; i < 3; ++i) {
+        pa.h[i] = P->h[i]; pa.df[i] = P->df[i]; pa.n[i] = P->n[i]; pa.nf[i] = P->nf[i];
+    }
+    pa.p = P->p;
+    pa.pf = P->pf;
+    pa.has_far = P->has_far ? 1 : 0;
+    if (N > 0)
+        point_data_kernel<<<1024, 256, 0, s>>>(xyz, d.perm, N, pa, d.pos, d.ns, d.nt, d.ntd, d.fs, d.fo, d.ft, d.ftd);
+    PIM_CK(cudaGetLastError());
+    // near-pair list
+    int* dimg = nullptr;
+    if ((st = pim_alloc(P, (void**)&dimg, sizeof(int) * 3 * P->nimg)) != PIM_OK) return st;
+    PIM_CK(cudaMemcpyAsync(dimg, P->img, sizeof(int) * 3 * P->nimg, cudaMemcpyHostToDevice, s));
+    double* dh = nullptr;
+    if ((st = pim_alloc(P, (void**)&dh, sizeof(double) * 3)) != PIM_OK) return st;
+    PIM_CK(cudaMemcpyAsync(dh, P->h, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    PairArgs pr{};
+    for (int i = 0; i < 3; ++i) { pr.nb[i] = P->nb[i]; pr.nL[i] = P->n[i] - 1; }
+    pr.b = P->b;
+    pr.cube = P->cube;
+    pr.nimg = P->nimg;
+    pr.img = dimg;
+    int* rowlen = key;  // reuse
+    if (N > 0) pair_count_kernel<<<1024, 256, 0, s>>>(d.pos, N, dh, pr, d.box_ptr, rowlen);
+    PIM_CK(cudaGetLastError());
+    if ((st = pim_alloc(P, (void**)&d.row_ptr, (N + 1) * sizeof(int64_t))) != PIM_OK) return st;
+    if ((st = scan<int64_t>(P, rowlen, d.row_ptr, N, s)) != PIM_OK) return st;
+    int64_t nnz = 0;
+    PIM_CK(cudaMemcpy(&nnz, d.row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    d.nnz = nnz;
+    if ((st = pim_alloc(P, (void**)&d.col, nnz * sizeof(uint32_t))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.val, nnz * sizeof(double2))) != PIM_OK) return st;
+    if (P->corr_mode == PIM_CORR_DOUBLE_FLOAT)
+        if ((st = pim_alloc(P, (void**)&d.valdf, nnz * sizeof(float4))) != PIM_OK) return st;
+    if (P->corr_mode == PIM_CORR_FP32)
+        if ((st = pim_alloc(P, (void**)&d.valf, nnz * sizeof(float2))) != PIM_OK) return st;
+    // table of g over the offsets a correction can reach
+    FillArgs fa{};
+    fa.pa = pr;
+    for (int i = 0; i < 3; ++i) { fa.h[i] = P->h[i]; fa.D[i] = P->D[i]; }
+    fa.k = P->k;
+    fa.p = P->p;
+    fa.R = P->b + 2 + 2 * P->p;
+    fa.W = 2 * fa.R + 1;
+    fa.corr_mode = P->corr_mode;
+    fa.self_img = -1;
+    for (int i = 0; i < P->nimg; ++i)
+        if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) fa.self_img = i;
+    double2* gtab = nullptr;
+    const size_t gsz = (size_t)fa.W * fa.W * fa.W * sizeof(double2);
+    if ((st = pim_alloc(P, (void**)&gtab, gsz)) != PIM_OK) return st;
+    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k);
+    fa.gtab = gtab;
+    if (N > 0 && nnz > 0)
+        pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.row_ptr, d.col, d.val,
+                                                   d.valdf, d.valf, P->dstatus);
+    PIM_CK(cudaGetLastError());
+    PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, gtab, gsz);
+    pim_free(P, dimg, sizeof(int) * 3 * P->nimg);
+    pim_free(P, dh, sizeof(double) * 3);
+    pim_free(P, key, N * sizeof(int));
+    pim_free(P, counts, nboxes * sizeof(int));
+    pim_free(P, cursor, nboxes * sizeof(int));
+    if (hstat) {
+        pim_set_error("internal bounds check tripped while building the correction list");
+        return PIM_ERR_DEVICE;
+    }
+    return PIM_OK;
+}
