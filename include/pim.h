@@ -104,7 +104,19 @@ typedef struct {
     size_t device_bytes; /* bytes the plan holds on the device                         */
     double plan_ms;      /* wall time of pim_plan_create                               */
     double points_ms;    /* wall time of the last pim_set_points                       */
+    int64_t launches;    /* kernels launched by this plan's applies so far             */
 } pim_info;
+
+/* Stages timed by the profiling ring (pim_set_profiling). */
+typedef enum {
+    PIM_STAGE_PERMUTE = 0,   /* regularise (Eq. neutral) and reorder the sources        */
+    PIM_STAGE_SPREAD = 1,    /* near step 1: anterpolation onto the grid                */
+    PIM_STAGE_FFT = 2,       /* near step 2: the five pruned FFT passes                 */
+    PIM_STAGE_GATHER = 3,    /* near steps 3-4 and far step 3: gather, correction, sum  */
+    PIM_STAGE_FAR = 4,       /* far steps 1-2: projection and grid sum (second stream)  */
+    PIM_STAGE_APPLY = 5,     /* the whole apply, first to last launch                   */
+    PIM_NUM_STAGES = 6
+} pim_stage;
 
 /* Fills *opt with the defaults documented above. */
 void pim_options_default(pim_options* opt);
@@ -190,6 +202,25 @@ pim_status pim_last_device_status(pim_plan plan);
 
 /* Sizes and timings of a plan. */
 pim_status pim_plan_info(pim_plan plan, pim_info* info);
+
+/*
+ * pim_set_profiling -- on != 0: every later apply records a CUDA event pair
+ * around each pim_stage on the stream that stage runs on (a ring of 512
+ * applies); on = 0 stops recording.  Either way the accumulated times are
+ * cleared.  Events cost a few microseconds of device time per apply.
+ */
+pim_status pim_set_profiling(pim_plan plan, int on);
+
+/*
+ * pim_stage_times -- synchronises, then writes for each stage s < n the
+ * total device time in ms (ms[s]) and the number of applies timed (count,
+ * may be NULL) since pim_set_profiling.  Applies beyond the ring's 512 are
+ * not included.
+ */
+pim_status pim_stage_times(pim_plan plan, double* ms, int n, int64_t* count);
+
+/* Name of a stage ("spread", "fft", ...), static string; NULL if out of range. */
+const char* pim_stage_name(int stage);
 
 /*
  * pim_debug_copy -- copies an internal table to host memory, for tests of

@@ -51,6 +51,13 @@ pim_status pim_alloc(pim_plan P, void** ptr, size_t bytes) {
     return PIM_OK;
 }
 
+void prof_mark(pim_plan P, int stage, int which, cudaStream_t s) {
+    if (!P->prof_on || P->prof_next >= pim_plan_s::PROF_RING) return;
+    const int slot = P->prof_next;
+    cudaEventRecord(P->prof_ev[(slot * PIM_NUM_STAGES + stage) * 2 + which], s);
+    if (which == 1) P->prof_mask[slot] |= (unsigned char)(1u << stage);
+}
+
 void pim_free(pim_plan P, void* ptr, size_t bytes) {
     if (!ptr) return;
     cudaFree(ptr);
@@ -116,6 +123,10 @@ void pim_destroy(pim_plan P) {
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
     pim_free(P, P->dphase, sizeof(double2) * PIM_MAX_IMAGES);
     pim_free(P, P->dstatus, sizeof(int));
+    if (P->prof_ev) {
+        for (int i = 0; i < pim_plan_s::PROF_RING * PIM_NUM_STAGES * 2; ++i) cudaEventDestroy(P->prof_ev[i]);
+        delete[] P->prof_ev;
+    }
     if (P->s_far) cudaStreamDestroy(P->s_far);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
@@ -396,7 +407,44 @@ pim_status pim_plan_info(pim_plan P, pim_info* info) {
     info->device_bytes = P->bytes;
     info->plan_ms = P->plan_ms;
     info->points_ms = P->points_ms;
+    info->launches = P->launches;
     return PIM_OK;
+}
+
+pim_status pim_set_profiling(pim_plan P, int on) {
+    if (!P) return PIM_ERR_ARG;
+    PIM_CK(cudaDeviceSynchronize());
+    if (on && !P->prof_ev) {
+        const int ne = pim_plan_s::PROF_RING * PIM_NUM_STAGES * 2;
+        P->prof_ev = new cudaEvent_t[ne];
+        for (int i = 0; i < ne; ++i) PIM_CK(cudaEventCreate(&P->prof_ev[i]));
+    }
+    P->prof_on = on != 0;
+    P->prof_next = 0;
+    std::memset(P->prof_mask, 0, sizeof(P->prof_mask));
+    return PIM_OK;
+}
+
+pim_status pim_stage_times(pim_plan P, double* ms, int n, int64_t* count) {
+    if (!P || (n > 0 && !ms)) return PIM_ERR_ARG;
+    PIM_CK(cudaDeviceSynchronize());
+    for (int st = 0; st < n; ++st) ms[st] = 0.0;
+    const int used = P->prof_next < pim_plan_s::PROF_RING ? P->prof_next : pim_plan_s::PROF_RING;
+    for (int slot = 0; slot < used && P->prof_ev; ++slot)
+        for (int st = 0; st < n && st < PIM_NUM_STAGES; ++st) {
+            if (!(P->prof_mask[slot] & (1u << st))) continue;
+            float t = 0.f;
+            PIM_CK(cudaEventElapsedTime(&t, P->prof_ev[(slot * PIM_NUM_STAGES + st) * 2],
+                                        P->prof_ev[(slot * PIM_NUM_STAGES + st) * 2 + 1]));
+            ms[st] += t;
+        }
+    if (count) *count = used;
+    return PIM_OK;
+}
+
+const char* pim_stage_name(int stage) {
+    static const char* names[PIM_NUM_STAGES] = {"permute", "spread", "fft", "gather_correct", "far", "apply"};
+    return stage >= 0 && stage < PIM_NUM_STAGES ? names[stage] : nullptr;
 }
 
 pim_status pim_debug_copy(pim_plan P, int what, void* host, size_t bytes) {

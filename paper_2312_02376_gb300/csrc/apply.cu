@@ -419,6 +419,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
     cplx<T>* gA = (cplx<T>*)P->gA;
     pim_status st;
     for (int r = 0; r < nrhs; ++r) {
+        prof_mark(P, PIM_STAGE_APPLY, 0, s);
+        prof_mark(P, PIM_STAGE_PERMUTE, 0, s);
         // 1. sorted, regularised sources (Eq. neutral)
         const double* mean = nullptr;
         if (P->npsp && !adj) {
@@ -428,10 +430,13 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         if (P->real_data) permute_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
         else permute_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
         PIM_CK(cudaGetLastError());
+        P->launches += 1 + (mean ? 2 : 0);
+        prof_mark(P, PIM_STAGE_PERMUTE, 1, s);
         // 2. far zone on the second stream
         if (P->has_far) {
             PIM_CK(cudaEventRecord(P->ev_fork, s));
             PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
+            prof_mark(P, PIM_STAGE_FAR, 0, P->s_far);
             FarSpreadArgs fa{};
             for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
             fa.pf = P->pf;
@@ -454,6 +459,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
                 far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)P->fB, G);
                 PIM_CK(cudaGetLastError());
             }
+            P->launches += 2 + 5 + (sizeof(T) == 4 ? 1 : 0);
+            prof_mark(P, PIM_STAGE_FAR, 1, P->s_far);
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
         // 3. near spread, 4. FFT convolution
@@ -471,10 +478,15 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         const int ntiles = sa.ntiles[0] * sa.ntiles[1] * sa.ntiles[2];
         const size_t sm = 2 * sizeof(T) * P->tile[0] * P->tile[1] * P->tile[2];
         PIM_CK(cudaFuncSetAttribute(spread_kernel<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        prof_mark(P, PIM_STAGE_SPREAD, 0, s);
         spread_kernel<T, PP><<<ntiles, 256, sm, s>>>(sa, qs, gA);
         PIM_CK(cudaGetLastError());
+        prof_mark(P, PIM_STAGE_SPREAD, 1, s);
+        prof_mark(P, PIM_STAGE_FFT, 0, s);
         if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, s)) != PIM_OK)
             return st;
+        prof_mark(P, PIM_STAGE_FFT, 1, s);
+        P->launches += 1 + 5;
         // 5. gather + correction + far gather
         if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
         GatherArgs ga{};
@@ -509,15 +521,21 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
+        prof_mark(P, PIM_STAGE_GATHER, 0, s);
         if (N > 0)
             gather_kernel<T, PP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ga, gA, ufar, qs, dst);
         PIM_CK(cudaGetLastError());
+        prof_mark(P, PIM_STAGE_GATHER, 1, s);
+        P->launches += N > 0 ? 1 : 0;
         if (post_mean) {
             if ((st = mean_of<T>(P, P->us, true, N, 1, 0, false, s)) != PIM_OK) return st;
             unpermute_kernel<T><<<1024, 256, 0, s>>>((const cplx<T>*)P->us, d.perm, N, nrhs, r, P->dsum,
                                                      P->real_data ? 1 : 0, u);
             PIM_CK(cudaGetLastError());
+            P->launches += 3;
         }
+        prof_mark(P, PIM_STAGE_APPLY, 1, s);
+        if (P->prof_on && P->prof_next < pim_plan_s::PROF_RING) P->prof_next++;
     }
     return PIM_OK;
 }

@@ -28,7 +28,7 @@ constexpr int PIM_MAX_IMAGES = 125;
 constexpr int PIM_MAX_P = 6;
 
 // device-side status flags (bit set)
-enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2 };
+enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2, PIM_DEV_COINCIDENT = 4 };
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -163,6 +163,13 @@ struct pim_plan_s {
     double* dsum = nullptr;       // FP64 scratch: [0..1] mean, [4..) reduction partials
     double2* dphase = nullptr;    // device copy of phase[]
     int* dstatus = nullptr;
+    // profiling ring (pim_set_profiling)
+    static constexpr int PROF_RING = 512;
+    bool prof_on = false;
+    int prof_next = 0;             // applies recorded since the reset
+    cudaEvent_t* prof_ev = nullptr;  // [PROF_RING][PIM_NUM_STAGES][2]
+    unsigned char prof_mask[512];    // stages recorded per ring slot
+    int64_t launches = 0;
     // streams and events
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -190,6 +197,9 @@ pim_status build_far_table(pim_plan P, cudaStream_t s);
 // points.cu
 pim_status points_build(pim_plan P, int64_t N, const double* xyz_dev, cudaStream_t s);
 void points_free(pim_plan P);
+
+// profiling: record the start / stop event of a stage of the current apply
+void prof_mark(pim_plan P, int stage, int which, cudaStream_t s);
 
 // apply.cu
 constexpr int PIM_RED_BLOCKS = 608;

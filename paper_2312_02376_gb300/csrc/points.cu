@@ -305,6 +305,10 @@ __device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32
             const double x = pos[3 * m + d] - pos[3 * n + d] - a.pa.img[3 * ii + d] * a.D[d];
             r2 += x * x;
         }
+        if (r2 == 0.0) {  // two points coincide modulo the lattice: Eq. 1 is singular
+            atomicOr(status, PIM_DEV_COINCIDENT);
+            return make_double2(0.0, 0.0);
+        }
         exact = G0(sqrt(r2), a.k);
     }
     return csub(exact, grid);
@@ -506,6 +510,10 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     pim_free(P, key, N * sizeof(int));
     pim_free(P, counts, nboxes * sizeof(int));
     pim_free(P, cursor, nboxes * sizeof(int));
+    if (hstat & PIM_DEV_COINCIDENT) {
+        pim_set_error("two points coincide (modulo the lattice): the periodic sum is singular");
+        return PIM_ERR_ARG;
+    }
     if (hstat) {
         pim_set_error("internal bounds check tripped while building the correction list");
         return PIM_ERR_DEVICE;

@@ -21,8 +21,9 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32 = 0, 1, 2
 
 # symbols declared in include/pim.h
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
-           "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_debug_copy",
-           "pim_destroy"]
+           "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
+           "pim_stage_times", "pim_stage_name", "pim_debug_copy", "pim_destroy"]
+STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
 
 class pim_options(ctypes.Structure):
@@ -36,7 +37,7 @@ class pim_info(ctypes.Structure):
                 ("corr_radius", ctypes.c_int), ("precision", ctypes.c_int), ("corr_mode", ctypes.c_int),
                 ("periodic_mask", ctypes.c_int), ("near_layers", ctypes.c_int), ("N", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double),
-                ("points_ms", ctypes.c_double)]
+                ("points_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
 class PimError(RuntimeError):
@@ -81,6 +82,12 @@ def load(path=LIB_PATH):
     lib.pim_last_device_status.restype = i32
     lib.pim_plan_info.argtypes = [vp, ctypes.POINTER(pim_info)]
     lib.pim_plan_info.restype = i32
+    lib.pim_set_profiling.argtypes = [vp, i32]
+    lib.pim_set_profiling.restype = i32
+    lib.pim_stage_times.argtypes = [vp, ctypes.POINTER(dbl), i32, ctypes.POINTER(i64)]
+    lib.pim_stage_times.restype = i32
+    lib.pim_stage_name.argtypes = [i32]
+    lib.pim_stage_name.restype = ctypes.c_char_p
     lib.pim_debug_copy.argtypes = [vp, i32, vp, ctypes.c_size_t]
     lib.pim_debug_copy.restype = i32
     lib.pim_destroy.argtypes = [vp]
@@ -158,6 +165,23 @@ def pim_plan_info(plan):
     info = pim_info()
     _check(load().pim_plan_info(plan, ctypes.byref(info)), "pim_plan_info")
     return info
+
+
+def pim_set_profiling(plan, on):
+    _check(load().pim_set_profiling(plan, int(on)), "pim_set_profiling")
+
+
+def pim_stage_times(plan):
+    """{stage name: total ms} and the number of applies timed."""
+    ms = (ctypes.c_double * len(STAGES))()
+    cnt = ctypes.c_int64()
+    _check(load().pim_stage_times(plan, ms, len(STAGES), ctypes.byref(cnt)), "pim_stage_times")
+    return {STAGES[i]: ms[i] for i in range(len(STAGES))}, cnt.value
+
+
+def pim_stage_name(stage):
+    r = load().pim_stage_name(int(stage))
+    return r.decode() if r is not None else None
 
 
 def pim_debug_copy(plan, what, out):
@@ -244,6 +268,12 @@ class Plan:
 
     def apply_adjoint(self, v, out=None, stream=None):
         return self.apply(v, out, stream, adjoint=True)
+
+    def set_profiling(self, on=True):
+        pim_set_profiling(self._h, on)
+
+    def stage_times(self):
+        return pim_stage_times(self._h)
 
     def device_status(self):
         return pim_last_device_status(self._h)

@@ -191,7 +191,7 @@ def test_edge_cases_faces_single_box_and_tiny():
     D = np.array([1.0, 1.0, 0.5])
     # points on the cell faces and corners, a cluster inside one box, ragged grid vs tiles
     pts = np.concatenate([
-        np.array([[0, 0, 0], [1, 1, 0.5], [1, 0, 0.25], [0, 1, 0.5], [0.5, 0, 0.5]]),
+        np.array([[0, 0, 0], [1, 1, 0.5], [1, 0, 0.25], [0, 1, 0.4], [0.5, 0, 0.5]]),
         0.31 + 0.001 * rng.random((40, 3)) * D,
         rng.random((60, 3)) * D,
     ])
@@ -242,6 +242,13 @@ def test_errors_are_status_codes():
     with pytest.raises(pim.PimError) as e:
         pim.pim_plan_create(np.diag(D), 1, 1.0, (0, 0, 0), (0.3, 0.125, 0.125), 4, 1, pim.PIM_FP64)
     assert e.value.status == pim.PIM_ERR_ARG
+    # two points that coincide modulo the lattice make Eq. 1 singular
+    pl2 = pim.Plan((1, 1, 1), (0, 1, 2), 0.0, (0, 0, 0), (9, 9, 9), p=4, precision="fp64", b=3, nf=(6, 6, 6))
+    with pytest.raises(pim.PimError) as e:
+        pl2.set_points(torch.tensor([[0.2, 0.3, 0.4], [1.0, 0.5, 0.5], [0.0, 0.5, 0.5]], dtype=torch.float64,
+                                    device="cuda"))
+    assert e.value.status == pim.PIM_ERR_ARG
+    pl2.close()
     # memory cap
     with pytest.raises(pim.PimError) as e:
         pim.Plan(D, (0, 1, 2), 1.0, (0, 0, 0), (33, 33, 33), p=4, precision="fp64", mem_cap=1 << 20)
