@@ -65,3 +65,15 @@ def box_index(x, h, n):
     """Box (cell of the grid) containing x: floor(x/h) clamped to [0, n-1]."""
     b = np.floor(np.asarray(x, dtype=np.float64) / h).astype(np.int64)
     return np.clip(b, 0, n - 1)
+
+
+def stencil_box(x, h, n, p):
+    """Box of x in the sense of the box-adaptive integral method: the set of
+    points that share one interpolation stencil.  Even p: the box centred on
+    node b = floor(x/h + 1/2), b in [0, n-1]; odd p: the grid cell
+    b = floor(x/h), b in [0, n-2].  All points of a box have the stencil
+    start min(max(b - lo, 0), n-1-p), lo = p/2 or (p-1)/2."""
+    u = np.asarray(x, dtype=np.float64) / h
+    if p % 2 == 0:
+        return np.clip(np.floor(u + 0.5).astype(np.int64), 0, n - 1)
+    return np.clip(np.floor(u).astype(np.int64), 0, n - 2)

@@ -16,9 +16,14 @@ Readings of the paper taken here (where it is silent or ambiguous):
   * padding: G_near has no periodicity, so every axis is treated as aperiodic
     (Sec. 3.3 step 2); here the convolution is summed directly.
   * grid kernel at zero offset: g(0) = 0 (the paper does not define it).
-  * correction region: box Chebyshev radius b around the observer box; for
-    every near image i the pair (m, n) is corrected for that image only
-    when |B(m) - B(n) - i o (n-1)|_inf <= b (Sec. 3.3 step 4, single-extra-image
+  * boxes (Sec. 3.3 step 4: "boxes defined by Delta"): boxes of one grid
+    step, placed so that all points of a box share one interpolation stencil
+    (node-centred for even p, the grid cells for odd p), as in the
+    box-adaptive integral method the near zone is built on.
+  * correction region: for every near image i the pair (m, n) is corrected
+    for that image only when the boxes B(m) and B(n) + i o (n-1) are at most
+    b grid steps apart (minimum distance between the boxes, i.e. |r - r_m|
+    <= D^ER with D^ER = b steps; Sec. 3.3 step 4 with the single-extra-image
     rule).  The grid part of the correction uses the image-i component of the
     tabulated kernel; the weights are those of steps 1 and 3.
   * far grids: source nodes l*Delta, observer nodes l*Delta + Delta/2,
@@ -93,7 +98,7 @@ def near_stencils(P, pts):
     for d in range(3):
         s[:, d], t = lagrange.stencil_start(pts[:, d], P.h[d], P.n[d], P.p)
         w[:, d, :] = lagrange.weights(t, P.p)
-        B[:, d] = lagrange.box_index(pts[:, d], P.h[d], P.n[d] - 1)
+        B[:, d] = lagrange.stencil_box(pts[:, d], P.h[d], P.n[d], P.p)
     return s, w, B
 
 

@@ -56,3 +56,15 @@ def test_stencil_rule_even_odd_and_clamp():
 def test_box_index():
     b = lagrange.box_index(np.array([0.0, 0.099, 0.1, 0.95, 1.0]), 0.1, 10)
     assert list(b) == [0, 0, 1, 9, 9]
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_points_of_a_box_share_one_stencil(p):
+    h, n = 0.1, 12
+    x = np.random.default_rng(0).random(4000) * (n - 1) * h
+    x = np.concatenate([x, [0.0, (n - 1) * h, 0.05, 0.15, 1.05]])
+    B = lagrange.stencil_box(x, h, n, p)
+    s, _ = lagrange.stencil_start(x, h, n, p)
+    lo = p // 2 if p % 2 == 0 else (p - 1) // 2
+    assert np.array_equal(s, np.clip(B - lo, 0, n - 1 - p))
+    assert B.min() >= 0 and B.max() <= (n - 1 if p % 2 == 0 else n - 2)
