@@ -193,7 +193,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
             return fail(PIM_ERR_ARG);
         }
         P->n[d] = (int)rs + 1;
-        P->nb[d] = P->n[d] - 1;
+        P->nb[d] = (p & 1) ? P->n[d] - 1 : P->n[d];
         P->h[d] = P->D[d] / rs;
         if (P->n[d] < p + 1 || P->n[d] > 1024) {
             pim_set_error("near grid must have p+1 .. 1024 nodes per axis");

@@ -88,15 +88,38 @@ struct SpreadArgs {
     const double* ntd;
 };
 
+// Lagrange weights of compile-time degree P (prefix/suffix products times
+// the constant inverse denominators).
+template <typename T, int P>
+__device__ __forceinline__ void lagrange_w(T t, T* w) {
+    T pre[P + 1], suf[P + 1];
+    pre[0] = T(1);
+#pragma unroll
+    for (int j = 1; j <= P; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
+    suf[P] = T(1);
+#pragma unroll
+    for (int j = P - 1; j >= 0; --j) suf[j] = suf[j + 1] * (t - T(j + 1));
+#pragma unroll
+    for (int j = 0; j <= P; ++j) {
+        double den = 1.0;
+        for (int l = 0; l <= P; ++l)
+            if (l != j) den *= (double)(j - l);
+        w[j] = pre[j] * suf[j] * T(1.0 / den);
+    }
+}
+
 // Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1).  One CTA owns a tile of grid
-// nodes and accumulates every point whose stencil reaches it in shared
-// memory, then writes the tile once: no global atomics, every node written
-// by exactly one CTA.  Candidate points are read box row by box row (boxes
-// are contiguous along x in the sorted order).
+// nodes and writes it once: no global atomics.  Every point of a box shares
+// the box's stencil, so a warp walks the points of a row of boxes in order
+// with each lane owning (P+1)^3 / 32 stencil nodes, accumulates in registers
+// while the stencil start is unchanged, and adds to the shared-memory tile
+// once per box (lane-distinct addresses).
 template <typename T, int P>
 __global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>* __restrict__ qs, cplx<T>* Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);  // 2 * TX*TY*TZ
+    constexpr int NP = P + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
+    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
     const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
     const int ntile = TX * TY * TZ;
     int t = blockIdx.x;
@@ -105,48 +128,71 @@ __global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>
     const int ty = t % a.ntiles[1];
     const int tz = t / a.ntiles[1];
     const int a0[3] = {tx * TX, ty * TY, tz * TZ};
+    const int T3[3] = {TX, TY, TZ};
     for (int i = threadIdx.x; i < 2 * ntile; i += blockDim.x) acc[i] = T(0);
     __syncthreads();
+    // boxes whose (clamped) stencil [s, s+P] meets [a0, a0+T-1]
     int blo[3], bhi[3];
-    const int T3[3] = {TX, TY, TZ};
     for (int d = 0; d < 3; ++d) {
-        blo[d] = max(0, a0[d] - P - 1);
-        bhi[d] = min(a.nb[d] - 1, a0[d] + T3[d] + P);
+        blo[d] = a0[d] <= P ? 0 : a0[d] - P + LO;
+        bhi[d] = a0[d] + T3[d] - 1 >= a.n[d] - 1 - P ? a.nb[d] - 1 : a0[d] + T3[d] - 1 + LO;
+        blo[d] = max(0, blo[d]);
+        bhi[d] = min(a.nb[d] - 1, bhi[d]);
     }
-    const int nry = bhi[1] - blo[1] + 1, nrz = bhi[2] - blo[2] + 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int row = wid; row < nry * nrz; row += nw) {
+    int jx[KPL], jy[KPL], jz[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) {
+        const int o = lane + 32 * k;
+        jx[k] = o % NP;
+        jy[k] = (o / NP) % NP;
+        jz[k] = o / (NP * NP);  // >= NP for o >= NP3: never inside
+    }
+    const int nry = max(0, bhi[1] - blo[1] + 1), nrz = max(0, bhi[2] - blo[2] + 1);
+    const int nrows = bhi[0] >= blo[0] ? nry * nrz : 0;
+    for (int row = wid; row < nrows; row += nw) {
         const int by = blo[1] + row % nry, bz = blo[2] + row / nry;
         const long long rb = ((long long)bz * a.nb[1] + by) * a.nb[0];
         const int lo = a.box_ptr[rb + blo[0]], hi = a.box_ptr[rb + bhi[0] + 1];
-        for (int m = lo + lane; m < hi; m += 32) {
-            int s[3];
-            unpack3(a.ns[m], s[0], s[1], s[2]);
-            int j0[3], j1[3];
-            bool hit = true;
-            for (int d = 0; d < 3; ++d) {
-                j0[d] = max(0, a0[d] - s[d]);
-                j1[d] = min(P, a0[d] + T3[d] - 1 - s[d]);
-                if (j0[d] > j1[d]) hit = false;
+        uint32_t cur = 0xffffffffu;
+        int loc[KPL];   // shared-memory node index of each lane's node, -1 if outside the tile
+        cplx<T> sum[KPL];
+        for (int m = lo; m <= hi; ++m) {
+            const uint32_t sm = m < hi ? a.ns[m] : 0xfffffffeu;
+            if (sm != cur) {
+                if (cur != 0xffffffffu) {
+#pragma unroll
+                    for (int k = 0; k < KPL; ++k)
+                        if (loc[k] >= 0) {
+                            atomicAdd(acc + 2 * loc[k], sum[k].x);
+                            atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
+                        }
+                }
+                if (m == hi) break;
+                cur = sm;
+                int s[3];
+                unpack3(sm, s[0], s[1], s[2]);
+#pragma unroll
+                for (int k = 0; k < KPL; ++k) {
+                    const int x = s[0] + jx[k] - a0[0], y = s[1] + jy[k] - a0[1], z = s[2] + jz[k] - a0[2];
+                    const bool in = jz[k] < NP && x >= 0 && x < TX && y >= 0 && y < TY && z >= 0 && z < TZ;
+                    loc[k] = in ? (z * TY + y) * TX + x : -1;
+                    sum[k] = mk<T>(T(0), T(0));
+                }
             }
-            if (!hit) continue;
-            T w[3][P + 1];
+            T w[3][NP];
+#pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-                lagrange_weights<T>(P, tt, w[d]);
+                lagrange_w<T, P>(tt, w[d]);
             }
             const cplx<T> qv = qs[m];
-            for (int jz = j0[2]; jz <= j1[2]; ++jz) {
-                const int lz = s[2] + jz - a0[2];
-                for (int jy = j0[1]; jy <= j1[1]; ++jy) {
-                    const int ly = s[1] + jy - a0[1];
-                    const T wzy = w[2][jz] * w[1][jy];
-                    T* rowp = acc + 2 * ((lz * TY + ly) * TX + (s[0] - a0[0]));
-                    for (int jx = j0[0]; jx <= j1[0]; ++jx) {
-                        const T ww = wzy * w[0][jx];
-                        atomicAdd(rowp + 2 * jx, ww * qv.x);
-                        atomicAdd(rowp + 2 * jx + 1, ww * qv.y);
-                    }
+#pragma unroll
+            for (int k = 0; k < KPL; ++k) {
+                if (jz[k] < NP) {
+                    const T ww = w[0][jx[k]] * w[1][jy[k]] * w[2][jz[k]];
+                    sum[k].x += ww * qv.x;
+                    sum[k].y += ww * qv.y;
                 }
             }
         }
@@ -171,40 +217,97 @@ struct FarSpreadArgs {
     int toff;
 };
 
-// Per-CTA partial far-grid charges (Eq. projection) in shared memory.
-template <typename T>
-__global__ void far_spread_kernel(FarSpreadArgs a, const cplx<T>* __restrict__ qs, cplx<T>* part) {
+// Per-CTA partial far-grid charges (Eq. projection) in shared memory.  Each
+// warp walks a contiguous run of (spatially sorted) points with lanes owning
+// stencil nodes; consecutive points mostly share a far stencil, so sums stay
+// in registers until the stencil start changes.
+template <typename T, int PF>
+__global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const cplx<T>* __restrict__ qs,
+                                                         cplx<T>* part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
+    constexpr int NP = PF + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
     const int G = a.nf[0] * a.nf[1] * a.nf[2];
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
     __syncthreads();
     const long long m0 = (long long)blockIdx.x * a.chunk;
     const long long m1 = min(a.N, m0 + a.chunk);
-    const int pf = a.pf, np = pf + 1;
-    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-        int s[3];
-        unpack3(a.fst[m], s[0], s[1], s[2]);
-        T w[3][PIM_MAX_P + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long per = (m1 - m0 + nw - 1) / nw;
+    const long long w0 = m0 + wid * per, w1 = min(m1, w0 + per);
+    int jx[KPL], jy[KPL], jz[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) {
+        const int o = lane + 32 * k;
+        jx[k] = o % NP;
+        jy[k] = (o / NP) % NP;
+        jz[k] = o / (NP * NP);
+    }
+    uint32_t cur = 0xffffffffu;
+    int loc[KPL];
+    cplx<T> sum[KPL];
+    for (long long m = w0; m <= w1 && w0 < w1; ++m) {
+        const uint32_t sm = m < w1 ? a.fst[m] : 0xfffffffeu;
+        if (sm != cur) {
+            if (cur != 0xffffffffu) {
+#pragma unroll
+                for (int k = 0; k < KPL; ++k)
+                    if (loc[k] >= 0) {
+                        atomicAdd(acc + 2 * loc[k], sum[k].x);
+                        atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
+                    }
+            }
+            if (m == w1) break;
+            cur = sm;
+            int s[3];
+            unpack3(sm, s[0], s[1], s[2]);
+#pragma unroll
+            for (int k = 0; k < KPL; ++k) {
+                loc[k] = jz[k] < NP ? ((s[2] + jz[k]) * a.nf[1] + (s[1] + jy[k])) * a.nf[0] + s[0] + jx[k] : -1;
+                sum[k] = mk<T>(T(0), T(0));
+            }
+        }
+        T w[3][NP];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
-            lagrange_weights<T>(pf, tt, w[d]);
+            lagrange_w<T, PF>(tt, w[d]);
         }
         const cplx<T> qv = qs[m];
-        for (int jz = 0; jz < np; ++jz)
-            for (int jy = 0; jy < np; ++jy) {
-                const T wzy = w[2][jz] * w[1][jy];
-                T* rowp = acc + 2 * (((s[2] + jz) * a.nf[1] + (s[1] + jy)) * a.nf[0] + s[0]);
-                for (int jx = 0; jx < np; ++jx) {
-                    const T ww = wzy * w[0][jx];
-                    atomicAdd(rowp + 2 * jx, ww * qv.x);
-                    atomicAdd(rowp + 2 * jx + 1, ww * qv.y);
-                }
+#pragma unroll
+        for (int k = 0; k < KPL; ++k)
+            if (jz[k] < NP) {
+                const T ww = w[0][jx[k]] * w[1][jy[k]] * w[2][jz[k]];
+                sum[k].x += ww * qv.x;
+                sum[k].y += ww * qv.y;
             }
     }
     __syncthreads();
     cplx<T>* out = part + (long long)blockIdx.x * G;
     for (int i = threadIdx.x; i < G; i += blockDim.x) out[i] = mk<T>(acc[2 * i], acc[2 * i + 1]);
+}
+
+template <typename T>
+pim_status launch_far_spread(int pf, int grid, size_t sm, cudaStream_t s, const FarSpreadArgs& fa, const cplx<T>* qs,
+                             cplx<T>* part) {
+#define PIM_FAR_CASE(PFV)                                                                                  \
+    case PFV: {                                                                                            \
+        PIM_CK(cudaFuncSetAttribute(far_spread_kernel<T, PFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)sm));                                                             \
+        far_spread_kernel<T, PFV><<<grid, 256, sm, s>>>(fa, qs, part);                                     \
+        break;                                                                                             \
+    }
+    switch (pf) {
+        PIM_FAR_CASE(2)
+        PIM_FAR_CASE(3)
+        PIM_FAR_CASE(4)
+        PIM_FAR_CASE(5)
+        PIM_FAR_CASE(6)
+        default: pim_set_error("far degree must be 2..6"); return PIM_ERR_UNSUPPORTED;
+    }
+#undef PIM_FAR_CASE
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
 }
 
 // qf[g] = sum over CTAs of the partials, in FP64, fixed order
@@ -448,9 +551,13 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             fa.toff = adj ? 3 : 0;
             const int G = P->nf[0] * P->nf[1] * P->nf[2];
             const size_t sm = 2 * sizeof(T) * G;
-            PIM_CK(cudaFuncSetAttribute(far_spread_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            if (N > 0) far_spread_kernel<T><<<P->far_chunks, 256, sm, P->s_far>>>(fa, qs, (cplx<T>*)P->fpart);
-            else PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, P->s_far));
+            if (N > 0) {
+                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, P->s_far, fa, qs, (cplx<T>*)P->fpart)) !=
+                    PIM_OK)
+                    return st;
+            } else {
+                PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, P->s_far));
+            }
             far_reduce_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks, G,
                                                                         P->fA);
             PIM_CK(cudaGetLastError());

@@ -80,6 +80,16 @@ __host__ __device__ __forceinline__ int stencil_start(double u, int n, int p) {
     return s;
 }
 
+// Box of a coordinate: the cell of points that share one stencil.  Even p:
+// the box centred on node floor(u + 1/2) (nb = n boxes); odd p: the grid
+// cell floor(u) (nb = n-1 boxes).  u = x / h in FP64, as in stencil_start.
+__host__ __device__ __forceinline__ int box_of(double u, int nb, int p) {
+    int b = (p & 1) ? (int)floor(u) : (int)floor(u + 0.5);
+    if (b < 0) b = 0;
+    if (b > nb - 1) b = nb - 1;
+    return b;
+}
+
 __host__ __device__ __forceinline__ uint32_t pack3(int a, int b, int c) {
     return (uint32_t)a | ((uint32_t)b << 10) | ((uint32_t)c << 20);
 }

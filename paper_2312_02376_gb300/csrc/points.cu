@@ -96,6 +96,7 @@ __global__ void scan_write(const int* in, long long n, const long long* partial,
 struct BinArgs {
     double D[3], h[3];
     int nb[3];
+    int p;
 };
 
 __global__ void keys_kernel(const double* xyz, long long N, BinArgs a, int* key, int* counts, int* status) {
@@ -105,9 +106,7 @@ __global__ void keys_kernel(const double* xyz, long long N, BinArgs a, int* key,
         for (int d = 0; d < 3; ++d) {
             const double x = xyz[3 * i + d];
             if (!(x >= 0.0 && x <= a.D[d])) ok = false;
-            int v = (int)floor(x / a.h[d]);
-            v = v < 0 ? 0 : (v > a.nb[d] - 1 ? a.nb[d] - 1 : v);
-            b[d] = v;
+            b[d] = box_of(x / a.h[d], a.nb[d], a.p);
         }
         if (!ok) atomicOr(status, 1);
         const int k = (b[2] * a.nb[1] + b[1]) * a.nb[0] + b[0];
@@ -183,7 +182,7 @@ __global__ void point_data_kernel(const double* xyz, const int* perm, long long 
 // ------------------------------- near pairs --------------------------------
 struct PairArgs {
     int nb[3], nL[3];
-    int b, cube;
+    int b, cube, p;
     int nimg;
     const int* img;     // nimg x 3
 };
@@ -236,10 +235,7 @@ __global__ void pair_count_kernel(const double* pos, long long N, const double* 
                                   int* rowlen) {
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
         int B[3];
-        for (int d = 0; d < 3; ++d) {
-            int v = (int)floor(pos[3 * m + d] / hh[d]);
-            B[d] = v < 0 ? 0 : (v > a.nb[d] - 1 ? a.nb[d] - 1 : v);
-        }
+        for (int d = 0; d < 3; ++d) B[d] = box_of(pos[3 * m + d] / hh[d], a.nb[d], a.p);
         long long cnt = 0;
         for_each_region_row(a, box_ptr, B, [&](int, int lo, int hi) { cnt += hi - lo; });
         rowlen[m] = (int)cnt;
@@ -322,10 +318,7 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long m = warp; m < N; m += nwarps) {
         int B[3];
-        for (int d = 0; d < 3; ++d) {
-            int v = (int)floor(pos[3 * m + d] / a.h[d]);
-            B[d] = v < 0 ? 0 : (v > a.pa.nb[d] - 1 ? a.pa.nb[d] - 1 : v);
-        }
+        for (int d = 0; d < 3; ++d) B[d] = box_of(pos[3 * m + d] / a.h[d], a.pa.nb[d], a.pa.p);
         long long off = row_ptr[m];
         for_each_region_row(a.pa, box_ptr, B, [&](int ii, int lo, int hi) {
             for (int n = lo + lane; n < hi; n += 32) {
@@ -411,6 +404,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     PIM_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
     BinArgs ba{};
     for (int i = 0; i < 3; ++i) { ba.D[i] = P->D[i]; ba.h[i] = P->h[i]; ba.nb[i] = P->nb[i]; }
+    ba.p = P->p;
     d.N = N;
     if (N > 0) keys_kernel<<<1024, 256, 0, s>>>(xyz, N, ba, key, counts, P->dstatus);
     PIM_CK(cudaGetLastError());
@@ -465,6 +459,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     for (int i = 0; i < 3; ++i) { pr.nb[i] = P->nb[i]; pr.nL[i] = P->n[i] - 1; }
     pr.b = P->b;
     pr.cube = P->cube;
+    pr.p = P->p;
     pr.nimg = P->nimg;
     pr.img = dimg;
     int* rowlen = key;  // reuse
