@@ -157,45 +157,58 @@ __global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>
         uint32_t cur = 0xffffffffu;
         int loc[KPL];   // shared-memory node index of each lane's node, -1 if outside the tile
         cplx<T> sum[KPL];
-        for (int m = lo; m <= hi; ++m) {
-            const uint32_t sm = m < hi ? a.ns[m] : 0xfffffffeu;
-            if (sm != cur) {
-                if (cur != 0xffffffffu) {
+        auto flush = [&]() {
+            if (cur == 0xffffffffu) return;
 #pragma unroll
-                    for (int k = 0; k < KPL; ++k)
-                        if (loc[k] >= 0) {
-                            atomicAdd(acc + 2 * loc[k], sum[k].x);
-                            atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
-                        }
+            for (int k = 0; k < KPL; ++k)
+                if (loc[k] >= 0) {
+                    atomicAdd(acc + 2 * loc[k], sum[k].x);
+                    atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
                 }
-                if (m == hi) break;
-                cur = sm;
-                int s[3];
-                unpack3(sm, s[0], s[1], s[2]);
+        };
+        for (int b0 = lo; b0 < hi; b0 += 32) {
+            // one coalesced load of 32 points, then walk them by shuffles
+            const int cnt = min(32, hi - b0);
+            const int ml = b0 + lane;
+            uint32_t sl = 0;
+            T tl[3] = {T(0), T(0), T(0)};
+            cplx<T> ql = mk<T>(T(0), T(0));
+            if (lane < cnt) {
+                sl = a.ns[ml];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) tl[d] = sizeof(T) == 8 ? (T)a.ntd[3 * ml + d] : (T)a.nt[3 * ml + d];
+                ql = qs[ml];
+            }
+            for (int j = 0; j < cnt; ++j) {
+                const uint32_t sm = __shfl_sync(0xffffffffu, sl, j);
+                if (sm != cur) {
+                    flush();
+                    cur = sm;
+                    int s[3];
+                    unpack3(sm, s[0], s[1], s[2]);
+#pragma unroll
+                    for (int k = 0; k < KPL; ++k) {
+                        const int x = s[0] + jx[k] - a0[0], y = s[1] + jy[k] - a0[1], z = s[2] + jz[k] - a0[2];
+                        const bool in = jz[k] < NP && x >= 0 && x < TX && y >= 0 && y < TY && z >= 0 && z < TZ;
+                        loc[k] = in ? (z * TY + y) * TX + x : -1;
+                        sum[k] = mk<T>(T(0), T(0));
+                    }
+                }
+                T w[3][NP];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
+                const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
 #pragma unroll
                 for (int k = 0; k < KPL; ++k) {
-                    const int x = s[0] + jx[k] - a0[0], y = s[1] + jy[k] - a0[1], z = s[2] + jz[k] - a0[2];
-                    const bool in = jz[k] < NP && x >= 0 && x < TX && y >= 0 && y < TY && z >= 0 && z < TZ;
-                    loc[k] = in ? (z * TY + y) * TX + x : -1;
-                    sum[k] = mk<T>(T(0), T(0));
-                }
-            }
-            T w[3][NP];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-                lagrange_w<T, P>(tt, w[d]);
-            }
-            const cplx<T> qv = qs[m];
-#pragma unroll
-            for (int k = 0; k < KPL; ++k) {
-                if (jz[k] < NP) {
-                    const T ww = w[0][jx[k]] * w[1][jy[k]] * w[2][jz[k]];
-                    sum[k].x += ww * qv.x;
-                    sum[k].y += ww * qv.y;
+                    if (jz[k] < NP) {
+                        const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
+                        sum[k].x += ww * qx;
+                        sum[k].y += ww * qy;
+                    }
                 }
             }
         }
+        flush();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
@@ -246,42 +259,55 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
     uint32_t cur = 0xffffffffu;
     int loc[KPL];
     cplx<T> sum[KPL];
-    for (long long m = w0; m <= w1 && w0 < w1; ++m) {
-        const uint32_t sm = m < w1 ? a.fst[m] : 0xfffffffeu;
-        if (sm != cur) {
-            if (cur != 0xffffffffu) {
-#pragma unroll
-                for (int k = 0; k < KPL; ++k)
-                    if (loc[k] >= 0) {
-                        atomicAdd(acc + 2 * loc[k], sum[k].x);
-                        atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
-                    }
-            }
-            if (m == w1) break;
-            cur = sm;
-            int s[3];
-            unpack3(sm, s[0], s[1], s[2]);
-#pragma unroll
-            for (int k = 0; k < KPL; ++k) {
-                loc[k] = jz[k] < NP ? ((s[2] + jz[k]) * a.nf[1] + (s[1] + jy[k])) * a.nf[0] + s[0] + jx[k] : -1;
-                sum[k] = mk<T>(T(0), T(0));
-            }
-        }
-        T w[3][NP];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
-            lagrange_w<T, PF>(tt, w[d]);
-        }
-        const cplx<T> qv = qs[m];
+    auto flush = [&]() {
+        if (cur == 0xffffffffu) return;
 #pragma unroll
         for (int k = 0; k < KPL; ++k)
-            if (jz[k] < NP) {
-                const T ww = w[0][jx[k]] * w[1][jy[k]] * w[2][jz[k]];
-                sum[k].x += ww * qv.x;
-                sum[k].y += ww * qv.y;
+            if (loc[k] >= 0) {
+                atomicAdd(acc + 2 * loc[k], sum[k].x);
+                atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
             }
+    };
+    for (long long b0 = w0; b0 < w1; b0 += 32) {
+        const int cnt = (int)min(32LL, w1 - b0);
+        const long long ml = b0 + lane;
+        uint32_t sl = 0;
+        T tl[3] = {T(0), T(0), T(0)};
+        cplx<T> ql = mk<T>(T(0), T(0));
+        if (lane < cnt) {
+            sl = a.fst[ml];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                tl[d] = sizeof(T) == 8 ? (T)a.ftd[6 * ml + a.toff + d] : (T)a.ft[6 * ml + a.toff + d];
+            ql = qs[ml];
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const uint32_t sm = __shfl_sync(0xffffffffu, sl, j);
+            if (sm != cur) {
+                flush();
+                cur = sm;
+                int s[3];
+                unpack3(sm, s[0], s[1], s[2]);
+#pragma unroll
+                for (int k = 0; k < KPL; ++k) {
+                    loc[k] = jz[k] < NP ? ((s[2] + jz[k]) * a.nf[1] + (s[1] + jy[k])) * a.nf[0] + s[0] + jx[k] : -1;
+                    sum[k] = mk<T>(T(0), T(0));
+                }
+            }
+            T w[3][NP];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) lagrange_w<T, PF>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
+            const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+#pragma unroll
+            for (int k = 0; k < KPL; ++k)
+                if (jz[k] < NP) {
+                    const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
+                    sum[k].x += ww * qx;
+                    sum[k].y += ww * qy;
+                }
+        }
     }
+    flush();
     __syncthreads();
     cplx<T>* out = part + (long long)blockIdx.x * G;
     for (int i = threadIdx.x; i < G; i += blockDim.x) out[i] = mk<T>(acc[2 * i], acc[2 * i + 1]);
@@ -362,7 +388,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
 // One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
 // correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
 // written in the caller's order.
-template <typename T, int P>
+template <typename T, int P, int CM>
 __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
                                                      const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
                                                      void* out) {
@@ -373,15 +399,19 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>
     int s[3];
     unpack3(a.ns[m], s[0], s[1], s[2]);
     T w[3][P + 1];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-        lagrange_weights<T>(P, tt, w[d]);
+        lagrange_w<T, P>(tt, w[d]);
     }
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
     cplx<T> acc = mk<T>(T(0), T(0));
-    for (int idx = lane; idx < NP3; idx += 32) {
+#pragma unroll
+    for (int k = 0; k < (NP3 + 31) / 32; ++k) {
+        const int idx = lane + 32 * k;
+        if (idx >= NP3) break;
         const int jx = idx % NP, jy = (idx / NP) % NP, jz = idx / (NP * NP);
-        const T ww = w[0][jx] * w[1][jy] * w[2][jz];
+        const T ww = pick<NP>(w[0], jx) * pick<NP>(w[1], jy) * pick<NP>(w[2], jz);
         const cplx<T> v = U[((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + (s[0] + jx)];
         acc.x += ww * v.x;
         acc.y += ww * v.y;
@@ -391,83 +421,126 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>
         int f[3];
         unpack3(a.fst[m], f[0], f[1], f[2]);
         T wf[3][PIM_MAX_P + 1];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
-            lagrange_weights<T>(a.pf, tt, wf[d]);
+            lagrange_weights_rt<T>(a.pf, tt, wf[d]);
         }
         const int np = a.pf + 1, np3 = np * np * np;
         for (int idx = lane; idx < np3; idx += 32) {
             const int jx = idx % np, jy = (idx / np) % np, jz = idx / (np * np);
-            const T ww = wf[0][jx] * wf[1][jy] * wf[2][jz];
+            const T ww = pick<PIM_MAX_P + 1>(wf[0], jx) * pick<PIM_MAX_P + 1>(wf[1], jy) * pick<PIM_MAX_P + 1>(wf[2], jz);
             const cplx<T> v = uf[((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + (f[0] + jx)];
             acc.x += ww * v.x;
             acc.y += ww * v.y;
         }
     }
     // near-pair correction: exp(-j k0.(i o L)) d q_n (forward) or
-    // exp(-j k0.(i o L)) conj(d) v_n (adjoint)
+    // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  Each lane takes UNR entries
+    // per trip, issuing all column and value loads (streaming, read once)
+    // before the dependent source loads.
     const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
     const double cs = a.adj ? -1.0 : 1.0;
     double2 accd = make_double2(0.0, 0.0);
-    if (a.cmode == PIM_CORR_FP64) {
-        for (long long q = r0 + lane; q < r1; q += 32) {
-            const uint32_t c = a.col[q];
-            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
-            double2 d = a.val[q];
-            d.y *= cs;
-            const cplx<T> x = qs[n];
-            double2 t = make_double2(d.x * (double)x.x - d.y * (double)x.y, d.x * (double)x.y + d.y * (double)x.x);
-            if (ii != a.self_img) t = cmul(a.phase[ii], t);
-            accd = cadd(accd, t);
+    constexpr int UNR = 4;
+    if (CM == PIM_CORR_FP64) {
+        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
+            uint32_t c[UNR];
+            double2 d[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const long long q = q0 + 32 * u;
+                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
+                d[u] = q < r1 ? __ldcs(a.val + q) : make_double2(0.0, 0.0);
+            }
+            cplx<T> x[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) x[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if (c[u] == 0xffffffffu) continue;
+                const int ii = (int)(c[u] >> PIM_COL_BITS);
+                const double dy = cs * d[u].y;
+                double2 t = make_double2(d[u].x * (double)x[u].x - dy * (double)x[u].y,
+                                         d[u].x * (double)x[u].y + dy * (double)x[u].x);
+                if (ii != a.self_img) t = cmul(a.phase[ii], t);
+                accd = cadd(accd, t);
+            }
         }
-    } else if (a.cmode == PIM_CORR_DOUBLE_FLOAT) {
+    } else if (CM == PIM_CORR_DOUBLE_FLOAT) {
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
         const float fs = (float)cs;
-        for (long long q = r0 + lane; q < r1; q += 32) {
-            const uint32_t c = a.col[q];
-            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
-            const float4 d = a.valdf[q];  // re_hi, re_lo, im_hi, im_lo
-            const cplx<T> xv = qs[n];
-            const float xr = (float)xv.x, xi = (float)xv.y;
-            const float dih = fs * d.z, dil = fs * d.w;
-            if (ii == a.self_img) {
-                // re += dr*xr - di*xi ; im += dr*xi + di*xr, products split exactly
-                const float p1 = d.x * xr, e1 = fmaf(d.x, xr, -p1);
-                const float p2 = dih * xi, e2 = fmaf(dih, xi, -p2);
-                const float p3 = d.x * xi, e3 = fmaf(d.x, xi, -p3);
-                const float p4 = dih * xr, e4 = fmaf(dih, xr, -p4);
-                two_sum_acc(rh, rl, p1);
-                two_sum_acc(rh, rl, -p2);
-                two_sum_acc(ih, il, p3);
-                two_sum_acc(ih, il, p4);
-                rl += (e1 - e2) + (d.y * xr - dil * xi);
-                il += (e3 + e4) + (d.y * xi + dil * xr);
-            } else {
-                const double dr = (double)d.x + (double)d.y, di = (double)dih + (double)dil;
-                double2 t = make_double2(dr * xr - di * xi, dr * xi + di * xr);
-                accd = cadd(accd, cmul(a.phase[ii], t));
+        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
+            uint32_t c[UNR];
+            float4 d[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const long long q = q0 + 32 * u;
+                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
+                d[u] = q < r1 ? __ldcs(a.valdf + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            cplx<T> xv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xv[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if (c[u] == 0xffffffffu) continue;
+                const int ii = (int)(c[u] >> PIM_COL_BITS);
+                const float xr = (float)xv[u].x, xi = (float)xv[u].y;
+                const float dih = fs * d[u].z, dil = fs * d[u].w;
+                if (ii == a.self_img) {
+                    // re += dr*xr - di*xi ; im += dr*xi + di*xr with exact product splits
+                    const float p1 = d[u].x * xr, e1 = fmaf(d[u].x, xr, -p1);
+                    const float p2 = dih * xi, e2 = fmaf(dih, xi, -p2);
+                    const float p3 = d[u].x * xi, e3 = fmaf(d[u].x, xi, -p3);
+                    const float p4 = dih * xr, e4 = fmaf(dih, xr, -p4);
+                    two_sum_acc(rh, rl, p1);
+                    two_sum_acc(rh, rl, -p2);
+                    two_sum_acc(ih, il, p3);
+                    two_sum_acc(ih, il, p4);
+                    rl += (e1 - e2) + (d[u].y * xr - dil * xi);
+                    il += (e3 + e4) + (d[u].y * xi + dil * xr);
+                } else {
+                    const double dr = (double)d[u].x + (double)d[u].y, di = (double)dih + (double)dil;
+                    double2 t = make_double2(dr * xr - di * xi, dr * xi + di * xr);
+                    accd = cadd(accd, cmul(a.phase[ii], t));
+                }
             }
         }
         accd.x += (double)rh + (double)rl;
         accd.y += (double)ih + (double)il;
     } else {
-        cplx<T> af = mk<T>(T(0), T(0));
-        for (long long q = r0 + lane; q < r1; q += 32) {
-            const uint32_t c = a.col[q];
-            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
-            float2 d = a.valf[q];
-            d.y *= (float)cs;
-            const cplx<T> x = qs[n];
-            float2 t = make_float2(d.x * (float)x.x - d.y * (float)x.y, d.x * (float)x.y + d.y * (float)x.x);
-            if (ii != a.self_img) {
-                const double2 ph = a.phase[ii];
-                t = make_float2((float)ph.x * t.x - (float)ph.y * t.y, (float)ph.x * t.y + (float)ph.y * t.x);
+        float ar = 0.f, ai = 0.f;
+        const float fs = (float)cs;
+        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
+            uint32_t c[UNR];
+            float2 d[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const long long q = q0 + 32 * u;
+                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
+                d[u] = q < r1 ? __ldcs(a.valf + q) : make_float2(0.f, 0.f);
             }
-            af.x += (T)t.x;
-            af.y += (T)t.y;
+            cplx<T> xv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xv[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if (c[u] == 0xffffffffu) continue;
+                const int ii = (int)(c[u] >> PIM_COL_BITS);
+                const float dy = fs * d[u].y;
+                float2 t = make_float2(d[u].x * (float)xv[u].x - dy * (float)xv[u].y,
+                                       d[u].x * (float)xv[u].y + dy * (float)xv[u].x);
+                if (ii != a.self_img) {
+                    const double2 ph = a.phase[ii];
+                    t = make_float2((float)ph.x * t.x - (float)ph.y * t.y, (float)ph.x * t.y + (float)ph.y * t.x);
+                }
+                ar += t.x;
+                ai += t.y;
+            }
         }
-        acc.x += af.x;
-        acc.y += af.y;
+        acc.x += (T)ar;
+        acc.y += (T)ai;
     }
     // warp reduction
     for (int o = 16; o > 0; o >>= 1) {
@@ -629,8 +702,15 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
         prof_mark(P, PIM_STAGE_GATHER, 0, s);
-        if (N > 0)
-            gather_kernel<T, PP><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ga, gA, ufar, qs, dst);
+        if (N > 0) {
+            const unsigned nb = (unsigned)((threads + 255) / 256);
+            if (ga.cmode == PIM_CORR_DOUBLE_FLOAT)
+                gather_kernel<T, PP, PIM_CORR_DOUBLE_FLOAT><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
+            else if (ga.cmode == PIM_CORR_FP32)
+                gather_kernel<T, PP, PIM_CORR_FP32><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
+            else
+                gather_kernel<T, PP, PIM_CORR_FP64><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
+        }
         PIM_CK(cudaGetLastError());
         prof_mark(P, PIM_STAGE_GATHER, 1, s);
         P->launches += N > 0 ? 1 : 0;

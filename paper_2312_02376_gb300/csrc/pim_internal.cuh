@@ -71,6 +71,37 @@ __host__ __device__ __forceinline__ void lagrange_weights(int p, T t, T* w) {
     }
 }
 
+// Register-only selection w[j] for a runtime j < N (no local memory).
+template <int N, typename T>
+__host__ __device__ __forceinline__ T pick(const T* w, int j) {
+    T r = w[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) r = (j == i) ? w[i] : r;
+    return r;
+}
+
+// Lagrange weights for a runtime degree p <= PIM_MAX_P with fully unrolled,
+// predicated loops (the array stays in registers).
+template <typename T>
+__host__ __device__ __forceinline__ void lagrange_weights_rt(int p, T t, T* w) {
+    T pre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1];
+    pre[0] = T(1);
+#pragma unroll
+    for (int j = 1; j <= PIM_MAX_P; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) suf[j] = T(1);
+#pragma unroll
+    for (int j = PIM_MAX_P - 1; j >= 0; --j) suf[j] = (j + 1 <= p) ? suf[j + 1] * (t - T(j + 1)) : T(1);
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) {
+        T den = T(1);
+#pragma unroll
+        for (int l = 0; l <= PIM_MAX_P; ++l)
+            if (l != j && l <= p) den *= T(j - l);
+        w[j] = j <= p ? pre[j] * suf[j] / den : T(0);
+    }
+}
+
 // Stencil rule: even p: floor(u + 1/2) - p/2; odd p: floor(u) - (p-1)/2;
 // clamped to [0, n-1-p].  Decided in FP64.
 __host__ __device__ __forceinline__ int stencil_start(double u, int n, int p) {
