@@ -1,4 +1,5 @@
 // The apply u = A q and its adjoint (Sec. 3.2 steps 1-3, Sec. 3.3 steps 1-4).
+#include <algorithm>
 #include <cmath>
 
 #include "pim_internal.cuh"
@@ -78,15 +79,6 @@ __global__ void permute_kernel(const void* q, const int* perm, long long N, int 
 }
 
 // ------------------------------- near spread -------------------------------
-struct SpreadArgs {
-    int n[3], nb[3];
-    int tile[3];
-    int ntiles[3];
-    const int* box_ptr;
-    const uint32_t* ns;
-    const float* nt;
-    const double* ntd;
-};
 
 // Lagrange weights of compile-time degree P (prefix/suffix products times
 // the constant inverse denominators).
@@ -108,92 +100,51 @@ __device__ __forceinline__ void lagrange_w(T t, T* w) {
     }
 }
 
-// Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1).  One CTA owns a tile of grid
-// nodes and writes it once: no global atomics.  Every point of a box shares
-// the box's stencil, so a warp walks the points of a row of boxes in order
-// with each lane owning (P+1)^3 / 32 stencil nodes, accumulates in registers
-// while the stencil start is unchanged, and adds to the shared-memory tile
-// once per box (lane-distinct addresses).
+// Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1) in two atomic-free phases.
+// Every point of a box shares the box's stencil start s_b, so
+//   Q(a) = sum_{boxes b whose stencil covers a} M_b(a - s_b),
+//   M_b(j) = sum_{n in b} w_n(j) q_n         (the box's (p+1)^3 moments).
+// Phase 1: one warp per non-empty box, lanes own stencil offsets, the box's
+// points are loaded 32 at a time and walked by shuffles.
+struct MomentArgs {
+    long long nne;
+    const int* blist;
+    const int* box_ptr;
+    const float* nt;
+    const double* ntd;
+};
+
 template <typename T, int P>
-__global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>* __restrict__ qs, cplx<T>* Q) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* acc = reinterpret_cast<T*>(smem_raw);  // 2 * TX*TY*TZ
+__global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>* __restrict__ qs, cplx<T>* mom) {
     constexpr int NP = P + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
-    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
-    const int TX = a.tile[0], TY = a.tile[1], TZ = a.tile[2];
-    const int ntile = TX * TY * TZ;
-    int t = blockIdx.x;
-    const int tx = t % a.ntiles[0];
-    t /= a.ntiles[0];
-    const int ty = t % a.ntiles[1];
-    const int tz = t / a.ntiles[1];
-    const int a0[3] = {tx * TX, ty * TY, tz * TZ};
-    const int T3[3] = {TX, TY, TZ};
-    for (int i = threadIdx.x; i < 2 * ntile; i += blockDim.x) acc[i] = T(0);
-    __syncthreads();
-    // boxes whose (clamped) stencil [s, s+P] meets [a0, a0+T-1]
-    int blo[3], bhi[3];
-    for (int d = 0; d < 3; ++d) {
-        blo[d] = a0[d] <= P ? 0 : a0[d] - P + LO;
-        bhi[d] = a0[d] + T3[d] - 1 >= a.n[d] - 1 - P ? a.nb[d] - 1 : a0[d] + T3[d] - 1 + LO;
-        blo[d] = max(0, blo[d]);
-        bhi[d] = min(a.nb[d] - 1, bhi[d]);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     int jx[KPL], jy[KPL], jz[KPL];
 #pragma unroll
     for (int k = 0; k < KPL; ++k) {
         const int o = lane + 32 * k;
         jx[k] = o % NP;
         jy[k] = (o / NP) % NP;
-        jz[k] = o / (NP * NP);  // >= NP for o >= NP3: never inside
+        jz[k] = o / (NP * NP);
     }
-    const int nry = max(0, bhi[1] - blo[1] + 1), nrz = max(0, bhi[2] - blo[2] + 1);
-    const int nrows = bhi[0] >= blo[0] ? nry * nrz : 0;
-    for (int row = wid; row < nrows; row += nw) {
-        const int by = blo[1] + row % nry, bz = blo[2] + row / nry;
-        const long long rb = ((long long)bz * a.nb[1] + by) * a.nb[0];
-        const int lo = a.box_ptr[rb + blo[0]], hi = a.box_ptr[rb + bhi[0] + 1];
-        uint32_t cur = 0xffffffffu;
-        int loc[KPL];   // shared-memory node index of each lane's node, -1 if outside the tile
+    for (long long slot = w0; slot < a.nne; slot += nw) {
+        const int b = a.blist[slot];
+        const int lo = a.box_ptr[b], hi = a.box_ptr[b + 1];
         cplx<T> sum[KPL];
-        auto flush = [&]() {
-            if (cur == 0xffffffffu) return;
 #pragma unroll
-            for (int k = 0; k < KPL; ++k)
-                if (loc[k] >= 0) {
-                    atomicAdd(acc + 2 * loc[k], sum[k].x);
-                    atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
-                }
-        };
+        for (int k = 0; k < KPL; ++k) sum[k] = mk<T>(T(0), T(0));
         for (int b0 = lo; b0 < hi; b0 += 32) {
-            // one coalesced load of 32 points, then walk them by shuffles
             const int cnt = min(32, hi - b0);
             const int ml = b0 + lane;
-            uint32_t sl = 0;
             T tl[3] = {T(0), T(0), T(0)};
             cplx<T> ql = mk<T>(T(0), T(0));
             if (lane < cnt) {
-                sl = a.ns[ml];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) tl[d] = sizeof(T) == 8 ? (T)a.ntd[3 * ml + d] : (T)a.nt[3 * ml + d];
                 ql = qs[ml];
             }
             for (int j = 0; j < cnt; ++j) {
-                const uint32_t sm = __shfl_sync(0xffffffffu, sl, j);
-                if (sm != cur) {
-                    flush();
-                    cur = sm;
-                    int s[3];
-                    unpack3(sm, s[0], s[1], s[2]);
-#pragma unroll
-                    for (int k = 0; k < KPL; ++k) {
-                        const int x = s[0] + jx[k] - a0[0], y = s[1] + jy[k] - a0[1], z = s[2] + jz[k] - a0[2];
-                        const bool in = jz[k] < NP && x >= 0 && x < TX && y >= 0 && y < TY && z >= 0 && z < TZ;
-                        loc[k] = in ? (z * TY + y) * TX + x : -1;
-                        sum[k] = mk<T>(T(0), T(0));
-                    }
-                }
                 T w[3][NP];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
@@ -208,15 +159,84 @@ __global__ void __launch_bounds__(256) spread_kernel(SpreadArgs a, const cplx<T>
                 }
             }
         }
-        flush();
+        cplx<T>* out = mom + slot * NP3;
+#pragma unroll
+        for (int k = 0; k < KPL; ++k)
+            if (jz[k] < NP) out[lane + 32 * k] = sum[k];
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < ntile; i += blockDim.x) {
-        const int lx = i % TX, ly = (i / TX) % TY, lz = i / (TX * TY);
-        const int x = a0[0] + lx, y = a0[1] + ly, z = a0[2] + lz;
-        if (x < a.n[0] && y < a.n[1] && z < a.n[2])
-            Q[((long long)z * a.n[1] + y) * a.n[0] + x] = mk<T>(acc[2 * i], acc[2 * i + 1]);
+}
+
+// Phase 2: one thread per grid node sums the moments of the boxes whose
+// (clamped) stencil covers it, in a fixed order (deterministic, no atomics).
+struct NodeArgs {
+    int n[3], nb[3];
+    const int* bslot;
+};
+
+template <int P>
+__device__ __forceinline__ void covering_boxes(int a, int n, int nb, int& lo, int& hi) {
+    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
+    lo = a <= P ? 0 : a - P + LO;
+    hi = a >= n - 1 - P ? nb - 1 : a + LO;
+    lo = max(lo, 0);
+    hi = min(hi, nb - 1);
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) node_gather_kernel(NodeArgs a, const cplx<T>* __restrict__ mom, cplx<T>* Q) {
+    constexpr int NP = P + 1, NP3 = NP * NP * NP;
+    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
+    const long long G = (long long)a.n[0] * a.n[1] * a.n[2];
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(g % a.n[0]), y = (int)((g / a.n[0]) % a.n[1]), z = (int)(g / ((long long)a.n[0] * a.n[1]));
+        int lo[3], hi[3];
+        covering_boxes<P>(x, a.n[0], a.nb[0], lo[0], hi[0]);
+        covering_boxes<P>(y, a.n[1], a.nb[1], lo[1], hi[1]);
+        covering_boxes<P>(z, a.n[2], a.nb[2], lo[2], hi[2]);
+        cplx<T> acc = mk<T>(T(0), T(0));
+        for (int bz = lo[2]; bz <= hi[2]; ++bz) {
+            const int jz = z - min(max(bz - LO, 0), a.n[2] - 1 - P);
+            if ((unsigned)jz > (unsigned)P) continue;
+            for (int by = lo[1]; by <= hi[1]; ++by) {
+                const int jy = y - min(max(by - LO, 0), a.n[1] - 1 - P);
+                if ((unsigned)jy > (unsigned)P) continue;
+                const int* rowslot = a.bslot + ((long long)bz * a.nb[1] + by) * a.nb[0];
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                    const int sl = rowslot[bx];
+                    if (sl < 0) continue;
+                    const int jx = x - min(max(bx - LO, 0), a.n[0] - 1 - P);
+                    if ((unsigned)jx > (unsigned)P) continue;
+                    const cplx<T> v = mom[(long long)sl * NP3 + (jz * NP + jy) * NP + jx];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+            }
+        }
+        Q[g] = acc;
     }
+}
+
+template <typename T, int P>
+pim_status spread_two_phase(pim_plan P_, const cplx<T>* qs, cplx<T>* Q, cudaStream_t s) {
+    const PointsData& d = P_->pts;
+    MomentArgs ma{};
+    ma.nne = d.nne;
+    ma.blist = d.blist;
+    ma.box_ptr = d.box_ptr;
+    ma.nt = d.nt;
+    ma.ntd = d.ntd;
+    if (d.nne > 0) {
+        const long long blocks = std::min<long long>((d.nne * 32 + 255) / 256, 152LL * 64);
+        moment_kernel<T, P><<<(unsigned)blocks, 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
+    }
+    NodeArgs na{};
+    for (int i = 0; i < 3; ++i) { na.n[i] = P_->n[i]; na.nb[i] = P_->nb[i]; }
+    na.bslot = d.bslot;
+    const long long G = (long long)P_->n[0] * P_->n[1] * P_->n[2];
+    node_gather_kernel<T, P><<<(unsigned)std::min<long long>((G + 255) / 256, 152LL * 32), 256, 0, s>>>(
+        na, (const cplx<T>*)d.mom, Q);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
 }
 
 // ------------------------------- far spread --------------------------------
@@ -643,30 +663,15 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             prof_mark(P, PIM_STAGE_FAR, 1, P->s_far);
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
-        // 3. near spread, 4. FFT convolution
-        SpreadArgs sa{};
-        for (int i = 0; i < 3; ++i) {
-            sa.n[i] = P->n[i];
-            sa.nb[i] = P->nb[i];
-            sa.tile[i] = P->tile[i];
-            sa.ntiles[i] = (P->n[i] + P->tile[i] - 1) / P->tile[i];
-        }
-        sa.box_ptr = d.box_ptr;
-        sa.ns = d.ns;
-        sa.nt = d.nt;
-        sa.ntd = d.ntd;
-        const int ntiles = sa.ntiles[0] * sa.ntiles[1] * sa.ntiles[2];
-        const size_t sm = 2 * sizeof(T) * P->tile[0] * P->tile[1] * P->tile[2];
-        PIM_CK(cudaFuncSetAttribute(spread_kernel<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        // 3. near spread (two phases), 4. FFT convolution
         prof_mark(P, PIM_STAGE_SPREAD, 0, s);
-        spread_kernel<T, PP><<<ntiles, 256, sm, s>>>(sa, qs, gA);
-        PIM_CK(cudaGetLastError());
+        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
         prof_mark(P, PIM_STAGE_SPREAD, 1, s);
         prof_mark(P, PIM_STAGE_FFT, 0, s);
         if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, s)) != PIM_OK)
             return st;
         prof_mark(P, PIM_STAGE_FFT, 1, s);
-        P->launches += 1 + 5;
+        P->launches += (d.nne > 0 ? 2 : 1) + 5;
         // 5. gather + correction + far gather
         if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
         GatherArgs ga{};
@@ -739,24 +744,7 @@ pim_status run_p(pim_plan P, const void* q, void* u, int nrhs, bool adj, cudaStr
 
 template <typename T, int PP>
 pim_status debug_spread_typed(pim_plan P, void* out, cudaStream_t s) {
-    const PointsData& d = P->pts;
-    SpreadArgs sa{};
-    for (int i = 0; i < 3; ++i) {
-        sa.n[i] = P->n[i];
-        sa.nb[i] = P->nb[i];
-        sa.tile[i] = P->tile[i];
-        sa.ntiles[i] = (P->n[i] + P->tile[i] - 1) / P->tile[i];
-    }
-    sa.box_ptr = d.box_ptr;
-    sa.ns = d.ns;
-    sa.nt = d.nt;
-    sa.ntd = d.ntd;
-    const int ntiles = sa.ntiles[0] * sa.ntiles[1] * sa.ntiles[2];
-    const size_t sm = 2 * sizeof(T) * P->tile[0] * P->tile[1] * P->tile[2];
-    PIM_CK(cudaFuncSetAttribute(spread_kernel<T, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    spread_kernel<T, PP><<<ntiles, 256, sm, s>>>(sa, (const cplx<T>*)P->qs, (cplx<T>*)out);
-    PIM_CK(cudaGetLastError());
-    return PIM_OK;
+    return spread_two_phase<T, PP>(P, (const cplx<T>*)P->qs, (cplx<T>*)out, s);
 }
 
 template <typename T>

@@ -152,6 +152,10 @@ struct PointsData {
     float* ft = nullptr;          // far local coordinates, source grid then observer grid (6N)
     double* ftd = nullptr;        // same in FP64 (FP64 plans)
     int* box_ptr = nullptr;       // nboxes + 1
+    int* bslot = nullptr;         // nboxes: compact index of a non-empty box, -1 if empty
+    int* blist = nullptr;         // nne: box id of each non-empty box (box order)
+    int64_t nne = 0;              // non-empty boxes
+    void* mom = nullptr;          // nne x (p+1)^3 box moments, complex<T> (apply scratch)
     int64_t* row_ptr = nullptr;   // N + 1
     uint32_t* col = nullptr;      // nnz
     double2* val = nullptr;       // nnz: G0 - G_grid (FP64)

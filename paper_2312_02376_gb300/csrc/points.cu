@@ -1,6 +1,7 @@
 // Point-dependent pre-processing (Sec. 3.2 and 3.3): binning into the grid's
 // boxes by counting sort, per-point stencil data, and the near-pair
 // correction list of Sec. 3.3 step 4 with its FP64 values.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -120,6 +121,24 @@ __global__ void scatter_kernel(const int* key, long long N, const int* box_ptr, 
         const int k = key[i];
         const int pos = box_ptr[k] + atomicAdd(&cursor[k], 1);
         slot[pos] = (int)i;
+    }
+}
+
+__global__ void nonempty_flags_kernel(const int* box_ptr, long long nboxes, int* flag) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nboxes;
+         b += (long long)gridDim.x * blockDim.x)
+        flag[b] = box_ptr[b + 1] > box_ptr[b] ? 1 : 0;
+}
+
+__global__ void box_slots_kernel(const int* flag, const int* pos, long long nboxes, int* bslot, int* blist) {
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nboxes;
+         b += (long long)gridDim.x * blockDim.x) {
+        if (flag[b]) {
+            bslot[b] = pos[b];
+            blist[pos[b]] = (int)b;
+        } else {
+            bslot[b] = -1;
+        }
     }
 }
 
@@ -383,6 +402,13 @@ void points_free(pim_plan P) {
     pim_free(P, d.ftd, 6 * N * sizeof(double));
     const size_t nboxes = (size_t)P->nb[0] * P->nb[1] * P->nb[2];
     pim_free(P, d.box_ptr, (nboxes + 1) * sizeof(int));
+    pim_free(P, d.bslot, nboxes * sizeof(int));
+    pim_free(P, d.blist, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
+    {
+        const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
+        const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+        pim_free(P, d.mom, (size_t)std::max<int64_t>(1, d.nne) * np3 * ge);
+    }
     pim_free(P, d.row_ptr, (N + 1) * sizeof(int64_t));
     pim_free(P, d.col, d.nnz * sizeof(uint32_t));
     pim_free(P, d.val, d.nnz * sizeof(double2));
@@ -427,6 +453,25 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         sort_boxes_kernel<<<(unsigned)((nboxes + 255) / 256), 256, 0, s>>>(d.box_ptr, nboxes, d.perm);
     }
     PIM_CK(cudaGetLastError());
+    // compact slots of the non-empty boxes (for the box-moment spread)
+    {
+        int* pos = nullptr;
+        if ((st = pim_alloc(P, (void**)&pos, (nboxes + 1) * sizeof(int))) != PIM_OK) return st;
+        nonempty_flags_kernel<<<1024, 256, 0, s>>>(d.box_ptr, nboxes, cursor);
+        if ((st = scan<int>(P, cursor, pos, nboxes, s)) != PIM_OK) return st;
+        int nne = 0;
+        PIM_CK(cudaMemcpy(&nne, pos + nboxes, sizeof(int), cudaMemcpyDeviceToHost));
+        d.nne = nne;
+        if ((st = pim_alloc(P, (void**)&d.bslot, nboxes * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.blist, (size_t)std::max(1, nne) * sizeof(int))) != PIM_OK) return st;
+        box_slots_kernel<<<1024, 256, 0, s>>>(cursor, pos, nboxes, d.bslot, d.blist);
+        PIM_CK(cudaGetLastError());
+        const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
+        const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+        if ((st = pim_alloc(P, &d.mom, (size_t)std::max(1, nne) * np3 * ge)) != PIM_OK) return st;
+        PIM_CK(cudaStreamSynchronize(s));
+        pim_free(P, pos, (nboxes + 1) * sizeof(int));
+    }
     // per-point data in sorted order
     if ((st = pim_alloc(P, (void**)&d.pos, 3 * N * sizeof(double))) != PIM_OK) return st;
     if ((st = pim_alloc(P, (void**)&d.ns, N * sizeof(uint32_t))) != PIM_OK) return st;
