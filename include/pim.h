@@ -93,6 +93,8 @@ typedef struct {
     double neutral_tol;  /* tau of the neutrality check; default 1e-6                  */
     double series_tol;   /* relative truncation of the far series; default 1e-16      */
     size_t mem_cap;      /* bytes; 0 = no cap.  Exceeding it -> PIM_ERR_OOM            */
+    int autotune;        /* 1: pim_set_points times the gather kernel's launch shapes
+                            and keeps the fastest; 0: default shape                    */
 } pim_options;
 
 typedef struct {
@@ -105,6 +107,7 @@ typedef struct {
     double plan_ms;      /* wall time of pim_plan_create                               */
     double points_ms;    /* wall time of the last pim_set_points                       */
     int64_t launches;    /* kernels launched by this plan's applies so far             */
+    int gather_variant;  /* launch shape of the gather kernel chosen by the autotuner  */
 } pim_info;
 
 /* Stages timed by the profiling ring (pim_set_profiling). */

@@ -148,12 +148,13 @@ def potential(points, q, tgt, L, pdims, k, k0, E, tol=1e-15, chunk=2048):
         kz = csqrt_neg_imag(k * k - KX ** 2 - KY ** 2)
         jkz = 1j * kz
         for t, m in enumerate(tgt):
-            d = points[m] - points
-            z = d[:, 2][:, None]
-            tph = np.exp(-1j * (np.outer(d[:, 0], KX) + np.outer(d[:, 1], KY)))
-            br = exp_erfc(-1j * kz[None, :] * z, jkz[None, :] / (2 * E) - z * E) \
-                + exp_erfc(1j * kz[None, :] * z, jkz[None, :] / (2 * E) + z * E)
-            u[t] += np.sum(q[:, None] * tph * br / (4j * kz[None, :] * A))
+            for s0 in range(0, len(points), chunk):
+                d = points[m] - points[s0:s0 + chunk]
+                z = d[:, 2][:, None]
+                tph = np.exp(-1j * (np.outer(d[:, 0], KX) + np.outer(d[:, 1], KY)))
+                br = exp_erfc(-1j * kz[None, :] * z, jkz[None, :] / (2 * E) - z * E) \
+                    + exp_erfc(1j * kz[None, :] * z, jkz[None, :] / (2 * E) + z * E)
+                u[t] += np.sum(q[s0:s0 + chunk, None] * tph * br / (4j * kz[None, :] * A))
     else:
         raise ValueError("Ewald ground truth implemented for 2D and 3D lattices")
     return u

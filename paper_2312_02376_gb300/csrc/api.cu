@@ -78,6 +78,7 @@ void pim_options_default(pim_options* o) {
     o->neutral_tol = 1e-6;
     o->series_tol = 1e-16;
     o->mem_cap = 0;
+    o->autotune = 1;
 }
 
 const char* pim_status_string(pim_status s) {
@@ -170,6 +171,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->layers = near_layers;
     P->prec = prec;
     P->mem_cap = o.mem_cap;
+    P->autotune = o.autotune ? 1 : 0;
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
@@ -326,6 +328,9 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     }
     if ((st = pim_alloc(P, &P->qs, (size_t)N * ge)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &P->us, (size_t)N * ge)) != PIM_OK) return st;
+    P->gather_variant = 0;
+    if (P->autotune && N > 0 && (st = apply_autotune(P, 0)) != PIM_OK) return st;
+    PIM_CK(cudaDeviceSynchronize());
     P->points_ms = now_ms() - t0;
     return PIM_OK;
 }
@@ -408,6 +413,7 @@ pim_status pim_plan_info(pim_plan P, pim_info* info) {
     info->plan_ms = P->plan_ms;
     info->points_ms = P->points_ms;
     info->launches = P->launches;
+    info->gather_variant = P->gather_variant;
     return PIM_OK;
 }
 

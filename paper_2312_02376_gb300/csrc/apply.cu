@@ -408,8 +408,8 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
 // One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
 // correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
 // written in the caller's order.
-template <typename T, int P, int CM>
-__global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
+template <typename T, int P, int CM, int UNR, int MINB>
+__global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
                                                      const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
                                                      void* out) {
     const int lane = threadIdx.x & 31;
@@ -462,7 +462,6 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a, const cplx<T>
     const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
     const double cs = a.adj ? -1.0 : 1.0;
     double2 accd = make_double2(0.0, 0.0);
-    constexpr int UNR = 4;
     if (CM == PIM_CORR_FP64) {
         for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
             uint32_t c[UNR];
@@ -594,6 +593,32 @@ __global__ void unpermute_kernel(const cplx<T>* us, const int* perm, long long N
 }
 
 // ------------------------------- driver ------------------------------------
+// Launch-shape variants of the gather kernel, chosen per plan by the
+// autotuner: (unroll depth of the correction loop, minimum resident CTAs).
+constexpr int GATHER_VARIANTS = 4;
+
+template <typename T, int PP, int CM>
+pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
+                            const cplx<T>* uf, const cplx<T>* qs, void* dst) {
+    switch (v) {
+        case 0: gather_kernel<T, PP, CM, 4, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 1: gather_kernel<T, PP, CM, 8, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 2: gather_kernel<T, PP, CM, 4, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        default: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+    }
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <typename T, int PP>
+pim_status launch_gather(int cm, int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
+                         const cplx<T>* uf, const cplx<T>* qs, void* dst) {
+    if (sizeof(T) == 8) return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+    if (cm == PIM_CORR_DOUBLE_FLOAT) return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
+    if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);
+    return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+}
+
 template <typename T>
 pim_status mean_of(pim_plan P, const void* q, bool sorted_complex, long long N, int nrhs, int r, bool check,
                    cudaStream_t s) {
@@ -709,12 +734,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         prof_mark(P, PIM_STAGE_GATHER, 0, s);
         if (N > 0) {
             const unsigned nb = (unsigned)((threads + 255) / 256);
-            if (ga.cmode == PIM_CORR_DOUBLE_FLOAT)
-                gather_kernel<T, PP, PIM_CORR_DOUBLE_FLOAT><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
-            else if (ga.cmode == PIM_CORR_FP32)
-                gather_kernel<T, PP, PIM_CORR_FP32><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
-            else
-                gather_kernel<T, PP, PIM_CORR_FP64><<<nb, 256, 0, s>>>(ga, gA, ufar, qs, dst);
+            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, s, ga, gA, ufar, qs, dst)) != PIM_OK)
+                return st;
         }
         PIM_CK(cudaGetLastError());
         prof_mark(P, PIM_STAGE_GATHER, 1, s);
@@ -762,6 +783,51 @@ pim_status debug_spread_p(pim_plan P, void* out, cudaStream_t s) {
 pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {
     if (P->prec == PIM_FP64) return debug_spread_p<double>(P, out, s);
     return debug_spread_p<float>(P, out, s);
+}
+
+// Times every gather variant on a forward apply of zero sources and keeps
+// the fastest (the other stages do not depend on the variant).
+pim_status apply_autotune(pim_plan P, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    if (d.N == 0) return PIM_OK;
+    const size_t el = P->prec == PIM_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = (size_t)d.N * el * (P->real_data ? 1 : 2);
+    void *q = nullptr, *u = nullptr;
+    pim_status st;
+    if ((st = pim_alloc(P, &q, bytes)) != PIM_OK) return st;
+    if ((st = pim_alloc(P, &u, bytes)) != PIM_OK) return st;
+    PIM_CK(cudaMemsetAsync(q, 0, bytes, s));
+    cudaEvent_t e0, e1;
+    PIM_CK(cudaEventCreate(&e0));
+    PIM_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestv = 0;
+    const bool prof = P->prof_on;
+    P->prof_on = false;
+    const int64_t launches = P->launches;
+    for (int v = 0; v < GATHER_VARIANTS; ++v) {
+        P->gather_variant = v;
+        if ((st = apply_run(P, q, u, 1, false, s)) != PIM_OK) return st;  // warm-up
+        PIM_CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2; ++r)
+            if ((st = apply_run(P, q, u, 1, false, s)) != PIM_OK) return st;
+        PIM_CK(cudaEventRecord(e1, s));
+        PIM_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PIM_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bestv = v;
+        }
+    }
+    P->prof_on = prof;
+    P->launches = launches;
+    P->gather_variant = bestv;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pim_free(P, q, bytes);
+    pim_free(P, u, bytes);
+    return PIM_OK;
 }
 
 pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s) {

@@ -215,6 +215,8 @@ struct pim_plan_s {
     cudaEvent_t* prof_ev = nullptr;  // [PROF_RING][PIM_NUM_STAGES][2]
     unsigned char prof_mask[512];    // stages recorded per ring slot
     int64_t launches = 0;
+    int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
+    int autotune = 1;
     // streams and events
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -250,4 +252,5 @@ void prof_mark(pim_plan P, int stage, int which, cudaStream_t s);
 constexpr int PIM_RED_BLOCKS = 608;
 pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s);
 pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
+pim_status apply_autotune(pim_plan P, cudaStream_t s);
 int pim_fft_len(int n);
