@@ -90,28 +90,41 @@ class Params:
 # --------------------------------------------------------------------------
 # stencils
 # --------------------------------------------------------------------------
-def near_stencils(P, pts):
-    """Near stencil starts s (N,3), weights w (N,3,p+1) and boxes B (N,3)."""
+def near_stencils(P, pts, frozen=None):
+    """Near stencil starts s (N,3), weights w (N,3,p+1), their x-derivatives
+    dw (N,3,p+1) and boxes B (N,3).  frozen = (s, B) keeps the stencil
+    starts and boxes of another position set (frozen topology)."""
     s = np.empty((len(pts), 3), np.int64)
     w = np.empty((len(pts), 3, P.p + 1))
+    dw = np.empty((len(pts), 3, P.p + 1))
     B = np.empty((len(pts), 3), np.int64)
     for d in range(3):
         s[:, d], t = lagrange.stencil_start(pts[:, d], P.h[d], P.n[d], P.p)
-        w[:, d, :] = lagrange.weights(t, P.p)
         B[:, d] = lagrange.stencil_box(pts[:, d], P.h[d], P.n[d], P.p)
-    return s, w, B
+        if frozen is not None:
+            s[:, d], B[:, d] = frozen[0][:, d], frozen[1][:, d]
+            t = pts[:, d] / P.h[d] - s[:, d]
+        w[:, d, :] = lagrange.weights(t, P.p)
+        dw[:, d, :] = lagrange.dweights(t, P.p) / P.h[d]
+    return s, w, B, dw
 
 
-def far_stencils(P, pts, observer):
+def far_stencils(P, pts, observer, frozen=None):
     """Far stencils on the source grid (observer=False) or on the observer
-    grid shifted by Delta/2 (observer=True), Eq. grid."""
+    grid shifted by Delta/2 (observer=True), Eq. grid: starts, weights and
+    x-derivatives of the weights.  frozen = fixed stencil starts."""
     s = np.empty((len(pts), 3), np.int64)
     w = np.empty((len(pts), 3, P.pf + 1))
+    dw = np.empty((len(pts), 3, P.pf + 1))
     for d in range(3):
         shift = 0.5 * P.delta_f[d] if observer else 0.0
         s[:, d], t = lagrange.stencil_start(pts[:, d], P.delta_f[d], P.nf[d], P.pf, shift)
+        if frozen is not None:
+            s[:, d] = frozen[:, d]
+            t = (pts[:, d] - shift) / P.delta_f[d] - s[:, d]
         w[:, d, :] = lagrange.weights(t, P.pf)
-    return s, w
+        dw[:, d, :] = lagrange.dweights(t, P.pf) / P.delta_f[d]
+    return s, w, dw
 
 
 def _stencil_nodes(s, w, p):
@@ -122,6 +135,25 @@ def _stencil_nodes(s, w, p):
     idx = s[:, None, :] + J[None, :, :]
     wt = w[:, 0, J[:, 0]] * w[:, 1, J[:, 1]] * w[:, 2, J[:, 2]]
     return idx, wt
+
+
+def _stencil_grad_nodes(s, w, dw, p, d):
+    """Node indices and the x_d-derivative of the tensor-product weights."""
+    j = np.arange(p + 1)
+    J = np.stack(np.meshgrid(j, j, j, indexing="ij"), -1).reshape(-1, 3)
+    idx = s[:, None, :] + J[None, :, :]
+    f = [dw if k == d else w for k in range(3)]
+    wt = f[0][:, 0, J[:, 0]] * f[1][:, 1, J[:, 1]] * f[2][:, 2, J[:, 2]]
+    return idx, wt
+
+
+def gather_grad(U, s, w, dw, p):
+    """(N, 3): sum_a grad_x omega_m(a) U(a)."""
+    out = np.zeros((len(s), 3), np.complex128)
+    for d in range(3):
+        idx, wt = _stencil_grad_nodes(s, w, dw, p, d)
+        out[:, d] = np.sum(wt * U[idx[..., 0], idx[..., 1], idx[..., 2]], axis=1)
+    return out
 
 
 def spread(shape, s, w, p, q):
@@ -302,6 +334,52 @@ def correction_values(P, pts, s, w, m, n, ii, batch=8192):
     return out
 
 
+def correction_grads(P, pts, s, w, dw, m, n, ii, batch=8192):
+    """D = d/dr_m of exp(-j k0.(i o L)) [G0(r_m - r_n - i o L) - G_grid,i(m, n)]
+    for each listed pair, (len, 3) complex: the gradient of the exact term
+    and of the grid term, whose x_d derivative replaces w_m,d by its
+    derivative in the tensor-product identity of correction_values."""
+    I = P.images()
+    out = np.zeros((len(m), 3), np.complex128)
+    if len(m) == 0:
+        return out
+    p = P.p
+    base_all = s[m] - s[n] - I[ii] * P.nL
+    R = int(np.max(np.abs(base_all))) + p
+    ax = np.arange(-R, R + 1)
+    gt = grid_kernel(P, np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1))
+    e = np.arange(-p, p + 1)
+    E = np.stack(np.meshgrid(e, e, e, indexing="ij"), -1).reshape(-1, 3)
+    for b0 in range(0, len(m), batch):
+        sl = slice(b0, b0 + batch)
+        mm, nn, iv = m[sl], n[sl], I[ii[sl]]
+        base = base_all[sl]
+        C = np.zeros((len(mm), 3, 2 * p + 1))
+        dC = np.zeros((len(mm), 3, 2 * p + 1))
+        for d in range(3):
+            for j in range(p + 1):
+                for l in range(p + 1):
+                    C[:, d, j - l + p] += w[mm, d, j] * w[nn, d, l]
+                    dC[:, d, j - l + p] += dw[mm, d, j] * w[nn, d, l]
+        idx = base[:, None, :] + E[None, :, :] + R
+        g = gt[idx[..., 0], idx[..., 1], idx[..., 2]]
+        r = pts[mm] - pts[nn] - iv * P.D
+        Rr = np.linalg.norm(r, axis=1)
+        selfpair = (mm == nn) & ~np.any(iv != 0, axis=1)
+        ph = np.exp(-1j * (iv * P.D) @ P.k0)
+        for d in range(3):
+            fac = [dC[:, 0] if d == 0 else C[:, 0], dC[:, 1] if d == 1 else C[:, 1], dC[:, 2] if d == 2 else C[:, 2]]
+            wgt = fac[0][:, E[:, 0] + p] * fac[1][:, E[:, 1] + p] * fac[2][:, E[:, 2] + p]
+            grid = np.sum(wgt * g, axis=1)
+            ex = np.zeros(len(mm), np.complex128)
+            ok = ~selfpair
+            # d/dx G0(R) = G0(R) (-jk - 1/R) x/R
+            G = greens.G0(Rr[ok], P.k)
+            ex[ok] = G * (-1j * P.k - 1.0 / Rr[ok]) * r[ok, d] / Rr[ok]
+            out[sl, d] = ph * (ex - grid)
+    return out
+
+
 # --------------------------------------------------------------------------
 # far zone
 # --------------------------------------------------------------------------
@@ -402,6 +480,7 @@ class Plan:
     pts: np.ndarray
     K: np.ndarray = field(default=None, repr=False)
     F: np.ndarray = field(default=None, repr=False)
+    frozen: object = field(default=None, repr=False)   # a Plan whose stencils, boxes and pairs are kept
 
     def __post_init__(self):
         P = self.P
@@ -414,10 +493,11 @@ class Plan:
             self.K = near_table(P)
         if self.F is None:
             self.F = far_table(P)
-        self.s, self.w, self.B = near_stencils(P, self.pts)
+        fz = self.frozen
+        self.s, self.w, self.B, self.dw = near_stencils(P, self.pts, None if fz is None else (fz.s, fz.B))
         if len(P.pdims):
-            self.ss, self.ws = far_stencils(P, self.pts, observer=False)
-            self.so, self.wo = far_stencils(P, self.pts, observer=True)
+            self.ss, self.ws, self.dws = far_stencils(P, self.pts, False, None if fz is None else fz.ss)
+            self.so, self.wo, self.dwo = far_stencils(P, self.pts, True, None if fz is None else fz.so)
         self._corr = None
 
     # --- neutrality (Eq. neutral) ----------------------------------------
@@ -432,7 +512,10 @@ class Plan:
 
     def corrections(self):
         if self._corr is None:
-            m, n, ii = correction_pairs(self.P, self.B)
+            if self.frozen is not None:
+                m, n, ii = self.frozen.corrections()[:3]
+            else:
+                m, n, ii = correction_pairs(self.P, self.B)
             c = correction_values(self.P, self.pts, self.s, self.w, m, n, ii)
             self._corr = (m, n, ii, c)
         return self._corr
@@ -493,3 +576,43 @@ class Plan:
         if P.npsp:
             w = w - np.mean(w)
         return w
+
+    def position_grad(self, q, g):
+        """(N, 3) real: d/dr_k Re sum_m conj(g_m) u_m with u = A(r) q, the
+        stencil starts, boxes and pair list held fixed (frozen topology).
+        Terms: observer side conj(g_k) grad_omega_k . U and source side
+        q_k conj(grad_omega_k . V) with V the adjoint grid potential of g,
+        for the near grid and the far grids, and for every pair of row k of
+        the correction list with D = d d_i(k, n)/d r_k:
+        conj(g_k) phase_i D q_n + q_k conj(g_n) phase_{-i} D
+        (the source-side term uses d_i(m, k) = d_{-i}(k, m))."""
+        P = self.P
+        q = self.regularise(q)
+        g = np.asarray(g, np.complex128)
+        Q = spread(tuple(P.n), self.s, self.w, P.p, q)
+        U = conv_direct_full(P, self.K, Q)
+        Gs = spread(tuple(P.n), self.s, self.w, P.p, g)
+        V = conv_direct_full(P, np.conj(self.K[::-1, ::-1, ::-1]), Gs)
+        obs = gather_grad(U, self.s, self.w, self.dw, P.p)
+        src = gather_grad(V, self.s, self.w, self.dw, P.p)
+        out = np.real(np.conj(g)[:, None] * obs) + np.real(q[:, None] * np.conj(src))
+        if len(P.pdims):
+            nf = tuple(P.nf)
+            A = far_matrix(P, self.F)
+            uf = (A @ spread(nf, self.ss, self.ws, P.pf, q).ravel()).reshape(nf)
+            vf = (A.conj().T @ spread(nf, self.so, self.wo, P.pf, g).ravel()).reshape(nf)
+            obs_f = gather_grad(uf, self.so, self.wo, self.dwo, P.pf)
+            src_f = gather_grad(vf, self.ss, self.ws, self.dws, P.pf)
+            out += np.real(np.conj(g)[:, None] * obs_f) + np.real(q[:, None] * np.conj(src_f))
+        m, n, ii = self.corrections()[:3]
+        D = correction_grads(P, self.pts, self.s, self.w, self.dw, m, n, ii)
+        I = P.images()
+        ph_minus = np.exp(1j * (I[ii] * P.D) @ P.k0)        # phase of image -i
+        ph = np.exp(-1j * (I[ii] * P.D) @ P.k0)
+        # D already carries phase_i; the source-side term needs phase_{-i}
+        t1 = np.real(np.conj(g[m])[:, None] * D * q[n][:, None])
+        t2 = np.real(q[m][:, None] * np.conj(g[n])[:, None] * D * (ph_minus / ph)[:, None])
+        for d in range(3):
+            out[:, d] += np.bincount(m, weights=t1[:, d] + t2[:, d], minlength=len(q))
+        return out
+

@@ -108,18 +108,24 @@ __device__ __forceinline__ void lagrange_w(T t, T* w) {
 // points are loaded 32 at a time and walked by shuffles.
 struct MomentArgs {
     long long nne;
-    const int* blist;
-    const int* box_ptr;
+    long long N;
+    const int* bstart;   // nne + 1 point offsets of the non-empty boxes
     const float* nt;
     const double* ntd;
+    int slots_per_warp;
 };
 
+// A warp walks a contiguous run of non-empty boxes: their points are
+// contiguous, so they are read 32 at a time (coalesced) and walked by
+// shuffles; a box's moment row is written when the walk leaves the box.
 template <typename T, int P>
 __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>* __restrict__ qs, cplx<T>* mom) {
     constexpr int NP = P + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
     const int lane = threadIdx.x & 31;
-    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long s0 = warp * a.slots_per_warp;
+    if (s0 >= a.nne) return;
+    const long long s1 = min(a.nne, s0 + a.slots_per_warp);
     int jx[KPL], jy[KPL], jz[KPL];
 #pragma unroll
     for (int k = 0; k < KPL; ++k) {
@@ -128,42 +134,53 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
         jy[k] = (o / NP) % NP;
         jz[k] = o / (NP * NP);
     }
-    for (long long slot = w0; slot < a.nne; slot += nw) {
-        const int b = a.blist[slot];
-        const int lo = a.box_ptr[b], hi = a.box_ptr[b + 1];
-        cplx<T> sum[KPL];
+    const int m0 = a.bstart[s0], m1 = a.bstart[s1];
+    long long slot = s0;
+    int next = a.bstart[slot + 1];
+    cplx<T> sum[KPL];
 #pragma unroll
-        for (int k = 0; k < KPL; ++k) sum[k] = mk<T>(T(0), T(0));
-        for (int b0 = lo; b0 < hi; b0 += 32) {
-            const int cnt = min(32, hi - b0);
-            const int ml = b0 + lane;
-            T tl[3] = {T(0), T(0), T(0)};
-            cplx<T> ql = mk<T>(T(0), T(0));
-            if (lane < cnt) {
+    for (int k = 0; k < KPL; ++k) sum[k] = mk<T>(T(0), T(0));
+    for (int b0 = m0; b0 < m1; b0 += 32) {
+        const int cnt = min(32, m1 - b0);
+        const int ml = b0 + lane;
+        T tl[3] = {T(0), T(0), T(0)};
+        cplx<T> ql = mk<T>(T(0), T(0));
+        if (lane < cnt) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) tl[d] = sizeof(T) == 8 ? (T)a.ntd[3 * ml + d] : (T)a.nt[3 * ml + d];
-                ql = qs[ml];
-            }
-            for (int j = 0; j < cnt; ++j) {
-                T w[3][NP];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
-                const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+            for (int d = 0; d < 3; ++d) tl[d] = sizeof(T) == 8 ? (T)a.ntd[3 * ml + d] : (T)a.nt[3 * ml + d];
+            ql = qs[ml];
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const int m = b0 + j;
+            while (m >= next) {  // the walk leaves box `slot`: write its row
+                cplx<T>* out = mom + slot * NP3;
 #pragma unroll
                 for (int k = 0; k < KPL; ++k) {
-                    if (jz[k] < NP) {
-                        const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
-                        sum[k].x += ww * qx;
-                        sum[k].y += ww * qy;
-                    }
+                    if (jz[k] < NP) out[lane + 32 * k] = sum[k];
+                    sum[k] = mk<T>(T(0), T(0));
+                }
+                ++slot;
+                next = a.bstart[slot + 1];
+            }
+            T w[3][NP];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
+            const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+#pragma unroll
+            for (int k = 0; k < KPL; ++k) {
+                if (jz[k] < NP) {
+                    const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
+                    sum[k].x += ww * qx;
+                    sum[k].y += ww * qy;
                 }
             }
         }
-        cplx<T>* out = mom + slot * NP3;
-#pragma unroll
-        for (int k = 0; k < KPL; ++k)
-            if (jz[k] < NP) out[lane + 32 * k] = sum[k];
     }
+    // the last box of the run
+    cplx<T>* out = mom + slot * NP3;
+#pragma unroll
+    for (int k = 0; k < KPL; ++k)
+        if (jz[k] < NP) out[lane + 32 * k] = sum[k];
 }
 
 // Phase 2: one thread per grid node sums the moments of the boxes whose
@@ -186,6 +203,7 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) node_gather_kernel(NodeArgs a, const cplx<T>* __restrict__ mom, cplx<T>* Q) {
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
     constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
+    constexpr int RMAX = P + LO + 1;  // the widest covering range (clamped edge stencils)
     const long long G = (long long)a.n[0] * a.n[1] * a.n[2];
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(g % a.n[0]), y = (int)((g / a.n[0]) % a.n[1]), z = (int)(g / ((long long)a.n[0] * a.n[1]));
@@ -194,19 +212,26 @@ __global__ void __launch_bounds__(256) node_gather_kernel(NodeArgs a, const cplx
         covering_boxes<P>(y, a.n[1], a.nb[1], lo[1], hi[1]);
         covering_boxes<P>(z, a.n[2], a.nb[2], lo[2], hi[2]);
         cplx<T> acc = mk<T>(T(0), T(0));
-        for (int bz = lo[2]; bz <= hi[2]; ++bz) {
+#pragma unroll
+        for (int iz = 0; iz < RMAX; ++iz) {
+            const int bz = lo[2] + iz;
             const int jz = z - min(max(bz - LO, 0), a.n[2] - 1 - P);
-            if ((unsigned)jz > (unsigned)P) continue;
-            for (int by = lo[1]; by <= hi[1]; ++by) {
+            if (bz > hi[2] || (unsigned)jz > (unsigned)P) continue;
+#pragma unroll
+            for (int iy = 0; iy < RMAX; ++iy) {
+                const int by = lo[1] + iy;
                 const int jy = y - min(max(by - LO, 0), a.n[1] - 1 - P);
-                if ((unsigned)jy > (unsigned)P) continue;
+                if (by > hi[1] || (unsigned)jy > (unsigned)P) continue;
                 const int* rowslot = a.bslot + ((long long)bz * a.nb[1] + by) * a.nb[0];
-                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
-                    const int sl = rowslot[bx];
-                    if (sl < 0) continue;
+                int sl[RMAX];
+#pragma unroll
+                for (int ix = 0; ix < RMAX; ++ix) sl[ix] = lo[0] + ix <= hi[0] ? __ldg(rowslot + lo[0] + ix) : -1;
+#pragma unroll
+                for (int ix = 0; ix < RMAX; ++ix) {
+                    const int bx = lo[0] + ix;
                     const int jx = x - min(max(bx - LO, 0), a.n[0] - 1 - P);
-                    if ((unsigned)jx > (unsigned)P) continue;
-                    const cplx<T> v = mom[(long long)sl * NP3 + (jz * NP + jy) * NP + jx];
+                    if (sl[ix] < 0 || (unsigned)jx > (unsigned)P) continue;
+                    const cplx<T> v = mom[(long long)sl[ix] * NP3 + (jz * NP + jy) * NP + jx];
                     acc.x += v.x;
                     acc.y += v.y;
                 }
@@ -221,13 +246,15 @@ pim_status spread_two_phase(pim_plan P_, const cplx<T>* qs, cplx<T>* Q, cudaStre
     const PointsData& d = P_->pts;
     MomentArgs ma{};
     ma.nne = d.nne;
-    ma.blist = d.blist;
-    ma.box_ptr = d.box_ptr;
+    ma.N = d.N;
+    ma.bstart = d.bstart;
     ma.nt = d.nt;
     ma.ntd = d.ntd;
+    // runs of boxes per warp: about 24 points each, at most 64 boxes
+    ma.slots_per_warp = (int)std::max<long long>(1, std::min<long long>(64, (24 * d.nne) / std::max<long long>(1, d.N)));
     if (d.nne > 0) {
-        const long long blocks = std::min<long long>((d.nne * 32 + 255) / 256, 152LL * 64);
-        moment_kernel<T, P><<<(unsigned)blocks, 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
+        const long long warps = (d.nne + ma.slots_per_warp - 1) / ma.slots_per_warp;
+        moment_kernel<T, P><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
     }
     NodeArgs na{};
     for (int i = 0; i < 3; ++i) { na.n[i] = P_->n[i]; na.nb[i] = P_->nb[i]; }
@@ -356,17 +383,26 @@ pim_status launch_far_spread(int pf, int grid, size_t sm, cudaStream_t s, const 
     return PIM_OK;
 }
 
-// qf[g] = sum over CTAs of the partials, in FP64, fixed order
+// qf[g] = sum over CTAs of the partials, in FP64, fixed order: one warp
+// per far node, lanes stride the partials, then a shuffle tree.
 template <typename T>
 __global__ void far_reduce_kernel(const cplx<T>* part, int nchunks, int G, double2* qf) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = w0; g < G; g += nw) {
         double2 s = make_double2(0.0, 0.0);
-        for (int c = 0; c < nchunks; ++c) {
+        for (int c = lane; c < nchunks; c += 32) {
             const cplx<T> v = part[(long long)c * G + g];
             s.x += (double)v.x;
             s.y += (double)v.y;
         }
-        qf[g] = s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) qf[g] = s;
     }
 }
 
@@ -595,16 +631,17 @@ __global__ void unpermute_kernel(const cplx<T>* us, const int* perm, long long N
 // ------------------------------- driver ------------------------------------
 // Launch-shape variants of the gather kernel, chosen per plan by the
 // autotuner: (unroll depth of the correction loop, minimum resident CTAs).
-constexpr int GATHER_VARIANTS = 4;
+constexpr int GATHER_VARIANTS = 5;
 
 template <typename T, int PP, int CM>
 pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
                             const cplx<T>* uf, const cplx<T>* qs, void* dst) {
     switch (v) {
-        case 0: gather_kernel<T, PP, CM, 4, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 1: gather_kernel<T, PP, CM, 8, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 2: gather_kernel<T, PP, CM, 4, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        default: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 0: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 1: gather_kernel<T, PP, CM, 4, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 2: gather_kernel<T, PP, CM, 2, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 3: gather_kernel<T, PP, CM, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        default: gather_kernel<T, PP, CM, 3, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
     }
     PIM_CK(cudaGetLastError());
     return PIM_OK;
@@ -676,8 +713,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             } else {
                 PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, P->s_far));
             }
-            far_reduce_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks, G,
-                                                                        P->fA);
+            far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks,
+                                                                             G, P->fA);
             PIM_CK(cudaGetLastError());
             if ((st = fft3_conv<double>(P, P->fg, P->fA, P->fB, P->fC, P->fspec, adj, P->s_far)) != PIM_OK) return st;
             if (sizeof(T) == 4) {

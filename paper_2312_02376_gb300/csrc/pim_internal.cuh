@@ -154,6 +154,7 @@ struct PointsData {
     int* box_ptr = nullptr;       // nboxes + 1
     int* bslot = nullptr;         // nboxes: compact index of a non-empty box, -1 if empty
     int* blist = nullptr;         // nne: box id of each non-empty box (box order)
+    int* bstart = nullptr;        // nne + 1: first sorted point of each non-empty box
     int64_t nne = 0;              // non-empty boxes
     void* mom = nullptr;          // nne x (p+1)^3 box moments, complex<T> (apply scratch)
     int64_t* row_ptr = nullptr;   // N + 1

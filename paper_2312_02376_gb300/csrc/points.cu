@@ -130,15 +130,18 @@ __global__ void nonempty_flags_kernel(const int* box_ptr, long long nboxes, int*
         flag[b] = box_ptr[b + 1] > box_ptr[b] ? 1 : 0;
 }
 
-__global__ void box_slots_kernel(const int* flag, const int* pos, long long nboxes, int* bslot, int* blist) {
+__global__ void box_slots_kernel(const int* flag, const int* pos, const int* box_ptr, long long nboxes, int* bslot,
+                                 int* blist, int* bstart) {
     for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nboxes;
          b += (long long)gridDim.x * blockDim.x) {
         if (flag[b]) {
             bslot[b] = pos[b];
             blist[pos[b]] = (int)b;
+            bstart[pos[b]] = box_ptr[b];
         } else {
             bslot[b] = -1;
         }
+        if (b == nboxes - 1) bstart[pos[nboxes]] = box_ptr[nboxes];
     }
 }
 
@@ -404,6 +407,7 @@ void points_free(pim_plan P) {
     pim_free(P, d.box_ptr, (nboxes + 1) * sizeof(int));
     pim_free(P, d.bslot, nboxes * sizeof(int));
     pim_free(P, d.blist, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
+    pim_free(P, d.bstart, (size_t)(d.nne + 1) * sizeof(int));
     {
         const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
         const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
@@ -464,7 +468,8 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         d.nne = nne;
         if ((st = pim_alloc(P, (void**)&d.bslot, nboxes * sizeof(int))) != PIM_OK) return st;
         if ((st = pim_alloc(P, (void**)&d.blist, (size_t)std::max(1, nne) * sizeof(int))) != PIM_OK) return st;
-        box_slots_kernel<<<1024, 256, 0, s>>>(cursor, pos, nboxes, d.bslot, d.blist);
+        if ((st = pim_alloc(P, (void**)&d.bstart, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
+        box_slots_kernel<<<1024, 256, 0, s>>>(cursor, pos, d.box_ptr, nboxes, d.bslot, d.blist, d.bstart);
         PIM_CK(cudaGetLastError());
         const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
         const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
