@@ -95,6 +95,9 @@ typedef struct {
     size_t mem_cap;      /* bytes; 0 = no cap.  Exceeding it -> PIM_ERR_OOM            */
     int autotune;        /* 1: pim_set_points times the gather kernel's launch shapes
                             and keeps the fastest; 0: default shape                    */
+    int with_gradient;   /* 1: pim_set_points also stores the position derivatives of
+                            the correction values (48 B per entry), which
+                            pim_position_grad needs                                    */
 } pim_options;
 
 typedef struct {
@@ -198,6 +201,35 @@ pim_status pim_apply(pim_plan plan, const void* q, void* u, int nrhs, void* stre
  * Neutral static plans remove the mean of w (the projector is self-adjoint).
  */
 pim_status pim_apply_adjoint(pim_plan plan, const void* v, void* w, int nrhs, void* stream);
+
+/*
+ * pim_position_grad -- the gradient of Re sum_{m,r} conj(g[m][r]) u[m][r]
+ * with respect to the point positions, u = A q (the same operator as
+ * pim_apply), with the discrete structure held fixed ("frozen topology":
+ * stencil starts, boxes and correction list as set by pim_set_points):
+ *   grad_xyz[k][d] = Re sum_{m,r} conj(g[m][r]) d u[m][r] / d x_{k,d}.
+ * With g = dL/du in PyTorch's convention this is dL/dx of a real loss L.
+ * It differentiates the Lagrange weights of every interpolation (near
+ * and far, observer and source side) and the exact and grid terms of every
+ * correction value.  Not part of the paper.
+ *   q, g      [N][nrhs], caller order, the plan's data type; device or host.
+ *   grad_xyz  N x 3 FP64, caller order, written; device or host.
+ * Requires a plan created with opt.with_gradient = 1 (PIM_ERR_STATE
+ * otherwise).  Neutral static plans remove the mean of q as pim_apply does.
+ */
+pim_status pim_position_grad(pim_plan plan, const void* q, const void* g, double* grad_xyz, int nrhs, void* stream);
+
+/*
+ * pim_update_positions -- moves the points of the last pim_set_points to new
+ * positions (N x 3 FP64, caller order, device or host) while keeping the
+ * discrete structure: the box order, every stencil start, the box of every
+ * point and the correction list stay as they were; local coordinates and
+ * correction values (and their derivatives, if stored) are recomputed.  For
+ * small moves between the steps of a simulation and for finite-difference
+ * checks of pim_position_grad.  Points must stay in the closed cell
+ * (PIM_ERR_OUT_OF_CELL).  Synchronises.
+ */
+pim_status pim_update_positions(pim_plan plan, const double* xyz);
 
 /* Device-side status of the calls issued so far: synchronises the plan's
  * streams, returns the first flag raised (PIM_OK if none) and clears it. */

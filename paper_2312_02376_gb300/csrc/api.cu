@@ -64,6 +64,19 @@ void pim_free(pim_plan P, void* ptr, size_t bytes) {
     P->bytes -= bytes;
 }
 
+static void free_grad_buffers(pim_plan P) {
+    const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const size_t Gf = P->has_far ? (size_t)P->nf[0] * P->nf[1] * P->nf[2] : 0;
+    pim_free(P, P->gD, G * ge);
+    pim_free(P, P->gsrt, (size_t)P->pts.N * ge);
+    pim_free(P, P->fD, Gf * sizeof(double2));
+    pim_free(P, P->fU, Gf * ge);
+    pim_free(P, P->fV, Gf * ge);
+    P->gD = P->gsrt = P->fU = P->fV = nullptr;
+    P->fD = nullptr;
+}
+
 extern "C" {
 
 const char* pim_last_error(void) { return g_last_error.c_str(); }
@@ -79,6 +92,7 @@ void pim_options_default(pim_options* o) {
     o->series_tol = 1e-16;
     o->mem_cap = 0;
     o->autotune = 1;
+    o->with_gradient = 0;
 }
 
 const char* pim_status_string(pim_status s) {
@@ -119,6 +133,7 @@ void pim_destroy(pim_plan P) {
         pim_free(P, P->fC, (long long)P->nf[2] * P->fg.L[1] * P->fg.L[0] * sizeof(double2));
         pim_free(P, P->fpart, (size_t)P->far_chunks * Gf * ge);
     }
+    free_grad_buffers(P);
     pim_free(P, P->tw32, 2048 * sizeof(float2));
     pim_free(P, P->tw64, 2048 * sizeof(double2));
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
@@ -172,6 +187,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->prec = prec;
     P->mem_cap = o.mem_cap;
     P->autotune = o.autotune ? 1 : 0;
+    P->with_gradient = o.with_gradient ? 1 : 0;
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
@@ -307,6 +323,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     cudaDeviceSynchronize();
     const size_t ge = grid_elem(P);
     if (P->pts.N > 0 || P->pts.box_ptr) {
+        free_grad_buffers(P);
         pim_free(P, P->qs, (size_t)P->pts.N * ge);
         pim_free(P, P->us, (size_t)P->pts.N * ge);
         P->qs = P->us = nullptr;
@@ -377,6 +394,82 @@ pim_status pim_apply(pim_plan P, const void* q, void* u, int nrhs, void* stream)
 
 pim_status pim_apply_adjoint(pim_plan P, const void* v, void* w, int nrhs, void* stream) {
     return apply_common(P, v, w, nrhs, stream, true);
+}
+
+pim_status pim_position_grad(pim_plan P, const void* q, const void* g, double* grad, int nrhs, void* stream) {
+    if (!P || !q || !g || !grad || nrhs < 1) {
+        pim_set_error("invalid argument");
+        return PIM_ERR_ARG;
+    }
+    if (!P->pts.box_ptr || !P->with_gradient || !P->pts.dval) {
+        pim_set_error("position gradient needs pim_set_points on a plan created with with_gradient = 1");
+        return PIM_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ge = grid_elem(P);
+    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const size_t Gf = P->has_far ? (size_t)P->nf[0] * P->nf[1] * P->nf[2] : 0;
+    pim_status st;
+    if (!P->gsrt) {
+        if ((st = pim_alloc(P, &P->gD, G * ge)) != PIM_OK) return st;
+        if ((st = pim_alloc(P, &P->gsrt, (size_t)P->pts.N * ge)) != PIM_OK) return st;
+        if (Gf) {
+            if ((st = pim_alloc(P, (void**)&P->fD, Gf * sizeof(double2))) != PIM_OK) return st;
+            if ((st = pim_alloc(P, &P->fU, Gf * ge)) != PIM_OK) return st;
+            if ((st = pim_alloc(P, &P->fV, Gf * ge)) != PIM_OK) return st;
+        }
+    }
+    const size_t bytes = (size_t)P->pts.N * nrhs * data_elem(P);
+    const size_t gbytes = (size_t)P->pts.N * 3 * sizeof(double);
+    const bool hq = !is_device_ptr(q), hg = !is_device_ptr(g), hd = !is_device_ptr(grad);
+    void *dq = (void*)q, *dg = (void*)g;
+    double* dgr = grad;
+    void *tq = nullptr, *tg = nullptr, *tgr = nullptr;
+    if (hq) {
+        if ((st = pim_alloc(P, &tq, bytes)) != PIM_OK) return st;
+        PIM_CK(cudaMemcpyAsync(tq, q, bytes, cudaMemcpyHostToDevice, s));
+        dq = tq;
+    }
+    if (hg) {
+        if ((st = pim_alloc(P, &tg, bytes)) != PIM_OK) return st;
+        PIM_CK(cudaMemcpyAsync(tg, g, bytes, cudaMemcpyHostToDevice, s));
+        dg = tg;
+    }
+    if (hd) {
+        if ((st = pim_alloc(P, &tgr, gbytes)) != PIM_OK) return st;
+        dgr = (double*)tgr;
+    }
+    st = grad_run(P, dq, dg, dgr, nrhs, s);
+    if (st == PIM_OK && hd) PIM_CK(cudaMemcpyAsync(grad, dgr, gbytes, cudaMemcpyDeviceToHost, s));
+    if (hq || hg || hd) PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, tq, bytes);
+    pim_free(P, tg, bytes);
+    pim_free(P, tgr, gbytes);
+    return st;
+}
+
+pim_status pim_update_positions(pim_plan P, const double* xyz) {
+    if (!P || (P->pts.N > 0 && !xyz)) {
+        pim_set_error("invalid argument");
+        return PIM_ERR_ARG;
+    }
+    if (!P->pts.box_ptr) {
+        pim_set_error("update before pim_set_points");
+        return PIM_ERR_STATE;
+    }
+    const int64_t N = P->pts.N;
+    PIM_CK(cudaDeviceSynchronize());
+    const double* dx = xyz;
+    double* tmp = nullptr;
+    pim_status st;
+    if (N > 0 && !is_device_ptr(xyz)) {
+        if ((st = pim_alloc(P, (void**)&tmp, 3 * N * sizeof(double))) != PIM_OK) return st;
+        PIM_CK(cudaMemcpy(tmp, xyz, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+        dx = tmp;
+    }
+    st = points_update(P, dx, 0);
+    pim_free(P, tmp, 3 * N * sizeof(double));
+    return st;
 }
 
 pim_status pim_last_device_status(pim_plan P) {

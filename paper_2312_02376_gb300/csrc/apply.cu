@@ -100,6 +100,49 @@ __device__ __forceinline__ void lagrange_w(T t, T* w) {
     }
 }
 
+// Derivatives of the Lagrange basis of degree P (product rule).
+template <typename T, int P>
+__device__ __forceinline__ void lagrange_dw(T t, T* dw) {
+#pragma unroll
+    for (int j = 0; j <= P; ++j) {
+        double den = 1.0;
+        for (int l = 0; l <= P; ++l)
+            if (l != j) den *= (double)(j - l);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+            if (k == j) continue;
+            T pr = T(1);
+#pragma unroll
+            for (int l = 0; l <= P; ++l)
+                if (l != j && l != k) pr *= (t - T(l));
+            s += pr;
+        }
+        dw[j] = s * T(1.0 / den);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void lagrange_dw_rt(int p, T t, T* dw) {
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) {
+        T den = T(1), s = T(0);
+#pragma unroll
+        for (int l = 0; l <= PIM_MAX_P; ++l)
+            if (l != j && l <= p) den *= T(j - l);
+#pragma unroll
+        for (int k = 0; k <= PIM_MAX_P; ++k) {
+            if (k == j || k > p) continue;
+            T pr = T(1);
+#pragma unroll
+            for (int l = 0; l <= PIM_MAX_P; ++l)
+                if (l != j && l != k && l <= p) pr *= (t - T(l));
+            s += pr;
+        }
+        dw[j] = j <= p ? s / den : T(0);
+    }
+}
+
 // Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1) in two atomic-free phases.
 // Every point of a box shares the box's stencil start s_b, so
 //   Q(a) = sum_{boxes b whose stencil covers a} M_b(a - s_b),
@@ -212,28 +255,29 @@ __global__ void __launch_bounds__(256) node_gather_kernel(NodeArgs a, const cplx
         covering_boxes<P>(y, a.n[1], a.nb[1], lo[1], hi[1]);
         covering_boxes<P>(z, a.n[2], a.nb[2], lo[2], hi[2]);
         cplx<T> acc = mk<T>(T(0), T(0));
-#pragma unroll
-        for (int iz = 0; iz < RMAX; ++iz) {
-            const int bz = lo[2] + iz;
+        // the covering range is at most RMAX boxes per axis except on small
+        // grids, where clamped stencils from both faces can cover a node:
+        // plain loops over z and y, unrolled chunks of RMAX along x
+        for (int bz = lo[2]; bz <= hi[2]; ++bz) {
             const int jz = z - min(max(bz - LO, 0), a.n[2] - 1 - P);
-            if (bz > hi[2] || (unsigned)jz > (unsigned)P) continue;
-#pragma unroll
-            for (int iy = 0; iy < RMAX; ++iy) {
-                const int by = lo[1] + iy;
+            if ((unsigned)jz > (unsigned)P) continue;
+            for (int by = lo[1]; by <= hi[1]; ++by) {
                 const int jy = y - min(max(by - LO, 0), a.n[1] - 1 - P);
-                if (by > hi[1] || (unsigned)jy > (unsigned)P) continue;
+                if ((unsigned)jy > (unsigned)P) continue;
                 const int* rowslot = a.bslot + ((long long)bz * a.nb[1] + by) * a.nb[0];
-                int sl[RMAX];
+                for (int bx0 = lo[0]; bx0 <= hi[0]; bx0 += RMAX) {
+                    int sl[RMAX];
 #pragma unroll
-                for (int ix = 0; ix < RMAX; ++ix) sl[ix] = lo[0] + ix <= hi[0] ? __ldg(rowslot + lo[0] + ix) : -1;
+                    for (int ix = 0; ix < RMAX; ++ix) sl[ix] = bx0 + ix <= hi[0] ? __ldg(rowslot + bx0 + ix) : -1;
 #pragma unroll
-                for (int ix = 0; ix < RMAX; ++ix) {
-                    const int bx = lo[0] + ix;
-                    const int jx = x - min(max(bx - LO, 0), a.n[0] - 1 - P);
-                    if (sl[ix] < 0 || (unsigned)jx > (unsigned)P) continue;
-                    const cplx<T> v = mom[(long long)sl[ix] * NP3 + (jz * NP + jy) * NP + jx];
-                    acc.x += v.x;
-                    acc.y += v.y;
+                    for (int ix = 0; ix < RMAX; ++ix) {
+                        const int bx = bx0 + ix;
+                        const int jx = x - min(max(bx - LO, 0), a.n[0] - 1 - P);
+                        if (sl[ix] < 0 || (unsigned)jx > (unsigned)P) continue;
+                        const cplx<T> v = mom[(long long)sl[ix] * NP3 + (jz * NP + jy) * NP + jx];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
                 }
             }
         }
@@ -616,6 +660,150 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
     }
 }
 
+// ------------------------------- position gradient -------------------------
+struct GradArgs {
+    int n[3], nf[3], pf;
+    double h[3], df[3];
+    long long N;
+    int has_far, self_img, first;
+    const int* perm;
+    const uint32_t* ns;
+    const float* nt;
+    const double* ntd;
+    const uint32_t* fs;
+    const uint32_t* fo;
+    const float* ft;
+    const double* ftd;
+    const int64_t* row_ptr;
+    const uint32_t* col;
+    const double2* dval;
+    const double2* phase;
+};
+
+// One warp per sorted point k:
+//   grad_k = Re[conj(g_k) (grad w_k . U + grad w^o_k . u_f)]
+//          + Re[q_k conj(grad w_k . V + grad w^s_k . v_f)]
+//          + sum over row k: Re[conj(g_k) ph_i D q_n] + Re[q_k conj(g_n) conj(ph_i) D]
+// with U, u_f the forward grid potentials of q, V, v_f the adjoint ones of g
+// and D = d d_i(k, n) / d r_k from the correction list (FP64).
+template <typename T, int P>
+__global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __restrict__ U,
+                                                   const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ uf,
+                                                   const cplx<T>* __restrict__ vf, const cplx<T>* __restrict__ qs,
+                                                   const cplx<T>* __restrict__ gs, double* grad) {
+    const int lane = threadIdx.x & 31;
+    const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (m >= a.N) return;
+    constexpr int NP = P + 1, NP3 = NP * NP * NP;
+    int s[3];
+    unpack3(a.ns[m], s[0], s[1], s[2]);
+    T w[3][NP], dw[3][NP];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+        lagrange_w<T, P>(tt, w[d]);
+        lagrange_dw<T, P>(tt, dw[d]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) dw[d][j] *= T(1.0 / a.h[d]);
+    }
+    // obs[d], src[d]: complex, accumulated in FP64 across the four sums
+    double2 obs[3], src[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) obs[d] = src[d] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < (NP3 + 31) / 32; ++k) {
+        const int idx = lane + 32 * k;
+        if (idx >= NP3) break;
+        const int jx = idx % NP, jy = (idx / NP) % NP, jz = idx / (NP * NP);
+        const T wx = pick<NP>(w[0], jx), wy = pick<NP>(w[1], jy), wz = pick<NP>(w[2], jz);
+        const T gx = pick<NP>(dw[0], jx) * wy * wz, gy = wx * pick<NP>(dw[1], jy) * wz, gz = wx * wy * pick<NP>(dw[2], jz);
+        const long long node = ((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + (s[0] + jx);
+        const cplx<T> u = U[node], v = V[node];
+        const T gw[3] = {gx, gy, gz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            obs[d].x += (double)(gw[d] * u.x);
+            obs[d].y += (double)(gw[d] * u.y);
+            src[d].x += (double)(gw[d] * v.x);
+            src[d].y += (double)(gw[d] * v.y);
+        }
+    }
+    if (a.has_far) {
+        // observer grid for U_far, source grid for V_far
+        for (int side = 0; side < 2; ++side) {
+            int f[3];
+            unpack3(side == 0 ? a.fo[m] : a.fs[m], f[0], f[1], f[2]);
+            const int toff = side == 0 ? 3 : 0;
+            T wf[3][PIM_MAX_P + 1], dwf[3][PIM_MAX_P + 1];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + toff + d] : (T)a.ft[6 * m + toff + d];
+                lagrange_weights_rt<T>(a.pf, tt, wf[d]);
+                lagrange_dw_rt<T>(a.pf, tt, dwf[d]);
+            }
+            const cplx<T>* grid = side == 0 ? uf : vf;
+            const int np = a.pf + 1, np3 = np * np * np;
+            for (int idx = lane; idx < np3; idx += 32) {
+                const int jx = idx % np, jy = (idx / np) % np, jz = idx / (np * np);
+                const T wx = pick<PIM_MAX_P + 1>(wf[0], jx), wy = pick<PIM_MAX_P + 1>(wf[1], jy),
+                        wz = pick<PIM_MAX_P + 1>(wf[2], jz);
+                const T gw[3] = {pick<PIM_MAX_P + 1>(dwf[0], jx) * wy * wz * T(1.0 / a.df[0]),
+                                 wx * pick<PIM_MAX_P + 1>(dwf[1], jy) * wz * T(1.0 / a.df[1]),
+                                 wx * wy * pick<PIM_MAX_P + 1>(dwf[2], jz) * T(1.0 / a.df[2])};
+                const cplx<T> v = grid[((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + (f[0] + jx)];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    double2& acc = side == 0 ? obs[d] : src[d];
+                    acc.x += (double)(gw[d] * v.x);
+                    acc.y += (double)(gw[d] * v.y);
+                }
+            }
+        }
+    }
+    // correction list
+    double2 c1[3], c2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c1[d] = c2[d] = make_double2(0.0, 0.0);
+    for (long long q = a.row_ptr[m] + lane; q < a.row_ptr[m + 1]; q += 32) {
+        const uint32_t c = a.col[q];
+        const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+        const cplx<T> xq = qs[n], xg = gs[n];
+        const double2 ph = a.phase[ii];
+        const double2 pq = cmul(ph, make_double2((double)xq.x, (double)xq.y));         // ph q_n
+        const double2 pg = cmul(cconj(ph), make_double2((double)xg.x, -(double)xg.y));  // conj(ph) conj(g_n)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double2 D = a.dval[3 * q + d];
+            c1[d] = cadd(c1[d], cmul(D, pq));
+            c2[d] = cadd(c2[d], cmul(D, pg));
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) {
+            obs[d].x += __shfl_xor_sync(0xffffffffu, obs[d].x, o);
+            obs[d].y += __shfl_xor_sync(0xffffffffu, obs[d].y, o);
+            src[d].x += __shfl_xor_sync(0xffffffffu, src[d].x, o);
+            src[d].y += __shfl_xor_sync(0xffffffffu, src[d].y, o);
+            c1[d].x += __shfl_xor_sync(0xffffffffu, c1[d].x, o);
+            c1[d].y += __shfl_xor_sync(0xffffffffu, c1[d].y, o);
+            c2[d].x += __shfl_xor_sync(0xffffffffu, c2[d].x, o);
+            c2[d].y += __shfl_xor_sync(0xffffffffu, c2[d].y, o);
+        }
+    if (lane == 0) {
+        const double2 qm = make_double2((double)qs[m].x, (double)qs[m].y);
+        const double2 gm = make_double2((double)gs[m].x, (double)gs[m].y);
+        for (int d = 0; d < 3; ++d) {
+            const double2 t1 = cmul(cconj(gm), cadd(obs[d], c1[d]));   // conj(g_k) (...)
+            const double2 t2 = cmul(qm, cconj(src[d]));                 // q_k conj(...)
+            const double2 t3 = cmul(qm, c2[d]);
+            const double v = t1.x + t2.x + t3.x;
+            const long long o = 3LL * a.perm[m] + d;
+            grad[o] = a.first ? v : grad[o] + v;
+        }
+    }
+}
+
 // u[perm[m]] = us[m] - mean  (the adjoint of the neutral static case)
 template <typename T>
 __global__ void unpermute_kernel(const cplx<T>* us, const int* perm, long long N, int nrhs, int r, const double* mean,
@@ -801,6 +989,105 @@ pim_status run_p(pim_plan P, const void* q, void* u, int nrhs, bool adj, cudaStr
 }
 
 template <typename T, int PP>
+pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    const long long N = d.N;
+    cplx<T>* qs = (cplx<T>*)P->qs;
+    cplx<T>* gs = (cplx<T>*)P->gsrt;
+    cplx<T>* gA = (cplx<T>*)P->gA;
+    cplx<T>* gD = (cplx<T>*)P->gD;
+    const int G = P->has_far ? P->nf[0] * P->nf[1] * P->nf[2] : 0;
+    pim_status st;
+    for (int r = 0; r < nrhs; ++r) {
+        const double* mean = nullptr;
+        if (P->npsp) {
+            if ((st = mean_of<T>(P, q, false, N, nrhs, r, true, s)) != PIM_OK) return st;
+            mean = P->dsum;
+        }
+        if (P->real_data) {
+            permute_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
+            permute_kernel<T, true><<<1024, 256, 0, s>>>(g, d.perm, N, nrhs, r, nullptr, gs);
+        } else {
+            permute_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
+            permute_kernel<T, false><<<1024, 256, 0, s>>>(g, d.perm, N, nrhs, r, nullptr, gs);
+        }
+        PIM_CK(cudaGetLastError());
+        // near grid potentials: U = K * Q(q), V = K^H * Q(g)
+        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
+        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, false, s)) !=
+            PIM_OK)
+            return st;
+        if ((st = spread_two_phase<T, PP>(P, gs, gD, s)) != PIM_OK) return st;
+        if ((st = fft3_conv<T>(P, P->ng, gD, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, true, s)) !=
+            PIM_OK)
+            return st;
+        // far grid potentials: u_f from the source-grid projection of q, v_f
+        // (adjoint) from the observer-grid projection of g
+        if (P->has_far) {
+            for (int side = 0; side < 2; ++side) {
+                FarSpreadArgs fa{};
+                for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
+                fa.pf = P->pf;
+                fa.N = N;
+                fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);
+                fa.fst = side == 0 ? d.fs : d.fo;
+                fa.ft = d.ft;
+                fa.ftd = d.ftd;
+                fa.toff = side == 0 ? 0 : 3;
+                const size_t sm = 2 * sizeof(T) * G;
+                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, s, fa, side == 0 ? qs : gs,
+                                               (cplx<T>*)P->fpart)) != PIM_OK)
+                    return st;
+                double2* fq = side == 0 ? P->fA : P->fD;
+                far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, s>>>((const cplx<T>*)P->fpart, P->far_chunks, G, fq);
+                if ((st = fft3_conv<double>(P, P->fg, fq, P->fB, P->fC, P->fspec, side == 1, s)) != PIM_OK) return st;
+                far_convert_kernel<T><<<(G + 255) / 256, 256, 0, s>>>(fq, (cplx<T>*)(side == 0 ? P->fU : P->fV), G);
+                PIM_CK(cudaGetLastError());
+            }
+        }
+        GradArgs ga{};
+        for (int i = 0; i < 3; ++i) {
+            ga.n[i] = P->n[i];
+            ga.nf[i] = P->nf[i];
+            ga.h[i] = P->h[i];
+            ga.df[i] = P->df[i];
+        }
+        ga.pf = P->pf;
+        ga.N = N;
+        ga.has_far = P->has_far ? 1 : 0;
+        ga.self_img = -1;
+        ga.first = r == 0 ? 1 : 0;
+        ga.perm = d.perm;
+        ga.ns = d.ns;
+        ga.nt = d.nt;
+        ga.ntd = d.ntd;
+        ga.fs = d.fs;
+        ga.fo = d.fo;
+        ga.ft = d.ft;
+        ga.ftd = d.ftd;
+        ga.row_ptr = d.row_ptr;
+        ga.col = d.col;
+        ga.dval = d.dval;
+        ga.phase = P->dphase;
+        if (N > 0)
+            grad_kernel<T, PP><<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(
+                ga, gA, gD, (const cplx<T>*)P->fU, (const cplx<T>*)P->fV, qs, gs, grad);
+        PIM_CK(cudaGetLastError());
+    }
+    return PIM_OK;
+}
+
+template <typename T>
+pim_status grad_p(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
+    switch (P->p) {
+        case 2: return grad_typed<T, 2>(P, q, g, grad, nrhs, s);
+        case 3: return grad_typed<T, 3>(P, q, g, grad, nrhs, s);
+        case 4: return grad_typed<T, 4>(P, q, g, grad, nrhs, s);
+        default: return PIM_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename T, int PP>
 pim_status debug_spread_typed(pim_plan P, void* out, cudaStream_t s) {
     return spread_two_phase<T, PP>(P, (const cplx<T>*)P->qs, (cplx<T>*)out, s);
 }
@@ -816,6 +1103,11 @@ pim_status debug_spread_p(pim_plan P, void* out, cudaStream_t s) {
 }
 
 }  // namespace
+
+pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
+    if (P->prec == PIM_FP64) return grad_p<double>(P, q, g, grad, nrhs, s);
+    return grad_p<float>(P, q, g, grad, nrhs, s);
+}
 
 pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {
     if (P->prec == PIM_FP64) return debug_spread_p<double>(P, out, s);

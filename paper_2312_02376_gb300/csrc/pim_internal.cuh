@@ -162,6 +162,7 @@ struct PointsData {
     double2* val = nullptr;       // nnz: G0 - G_grid (FP64)
     float4* valdf = nullptr;      // nnz: double-float split (re_hi, re_lo, im_hi, im_lo)
     float2* valf = nullptr;       // nnz: complex64
+    double2* dval = nullptr;      // 3 nnz: d/dr_m of the values (with_gradient)
     int64_t nnz = 0;
 };
 
@@ -218,6 +219,12 @@ struct pim_plan_s {
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
     int autotune = 1;
+    int with_gradient = 0;
+    void* gD = nullptr;           // second full grid (adjoint potential of the gradient)
+    void* gsrt = nullptr;         // sorted upstream gradient g, complex<T>, N
+    double2* fD = nullptr;        // second far grid
+    void* fU = nullptr;           // far potentials in plan precision (gradient)
+    void* fV = nullptr;
     // streams and events
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -244,6 +251,7 @@ pim_status build_far_table(pim_plan P, cudaStream_t s);
 
 // points.cu
 pim_status points_build(pim_plan P, int64_t N, const double* xyz_dev, cudaStream_t s);
+pim_status points_update(pim_plan P, const double* xyz_dev, cudaStream_t s);
 void points_free(pim_plan P);
 
 // profiling: record the start / stop event of a stage of the current apply
@@ -254,4 +262,5 @@ constexpr int PIM_RED_BLOCKS = 608;
 pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s);
 pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
+pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
 int pim_fft_len(int n);

@@ -272,69 +272,137 @@ struct FillArgs {
     int corr_mode;
 };
 
+// d/dt of the Lagrange basis (product rule), runtime degree p
+__device__ __forceinline__ void lagrange_dweights(int p, double t, double* dw) {
+    for (int j = 0; j <= p; ++j) {
+        double den = 1.0;
+        for (int l = 0; l <= p; ++l)
+            if (l != j) den *= (double)(j - l);
+        double s = 0.0;
+        for (int k = 0; k <= p; ++k) {
+            if (k == j) continue;
+            double pr = 1.0;
+            for (int l = 0; l <= p; ++l)
+                if (l != j && l != k) pr *= (t - l);
+            s += pr;
+        }
+        dw[j] = s / den;
+    }
+}
+
 // Correction value (Eq. er) for observer m, source n, image ii, before the
 // phase: G0(r_m - r_n - i o L) [not for m = n, i = 0] minus the grid
 // interaction sum_a sum_c w_m(a) w_n(c) g(a - c - i o (n-1)), the latter via
 //   sum_e g(s_m - s_n - i o (n-1) + e) Cx(e_x) Cy(e_y) Cz(e_z),
 //   Cd(e) = sum_{j - l = e} w_{m,d}[j] w_{n,d}[l].
+// With GRAD, also its gradient with respect to r_m (the observer's weights
+// replaced by their derivatives along one axis at a time).
+template <bool GRAD>
 __device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32_t* ns, const double* ntd, long long m,
-                              long long n, int ii, int* status) {
+                              long long n, int ii, int* status, double2* grad) {
     const int p = a.p;
     int sm[3], sn[3];
     unpack3(ns[m], sm[0], sm[1], sm[2]);
     unpack3(ns[n], sn[0], sn[1], sn[2]);
-    double C[3][2 * PIM_MAX_P + 1];
+    double C[3][2 * PIM_MAX_P + 1], dC[3][2 * PIM_MAX_P + 1];
     int base[3];
     for (int d = 0; d < 3; ++d) {
-        double wm[PIM_MAX_P + 1], wn[PIM_MAX_P + 1];
+        double wm[PIM_MAX_P + 1], wn[PIM_MAX_P + 1], dwm[PIM_MAX_P + 1];
         lagrange_weights<double>(p, ntd[3 * m + d], wm);
         lagrange_weights<double>(p, ntd[3 * n + d], wn);
-        for (int e = 0; e <= 2 * p; ++e) C[d][e] = 0.0;
+        if (GRAD) lagrange_dweights(p, ntd[3 * m + d], dwm);
+        for (int e = 0; e <= 2 * p; ++e) C[d][e] = dC[d][e] = 0.0;
         for (int j = 0; j <= p; ++j)
-            for (int l = 0; l <= p; ++l) C[d][j - l + p] += wm[j] * wn[l];
+            for (int l = 0; l <= p; ++l) {
+                C[d][j - l + p] += wm[j] * wn[l];
+                if (GRAD) dC[d][j - l + p] += dwm[j] * wn[l] / a.h[d];
+            }
         base[d] = sm[d] - sn[d] - a.pa.img[3 * ii + d] * a.pa.nL[d];
         if (abs(base[d]) + p > a.R) {
             atomicOr(status, PIM_DEV_BOUNDS);
+            if (GRAD)
+                for (int k = 0; k < 3; ++k) grad[k] = make_double2(0.0, 0.0);
             return make_double2(0.0, 0.0);
         }
     }
-    double2 grid = make_double2(0.0, 0.0);
+    double2 grid = make_double2(0.0, 0.0), gg[3];
+    for (int k = 0; k < 3; ++k) gg[k] = make_double2(0.0, 0.0);
     for (int ez = 0; ez <= 2 * p; ++ez) {
-        double2 sy = make_double2(0.0, 0.0);
+        double2 sy = make_double2(0.0, 0.0), dsyx = sy, dsyy = sy;
         for (int ey = 0; ey <= 2 * p; ++ey) {
             const double2* row =
                 a.gtab + ((long long)(base[2] + ez - p + a.R) * a.W + (base[1] + ey - p + a.R)) * a.W + (base[0] - p + a.R);
-            double2 sx = make_double2(0.0, 0.0);
+            double2 sx = make_double2(0.0, 0.0), dsx = sx;
             for (int ex = 0; ex <= 2 * p; ++ex) {
                 const double2 g = row[ex];
                 sx.x += C[0][ex] * g.x;
                 sx.y += C[0][ex] * g.y;
+                if (GRAD) {
+                    dsx.x += dC[0][ex] * g.x;
+                    dsx.y += dC[0][ex] * g.y;
+                }
             }
             sy.x += C[1][ey] * sx.x;
             sy.y += C[1][ey] * sx.y;
+            if (GRAD) {
+                dsyx.x += C[1][ey] * dsx.x;
+                dsyx.y += C[1][ey] * dsx.y;
+                dsyy.x += dC[1][ey] * sx.x;
+                dsyy.y += dC[1][ey] * sx.y;
+            }
         }
         grid.x += C[2][ez] * sy.x;
         grid.y += C[2][ez] * sy.y;
+        if (GRAD) {
+            gg[0].x += C[2][ez] * dsyx.x;
+            gg[0].y += C[2][ez] * dsyx.y;
+            gg[1].x += C[2][ez] * dsyy.x;
+            gg[1].y += C[2][ez] * dsyy.y;
+            gg[2].x += dC[2][ez] * sy.x;
+            gg[2].y += dC[2][ez] * sy.y;
+        }
     }
     double2 exact = make_double2(0.0, 0.0);
+    double2 dex[3] = {exact, exact, exact};
     if (!(m == n && ii == a.self_img)) {
-        double r2 = 0.0;
+        double r[3], r2 = 0.0;
         for (int d = 0; d < 3; ++d) {
-            const double x = pos[3 * m + d] - pos[3 * n + d] - a.pa.img[3 * ii + d] * a.D[d];
-            r2 += x * x;
+            r[d] = pos[3 * m + d] - pos[3 * n + d] - a.pa.img[3 * ii + d] * a.D[d];
+            r2 += r[d] * r[d];
         }
         if (r2 == 0.0) {  // two points coincide modulo the lattice: Eq. 1 is singular
             atomicOr(status, PIM_DEV_COINCIDENT);
+            if (GRAD)
+                for (int k = 0; k < 3; ++k) grad[k] = make_double2(0.0, 0.0);
             return make_double2(0.0, 0.0);
         }
-        exact = G0(sqrt(r2), a.k);
+        const double R = sqrt(r2);
+        exact = G0(R, a.k);
+        if (GRAD) {
+            // grad G0(R) = G0(R) (-jk - 1/R) r / R
+            const double2 f = cmul(exact, make_double2(-1.0 / R, -a.k));
+            for (int d = 0; d < 3; ++d) dex[d] = make_double2(f.x * r[d] / R, f.y * r[d] / R);
+        }
     }
+    if (GRAD)
+        for (int d = 0; d < 3; ++d) grad[d] = csub(dex[d], gg[d]);
     return csub(exact, grid);
+}
+
+__device__ __forceinline__ void store_value(const FillArgs& a, long long q, double2 d, double2* val, float4* valdf,
+                                            float2* valf) {
+    val[q] = d;
+    if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
+        const float rh = (float)d.x, ih = (float)d.y;
+        valdf[q] = make_float4(rh, (float)(d.x - (double)rh), ih, (float)(d.y - (double)ih));
+    } else if (a.corr_mode == PIM_CORR_FP32) {
+        valf[q] = make_float2((float)d.x, (float)d.y);
+    }
 }
 
 __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
                                  const int* box_ptr, const int64_t* row_ptr, uint32_t* col, double2* val,
-                                 float4* valdf, float2* valf, int* status) {
+                                 float4* valdf, float2* valf, double2* dval, int* status) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -345,18 +413,73 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
         for_each_region_row(a.pa, box_ptr, B, [&](int ii, int lo, int hi) {
             for (int n = lo + lane; n < hi; n += 32) {
                 const long long q = off + (n - lo);
-                const double2 d = corr_value(a, pos, ns, ntd, m, n, ii, status);
                 col[q] = (uint32_t)n | ((uint32_t)ii << PIM_COL_BITS);
-                val[q] = d;
-                if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
-                    const float rh = (float)d.x, ih = (float)d.y;
-                    valdf[q] = make_float4(rh, (float)(d.x - (double)rh), ih, (float)(d.y - (double)ih));
-                } else if (a.corr_mode == PIM_CORR_FP32) {
-                    valf[q] = make_float2((float)d.x, (float)d.y);
+                if (dval) {
+                    double2 gr[3];
+                    const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
+                    store_value(a, q, d, val, valdf, valf);
+                    for (int k = 0; k < 3; ++k) dval[3 * q + k] = gr[k];
+                } else {
+                    const double2 d = corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr);
+                    store_value(a, q, d, val, valdf, valf);
                 }
             }
             off += hi - lo;
         });
+    }
+}
+
+// Recomputes the values of an existing correction list (frozen topology).
+__global__ void pair_refill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
+                                   const int64_t* row_ptr, const uint32_t* col, double2* val, float4* valdf,
+                                   float2* valf, double2* dval, int* status) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long m = warp; m < N; m += nwarps) {
+        for (long long q = row_ptr[m] + lane; q < row_ptr[m + 1]; q += 32) {
+            const uint32_t c = col[q];
+            const long long n = c & PIM_COL_MASK;
+            const int ii = (int)(c >> PIM_COL_BITS);
+            if (dval) {
+                double2 gr[3];
+                const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
+                store_value(a, q, d, val, valdf, valf);
+                for (int k = 0; k < 3; ++k) dval[3 * q + k] = gr[k];
+            } else {
+                store_value(a, q, corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr), val, valdf, valf);
+            }
+        }
+    }
+}
+
+// New positions with the stencil starts kept (frozen topology).
+__global__ void point_update_kernel(const double* xyz, const int* perm, long long N, PtArgs a, const double* D,
+                                    double* pos, const uint32_t* ns, float* nt, double* ntd, const uint32_t* fs,
+                                    const uint32_t* fo, float* ft, double* ftd, int* status) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const long long i = perm[m];
+        int s[3], ss[3], so[3];
+        unpack3(ns[m], s[0], s[1], s[2]);
+        if (a.has_far) {
+            unpack3(fs[m], ss[0], ss[1], ss[2]);
+            unpack3(fo[m], so[0], so[1], so[2]);
+        }
+        for (int d = 0; d < 3; ++d) {
+            const double x = xyz[3 * i + d];
+            if (!(x >= 0.0 && x <= D[d])) atomicOr(status, 8);
+            pos[3 * m + d] = x;
+            const double t = x / a.h[d] - s[d];
+            nt[3 * m + d] = (float)t;
+            ntd[3 * m + d] = t;
+            if (a.has_far) {
+                const double ts = x / a.df[d] - ss[d], to = (x - 0.5 * a.df[d]) / a.df[d] - so[d];
+                ft[6 * m + d] = (float)ts;
+                ft[6 * m + 3 + d] = (float)to;
+                ftd[6 * m + d] = ts;
+                ftd[6 * m + 3 + d] = to;
+            }
+        }
     }
 }
 
@@ -389,7 +512,85 @@ pim_status scan(pim_plan P, const int* in, OutT* out, long long n, cudaStream_t 
     return PIM_OK;
 }
 
+FillArgs fill_args(pim_plan P, const PairArgs& pr) {
+    FillArgs fa{};
+    fa.pa = pr;
+    for (int i = 0; i < 3; ++i) { fa.h[i] = P->h[i]; fa.D[i] = P->D[i]; }
+    fa.k = P->k;
+    fa.p = P->p;
+    fa.R = P->b + 2 + 2 * P->p;
+    fa.W = 2 * fa.R + 1;
+    fa.corr_mode = P->corr_mode;
+    fa.self_img = -1;
+    for (int i = 0; i < P->nimg; ++i)
+        if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) fa.self_img = i;
+    return fa;
+}
+
 }  // namespace
+
+// New positions for the current points with the discrete structure kept.
+pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
+    PointsData& d = P->pts;
+    const long long N = d.N;
+    pim_status st;
+    PIM_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
+    double* dD = nullptr;
+    if ((st = pim_alloc(P, (void**)&dD, sizeof(double) * 3)) != PIM_OK) return st;
+    PIM_CK(cudaMemcpyAsync(dD, P->D, sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    PtArgs pa{};
+    for (int i = 0; i < 3; ++i) {
+        pa.h[i] = P->h[i]; pa.df[i] = P->df[i]; pa.n[i] = P->n[i]; pa.nf[i] = P->nf[i];
+    }
+    pa.p = P->p;
+    pa.pf = P->pf;
+    pa.has_far = P->has_far ? 1 : 0;
+    if (N > 0)
+        point_update_kernel<<<1024, 256, 0, s>>>(xyz, d.perm, N, pa, dD, d.pos, d.ns, d.nt, d.ntd, d.fs, d.fo, d.ft,
+                                                 d.ftd, P->dstatus);
+    PIM_CK(cudaGetLastError());
+    int hstat = 0;
+    PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, dD, sizeof(double) * 3);
+    if (hstat) {
+        pim_set_error("a point lies outside the closed cell [0, D]");
+        return PIM_ERR_OUT_OF_CELL;
+    }
+    int* dimg = nullptr;
+    if ((st = pim_alloc(P, (void**)&dimg, sizeof(int) * 3 * P->nimg)) != PIM_OK) return st;
+    PIM_CK(cudaMemcpyAsync(dimg, P->img, sizeof(int) * 3 * P->nimg, cudaMemcpyHostToDevice, s));
+    PairArgs pr{};
+    for (int i = 0; i < 3; ++i) { pr.nb[i] = P->nb[i]; pr.nL[i] = P->n[i] - 1; }
+    pr.b = P->b;
+    pr.cube = P->cube;
+    pr.p = P->p;
+    pr.nimg = P->nimg;
+    pr.img = dimg;
+    FillArgs fa = fill_args(P, pr);
+    double2* gtab = nullptr;
+    const size_t gsz = (size_t)fa.W * fa.W * fa.W * sizeof(double2);
+    if ((st = pim_alloc(P, (void**)&gtab, gsz)) != PIM_OK) return st;
+    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k);
+    fa.gtab = gtab;
+    if (N > 0 && d.nnz > 0)
+        pair_refill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.row_ptr, d.col, d.val, d.valdf,
+                                                     d.valf, d.dval, P->dstatus);
+    PIM_CK(cudaGetLastError());
+    PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, gtab, gsz);
+    pim_free(P, dimg, sizeof(int) * 3 * P->nimg);
+    if (hstat & PIM_DEV_COINCIDENT) {
+        pim_set_error("two points coincide (modulo the lattice): the periodic sum is singular");
+        return PIM_ERR_ARG;
+    }
+    if (hstat) {
+        pim_set_error("internal bounds check tripped while updating the correction values");
+        return PIM_ERR_DEVICE;
+    }
+    return PIM_OK;
+}
 
 void points_free(pim_plan P) {
     PointsData& d = P->pts;
@@ -418,6 +619,7 @@ void points_free(pim_plan P) {
     pim_free(P, d.val, d.nnz * sizeof(double2));
     pim_free(P, d.valdf, d.nnz * sizeof(float4));
     pim_free(P, d.valf, d.nnz * sizeof(float2));
+    pim_free(P, d.dval, 3 * d.nnz * sizeof(double2));
     d = PointsData{};
 }
 
@@ -526,18 +728,10 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         if ((st = pim_alloc(P, (void**)&d.valdf, nnz * sizeof(float4))) != PIM_OK) return st;
     if (P->corr_mode == PIM_CORR_FP32)
         if ((st = pim_alloc(P, (void**)&d.valf, nnz * sizeof(float2))) != PIM_OK) return st;
+    if (P->with_gradient)
+        if ((st = pim_alloc(P, (void**)&d.dval, 3 * nnz * sizeof(double2))) != PIM_OK) return st;
     // table of g over the offsets a correction can reach
-    FillArgs fa{};
-    fa.pa = pr;
-    for (int i = 0; i < 3; ++i) { fa.h[i] = P->h[i]; fa.D[i] = P->D[i]; }
-    fa.k = P->k;
-    fa.p = P->p;
-    fa.R = P->b + 2 + 2 * P->p;
-    fa.W = 2 * fa.R + 1;
-    fa.corr_mode = P->corr_mode;
-    fa.self_img = -1;
-    for (int i = 0; i < P->nimg; ++i)
-        if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) fa.self_img = i;
+    FillArgs fa = fill_args(P, pr);
     double2* gtab = nullptr;
     const size_t gsz = (size_t)fa.W * fa.W * fa.W * sizeof(double2);
     if ((st = pim_alloc(P, (void**)&gtab, gsz)) != PIM_OK) return st;
@@ -545,7 +739,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     fa.gtab = gtab;
     if (N > 0 && nnz > 0)
         pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.row_ptr, d.col, d.val,
-                                                   d.valdf, d.valf, P->dstatus);
+                                                   d.valdf, d.valf, d.dval, P->dstatus);
     PIM_CK(cudaGetLastError());
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     PIM_CK(cudaStreamSynchronize(s));

@@ -22,7 +22,8 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32 = 0, 1, 2
 # symbols declared in include/pim.h
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
            "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
-           "pim_stage_times", "pim_stage_name", "pim_debug_copy", "pim_destroy"]
+           "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_update_positions", "pim_debug_copy",
+           "pim_destroy"]
 STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
 
@@ -30,7 +31,7 @@ class pim_options(ctypes.Structure):
     _fields_ = [("far_n", ctypes.c_int * 3), ("far_p", ctypes.c_int), ("corr_radius", ctypes.c_int),
                 ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int)]
 
 
 class pim_info(ctypes.Structure):
@@ -89,6 +90,10 @@ def load(path=LIB_PATH):
     lib.pim_stage_times.restype = i32
     lib.pim_stage_name.argtypes = [i32]
     lib.pim_stage_name.restype = ctypes.c_char_p
+    lib.pim_position_grad.argtypes = [vp, vp, vp, vp, i32, vp]
+    lib.pim_position_grad.restype = i32
+    lib.pim_update_positions.argtypes = [vp, vp]
+    lib.pim_update_positions.restype = i32
     lib.pim_debug_copy.argtypes = [vp, i32, vp, ctypes.c_size_t]
     lib.pim_debug_copy.restype = i32
     lib.pim_destroy.argtypes = [vp]
@@ -185,6 +190,15 @@ def pim_stage_name(stage):
     return r.decode() if r is not None else None
 
 
+def pim_position_grad(plan, q, g, grad_xyz, nrhs=1, stream=None):
+    _check(load().pim_position_grad(plan, _ptr(q), _ptr(g), _ptr(grad_xyz), int(nrhs), _stream_ptr(stream)),
+           "pim_position_grad")
+
+
+def pim_update_positions(plan, xyz):
+    _check(load().pim_update_positions(plan, _ptr(xyz)), "pim_update_positions")
+
+
 def pim_debug_copy(plan, what, out):
     _check(load().pim_debug_copy(plan, int(what), _ptr(out), out.nbytes), "pim_debug_copy")
 
@@ -211,7 +225,8 @@ class Plan:
     """
 
     def __init__(self, D, pdims, k, k0, n, p=4, layers=1, precision="fp32", b=None, nf=None, pf=None,
-                 corr_mode=None, cube=False, tile=None, neutral_tol=None, mem_cap=0, autotune=None, stream=None):
+                 corr_mode=None, cube=False, tile=None, neutral_tol=None, mem_cap=0, autotune=None,
+                 with_gradient=False, stream=None):
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
         self.pdims = tuple(pdims)
@@ -236,6 +251,7 @@ class Plan:
         opt.corr_cube = 1 if cube else 0
         if autotune is not None:
             opt.autotune = 1 if autotune else 0
+        opt.with_gradient = 1 if with_gradient else 0
         opt.mem_cap = int(mem_cap)
         mask = sum(1 << d for d in self.pdims)
         h = self.D / (self.n - 1)
@@ -271,6 +287,23 @@ class Plan:
 
     def apply_adjoint(self, v, out=None, stream=None):
         return self.apply(v, out, stream, adjoint=True)
+
+    def position_grad(self, q, g, out=None, stream=None):
+        """(N, 3) float64: d/dx Re sum conj(g) (A q) with the discrete
+        structure frozen (plan created with with_gradient=True)."""
+        nrhs = 1 if q.ndim == 1 else int(q.shape[1])
+        if out is None:
+            if hasattr(q, "data_ptr") and not isinstance(q, np.ndarray):
+                import torch
+                out = torch.empty((self.N, 3), dtype=torch.float64, device=q.device)
+            else:
+                out = np.empty((self.N, 3), np.float64)
+        pim_position_grad(self._h, q, g, out, nrhs, stream)
+        return out
+
+    def update_positions(self, xyz):
+        """New positions with the stencils, boxes and correction list kept."""
+        pim_update_positions(self._h, xyz)
 
     def set_profiling(self, on=True):
         pim_set_profiling(self._h, on)

@@ -211,3 +211,57 @@ def test_bloch_phase_when_a_source_crosses_the_cell():
     scale = np.linalg.norm(u1)
     assert np.linalg.norm(u2[1:] - u1[1:]) / scale < 3e-4
     assert abs(u2[0] - ph * u1[0]) / np.abs(u1).mean() < 3e-3
+
+
+@pytest.mark.parametrize("case", ["helmholtz2d", "npsp3d"])
+def test_position_gradient_matches_finite_differences(case):
+    # d/dr Re <g, A(r) q> with the stencils, boxes and pair list frozen at r
+    rng = np.random.default_rng(13)
+    N = 50
+    if case == "helmholtz2d":
+        P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=4.0, k0=(1.2, 0.4, 0.0), n=(9, 9, 6), p=3, layers=1, b=3,
+                       nf=(7, 7, 5), pf=3)
+        q = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    else:
+        P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=0.0, k0=(0, 0, 0), n=(9, 9, 9), p=4, layers=1, b=4,
+                       nf=(6, 6, 6), pf=4)
+        q = rng.standard_normal(N)
+        q = (q - q.mean()).astype(complex)
+    pts = rng.random((N, 3)) * P.D * 0.98 + 0.01 * P.D
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    base = pim.Plan(P, pts)
+    G = base.position_grad(q, g)
+    eps = 1e-6
+    for k in (0, 17, 41):
+        for d in range(3):
+            pp = pts.copy()
+            pp[k, d] += eps
+            up = pim.Plan(P, pp, K=base.K, F=base.F, frozen=base).apply(q)
+            pp[k, d] -= 2 * eps
+            um = pim.Plan(P, pp, K=base.K, F=base.F, frozen=base).apply(q)
+            fd = np.real(np.vdot(g, up) - np.vdot(g, um)) / (2 * eps)
+            assert abs(fd - G[k, d]) < 1e-7 * np.abs(G).max()
+
+
+def test_position_gradient_all_pairs_equals_exact_gradient():
+    # every pair corrected, no periodicity: A is the exact kernel matrix, so
+    # the gradient is the closed form of d/dr_k Re sum conj(g_m) G0(r_m-r_n) q_n
+    rng = np.random.default_rng(14)
+    N, k = 40, 3.0
+    pts = rng.random((N, 3)) * np.array([1, 1, 0.5])
+    q = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    g = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    P = pim.Params(D=(1, 1, 0.5), pdims=(), k=k, k0=(0, 0, 0), n=(10, 10, 6), p=4, layers=0, b=100)
+    G = pim.Plan(P, pts).position_grad(q, g)
+    d = pts[:, None, :] - pts[None, :, :]
+    R = np.linalg.norm(d, axis=-1)
+    np.fill_diagonal(R, 1.0)
+    dG = (greens.G0(R, k) * (-1j * k - 1.0 / R) / R)[..., None] * d   # grad wrt r_m of G0(r_m - r_n)
+    dG[np.arange(N), np.arange(N)] = 0
+    # observer side: conj(g_k) dG[k, n] q_n; source side: conj(g_m) d/dr_k G0(r_m - r_k) q_k = -dG[m, k]
+    ref2 = np.zeros((N, 3))
+    for kk in range(N):
+        for dd in range(3):
+            ref2[kk, dd] = np.real(np.sum(np.conj(g[kk]) * dG[kk, :, dd] * q)) + \
+                np.real(np.sum(np.conj(g) * (-dG[:, kk, dd]) * q[kk]))
+    assert np.allclose(G, ref2, rtol=0, atol=1e-10 * np.abs(ref2).max())
