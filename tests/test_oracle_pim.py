@@ -64,7 +64,7 @@ def test_separable_correction_equals_explicit_double_sum():
     rng = np.random.default_rng(3)
     pts = rng.random((120, 3))
     P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=3.0, k0=(1.0, 0.5, 0.2), n=(12, 12, 12), p=4, layers=1, b=4)
-    s, w, B = pim.near_stencils(P, pts)
+    s, w, B, _ = pim.near_stencils(P, pts)
     m, n, ii = pim.correction_pairs(P, B)
     sel = np.random.default_rng(0).choice(len(m), 1500, replace=False)
     a = pim.correction_values_explicit(P, pts, s, w, m[sel], n[sel], ii[sel])
