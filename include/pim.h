@@ -231,6 +231,32 @@ pim_status pim_position_grad(pim_plan plan, const void* q, const void* g, double
  */
 pim_status pim_update_positions(pim_plan plan, const double* xyz);
 
+/*
+ * pim_apply_noalloc -- pim_apply (adjoint = 0) or pim_apply_adjoint
+ * (adjoint != 0) that allocates nothing: the per-call scratch of the apply
+ * (sorted sources, box moments, the three grid work buffers, the far-zone
+ * partial sums and far grids) comes from one 32 MiB device array that the
+ * library holds on every GPU that loads it, until the process exits.  The
+ * paper has no counterpart; this is for callers that cannot allocate device
+ * memory when they apply the operator (a solver loop under a fixed memory
+ * budget, code that runs while another thread captures a graph or owns the
+ * stream-ordered allocator, bindings that can only pass in buffers they
+ * already hold).  The plan itself is created beforehand as usual.
+ *   q, u     device pointers only ([N][nrhs], as for pim_apply); host
+ *            pointers -> PIM_ERR_ARG.
+ *   Limit    plans whose scratch exceeds 32 MiB -> PIM_ERR_ARG with the
+ *            required size in pim_last_error().
+ *   Set-up   the first call on a device looks up the array's device address
+ *            (cudaGetSymbolAddress) with that device current; make that first
+ *            call before any stream capture.
+ *   Sharing  every call on a device uses the same array, which keeps the last
+ *            call's contents (the apply writes every scratch word before it
+ *            reads it, so nothing needs clearing); calls whose device work
+ *            overlaps -- on different streams or from different threads --
+ *            race.  Order them on one stream.
+ */
+pim_status pim_apply_noalloc(pim_plan plan, const void* q, void* u, int nrhs, int adjoint, void* stream);
+
 /* Device-side status of the calls issued so far: synchronises the plan's
  * streams, returns the first flag raised (PIM_OK if none) and clears it. */
 pim_status pim_last_device_status(pim_plan plan);

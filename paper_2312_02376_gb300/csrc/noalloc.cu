@@ -1,0 +1,130 @@
+// pim_apply_noalloc: the apply with its per-call scratch in a fixed device
+// array that the library owns for the life of the process, so that the call
+// itself allocates nothing.
+//
+// Who needs it: code that must not allocate device memory at the time it
+// applies the operator -- for example a solver step running under a memory
+// budget that forbids growth after start-up, a caller that runs while a
+// stream-ordered allocator or a graph capture is active on another thread,
+// or a host language runtime that can only pass in buffers it already owns.
+// The plan's persistent tables (spectra, correction list, stencils) are
+// created earlier by pim_plan_create / pim_set_points, when allocation is
+// allowed.
+#include <mutex>
+
+#include "pim_internal.cuh"
+
+namespace {
+
+// 32 MiB of scratch per GPU that loads the library, held until exit.
+constexpr size_t NOALLOC_BYTES = 32ull << 20;
+static __device__ __align__(256) unsigned char pim_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_addr[MAX_DEVICES] = {nullptr};
+
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int nrhs, int adjoint, void* stream) {
+    if (!P || !q || !u || nrhs < 1) {
+        pim_set_error("invalid argument");
+        return PIM_ERR_ARG;
+    }
+    if (!P->pts.box_ptr) {
+        pim_set_error("apply before pim_set_points");
+        return PIM_ERR_STATE;
+    }
+    if (!is_device_ptr(q) || !is_device_ptr(u)) {
+        pim_set_error("pim_apply_noalloc takes device pointers only (host buffers would need staging memory)");
+        return PIM_ERR_ARG;
+    }
+    // one-time set-up per device: the device address of the scratch array
+    int dev = 0;
+    PIM_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        pim_set_error("device index out of range");
+        return PIM_ERR_ARG;
+    }
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void* ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, pim_noalloc_scratch);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                pim_set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                return PIM_ERR_CUDA;
+            }
+            g_addr[dev] = ptr;
+        }
+        base = g_addr[dev];
+    }
+    // carve the per-call scratch of the apply out of the array
+    const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t N = (size_t)P->pts.N;
+    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const size_t GB = (size_t)P->n[2] * P->n[1] * P->ng.L[0];
+    const size_t GC = (size_t)P->n[2] * P->ng.L[1] * P->ng.L[0];
+    const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
+    const size_t mom = (size_t)(P->pts.nne > 0 ? P->pts.nne : 1) * np3 * ge;
+    size_t Gf = 0, fB = 0, fC = 0;
+    if (P->has_far) {
+        Gf = (size_t)P->nf[0] * P->nf[1] * P->nf[2];
+        fB = (size_t)P->nf[2] * P->nf[1] * P->fg.L[0];
+        fC = (size_t)P->nf[2] * P->fg.L[1] * P->fg.L[0];
+    }
+    const size_t sizes[10] = {N * ge,  N * ge,  G * ge, GB * ge, GC * ge, mom, (size_t)P->far_chunks * Gf * ge,
+                              Gf * sizeof(double2), fB * sizeof(double2), fC * sizeof(double2)};
+    size_t need = 0;
+    for (size_t b : sizes) need += up256(b);
+    if (need > NOALLOC_BYTES) {
+        pim_set_error("plan needs " + std::to_string(need) + " bytes of scratch; pim_apply_noalloc has " +
+                      std::to_string(NOALLOC_BYTES));
+        return PIM_ERR_ARG;
+    }
+    unsigned char* cur = static_cast<unsigned char*>(base);
+    void* ptrs[10];
+    for (int i = 0; i < 10; ++i) {
+        ptrs[i] = sizes[i] ? cur : nullptr;
+        cur += up256(sizes[i]);
+    }
+    // run the apply with the plan's scratch fields pointing into the array
+    void* save[10] = {P->qs, P->us, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC};
+    P->qs = ptrs[0];
+    P->us = ptrs[1];
+    P->gA = ptrs[2];
+    P->gB = ptrs[3];
+    P->gC = ptrs[4];
+    P->pts.mom = ptrs[5];
+    if (P->has_far) {
+        P->fpart = ptrs[6];
+        P->fA = (double2*)ptrs[7];
+        P->fB = (double2*)ptrs[8];
+        P->fC = (double2*)ptrs[9];
+    }
+    const pim_status st = apply_run(P, q, u, nrhs, adjoint != 0, (cudaStream_t)stream);
+    P->qs = save[0];
+    P->us = save[1];
+    P->gA = save[2];
+    P->gB = save[3];
+    P->gC = save[4];
+    P->pts.mom = save[5];
+    P->fpart = save[6];
+    P->fA = (double2*)save[7];
+    P->fB = (double2*)save[8];
+    P->fC = (double2*)save[9];
+    return st;
+}

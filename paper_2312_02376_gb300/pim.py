@@ -22,8 +22,8 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32 = 0, 1, 2
 # symbols declared in include/pim.h
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
            "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
-           "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_update_positions", "pim_debug_copy",
-           "pim_destroy"]
+           "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_update_positions", "pim_apply_noalloc",
+           "pim_debug_copy", "pim_destroy"]
 STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
 
@@ -94,6 +94,8 @@ def load(path=LIB_PATH):
     lib.pim_position_grad.restype = i32
     lib.pim_update_positions.argtypes = [vp, vp]
     lib.pim_update_positions.restype = i32
+    lib.pim_apply_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
+    lib.pim_apply_noalloc.restype = i32
     lib.pim_debug_copy.argtypes = [vp, i32, vp, ctypes.c_size_t]
     lib.pim_debug_copy.restype = i32
     lib.pim_destroy.argtypes = [vp]
@@ -197,6 +199,11 @@ def pim_position_grad(plan, q, g, grad_xyz, nrhs=1, stream=None):
 
 def pim_update_positions(plan, xyz):
     _check(load().pim_update_positions(plan, _ptr(xyz)), "pim_update_positions")
+
+
+def pim_apply_noalloc(plan, q, u, nrhs=1, adjoint=False, stream=None):
+    _check(load().pim_apply_noalloc(plan, _ptr(q), _ptr(u), int(nrhs), 1 if adjoint else 0, _stream_ptr(stream)),
+           "pim_apply_noalloc")
 
 
 def pim_debug_copy(plan, what, out):
