@@ -81,7 +81,7 @@ def coulomb3d(N=4096, n=32, index=0, salt=0, b=5, nf=10):
                     (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp64", N, 1, pts, q.astype(np.float64))
 
 
-def helmholtz2d(N=262144, n=(128, 128, 64), index=1, salt=0, b=5, nf=(21, 21, 11)):
+def helmholtz2d(N=262144, n=(128, 128, 64), index=1, salt=0, b=4, nf=(21, 21, 11)):
     rng = _rng(index, salt)
     D = np.array([1.0, 1.0, 0.5])
     nu = N // 2
