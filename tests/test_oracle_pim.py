@@ -265,3 +265,16 @@ def test_position_gradient_all_pairs_equals_exact_gradient():
             ref2[kk, dd] = np.real(np.sum(np.conj(g[kk]) * dG[kk, :, dd] * q)) + \
                 np.real(np.sum(np.conj(g) * (-dG[:, kk, dd]) * q[kk]))
     assert np.allclose(G, ref2, rtol=0, atol=1e-10 * np.abs(ref2).max())
+
+
+def test_full_size_helmholtz2d_rows_vs_ewald_golden():
+    # the 262144-point 2D Helmholtz workload: FFT-PIM rows vs the committed
+    # Ewald ground truth (tests/golden/make_helmholtz2d_262k_ewald_rows.py)
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "helmholtz2d_262k_ewald_rows.txt")
+    d = np.loadtxt(path, comments="#")
+    rows, ref = d[:, 0].astype(np.int64), d[:, 1] + 1j * d[:, 2]
+    W = inputs.helmholtz2d()
+    P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b, nf=W.nf, pf=W.pf)
+    u = pim.Plan(P, W.points).apply_rows(W.q.astype(np.complex128), rows)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 5e-5
