@@ -149,40 +149,44 @@ __device__ __forceinline__ void lagrange_dw_rt(int p, T t, T* dw) {
 //   M_b(j) = sum_{n in b} w_n(j) q_n         (the box's (p+1)^3 moments).
 // Phase 1: one warp per non-empty box, lanes own stencil offsets, the box's
 // points are loaded 32 at a time and walked by shuffles.
+template <int P>
+__device__ __forceinline__ void covering_boxes(int a, int n, int nb, int& lo, int& hi) {
+    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
+    lo = a <= P ? 0 : a - P + LO;
+    hi = a >= n - 1 - P ? nb - 1 : a + LO;
+    lo = max(lo, 0);
+    hi = min(hi, nb - 1);
+}
+
 struct MomentArgs {
-    long long nne;
-    long long N;
+    long long nne, nmw;
     const int* bstart;   // nne + 1 point offsets of the non-empty boxes
+    const int* wbeg;     // nmw + 1 first slot of each warp (about 32 points each)
     const float* nt;
     const double* ntd;
-    int slots_per_warp;
 };
 
-// A warp walks a contiguous run of non-empty boxes: their points are
-// contiguous, so they are read 32 at a time (coalesced) and walked by
-// shuffles; a box's moment row is written when the walk leaves the box.
+// A warp walks the points of the boxes [wbeg[w], wbeg[w+1]) (contiguous in
+// the sorted order), 32 at a time (coalesced loads, then shuffles).  Lane l
+// < (P+1)^2 owns the stencil offsets (jx = 0..P, jy = l % (P+1),
+// jz = l / (P+1)); a box's moment row is written when the walk leaves it
+// (lane l writes P+1 consecutive values, the warp one contiguous row).
 template <typename T, int P>
 __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>* __restrict__ qs, cplx<T>* mom) {
-    constexpr int NP = P + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
+    constexpr int NP = P + 1, NP3 = NP * NP * NP;
+    static_assert(NP * NP <= 32, "one lane per (jy, jz) pair");
     const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long s0 = warp * a.slots_per_warp;
-    if (s0 >= a.nne) return;
-    const long long s1 = min(a.nne, s0 + a.slots_per_warp);
-    int jx[KPL], jy[KPL], jz[KPL];
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-        const int o = lane + 32 * k;
-        jx[k] = o % NP;
-        jy[k] = (o / NP) % NP;
-        jz[k] = o / (NP * NP);
-    }
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (w >= a.nmw) return;
+    const long long s0 = a.wbeg[w], s1 = a.wbeg[w + 1];
+    const bool act = lane < NP * NP;
+    const int jy = lane % NP, jz = lane / NP;
     const int m0 = a.bstart[s0], m1 = a.bstart[s1];
     long long slot = s0;
     int next = a.bstart[slot + 1];
-    cplx<T> sum[KPL];
+    cplx<T> sum[NP];
 #pragma unroll
-    for (int k = 0; k < KPL; ++k) sum[k] = mk<T>(T(0), T(0));
+    for (int j = 0; j < NP; ++j) sum[j] = mk<T>(T(0), T(0));
     for (int b0 = m0; b0 < m1; b0 += 32) {
         const int cnt = min(32, m1 - b0);
         const int ml = b0 + lane;
@@ -196,93 +200,98 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
         for (int j = 0; j < cnt; ++j) {
             const int m = b0 + j;
             while (m >= next) {  // the walk leaves box `slot`: write its row
-                cplx<T>* out = mom + slot * NP3;
+                if (act) {
+                    cplx<T>* out = mom + slot * NP3 + lane * NP;
 #pragma unroll
-                for (int k = 0; k < KPL; ++k) {
-                    if (jz[k] < NP) out[lane + 32 * k] = sum[k];
-                    sum[k] = mk<T>(T(0), T(0));
+                    for (int i = 0; i < NP; ++i) out[i] = sum[i];
                 }
+#pragma unroll
+                for (int i = 0; i < NP; ++i) sum[i] = mk<T>(T(0), T(0));
                 ++slot;
                 next = a.bstart[slot + 1];
             }
-            T w[3][NP];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
+            T wx[NP], wy[NP], wz[NP];
+            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[0], j), wx);
+            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[1], j), wy);
+            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[2], j), wz);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+            const T wyz = pick<NP>(wy, jy) * pick<NP>(wz, jz);
+            const T cx = wyz * qx, cy = wyz * qy;
 #pragma unroll
-            for (int k = 0; k < KPL; ++k) {
-                if (jz[k] < NP) {
-                    const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
-                    sum[k].x += ww * qx;
-                    sum[k].y += ww * qy;
-                }
+            for (int i = 0; i < NP; ++i) {
+                sum[i].x += wx[i] * cx;
+                sum[i].y += wx[i] * cy;
             }
         }
     }
-    // the last box of the run
-    cplx<T>* out = mom + slot * NP3;
+    if (act) {
+        cplx<T>* out = mom + slot * NP3 + lane * NP;
 #pragma unroll
-    for (int k = 0; k < KPL; ++k)
-        if (jz[k] < NP) out[lane + 32 * k] = sum[k];
+        for (int i = 0; i < NP; ++i) out[i] = sum[i];
+    }
 }
 
-// Phase 2: one thread per grid node sums the moments of the boxes whose
-// (clamped) stencil covers it, in a fixed order (deterministic, no atomics).
-struct NodeArgs {
+// Phase 2: one warp per grid line (y, z) along x.  The line gathers the
+// moments of the (<= (P+1)^2 in the interior) box rows whose stencils cover
+// (y, z); each non-empty box of a row adds its P+1 contiguous moments
+// M_b(jz, jy, 0..P) at x = s_x(b)..s_x(b)+P of the line, kept in shared
+// memory.  No global atomics; every node written once.
+struct LineArgs {
     int n[3], nb[3];
-    const int* bslot;
+    const int* rsp;      // first slot of each box row
+    const int* blist;    // box id of each slot
 };
 
 template <int P>
-__device__ __forceinline__ void covering_boxes(int a, int n, int nb, int& lo, int& hi) {
+__device__ __forceinline__ int sclamp(int b, int n) {
     constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
-    lo = a <= P ? 0 : a - P + LO;
-    hi = a >= n - 1 - P ? nb - 1 : a + LO;
-    lo = max(lo, 0);
-    hi = min(hi, nb - 1);
+    return min(max(b - LO, 0), n - 1 - P);
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(256) node_gather_kernel(NodeArgs a, const cplx<T>* __restrict__ mom, cplx<T>* Q) {
+__global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __restrict__ mom, cplx<T>* Q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
-    constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
-    constexpr int RMAX = P + LO + 1;  // the widest covering range (clamped edge stencils)
-    const long long G = (long long)a.n[0] * a.n[1] * a.n[2];
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G; g += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(g % a.n[0]), y = (int)((g / a.n[0]) % a.n[1]), z = (int)(g / ((long long)a.n[0] * a.n[1]));
-        int lo[3], hi[3];
-        covering_boxes<P>(x, a.n[0], a.nb[0], lo[0], hi[0]);
-        covering_boxes<P>(y, a.n[1], a.nb[1], lo[1], hi[1]);
-        covering_boxes<P>(z, a.n[2], a.nb[2], lo[2], hi[2]);
-        cplx<T> acc = mk<T>(T(0), T(0));
-        // the covering range is at most RMAX boxes per axis except on small
-        // grids, where clamped stencils from both faces can cover a node:
-        // plain loops over z and y, unrolled chunks of RMAX along x
-        for (int bz = lo[2]; bz <= hi[2]; ++bz) {
-            const int jz = z - min(max(bz - LO, 0), a.n[2] - 1 - P);
-            if ((unsigned)jz > (unsigned)P) continue;
-            for (int by = lo[1]; by <= hi[1]; ++by) {
-                const int jy = y - min(max(by - LO, 0), a.n[1] - 1 - P);
-                if ((unsigned)jy > (unsigned)P) continue;
-                const int* rowslot = a.bslot + ((long long)bz * a.nb[1] + by) * a.nb[0];
-                for (int bx0 = lo[0]; bx0 <= hi[0]; bx0 += RMAX) {
-                    int sl[RMAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nx = a.n[0];
+    T* L = reinterpret_cast<T*>(smem_raw) + 2 * (size_t)wid * nx;
+    const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (line >= (long long)a.n[1] * a.n[2]) return;
+    const int y = (int)(line % a.n[1]), z = (int)(line / a.n[1]);
+    for (int i = lane; i < 2 * nx; i += 32) L[i] = T(0);
+    __syncwarp();
+    int ylo, yhi, zlo, zhi;
+    covering_boxes<P>(y, a.n[1], a.nb[1], ylo, yhi);
+    covering_boxes<P>(z, a.n[2], a.nb[2], zlo, zhi);
+    for (int bz = zlo; bz <= zhi; ++bz) {
+        const int jz = z - sclamp<P>(bz, a.n[2]);
+        if ((unsigned)jz > (unsigned)P) continue;
+        for (int by = ylo; by <= yhi; ++by) {
+            const int jy = y - sclamp<P>(by, a.n[1]);
+            if ((unsigned)jy > (unsigned)P) continue;
+            const long long r = (long long)bz * a.nb[1] + by;
+            const int s0 = a.rsp[r], s1 = a.rsp[r + 1];
+            for (int sb = s0; sb < s1; sb += 32) {
+                const int slot = sb + lane;
+                if (slot < s1) {
+                    const int bx = a.blist[slot] % a.nb[0];
+                    const int sx = sclamp<P>(bx, nx);
+                    const cplx<T>* src = mom + (long long)slot * NP3 + (jz * NP + jy) * NP;
+                    cplx<T> v[NP];
 #pragma unroll
-                    for (int ix = 0; ix < RMAX; ++ix) sl[ix] = bx0 + ix <= hi[0] ? __ldg(rowslot + bx0 + ix) : -1;
+                    for (int j = 0; j < NP; ++j) v[j] = src[j];
 #pragma unroll
-                    for (int ix = 0; ix < RMAX; ++ix) {
-                        const int bx = bx0 + ix;
-                        const int jx = x - min(max(bx - LO, 0), a.n[0] - 1 - P);
-                        if (sl[ix] < 0 || (unsigned)jx > (unsigned)P) continue;
-                        const cplx<T> v = mom[(long long)sl[ix] * NP3 + (jz * NP + jy) * NP + jx];
-                        acc.x += v.x;
-                        acc.y += v.y;
+                    for (int j = 0; j < NP; ++j) {
+                        atomicAdd(L + 2 * (sx + j), v[j].x);
+                        atomicAdd(L + 2 * (sx + j) + 1, v[j].y);
                     }
                 }
             }
         }
-        Q[g] = acc;
     }
+    __syncwarp();
+    cplx<T>* out = Q + ((long long)z * a.n[1] + y) * nx;
+    for (int x = lane; x < nx; x += 32) out[x] = mk<T>(L[2 * x], L[2 * x + 1]);
 }
 
 template <typename T, int P>
@@ -290,22 +299,20 @@ pim_status spread_two_phase(pim_plan P_, const cplx<T>* qs, cplx<T>* Q, cudaStre
     const PointsData& d = P_->pts;
     MomentArgs ma{};
     ma.nne = d.nne;
-    ma.N = d.N;
+    ma.nmw = d.nmw;
     ma.bstart = d.bstart;
+    ma.wbeg = d.wbeg;
     ma.nt = d.nt;
     ma.ntd = d.ntd;
-    // runs of boxes per warp: about 24 points each, at most 64 boxes
-    ma.slots_per_warp = (int)std::max<long long>(1, std::min<long long>(64, (24 * d.nne) / std::max<long long>(1, d.N)));
-    if (d.nne > 0) {
-        const long long warps = (d.nne + ma.slots_per_warp - 1) / ma.slots_per_warp;
-        moment_kernel<T, P><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
-    }
-    NodeArgs na{};
-    for (int i = 0; i < 3; ++i) { na.n[i] = P_->n[i]; na.nb[i] = P_->nb[i]; }
-    na.bslot = d.bslot;
-    const long long G = (long long)P_->n[0] * P_->n[1] * P_->n[2];
-    node_gather_kernel<T, P><<<(unsigned)std::min<long long>((G + 255) / 256, 152LL * 32), 256, 0, s>>>(
-        na, (const cplx<T>*)d.mom, Q);
+    if (d.nmw > 0) moment_kernel<T, P><<<(unsigned)((d.nmw * 32 + 255) / 256), 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
+    LineArgs la{};
+    for (int i = 0; i < 3; ++i) { la.n[i] = P_->n[i]; la.nb[i] = P_->nb[i]; }
+    la.rsp = d.rsp;
+    la.blist = d.blist;
+    const long long nlines = (long long)P_->n[1] * P_->n[2];
+    const size_t sm = 8 * 2 * sizeof(T) * (size_t)P_->n[0];
+    PIM_CK(cudaFuncSetAttribute(line_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    line_kernel<T, P><<<(unsigned)((nlines + 7) / 8), 256, sm, s>>>(la, (const cplx<T>*)d.mom, Q);
     PIM_CK(cudaGetLastError());
     return PIM_OK;
 }
@@ -959,8 +966,10 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         prof_mark(P, PIM_STAGE_GATHER, 0, s);
         if (N > 0) {
             const unsigned nb = (unsigned)((threads + 255) / 256);
+            if (P->tune_ev[0]) PIM_CK(cudaEventRecord(P->tune_ev[0], s));
             if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, s, ga, gA, ufar, qs, dst)) != PIM_OK)
                 return st;
+            if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], s));
         }
         PIM_CK(cudaGetLastError());
         prof_mark(P, PIM_STAGE_GATHER, 1, s);
@@ -1126,9 +1135,8 @@ pim_status apply_autotune(pim_plan P, cudaStream_t s) {
     if ((st = pim_alloc(P, &q, bytes)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &u, bytes)) != PIM_OK) return st;
     PIM_CK(cudaMemsetAsync(q, 0, bytes, s));
-    cudaEvent_t e0, e1;
-    PIM_CK(cudaEventCreate(&e0));
-    PIM_CK(cudaEventCreate(&e1));
+    PIM_CK(cudaEventCreate(&P->tune_ev[0]));
+    PIM_CK(cudaEventCreate(&P->tune_ev[1]));
     float best = 1e30f;
     int bestv = 0;
     const bool prof = P->prof_on;
@@ -1137,23 +1145,25 @@ pim_status apply_autotune(pim_plan P, cudaStream_t s) {
     for (int v = 0; v < GATHER_VARIANTS; ++v) {
         P->gather_variant = v;
         if ((st = apply_run(P, q, u, 1, false, s)) != PIM_OK) return st;  // warm-up
-        PIM_CK(cudaEventRecord(e0, s));
-        for (int r = 0; r < 2; ++r)
+        float tot = 0.f;
+        for (int r = 0; r < 3; ++r) {
             if ((st = apply_run(P, q, u, 1, false, s)) != PIM_OK) return st;
-        PIM_CK(cudaEventRecord(e1, s));
-        PIM_CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        PIM_CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
+            PIM_CK(cudaEventSynchronize(P->tune_ev[1]));
+            float ms = 0.f;
+            PIM_CK(cudaEventElapsedTime(&ms, P->tune_ev[0], P->tune_ev[1]));
+            tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
             bestv = v;
         }
     }
+    cudaEventDestroy(P->tune_ev[0]);
+    cudaEventDestroy(P->tune_ev[1]);
+    P->tune_ev[0] = P->tune_ev[1] = nullptr;
     P->prof_on = prof;
     P->launches = launches;
     P->gather_variant = bestv;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     pim_free(P, q, bytes);
     pim_free(P, u, bytes);
     return PIM_OK;

@@ -155,6 +155,10 @@ struct PointsData {
     int* bslot = nullptr;         // nboxes: compact index of a non-empty box, -1 if empty
     int* blist = nullptr;         // nne: box id of each non-empty box (box order)
     int* bstart = nullptr;        // nne + 1: first sorted point of each non-empty box
+    int* rsp = nullptr;           // nrows + 1: first slot of each box row (y, z)
+    long long nrows = 0;
+    int* wbeg = nullptr;          // nmw + 1: first slot of each moment-kernel warp
+    long long nmw = 0;
     int64_t nne = 0;              // non-empty boxes
     void* mom = nullptr;          // nne x (p+1)^3 box moments, complex<T> (apply scratch)
     int64_t* row_ptr = nullptr;   // N + 1
@@ -218,6 +222,7 @@ struct pim_plan_s {
     unsigned char prof_mask[512];    // stages recorded per ring slot
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // around the gather launch while autotuning
     int autotune = 1;
     int with_gradient = 0;
     void* gD = nullptr;           // second full grid (adjoint potential of the gradient)

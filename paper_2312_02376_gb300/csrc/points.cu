@@ -145,6 +145,26 @@ __global__ void box_slots_kernel(const int* flag, const int* pos, const int* box
     }
 }
 
+// first slot of each box row (box rows are runs of nb_x boxes along x)
+__global__ void row_slots_kernel(const int* pos, long long nrows, int nbx, int* rsp) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r <= nrows;
+         r += (long long)gridDim.x * blockDim.x)
+        rsp[r] = pos[r * nbx];
+}
+
+// warp boundaries of the moment kernel: a warp starts at every slot whose
+// first point crosses a multiple of K points (work balanced by points)
+__global__ void warp_flags_kernel(const int* bstart, long long nne, int K, int* flag) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x)
+        flag[s] = (s == 0 || bstart[s] / K != bstart[s - 1] / K) ? 1 : 0;
+}
+
+__global__ void warp_begin_kernel(const int* flag, const int* pos, long long nne, int* wbeg) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x)
+        if (flag[s]) wbeg[pos[s]] = (int)s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) wbeg[pos[nne]] = (int)nne;
+}
+
 // order each box's points by caller index (deterministic layout)
 __global__ void sort_boxes_kernel(const int* box_ptr, long long nboxes, int* slot) {
     for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nboxes;
@@ -609,6 +629,8 @@ void points_free(pim_plan P) {
     pim_free(P, d.bslot, nboxes * sizeof(int));
     pim_free(P, d.blist, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
     pim_free(P, d.bstart, (size_t)(d.nne + 1) * sizeof(int));
+    pim_free(P, d.rsp, (size_t)(d.nrows + 1) * sizeof(int));
+    pim_free(P, d.wbeg, (size_t)(d.nmw + 1) * sizeof(int));
     {
         const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
         const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
@@ -676,7 +698,23 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
         const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
         if ((st = pim_alloc(P, &d.mom, (size_t)std::max(1, nne) * np3 * ge)) != PIM_OK) return st;
+        // row slot pointers
+        d.nrows = (long long)P->nb[1] * P->nb[2];
+        if ((st = pim_alloc(P, (void**)&d.rsp, (d.nrows + 1) * sizeof(int))) != PIM_OK) return st;
+        row_slots_kernel<<<256, 256, 0, s>>>(pos, d.nrows, P->nb[0], d.rsp);
+        // point-balanced warp boundaries for the moment kernel
+        int* wpos = nullptr;
+        if ((st = pim_alloc(P, (void**)&wpos, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
+        if (nne > 0) warp_flags_kernel<<<1024, 256, 0, s>>>(d.bstart, nne, 32, cursor);
+        if ((st = scan<int>(P, cursor, wpos, nne, s)) != PIM_OK) return st;
+        int nwarps = 0;
+        PIM_CK(cudaMemcpy(&nwarps, wpos + nne, sizeof(int), cudaMemcpyDeviceToHost));
+        d.nmw = nwarps;
+        if ((st = pim_alloc(P, (void**)&d.wbeg, (size_t)(nwarps + 1) * sizeof(int))) != PIM_OK) return st;
+        warp_begin_kernel<<<1024, 256, 0, s>>>(cursor, wpos, nne, d.wbeg);
+        PIM_CK(cudaGetLastError());
         PIM_CK(cudaStreamSynchronize(s));
+        pim_free(P, wpos, (size_t)(nne + 1) * sizeof(int));
         pim_free(P, pos, (nboxes + 1) * sizeof(int));
     }
     // per-point data in sorted order
