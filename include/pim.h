@@ -232,6 +232,25 @@ pim_status pim_position_grad(pim_plan plan, const void* q, const void* g, double
 pim_status pim_update_positions(pim_plan plan, const double* xyz);
 
 /*
+ * pim_apply_batched -- u_i = A_i q_i (adjoint = 0) or A_i^H q_i (adjoint != 0)
+ * for nplans plans -- several point sets, each with its own cell, grid and
+ * kernel -- with nrhs right-hand sides each, as one unit of work.  The first
+ * call with a given argument set (the plans, the q_i and u_i pointers, nrhs,
+ * adjoint) is captured into a CUDA graph in which every plan's apply runs on
+ * the plan's own stream, forked from and joined back to `stream`; identical
+ * later calls replay that graph with a single launch.  Not part of the paper.
+ *   plans, q, u  arrays of nplans entries; q[i], u[i] device pointers laid out
+ *                as for pim_apply; a plan may appear only once.
+ *   stream       cudaStream_t; NULL uses a library stream and synchronises.
+ * The graphs of a plan are dropped by pim_set_points and pim_destroy (after
+ * pim_update_positions a replay uses the new values, which are rewritten in
+ * place).  Several right-hand sides (2..128) stream each plan's correction
+ * list once for all of them.
+ */
+pim_status pim_apply_batched(int nplans, pim_plan const* plans, const void* const* q, void* const* u, int nrhs,
+                             int adjoint, void* stream);
+
+/*
  * pim_apply_noalloc -- pim_apply (adjoint = 0) or pim_apply_adjoint
  * (adjoint != 0) that allocates nothing: the per-call scratch of the apply
  * (sorted sources, box moments, the three grid work buffers, the far-zone

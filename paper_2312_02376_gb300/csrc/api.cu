@@ -115,6 +115,7 @@ const char* pim_status_string(pim_status s) {
 void pim_destroy(pim_plan P) {
     if (!P) return;
     cudaDeviceSynchronize();
+    batch_forget(P);
     points_free(P);
     const size_t ge = grid_elem(P);
     const long long G = (long long)P->n[0] * P->n[1] * P->n[2];
@@ -134,6 +135,8 @@ void pim_destroy(pim_plan P) {
         pim_free(P, P->fpart, (size_t)P->far_chunks * Gf * ge);
     }
     free_grad_buffers(P);
+    pim_free(P, P->qsall, P->qsall_bytes);
+    pim_free(P, P->dmeans, 2 * 128 * sizeof(double));
     pim_free(P, P->tw32, 2048 * sizeof(float2));
     pim_free(P, P->tw64, 2048 * sizeof(double2));
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
@@ -144,6 +147,7 @@ void pim_destroy(pim_plan P) {
         delete[] P->prof_ev;
     }
     if (P->s_far) cudaStreamDestroy(P->s_far);
+    if (P->s_main) cudaStreamDestroy(P->s_main);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     delete P;
@@ -264,6 +268,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     cudaStream_t s = (cudaStream_t)stream;
     pim_status st;
     if (cudaStreamCreateWithFlags(&P->s_far, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&P->s_main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -321,9 +326,13 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     }
     const double t0 = now_ms();
     cudaDeviceSynchronize();
+    batch_forget(P);
     const size_t ge = grid_elem(P);
     if (P->pts.N > 0 || P->pts.box_ptr) {
         free_grad_buffers(P);
+        pim_free(P, P->qsall, P->qsall_bytes);
+        P->qsall = nullptr;
+        P->qsall_bytes = 0;
         pim_free(P, P->qs, (size_t)P->pts.N * ge);
         pim_free(P, P->us, (size_t)P->pts.N * ge);
         P->qs = P->us = nullptr;

@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
     // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  Each lane takes UNR entries
     // per trip, issuing all column and value loads (streaming, read once)
     // before the dependent source loads.
-    const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
+    const long long r0 = CM < 0 ? 0 : a.row_ptr[m], r1 = CM < 0 ? 0 : a.row_ptr[m + 1];
     const double cs = a.adj ? -1.0 : 1.0;
     double2 accd = make_double2(0.0, 0.0);
     if (CM == PIM_CORR_FP64) {
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
         }
         accd.x += (double)rh + (double)rl;
         accd.y += (double)ih + (double)il;
-    } else {
+    } else if (CM == PIM_CORR_FP32) {
         float ar = 0.f, ai = 0.f;
         const float fs = (float)cs;
         for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
@@ -823,6 +823,137 @@ __global__ void unpermute_kernel(const cplx<T>* us, const int* perm, long long N
     }
 }
 
+// ------------------------------- multi-RHS correction ----------------------
+// u[perm[m]][r] += sum_row exp(-j k0.(i o L)) d q_n[r] (conj(d) for the
+// adjoint) for every right-hand side r: one warp per sorted row, lanes over
+// right-hand sides; each entry's column and value are loaded once (broadcast)
+// and used for all right-hand sides, the sources q_n[0..R) are one coalesced
+// row.  Accumulation as in the single-RHS kernel (FP64, double-float or FP32).
+struct CorrMultiArgs {
+    long long N;
+    int nrhs, adj, self_img, real_out;
+    const int* perm;
+    const int64_t* row_ptr;
+    const uint32_t* col;
+    const double2* val;
+    const float4* valdf;
+    const float2* valf;
+    const double2* phase;
+};
+
+template <typename T, int CM, int RPL>
+__global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const cplx<T>* __restrict__ qsall, void* out) {
+    const int lane = threadIdx.x & 31;
+    const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (m >= a.N) return;
+    const int R = a.nrhs;
+    double2 acc[RPL];
+    float rh[RPL], rl[RPL], ih[RPL], il[RPL];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        acc[k] = make_double2(0.0, 0.0);
+        rh[k] = rl[k] = ih[k] = il[k] = 0.f;
+    }
+    const double cs = a.adj ? -1.0 : 1.0;
+    for (long long q = a.row_ptr[m]; q < a.row_ptr[m + 1]; ++q) {
+        const uint32_t c = __ldg(a.col + q);
+        const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+        const cplx<T>* xr = qsall + (long long)n * R;
+        if (CM == PIM_CORR_DOUBLE_FLOAT && ii == a.self_img) {
+            const float4 d = __ldg(a.valdf + q);
+            const float fs = (float)cs, dih = fs * d.z, dil = fs * d.w;
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int r = lane + 32 * k;
+                if (r >= R) break;
+                const cplx<T> xv = xr[r];
+                const float x_r = (float)xv.x, x_i = (float)xv.y;
+                const float p1 = d.x * x_r, e1 = fmaf(d.x, x_r, -p1);
+                const float p2 = dih * x_i, e2 = fmaf(dih, x_i, -p2);
+                const float p3 = d.x * x_i, e3 = fmaf(d.x, x_i, -p3);
+                const float p4 = dih * x_r, e4 = fmaf(dih, x_r, -p4);
+                two_sum_acc(rh[k], rl[k], p1);
+                two_sum_acc(rh[k], rl[k], -p2);
+                two_sum_acc(ih[k], il[k], p3);
+                two_sum_acc(ih[k], il[k], p4);
+                rl[k] += (e1 - e2) + (d.y * x_r - dil * x_i);
+                il[k] += (e3 + e4) + (d.y * x_i + dil * x_r);
+            }
+        } else if (CM == PIM_CORR_FP32) {
+            const float2 d = __ldg(a.valf + q);
+            float2 dd = make_float2(d.x, (float)cs * d.y);
+            if (ii != a.self_img) {
+                const double2 ph = a.phase[ii];
+                dd = make_float2((float)ph.x * dd.x - (float)ph.y * dd.y, (float)ph.x * dd.y + (float)ph.y * dd.x);
+            }
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int r = lane + 32 * k;
+                if (r >= R) break;
+                const cplx<T> xv = xr[r];
+                rh[k] += dd.x * (float)xv.x - dd.y * (float)xv.y;
+                ih[k] += dd.x * (float)xv.y + dd.y * (float)xv.x;
+            }
+        } else {
+            // FP64 values (also the non-self images of the double-float mode)
+            double2 d;
+            if (CM == PIM_CORR_DOUBLE_FLOAT) {
+                const float4 v = __ldg(a.valdf + q);
+                d = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+            } else {
+                d = __ldg(a.val + q);
+            }
+            d.y *= cs;
+            if (ii != a.self_img) d = cmul(a.phase[ii], d);
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) {
+                const int r = lane + 32 * k;
+                if (r >= R) break;
+                const cplx<T> xv = xr[r];
+                acc[k].x += d.x * (double)xv.x - d.y * (double)xv.y;
+                acc[k].y += d.x * (double)xv.y + d.y * (double)xv.x;
+            }
+        }
+    }
+    const long long o = (long long)a.perm[m] * R;
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        const int r = lane + 32 * k;
+        if (r >= R) break;
+        const double re = acc[k].x + (double)rh[k] + (double)rl[k];
+        const double im = acc[k].y + (double)ih[k] + (double)il[k];
+        if (a.real_out) {
+            T* u = (T*)out + o + r;
+            *u = (T)((double)*u + re);
+        } else {
+            cplx<T>* u = (cplx<T>*)out + o + r;
+            cplx<T> v = *u;
+            v.x = (T)((double)v.x + re);
+            v.y = (T)((double)v.y + im);
+            *u = v;
+        }
+    }
+}
+
+// qsall[m][r] = q[perm[m]][r] - mean[r] for all right-hand sides
+template <typename T, bool REAL>
+__global__ void permute_all_kernel(const void* q, const int* perm, long long N, int nrhs, const double* means,
+                                   cplx<T>* qsall) {
+    const long long tot = N * nrhs;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const long long m = e / nrhs;
+        const int r = (int)(e % nrhs);
+        const double2 v = load_val<T, REAL>(q, (long long)perm[m] * nrhs + r);
+        const double mr = means ? means[2 * r] : 0.0, mi = means ? means[2 * r + 1] : 0.0;
+        qsall[e] = mk<T>((T)(v.x - mr), (T)(v.y - mi));
+    }
+}
+
+__global__ void copy_mean_kernel(const double* src, double* dst) {
+    dst[0] = src[0];
+    dst[1] = src[1];
+}
+
 // ------------------------------- driver ------------------------------------
 // Launch-shape variants of the gather kernel, chosen per plan by the
 // autotuner: (unroll depth of the correction loop, minimum resident CTAs).
@@ -845,6 +976,7 @@ pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs
 template <typename T, int PP>
 pim_status launch_gather(int cm, int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
                          const cplx<T>* uf, const cplx<T>* qs, void* dst) {
+    if (cm < 0) return launch_gather_cm<T, PP, -1>(0, nb, s, ga, U, uf, qs, dst);
     if (sizeof(T) == 8) return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
     if (cm == PIM_CORR_DOUBLE_FLOAT) return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
     if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);
@@ -871,6 +1003,20 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
     cplx<T>* qs = (cplx<T>*)P->qs;
     cplx<T>* gA = (cplx<T>*)P->gA;
     pim_status st;
+    // several right-hand sides: the per-RHS gathers skip the correction and one
+    // multi-RHS kernel adds it for all of them (the list is streamed once)
+    const bool multi = nrhs > 1 && nrhs <= 128 && !P->no_multi && !(P->npsp && adj) && N > 0;
+    if (multi) {
+        const size_t need = (size_t)N * nrhs * sizeof(cplx<T>);
+        if (P->qsall_bytes < need) {
+            pim_free(P, P->qsall, P->qsall_bytes);
+            P->qsall = nullptr;
+            P->qsall_bytes = 0;
+            if ((st = pim_alloc(P, &P->qsall, need)) != PIM_OK) return st;
+            P->qsall_bytes = need;
+        }
+        if (!P->dmeans && (st = pim_alloc(P, (void**)&P->dmeans, 2 * 128 * sizeof(double))) != PIM_OK) return st;
+    }
     for (int r = 0; r < nrhs; ++r) {
         prof_mark(P, PIM_STAGE_APPLY, 0, s);
         prof_mark(P, PIM_STAGE_PERMUTE, 0, s);
@@ -879,6 +1025,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         if (P->npsp && !adj) {
             if ((st = mean_of<T>(P, q, false, N, nrhs, r, true, s)) != PIM_OK) return st;
             mean = P->dsum;
+            if (multi) copy_mean_kernel<<<1, 1, 0, s>>>(P->dsum, P->dmeans + 2 * r);
         }
         if (P->real_data) permute_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
         else permute_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
@@ -937,7 +1084,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ga.N = N;
         ga.nrhs = nrhs;
         ga.r = r;
-        ga.cmode = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
+        ga.cmode = multi ? -1 : (sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode);
         ga.adj = adj ? 1 : 0;
         ga.has_far = P->has_far ? 1 : 0;
         ga.real_out = P->real_data ? 1 : 0;
@@ -983,6 +1130,41 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         }
         prof_mark(P, PIM_STAGE_APPLY, 1, s);
         if (P->prof_on && P->prof_next < pim_plan_s::PROF_RING) P->prof_next++;
+    }
+    if (multi) {
+        cplx<T>* qsall = (cplx<T>*)P->qsall;
+        const double* means = (P->npsp && !adj) ? P->dmeans : nullptr;
+        if (P->real_data) permute_all_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, means, qsall);
+        else permute_all_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, means, qsall);
+        CorrMultiArgs ca{};
+        ca.N = N;
+        ca.nrhs = nrhs;
+        ca.adj = adj ? 1 : 0;
+        ca.self_img = -1;
+        for (int i = 0; i < P->nimg; ++i)
+            if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) ca.self_img = i;
+        ca.real_out = P->real_data ? 1 : 0;
+        ca.perm = d.perm;
+        ca.row_ptr = d.row_ptr;
+        ca.col = d.col;
+        ca.val = d.val;
+        ca.valdf = d.valdf;
+        ca.valf = d.valf;
+        ca.phase = P->dphase;
+        const int cm = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
+        const unsigned nb = (unsigned)((N * 32 + 255) / 256);
+#define PIM_CM_LAUNCH(CMV)                                                                                   \
+    do {                                                                                                     \
+        if (nrhs <= 32) corr_multi_kernel<T, CMV, 1><<<nb, 256, 0, s>>>(ca, qsall, u);                      \
+        else if (nrhs <= 64) corr_multi_kernel<T, CMV, 2><<<nb, 256, 0, s>>>(ca, qsall, u);                 \
+        else corr_multi_kernel<T, CMV, 4><<<nb, 256, 0, s>>>(ca, qsall, u);                                 \
+    } while (0)
+        if (cm == PIM_CORR_DOUBLE_FLOAT) PIM_CM_LAUNCH(PIM_CORR_DOUBLE_FLOAT);
+        else if (cm == PIM_CORR_FP32) PIM_CM_LAUNCH(PIM_CORR_FP32);
+        else PIM_CM_LAUNCH(PIM_CORR_FP64);
+#undef PIM_CM_LAUNCH
+        PIM_CK(cudaGetLastError());
+        P->launches += 2;
     }
     return PIM_OK;
 }
@@ -1121,6 +1303,26 @@ pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int 
 pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {
     if (P->prec == PIM_FP64) return debug_spread_p<double>(P, out, s);
     return debug_spread_p<float>(P, out, s);
+}
+
+// Allocates what an apply with these arguments would allocate on first use
+// (the multi-RHS source buffer), so that the apply itself can be captured.
+pim_status apply_prepare(pim_plan P, int nrhs, bool adj) {
+    const long long N = P->pts.N;
+    const bool multi = nrhs > 1 && nrhs <= 128 && !P->no_multi && !(P->npsp && adj) && N > 0;
+    if (!multi) return PIM_OK;
+    pim_status st;
+    const size_t el = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t need = (size_t)N * nrhs * el;
+    if (P->qsall_bytes < need) {
+        pim_free(P, P->qsall, P->qsall_bytes);
+        P->qsall = nullptr;
+        P->qsall_bytes = 0;
+        if ((st = pim_alloc(P, &P->qsall, need)) != PIM_OK) return st;
+        P->qsall_bytes = need;
+    }
+    if (!P->dmeans && (st = pim_alloc(P, (void**)&P->dmeans, 2 * 128 * sizeof(double))) != PIM_OK) return st;
+    return PIM_OK;
 }
 
 // Times every gather variant on a forward apply of zero sources and keeps

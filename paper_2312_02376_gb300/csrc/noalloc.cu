@@ -115,7 +115,10 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         P->fB = (double2*)ptrs[8];
         P->fC = (double2*)ptrs[9];
     }
+    const bool no_multi = P->no_multi;
+    P->no_multi = true;  // the multi-RHS path would allocate its source buffer
     const pim_status st = apply_run(P, q, u, nrhs, adjoint != 0, (cudaStream_t)stream);
+    P->no_multi = no_multi;
     P->qs = save[0];
     P->us = save[1];
     P->gA = save[2];

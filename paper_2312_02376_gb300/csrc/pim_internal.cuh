@@ -223,6 +223,10 @@ struct pim_plan_s {
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // around the gather launch while autotuning
+    void* qsall = nullptr;        // sorted sources of every right-hand side (multi-RHS correction)
+    size_t qsall_bytes = 0;
+    double* dmeans = nullptr;     // per-RHS means (neutral static case), 2 x 128
+    bool no_multi = false;        // keep the fused per-RHS path (set by pim_apply_noalloc)
     int autotune = 1;
     int with_gradient = 0;
     void* gD = nullptr;           // second full grid (adjoint potential of the gradient)
@@ -231,6 +235,7 @@ struct pim_plan_s {
     void* fU = nullptr;           // far potentials in plan precision (gradient)
     void* fV = nullptr;
     // streams and events
+    cudaStream_t s_main = nullptr;  // the plan's own stream inside a batched graph
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double plan_ms = 0, points_ms = 0;
@@ -268,4 +273,8 @@ pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint,
 pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
 pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
+pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
+
+// batch.cu
+void batch_forget(pim_plan P);
 int pim_fft_len(int n);

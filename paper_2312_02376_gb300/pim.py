@@ -23,7 +23,7 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32 = 0, 1, 2
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
            "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
            "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_update_positions", "pim_apply_noalloc",
-           "pim_debug_copy", "pim_destroy"]
+           "pim_apply_batched", "pim_debug_copy", "pim_destroy"]
 STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
 
@@ -94,6 +94,8 @@ def load(path=LIB_PATH):
     lib.pim_position_grad.restype = i32
     lib.pim_update_positions.argtypes = [vp, vp]
     lib.pim_update_positions.restype = i32
+    lib.pim_apply_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32, vp]
+    lib.pim_apply_batched.restype = i32
     lib.pim_apply_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
     lib.pim_apply_noalloc.restype = i32
     lib.pim_debug_copy.argtypes = [vp, i32, vp, ctypes.c_size_t]
@@ -199,6 +201,17 @@ def pim_position_grad(plan, q, g, grad_xyz, nrhs=1, stream=None):
 
 def pim_update_positions(plan, xyz):
     _check(load().pim_update_positions(plan, _ptr(xyz)), "pim_update_positions")
+
+
+def pim_apply_batched(plans, qs, us, nrhs=1, adjoint=False, stream=None):
+    """plans: list of Plan or handles; qs, us: lists of device tensors."""
+    n = len(plans)
+    hs = [p._h if isinstance(p, Plan) else p for p in plans]
+    P = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in hs])
+    Q = (ctypes.c_void_p * n)(*[_ptr(x).value for x in qs])
+    U = (ctypes.c_void_p * n)(*[_ptr(x).value for x in us])
+    _check(load().pim_apply_batched(n, P, Q, U, int(nrhs), 1 if adjoint else 0, _stream_ptr(stream)),
+           "pim_apply_batched")
 
 
 def pim_apply_noalloc(plan, q, u, nrhs=1, adjoint=False, stream=None):
