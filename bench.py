@@ -323,6 +323,116 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """16 point sets x 64 right-hand sides, one captured graph per direction."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2312_02376_gb300 import inputs, pim
+    torch.cuda.set_device(0)
+    sets = inputs.helmholtz1d_batch()
+    plans, qs, us, ws = [], [], [], []
+    t0 = time.perf_counter()
+    for W in sets:
+        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, pf=W.pf,
+                      corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
+        pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+        plans.append(pl)
+        qs.append(torch.tensor(W.q, device="cuda"))
+        us.append(torch.empty_like(qs[-1]))
+        ws.append(torch.empty_like(qs[-1]))
+    t_plan = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    R = sets[0].nrhs
+
+    def step():
+        pim.pim_apply_batched(plans, qs, us, R, False, stream)
+        pim.pim_apply_batched(plans, us, ws, R, True, stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clk = ClockSampler(0)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    ms = float(np.mean(times))
+    NT = sum(W.N for W in sets)
+    nnz = sum(pl.info().nnz for pl in plans)
+    out = {"metric": METRIC, "value": round(2.0 * NT * R / (ms * 1e-3) / 1e6, 3), "unit": "Mpts/s (x RHS)",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+           "data": "synthetic",
+           "config": {"workload": "helmholtz1d_batch", "sets": len(sets), "N_total": NT, "nrhs": R,
+                      "nnz_total": int(nnz), "corr_radius_steps": sets[0].b, "set_points_s": round(t_plan, 1),
+                      "graph": "one captured graph per direction, replayed"},
+           "clocks": clocks}
+    for pl in plans:
+        pl.close()
+    return out
+
+
+def run_coulomb_grad(args):
+    """Differentiated 3D Coulomb, N = 1e6, 256^3, FP32 bulk: forward,
+    adjoint and position gradient per step."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2312_02376_gb300 import inputs, pim
+    torch.cuda.set_device(0)
+    W = inputs.coulomb3d_big()
+    t0 = time.perf_counter()
+    pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
+                  pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT, with_gradient=True)
+    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    t_plan = time.perf_counter() - t0
+    q = torch.tensor(W.q, device="cuda")
+    u = torch.empty_like(q)
+    w = torch.empty_like(q)
+    gx = torch.empty((W.N, 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pim.pim_apply(pl._h, q, u, 1, stream)
+        pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
+        pim.pim_position_grad(pl._h, q, u, gx, 1, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pl.set_profiling(True)
+    clk = ClockSampler(0)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    stage_ms, nap = pl.stage_times()
+    ms = float(np.mean(times))
+    out = {"metric": METRIC, "value": round(2.0 * W.N / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "coulomb3d_1m", "N": W.N, "grid": list(W.n), "nnz": int(pl.info().nnz),
+                      "corr_radius_steps": W.b, "step": "forward + adjoint + position gradient",
+                      "set_points_s": round(t_plan, 1)},
+           "stages_ms_per_apply": {k: round(v / max(1, nap), 4) for k, v in stage_ms.items()},
+           "clocks": clocks}
+    pl.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,12 +440,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "helmholtz2d_65k"],
-                    help="helmholtz2d_65k: the same recipe, smaller, for profiler captures")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "helmholtz2d_65k", "helmholtz1d_batch", "coulomb3d_1m"],
+                    help="helmholtz2d_65k: the same recipe, smaller, for profiler captures; "
+                         "helmholtz1d_batch: 16 sets x 64 right-hand sides, batched graph; "
+                         "coulomb3d_1m: forward + adjoint + position gradient")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "helmholtz1d_batch":
+        print(json.dumps(run_batch(args)))
+        return
+    if args.workload == "coulomb3d_1m":
+        print(json.dumps(run_coulomb_grad(args)))
         return
     rank, world, result = run_gpu(args)
     if rank == 0:

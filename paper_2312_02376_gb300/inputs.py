@@ -94,6 +94,46 @@ def helmholtz2d(N=262144, n=(128, 128, 64), index=1, salt=0, b=4, nf=(21, 21, 11
                     tuple(n), 4, 1, b, tuple(nf), 4, "fp32", N, 1, pts, q.astype(np.complex64))
 
 
+def helmholtz1d_set(N, index=2, salt=0, b=2, nrhs=64, rng=None):
+    """One point set of the batched 1D-periodic Helmholtz workload: cell
+    1 x 0.25 x 0.25, periodic along z (L_z = 0.25), k = 2 pi 0.5, no phase
+    shift; half the points uniform, half in 8 Gaussian clusters (sigma 0.02,
+    centres uniform, wrapped along z, redrawn if outside the cell in x or y);
+    grid step (V/N)^(1/3) (about one point per node); nrhs CN(0,1) sources."""
+    rng = rng if rng is not None else _rng(index, salt)
+    D = np.array([1.0, 0.25, 0.25])
+    nu = N // 2
+    uni = rng.random((nu, 3)) * D
+    centres = rng.random((8, 3)) * D
+    rest = N - nu
+    per = np.full(8, rest // 8)
+    per[: rest - per.sum()] += 1
+    cl = []
+    for c, cnt in zip(centres, per):
+        pts = c + 0.02 * rng.standard_normal((cnt, 3))
+        bad = np.any((pts[:, :2] < 0) | (pts[:, :2] >= D[:2]), axis=1)
+        while bad.any():
+            pts[bad] = c + 0.02 * rng.standard_normal((int(bad.sum()), 3))
+            bad = np.any((pts[:, :2] < 0) | (pts[:, :2] >= D[:2]), axis=1)
+        pts[:, 2] = np.mod(pts[:, 2], D[2])
+        cl.append(pts)
+    pts = np.concatenate([uni] + cl)
+    h = (np.prod(D) / N) ** (1.0 / 3.0)
+    n = tuple(int(max(5, round(D[d] / h) + 1)) for d in range(3))
+    q = _cn(rng, (N, nrhs)).astype(np.complex64)
+    k = 2 * np.pi * 0.5
+    return Workload("helmholtz1d_%d" % N, tuple(D), (2,), k, (0.0, 0.0, 0.0), n, 4, 1, b,
+                    (0, 0, 0), 4, "fp32", N, nrhs, pts, q)
+
+
+def helmholtz1d_batch(nsets=16, Nmin=10_000, Nmax=500_000, index=2, salt=0, b=2, nrhs=64):
+    """The batched workload: nsets point sets with N log-uniform in
+    [Nmin, Nmax] (helmholtz1d_set each)."""
+    rng = _rng(index, salt)
+    Ns = np.floor(np.exp(rng.uniform(np.log(Nmin), np.log(Nmax), nsets))).astype(np.int64)
+    return [helmholtz1d_set(int(N), b=b, nrhs=nrhs, rng=rng) for N in Ns]
+
+
 def coulomb3d_big(N=1_000_000, n=256, index=3, salt=0, b=5, nf=10):
     rng = _rng(index, salt)
     pts = rng.random((N, 3))
