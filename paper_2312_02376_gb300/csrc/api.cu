@@ -140,7 +140,7 @@ void pim_destroy(pim_plan P) {
     pim_free(P, P->tw32, 2048 * sizeof(float2));
     pim_free(P, P->tw64, 2048 * sizeof(double2));
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
-    pim_free(P, P->dphase, sizeof(double2) * PIM_MAX_IMAGES);
+    pim_free(P, P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES);
     pim_free(P, P->dstatus, sizeof(int));
     if (P->prof_ev) {
         for (int i = 0; i < pim_plan_s::PROF_RING * PIM_NUM_STAGES * 2; ++i) cudaEventDestroy(P->prof_ev[i]);
@@ -277,9 +277,17 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     }
     if ((st = pim_alloc(P, (void**)&P->dstatus, sizeof(int))) != PIM_OK) return fail(st);
     if ((st = pim_alloc(P, (void**)&P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS))) != PIM_OK) return fail(st);
-    if ((st = pim_alloc(P, (void**)&P->dphase, sizeof(double2) * PIM_MAX_IMAGES)) != PIM_OK) return fail(st);
+    if ((st = pim_alloc(P, (void**)&P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES)) != PIM_OK)
+        return fail(st);
+    P->dphasedf = reinterpret_cast<float4*>(P->dphase + PIM_MAX_IMAGES);
+    float4 phdf[PIM_MAX_IMAGES];
+    for (int i = 0; i < P->nimg; ++i) {
+        const float rh = (float)P->phase[i].x, ih = (float)P->phase[i].y;
+        phdf[i] = make_float4(rh, (float)(P->phase[i].x - (double)rh), ih, (float)(P->phase[i].y - (double)ih));
+    }
     if (cudaMemset(P->dstatus, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemcpy(P->dphase, P->phase, sizeof(double2) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(P->dphase, P->phase, sizeof(double2) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->dphasedf, phdf, sizeof(float4) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess) {
         pim_set_error("initial copies failed");
         return fail(PIM_ERR_CUDA);
     }

@@ -483,6 +483,7 @@ struct GatherArgs {
     const float4* valdf;
     const float2* valf;
     const double2* phase;
+    const float4* phasedf;
 };
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
@@ -492,9 +493,146 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
     hi = s;
 }
 
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Double-float complex numbers are float4 (re hi, re lo, im hi, im lo).
+// (rh + rl) + j (ih + il) += d x for a double-float d and an FP32 x, with the
+// four leading products split exactly by fma and the rest in FP32.
+__device__ __forceinline__ void df_cmac(float& rh, float& rl, float& ih, float& il, const float4 d, float xr,
+                                        float xi) {
+    const float p1 = d.x * xr, e1 = fmaf(d.x, xr, -p1);
+    const float p2 = d.z * xi, e2 = fmaf(d.z, xi, -p2);
+    const float p3 = d.x * xi, e3 = fmaf(d.x, xi, -p3);
+    const float p4 = d.z * xr, e4 = fmaf(d.z, xr, -p4);
+    two_sum_acc(rh, rl, p1);
+    two_sum_acc(rh, rl, -p2);
+    two_sum_acc(ih, il, p3);
+    two_sum_acc(ih, il, p4);
+    rl += (e1 - e2) + (d.y * xr - d.w * xi);
+    il += (e3 + e4) + (d.y * xi + d.w * xr);
+}
+
+// p d for double-float p and d (the image phase times a correction value),
+// rounded back to a normalised double-float pair per component.
+__device__ __forceinline__ float4 df_cmul(const float4 p, const float4 d) {
+    float s, e;
+    float4 r;
+    const float p1 = p.x * d.x, e1 = fmaf(p.x, d.x, -p1);
+    const float p2 = p.z * d.z, e2 = fmaf(p.z, d.z, -p2);
+    two_sum(p1, -p2, s, e);
+    two_sum(s, e + (e1 - e2) + (fmaf(p.x, d.y, p.y * d.x) - fmaf(p.z, d.w, p.w * d.z)), r.x, r.y);
+    const float p3 = p.x * d.z, e3 = fmaf(p.x, d.z, -p3);
+    const float p4 = p.z * d.x, e4 = fmaf(p.z, d.x, -p4);
+    two_sum(p3, p4, s, e);
+    two_sum(s, e + (e3 + e4) + (fmaf(p.x, d.w, p.y * d.z) + fmaf(p.z, d.y, p.w * d.x)), r.z, r.w);
+    return r;
+}
+
+// sum of a double-float over the warp (lane 0 holds the result)
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float s, e;
+        two_sum(h, oh, s, e);
+        h = s;
+        l += ol + e;
+    }
+}
+
+// Inverse Lagrange denominator 1 / prod_{l != j, l <= p} (j - l) of node j
+// at degree p (Sec. 3.2), evaluated at compile time.
+constexpr double lag_inv_den(int p, int j) {
+    double den = 1.0;
+    for (int l = 0; l <= p; ++l)
+        if (l != j) den *= (double)(j - l);
+    return 1.0 / den;
+}
+struct LagInv {
+    double v[PIM_MAX_P + 1][PIM_MAX_P + 1];
+};
+constexpr LagInv make_lag_inv() {
+    LagInv r{};
+    for (int p = 0; p <= PIM_MAX_P; ++p)
+        for (int j = 0; j <= p; ++j) r.v[p][j] = lag_inv_den(p, j);
+    return r;
+}
+__constant__ LagInv c_lag_inv = make_lag_inv();
+
+// One Lagrange weight w_j(t) of compile-time degree P for a runtime node j.
+template <typename T, int P>
+__device__ __forceinline__ T lag1(T t, int j) {
+    T r = T(1), c = T(lag_inv_den(P, 0));
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+        r *= (l == j) ? T(1) : (t - T(l));
+        if (l > 0) c = (l == j) ? T(lag_inv_den(P, l)) : c;
+    }
+    return r * c;
+}
+
+// One Lagrange weight w_j(t) of runtime degree p <= PIM_MAX_P.
+template <typename T>
+__device__ __forceinline__ T lag1_rt(int p, T t, int j) {
+    T r = T(1);
+#pragma unroll
+    for (int l = 0; l <= PIM_MAX_P; ++l) r *= (l == j || l > p) ? T(1) : (t - T(l));
+    return r * T(c_lag_inv.v[p][j]);
+}
+
+// Lagrange weights of runtime degree p <= PIM_MAX_P without divisions
+// (prefix/suffix products times the tabulated inverse denominators).
+template <typename T>
+__device__ __forceinline__ void lagrange_w_rt(int p, T t, T* w) {
+    T pre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1];
+    pre[0] = T(1);
+#pragma unroll
+    for (int j = 1; j <= PIM_MAX_P; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
+    suf[PIM_MAX_P] = T(1);
+#pragma unroll
+    for (int j = PIM_MAX_P - 1; j >= 0; --j) suf[j] = (j + 1 <= p) ? suf[j + 1] * (t - T(j + 1)) : T(1);
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) w[j] = j <= p ? pre[j] * suf[j] * T(c_lag_inv.v[p][j]) : T(0);
+}
+
+// Near-pair correction of one row, all lanes of the warp: entry q = lane,
+// lane + 32, ... of [0, len).  Full trips take UNR entries per lane with every
+// column and value load issued before the dependent source loads and no
+// bounds tests; the tail takes one entry per lane.  body(c, d, x) gets the
+// column word, the value and the source q_n.
+template <int UNR, typename V, typename C, typename F>
+__device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __restrict__ colr,
+                                         const V* __restrict__ valr, const C* __restrict__ qs, F&& body) {
+    int q = lane;
+    for (; q + 32 * (UNR - 1) < len; q += 32 * UNR) {
+        uint32_t c[UNR];
+        V d[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            c[u] = __ldcs(colr + q + 32 * u);
+            d[u] = __ldcs(valr + q + 32 * u);
+        }
+        C x[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) x[u] = qs[c[u] & PIM_COL_MASK];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) body(c[u], d[u], x[u]);
+    }
+    for (; q < len; q += 32) {
+        const uint32_t c = __ldcs(colr + q);
+        const V d = __ldcs(valr + q);
+        body(c, d, qs[c & PIM_COL_MASK]);
+    }
+}
+
 // One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
 // correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
-// written in the caller's order.
+// written in the caller's order.  In both gathers lane (jy, jz) takes one
+// x-row of the stencil.
 template <typename T, int P, int CM, int UNR, int MINB>
 __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
                                                      const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
@@ -502,160 +640,130 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
     const int lane = threadIdx.x & 31;
     const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (m >= a.N) return;
-    // near gather
-    int s[3];
-    unpack3(a.ns[m], s[0], s[1], s[2]);
-    T w[3][P + 1];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-        lagrange_w<T, P>(tt, w[d]);
-    }
-    constexpr int NP = P + 1, NP3 = NP * NP * NP;
+    constexpr int NP = P + 1;
     cplx<T> acc = mk<T>(T(0), T(0));
+    // near gather
+    if (lane < NP * NP) {
+        const int jy = lane % NP, jz = lane / NP;
+        int s[3];
+        unpack3(a.ns[m], s[0], s[1], s[2]);
+        T t[3];
 #pragma unroll
-    for (int k = 0; k < (NP3 + 31) / 32; ++k) {
-        const int idx = lane + 32 * k;
-        if (idx >= NP3) break;
-        const int jx = idx % NP, jy = (idx / NP) % NP, jz = idx / (NP * NP);
-        const T ww = pick<NP>(w[0], jx) * pick<NP>(w[1], jy) * pick<NP>(w[2], jz);
-        const cplx<T> v = U[((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + (s[0] + jx)];
-        acc.x += ww * v.x;
-        acc.y += ww * v.y;
+        for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+        const T wyz = lag1<T, P>(t[1], jy) * lag1<T, P>(t[2], jz);
+        T wx[NP];
+        lagrange_w<T, P>(t[0], wx);
+        const cplx<T>* row = U + ((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + s[0];
+        cplx<T> r = mk<T>(T(0), T(0));
+#pragma unroll
+        for (int jx = 0; jx < NP; ++jx) {
+            const cplx<T> v = row[jx];
+            r.x += wx[jx] * v.x;
+            r.y += wx[jx] * v.y;
+        }
+        acc.x = wyz * r.x;
+        acc.y = wyz * r.y;
     }
     // far gather
     if (a.has_far) {
-        int f[3];
-        unpack3(a.fst[m], f[0], f[1], f[2]);
-        T wf[3][PIM_MAX_P + 1];
+        const int np = a.pf + 1;
+        for (int l = lane; l < np * np; l += 32) {
+            const int jy = l % np, jz = l / np;
+            int f[3];
+            unpack3(a.fst[m], f[0], f[1], f[2]);
+            T t[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
-            lagrange_weights_rt<T>(a.pf, tt, wf[d]);
-        }
-        const int np = a.pf + 1, np3 = np * np * np;
-        for (int idx = lane; idx < np3; idx += 32) {
-            const int jx = idx % np, jy = (idx / np) % np, jz = idx / (np * np);
-            const T ww = pick<PIM_MAX_P + 1>(wf[0], jx) * pick<PIM_MAX_P + 1>(wf[1], jy) * pick<PIM_MAX_P + 1>(wf[2], jz);
-            const cplx<T> v = uf[((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + (f[0] + jx)];
-            acc.x += ww * v.x;
-            acc.y += ww * v.y;
+            for (int d = 0; d < 3; ++d)
+                t[d] = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
+            const T wyz = lag1_rt<T>(a.pf, t[1], jy) * lag1_rt<T>(a.pf, t[2], jz);
+            T wx[PIM_MAX_P + 1];
+            lagrange_w_rt<T>(a.pf, t[0], wx);
+            const cplx<T>* row = uf + ((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
+            cplx<T> r = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int jx = 0; jx <= PIM_MAX_P; ++jx) {
+                if (jx < np) {
+                    const cplx<T> v = row[jx];
+                    r.x += wx[jx] * v.x;
+                    r.y += wx[jx] * v.y;
+                }
+            }
+            acc.x += wyz * r.x;
+            acc.y += wyz * r.y;
         }
     }
     // near-pair correction: exp(-j k0.(i o L)) d q_n (forward) or
-    // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  Each lane takes UNR entries
-    // per trip, issuing all column and value loads (streaming, read once)
-    // before the dependent source loads.
-    const long long r0 = CM < 0 ? 0 : a.row_ptr[m], r1 = CM < 0 ? 0 : a.row_ptr[m + 1];
-    const double cs = a.adj ? -1.0 : 1.0;
+    // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  The adjoint is summed as the
+    // conjugate of sum conj(phase) d conj(v_n), so that the values are used
+    // as stored.
+    const long long r0 = CM < 0 ? 0 : a.row_ptr[m];
+    const int len = CM < 0 ? 0 : (int)(a.row_ptr[m + 1] - r0);
+    const uint32_t* colr = a.col + r0;
+    const float fs = a.adj ? -1.f : 1.f;
     double2 accd = make_double2(0.0, 0.0);
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     if (CM == PIM_CORR_FP64) {
-        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
-            uint32_t c[UNR];
-            double2 d[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const long long q = q0 + 32 * u;
-                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
-                d[u] = q < r1 ? __ldcs(a.val + q) : make_double2(0.0, 0.0);
+        corr_row<UNR>(lane, len, colr, a.val + r0, qs, [&](uint32_t c, const double2& d, const cplx<T>& x) {
+            const double xr = (double)x.x, xi = (double)fs * (double)x.y;
+            double2 t = make_double2(d.x * xr - d.y * xi, d.x * xi + d.y * xr);
+            const int ii = (int)(c >> PIM_COL_BITS);
+            if (ii != a.self_img) {
+                const double2 ph = a.phase[ii];
+                t = cmul(make_double2(ph.x, (double)fs * ph.y), t);
             }
-            cplx<T> x[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) x[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                if (c[u] == 0xffffffffu) continue;
-                const int ii = (int)(c[u] >> PIM_COL_BITS);
-                const double dy = cs * d[u].y;
-                double2 t = make_double2(d[u].x * (double)x[u].x - dy * (double)x[u].y,
-                                         d[u].x * (double)x[u].y + dy * (double)x[u].x);
-                if (ii != a.self_img) t = cmul(a.phase[ii], t);
-                accd = cadd(accd, t);
-            }
-        }
+            accd = cadd(accd, t);
+        });
     } else if (CM == PIM_CORR_DOUBLE_FLOAT) {
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        const float fs = (float)cs;
-        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
-            uint32_t c[UNR];
-            float4 d[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const long long q = q0 + 32 * u;
-                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
-                d[u] = q < r1 ? __ldcs(a.valdf + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // FP32 arithmetic throughout: values of other images are multiplied by
+        // their phase in double-float, every entry is added by df_cmac and the
+        // warp sum is double-float too
+        corr_row<UNR>(lane, len, colr, a.valdf + r0, qs, [&](uint32_t c, const float4& d, const cplx<T>& x) {
+            const int ii = (int)(c >> PIM_COL_BITS);
+            float4 v = d;
+            if (ii != a.self_img) {
+                float4 ph = a.phasedf[ii];
+                ph.z *= fs;
+                ph.w *= fs;
+                v = df_cmul(ph, v);
             }
-            cplx<T> xv[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) xv[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                if (c[u] == 0xffffffffu) continue;
-                const int ii = (int)(c[u] >> PIM_COL_BITS);
-                const float xr = (float)xv[u].x, xi = (float)xv[u].y;
-                const float dih = fs * d[u].z, dil = fs * d[u].w;
-                if (ii == a.self_img) {
-                    // re += dr*xr - di*xi ; im += dr*xi + di*xr with exact product splits
-                    const float p1 = d[u].x * xr, e1 = fmaf(d[u].x, xr, -p1);
-                    const float p2 = dih * xi, e2 = fmaf(dih, xi, -p2);
-                    const float p3 = d[u].x * xi, e3 = fmaf(d[u].x, xi, -p3);
-                    const float p4 = dih * xr, e4 = fmaf(dih, xr, -p4);
-                    two_sum_acc(rh, rl, p1);
-                    two_sum_acc(rh, rl, -p2);
-                    two_sum_acc(ih, il, p3);
-                    two_sum_acc(ih, il, p4);
-                    rl += (e1 - e2) + (d[u].y * xr - dil * xi);
-                    il += (e3 + e4) + (d[u].y * xi + dil * xr);
-                } else {
-                    const double dr = (double)d[u].x + (double)d[u].y, di = (double)dih + (double)dil;
-                    double2 t = make_double2(dr * xr - di * xi, dr * xi + di * xr);
-                    accd = cadd(accd, cmul(a.phase[ii], t));
-                }
-            }
-        }
-        accd.x += (double)rh + (double)rl;
-        accd.y += (double)ih + (double)il;
+            df_cmac(rh, rl, ih, il, v, (float)x.x, fs * (float)x.y);
+        });
     } else if (CM == PIM_CORR_FP32) {
-        float ar = 0.f, ai = 0.f;
-        const float fs = (float)cs;
-        for (long long q0 = r0 + lane; q0 < r1; q0 += 32 * UNR) {
-            uint32_t c[UNR];
-            float2 d[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const long long q = q0 + 32 * u;
-                c[u] = q < r1 ? __ldcs(a.col + q) : 0xffffffffu;
-                d[u] = q < r1 ? __ldcs(a.valf + q) : make_float2(0.f, 0.f);
+        corr_row<UNR>(lane, len, colr, a.valf + r0, qs, [&](uint32_t c, const float2& d, const cplx<T>& x) {
+            const float xr = (float)x.x, xi = fs * (float)x.y;
+            float2 t = make_float2(d.x * xr - d.y * xi, d.x * xi + d.y * xr);
+            const int ii = (int)(c >> PIM_COL_BITS);
+            if (ii != a.self_img) {
+                const float4 ph = a.phasedf[ii];
+                const float pr = ph.x, pi = fs * ph.z;
+                t = make_float2(pr * t.x - pi * t.y, pr * t.y + pi * t.x);
             }
-            cplx<T> xv[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) xv[u] = c[u] != 0xffffffffu ? qs[c[u] & PIM_COL_MASK] : mk<T>(T(0), T(0));
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                if (c[u] == 0xffffffffu) continue;
-                const int ii = (int)(c[u] >> PIM_COL_BITS);
-                const float dy = fs * d[u].y;
-                float2 t = make_float2(d[u].x * (float)xv[u].x - dy * (float)xv[u].y,
-                                       d[u].x * (float)xv[u].y + dy * (float)xv[u].x);
-                if (ii != a.self_img) {
-                    const double2 ph = a.phase[ii];
-                    t = make_float2((float)ph.x * t.x - (float)ph.y * t.y, (float)ph.x * t.y + (float)ph.y * t.x);
-                }
-                ar += t.x;
-                ai += t.y;
-            }
-        }
-        acc.x += (T)ar;
-        acc.y += (T)ai;
+            rh += t.x;
+            ih += t.y;
+        });
     }
     // warp reduction
     for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        accd.x += __shfl_xor_sync(0xffffffffu, accd.x, o);
-        accd.y += __shfl_xor_sync(0xffffffffu, accd.y, o);
+        if (CM == PIM_CORR_FP64) {
+            accd.x += __shfl_xor_sync(0xffffffffu, accd.x, o);
+            accd.y += __shfl_xor_sync(0xffffffffu, accd.y, o);
+        } else if (CM == PIM_CORR_FP32) {
+            rh += __shfl_xor_sync(0xffffffffu, rh, o);
+            ih += __shfl_xor_sync(0xffffffffu, ih, o);
+        }
+    }
+    if (CM == PIM_CORR_DOUBLE_FLOAT) {
+        df_warp_sum(rh, rl);
+        df_warp_sum(ih, il);
     }
     if (lane == 0) {
+        if (CM == PIM_CORR_DOUBLE_FLOAT || CM == PIM_CORR_FP32) {
+            accd.x = (double)rh + (double)rl;
+            accd.y = (double)ih + (double)il;
+        }
+        accd.y *= (double)fs;  // undo the conjugation of the adjoint sum
         const double re = (double)acc.x + accd.x, im = (double)acc.y + accd.y;
         if (a.sorted_out) {
             ((cplx<T>*)out)[m] = mk<T>((T)re, (T)im);
@@ -839,6 +947,7 @@ struct CorrMultiArgs {
     const float4* valdf;
     const float2* valf;
     const double2* phase;
+    const float4* phasedf;
 };
 
 template <typename T, int CM, int RPL>
@@ -859,25 +968,17 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
         const uint32_t c = __ldg(a.col + q);
         const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
         const cplx<T>* xr = qsall + (long long)n * R;
-        if (CM == PIM_CORR_DOUBLE_FLOAT && ii == a.self_img) {
+        if (CM == PIM_CORR_DOUBLE_FLOAT) {
             const float4 d = __ldg(a.valdf + q);
-            const float fs = (float)cs, dih = fs * d.z, dil = fs * d.w;
+            const float fs = (float)cs;
+            float4 v = make_float4(d.x, d.y, fs * d.z, fs * d.w);
+            if (ii != a.self_img) v = df_cmul(a.phasedf[ii], v);
 #pragma unroll
             for (int k = 0; k < RPL; ++k) {
                 const int r = lane + 32 * k;
                 if (r >= R) break;
                 const cplx<T> xv = xr[r];
-                const float x_r = (float)xv.x, x_i = (float)xv.y;
-                const float p1 = d.x * x_r, e1 = fmaf(d.x, x_r, -p1);
-                const float p2 = dih * x_i, e2 = fmaf(dih, x_i, -p2);
-                const float p3 = d.x * x_i, e3 = fmaf(d.x, x_i, -p3);
-                const float p4 = dih * x_r, e4 = fmaf(dih, x_r, -p4);
-                two_sum_acc(rh[k], rl[k], p1);
-                two_sum_acc(rh[k], rl[k], -p2);
-                two_sum_acc(ih[k], il[k], p3);
-                two_sum_acc(ih[k], il[k], p4);
-                rl[k] += (e1 - e2) + (d.y * x_r - dil * x_i);
-                il[k] += (e3 + e4) + (d.y * x_i + dil * x_r);
+                df_cmac(rh[k], rl[k], ih[k], il[k], v, (float)xv.x, (float)xv.y);
             }
         } else if (CM == PIM_CORR_FP32) {
             const float2 d = __ldg(a.valf + q);
@@ -895,14 +996,7 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
                 ih[k] += dd.x * (float)xv.y + dd.y * (float)xv.x;
             }
         } else {
-            // FP64 values (also the non-self images of the double-float mode)
-            double2 d;
-            if (CM == PIM_CORR_DOUBLE_FLOAT) {
-                const float4 v = __ldg(a.valdf + q);
-                d = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
-            } else {
-                d = __ldg(a.val + q);
-            }
+            double2 d = __ldg(a.val + q);
             d.y *= cs;
             if (ii != a.self_img) d = cmul(a.phase[ii], d);
 #pragma unroll
@@ -963,11 +1057,11 @@ template <typename T, int PP, int CM>
 pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
                             const cplx<T>* uf, const cplx<T>* qs, void* dst) {
     switch (v) {
-        case 0: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 1: gather_kernel<T, PP, CM, 4, 1><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 2: gather_kernel<T, PP, CM, 2, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 3: gather_kernel<T, PP, CM, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        default: gather_kernel<T, PP, CM, 3, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 0: gather_kernel<T, PP, CM, 2, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 1: gather_kernel<T, PP, CM, 4, 4><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 2: gather_kernel<T, PP, CM, 3, 5><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 3: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        default: gather_kernel<T, PP, CM, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
     }
     PIM_CK(cudaGetLastError());
     return PIM_OK;
@@ -976,11 +1070,20 @@ pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs
 template <typename T, int PP>
 pim_status launch_gather(int cm, int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
                          const cplx<T>* uf, const cplx<T>* qs, void* dst) {
-    if (cm < 0) return launch_gather_cm<T, PP, -1>(0, nb, s, ga, U, uf, qs, dst);
-    if (sizeof(T) == 8) return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
-    if (cm == PIM_CORR_DOUBLE_FLOAT) return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
-    if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);
-    return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+    if (cm < 0) {
+        // near and far gathers only (the correction runs in the multi-RHS kernel)
+        gather_kernel<T, PP, -1, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst);
+        PIM_CK(cudaGetLastError());
+        return PIM_OK;
+    }
+    if constexpr (sizeof(T) == 8) {
+        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+    } else {
+        if (cm == PIM_CORR_DOUBLE_FLOAT)
+            return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
+        if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);
+        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+    }
 }
 
 template <typename T>
@@ -1107,6 +1210,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ga.valdf = d.valdf;
         ga.valf = d.valf;
         ga.phase = P->dphase;
+        ga.phasedf = P->dphasedf;
         const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
@@ -1151,6 +1255,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ca.valdf = d.valdf;
         ca.valf = d.valf;
         ca.phase = P->dphase;
+        ca.phasedf = P->dphasedf;
         const int cm = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
         const unsigned nb = (unsigned)((N * 32 + 255) / 256);
 #define PIM_CM_LAUNCH(CMV)                                                                                   \

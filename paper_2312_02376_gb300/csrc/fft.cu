@@ -122,6 +122,9 @@ struct PassArgs {
 };
 
 // FFT along a strided axis: CTA = (plane, group of B consecutive columns).
+// Every thread issues all of its global loads (and, in the z pass, its
+// spectrum loads) before it stores to shared memory, so their latencies
+// overlap instead of forming a chain.
 template <typename T, int L, int B, int NBS>
 __global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, cplx<T>* out,
                                                               PassArgs a, const cplx<T>* __restrict__ tw,
@@ -129,19 +132,32 @@ __global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
     constexpr int LD = B + 1;
+    constexpr int NT = B * NBS;
+    constexpr int EPT = L * B / NT;  // elements per thread
     const int plane = blockIdx.x / a.ngroups;
     const int c0 = (blockIdx.x % a.ngroups) * B;
     const int tid = threadIdx.x;
     const int col = tid % B, bslot = tid / B;
-    constexpr int NT = B * NBS;
     const cplx<T> zero = mk<T>(T(0), T(0));
     const cplx<T>* ib = in + plane * a.in_plane + c0;
-    for (int i = tid; i < L * B; i += NT) {
-        const int r = i / B, c = i % B;
-        cplx<T> v = zero;
-        if (r < a.n_in && c0 + c < a.width) v = ib[r * a.in_row + c];
-        s[r * LD + c] = v;
+    const bool cok = c0 + col < a.width;   // i % B == col for every i = tid + k NT
+    cplx<T> v[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int r = (tid + k * NT) / B;
+        v[k] = (r < a.n_in && cok) ? ib[r * a.in_row + col] : zero;
     }
+    cplx<T> sp[EPT];
+    if (a.mode >= 2) {
+        const cplx<T>* spb = spec + plane * a.spec_plane + c0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            const int r = (tid + k * NT) / B;
+            sp[k] = cok ? spb[r * a.spec_row + col] : zero;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) s[((tid + k * NT) / B) * LD + col] = v[k];
     __syncthreads();
     if (a.mode == 1) {
         fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
@@ -149,22 +165,23 @@ __global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, 
         fft_stages<T, L, B, NBS, 1, false>(s, tw, col, bslot);
     }
     if (a.mode >= 2) {
-        const cplx<T>* sp = spec + plane * a.spec_plane + c0;
-        for (int i = tid; i < L * B; i += NT) {
-            const int r = i / B, c = i % B;
-            if (c0 + c < a.width) {
-                cplx<T> w = sp[r * a.spec_row + c];
-                if (a.mode == 3) w.y = -w.y;
-                s[r * LD + c] = cmul(s[r * LD + c], w);
-            }
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            const int r = (tid + k * NT) / B;
+            cplx<T> w = sp[k];
+            if (a.mode == 3) w.y = -w.y;
+            s[r * LD + col] = cmul(s[r * LD + col], w);
         }
         __syncthreads();
         fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
     }
     cplx<T>* ob = out + plane * a.out_plane + c0;
-    for (int i = tid; i < a.n_keep * B; i += NT) {
-        const int r = i / B, c = i % B;
-        if (c0 + c < a.width) ob[r * a.out_row + c] = s[r * LD + c];
+    if (cok) {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            const int r = (tid + k * NT) / B;
+            if (r < a.n_keep) ob[r * a.out_row + col] = s[r * LD + col];
+        }
     }
 }
 
@@ -175,16 +192,23 @@ __global__ void __launch_bounds__(B* NBS) fft_contig_kernel(const cplx<T>* in, c
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* s = reinterpret_cast<cplx<T>*>(smem_raw);
     constexpr int LD = B + 1;
+    constexpr int NT = B * NBS;
+    constexpr int EPT = L * B / NT;
     const int l0 = blockIdx.x * B;
     const int tid = threadIdx.x;
     const int col = tid % B, bslot = tid / B;
-    constexpr int NT = B * NBS;
     const cplx<T> zero = mk<T>(T(0), T(0));
-    for (int i = tid; i < L * B; i += NT) {
+    cplx<T> v[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int i = tid + k * NT;
         const int c = i / L, x = i % L;
-        cplx<T> v = zero;
-        if (x < a.n_in && l0 + c < a.width) v = in[(long long)(l0 + c) * a.in_row + x];
-        s[x * LD + c] = v;
+        v[k] = (x < a.n_in && l0 + c < a.width) ? in[(long long)(l0 + c) * a.in_row + x] : zero;
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        const int i = tid + k * NT;
+        s[(i % L) * LD + i / L] = v[k];
     }
     __syncthreads();
     if (a.mode == 1) fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
@@ -196,13 +220,13 @@ __global__ void __launch_bounds__(B* NBS) fft_contig_kernel(const cplx<T>* in, c
 }
 
 template <typename T> struct TileCfg;
-// columns per CTA by length: keep the CTA's smem near 64-70 KB so that three
-// CTAs fit on an SM.
+// columns per CTA by length: one 128-byte line per row at most, and a few
+// elements per thread, so that several CTAs fit on an SM.
 template <> struct TileCfg<float> {
-    static constexpr int B(int L) { return L <= 256 ? 32 : (L == 512 ? 16 : 8); }
+    static constexpr int B(int L) { return L <= 64 ? 32 : (L <= 512 ? 16 : 8); }
 };
 template <> struct TileCfg<double> {
-    static constexpr int B(int L) { return L <= 128 ? 32 : (L == 256 ? 16 : (L == 512 ? 8 : 4)); }
+    static constexpr int B(int L) { return L <= 128 ? 16 : (L == 256 ? 8 : 4); }
 };
 
 template <typename T, int L>

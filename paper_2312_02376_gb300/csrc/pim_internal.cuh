@@ -212,7 +212,8 @@ struct pim_plan_s {
     void* hq = nullptr;           // device staging of caller buffers (host pointers)
     void* hu = nullptr;
     double* dsum = nullptr;       // FP64 scratch: [0..1] mean, [4..) reduction partials
-    double2* dphase = nullptr;    // device copy of phase[]
+    double2* dphase = nullptr;    // device copy of phase[], followed by its double-float split
+    float4* dphasedf = nullptr;   // (re hi, re lo, im hi, im lo), inside the dphase allocation
     int* dstatus = nullptr;
     // profiling ring (pim_set_profiling)
     static constexpr int PROF_RING = 512;
