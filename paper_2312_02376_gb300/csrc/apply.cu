@@ -100,6 +100,61 @@ __device__ __forceinline__ void lagrange_w(T t, T* w) {
     }
 }
 
+// Inverse Lagrange denominator 1 / prod_{l != j, l <= p} (j - l) of node j
+// at degree p (Sec. 3.2), evaluated at compile time.
+constexpr double lag_inv_den(int p, int j) {
+    double den = 1.0;
+    for (int l = 0; l <= p; ++l)
+        if (l != j) den *= (double)(j - l);
+    return 1.0 / den;
+}
+struct LagInv {
+    double v[PIM_MAX_P + 1][PIM_MAX_P + 1];
+};
+constexpr LagInv make_lag_inv() {
+    LagInv r{};
+    for (int p = 0; p <= PIM_MAX_P; ++p)
+        for (int j = 0; j <= p; ++j) r.v[p][j] = lag_inv_den(p, j);
+    return r;
+}
+__constant__ LagInv c_lag_inv = make_lag_inv();
+
+// One Lagrange weight w_j(t) of compile-time degree P for a runtime node j.
+template <typename T, int P>
+__device__ __forceinline__ T lag1(T t, int j) {
+    T r = T(1), c = T(lag_inv_den(P, 0));
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+        r *= (l == j) ? T(1) : (t - T(l));
+        if (l > 0) c = (l == j) ? T(lag_inv_den(P, l)) : c;
+    }
+    return r * c;
+}
+
+// One Lagrange weight w_j(t) of runtime degree p <= PIM_MAX_P.
+template <typename T>
+__device__ __forceinline__ T lag1_rt(int p, T t, int j) {
+    T r = T(1);
+#pragma unroll
+    for (int l = 0; l <= PIM_MAX_P; ++l) r *= (l == j || l > p) ? T(1) : (t - T(l));
+    return r * T(c_lag_inv.v[p][j]);
+}
+
+// Lagrange weights of runtime degree p <= PIM_MAX_P without divisions
+// (prefix/suffix products times the tabulated inverse denominators).
+template <typename T>
+__device__ __forceinline__ void lagrange_w_rt(int p, T t, T* w) {
+    T pre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1];
+    pre[0] = T(1);
+#pragma unroll
+    for (int j = 1; j <= PIM_MAX_P; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
+    suf[PIM_MAX_P] = T(1);
+#pragma unroll
+    for (int j = PIM_MAX_P - 1; j >= 0; --j) suf[j] = (j + 1 <= p) ? suf[j + 1] * (t - T(j + 1)) : T(1);
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) w[j] = j <= p ? pre[j] * suf[j] * T(c_lag_inv.v[p][j]) : T(0);
+}
+
 // Derivatives of the Lagrange basis of degree P (product rule).
 template <typename T, int P>
 __device__ __forceinline__ void lagrange_dw(T t, T* dw) {
@@ -181,9 +236,14 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
     const long long s0 = a.wbeg[w], s1 = a.wbeg[w + 1];
     const bool act = lane < NP * NP;
     const int jy = lane % NP, jz = lane / NP;
-    const int m0 = a.bstart[s0], m1 = a.bstart[s1];
-    long long slot = s0;
-    int next = a.bstart[slot + 1];
+    // a warp's boxes start inside one 32-point block, so there are at most
+    // 32 of them: lane b keeps the first point of box s0 + b
+    const int nbw = (int)(s1 - s0);
+    const int bs = lane < nbw ? a.bstart[s0 + lane] : 0;
+    const int m1 = a.bstart[s1];
+    const int m0 = __shfl_sync(0xffffffffu, bs, 0);
+    int slot = 0;  // box s0 + slot
+    int next = nbw > 1 ? __shfl_sync(0xffffffffu, bs, 1) : m1;
     cplx<T> sum[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) sum[j] = mk<T>(T(0), T(0));
@@ -199,23 +259,24 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
         }
         for (int j = 0; j < cnt; ++j) {
             const int m = b0 + j;
-            while (m >= next) {  // the walk leaves box `slot`: write its row
+            while (m >= next) {  // the walk leaves box s0 + slot: write its row
                 if (act) {
-                    cplx<T>* out = mom + slot * NP3 + lane * NP;
+                    cplx<T>* out = mom + (s0 + slot) * NP3 + lane * NP;
 #pragma unroll
                     for (int i = 0; i < NP; ++i) out[i] = sum[i];
                 }
 #pragma unroll
                 for (int i = 0; i < NP; ++i) sum[i] = mk<T>(T(0), T(0));
                 ++slot;
-                next = a.bstart[slot + 1];
+                const int nx = __shfl_sync(0xffffffffu, bs, (slot + 1) & 31);
+                next = slot + 1 < nbw ? nx : m1;
             }
-            T wx[NP], wy[NP], wz[NP];
-            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[0], j), wx);
-            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[1], j), wy);
-            lagrange_w<T, P>(__shfl_sync(0xffffffffu, tl[2], j), wz);
+            const T tx = __shfl_sync(0xffffffffu, tl[0], j), ty = __shfl_sync(0xffffffffu, tl[1], j),
+                    tz = __shfl_sync(0xffffffffu, tl[2], j);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
-            const T wyz = pick<NP>(wy, jy) * pick<NP>(wz, jz);
+            T wx[NP];
+            lagrange_w<T, P>(tx, wx);
+            const T wyz = lag1<T, P>(ty, jy) * lag1<T, P>(tz, jz);
             const T cx = wyz * qx, cy = wyz * qy;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
@@ -225,7 +286,7 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
         }
     }
     if (act) {
-        cplx<T>* out = mom + slot * NP3 + lane * NP;
+        cplx<T>* out = mom + (s0 + slot) * NP3 + lane * NP;
 #pragma unroll
         for (int i = 0; i < NP; ++i) out[i] = sum[i];
     }
@@ -235,7 +296,10 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
 // moments of the (<= (P+1)^2 in the interior) box rows whose stencils cover
 // (y, z); each non-empty box of a row adds its P+1 contiguous moments
 // M_b(jz, jy, 0..P) at x = s_x(b)..s_x(b)+P of the line, kept in shared
-// memory.  No global atomics; every node written once.
+// memory.  No global atomics; every node written once.  The candidate rows
+// go to lanes and their non-empty boxes are enumerated as one flat list
+// (a warp prefix sum of the row counts), so that the dependent loads of all
+// rows are in flight together.
 struct LineArgs {
     int n[3], nb[3];
     const int* rsp;      // first slot of each box row
@@ -263,28 +327,59 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
     int ylo, yhi, zlo, zhi;
     covering_boxes<P>(y, a.n[1], a.nb[1], ylo, yhi);
     covering_boxes<P>(z, a.n[2], a.nb[2], zlo, zhi);
-    for (int bz = zlo; bz <= zhi; ++bz) {
-        const int jz = z - sclamp<P>(bz, a.n[2]);
-        if ((unsigned)jz > (unsigned)P) continue;
-        for (int by = ylo; by <= yhi; ++by) {
-            const int jy = y - sclamp<P>(by, a.n[1]);
-            if ((unsigned)jy > (unsigned)P) continue;
+    const int nyc = yhi - ylo + 1, ncand = nyc * (zhi - zlo + 1);
+    for (int c0 = 0; c0 < ncand; c0 += 32) {
+        // lane: one candidate box row (by, bz) and its slot range
+        const int c = c0 + lane;
+        const int by = ylo + c % nyc, bz = zlo + c / nyc;
+        const int jy = y - sclamp<P>(by, a.n[1]), jz = z - sclamp<P>(bz, a.n[2]);
+        int s0 = 0, cnt = 0;
+        if (c < ncand && (unsigned)jy <= (unsigned)P && (unsigned)jz <= (unsigned)P) {
             const long long r = (long long)bz * a.nb[1] + by;
-            const int s0 = a.rsp[r], s1 = a.rsp[r + 1];
-            for (int sb = s0; sb < s1; sb += 32) {
-                const int slot = sb + lane;
-                if (slot < s1) {
-                    const int bx = a.blist[slot] % a.nb[0];
-                    const int sx = sclamp<P>(bx, nx);
-                    const cplx<T>* src = mom + (long long)slot * NP3 + (jz * NP + jy) * NP;
-                    cplx<T> v[NP];
+            s0 = a.rsp[r];
+            cnt = a.rsp[r + 1] - s0;
+        }
+        int incl = cnt;
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) v[j] = src[j];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
+        const int moff = (jz * NP + jy) * NP;
+        for (int t0 = 0; t0 < total; t0 += 64) {
+            // two list entries per lane, all loads issued before the adds
+            int slot[2], off[2], bx[2];
+            bool ok[2];
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        atomicAdd(L + 2 * (sx + j), v[j].x);
-                        atomicAdd(L + 2 * (sx + j) + 1, v[j].y);
-                    }
+            for (int h = 0; h < 2; ++h) {
+                const int t = t0 + 32 * h + lane;
+                int k = 0;  // owner: the last lane whose range starts at or before t
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int e = __shfl_sync(0xffffffffu, excl, k + st);
+                    if (e <= t) k += st;
+                }
+                ok[h] = t < total;
+                slot[h] = __shfl_sync(0xffffffffu, s0, k) + (t - __shfl_sync(0xffffffffu, excl, k));
+                off[h] = __shfl_sync(0xffffffffu, moff, k);
+                bx[h] = ok[h] ? a.blist[slot[h]] : 0;
+            }
+            cplx<T> v[2][NP];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const cplx<T>* src = mom + (long long)slot[h] * NP3 + off[h];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) v[h][j] = ok[h] ? src[j] : mk<T>(T(0), T(0));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok[h]) continue;
+                const int sx = sclamp<P>(bx[h] % a.nb[0], nx);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    atomicAdd(L + 2 * (sx + j), v[h][j].x);
+                    atomicAdd(L + 2 * (sx + j) + 1, v[h][j].y);
                 }
             }
         }
@@ -542,61 +637,6 @@ __device__ __forceinline__ void df_warp_sum(float& h, float& l) {
         h = s;
         l += ol + e;
     }
-}
-
-// Inverse Lagrange denominator 1 / prod_{l != j, l <= p} (j - l) of node j
-// at degree p (Sec. 3.2), evaluated at compile time.
-constexpr double lag_inv_den(int p, int j) {
-    double den = 1.0;
-    for (int l = 0; l <= p; ++l)
-        if (l != j) den *= (double)(j - l);
-    return 1.0 / den;
-}
-struct LagInv {
-    double v[PIM_MAX_P + 1][PIM_MAX_P + 1];
-};
-constexpr LagInv make_lag_inv() {
-    LagInv r{};
-    for (int p = 0; p <= PIM_MAX_P; ++p)
-        for (int j = 0; j <= p; ++j) r.v[p][j] = lag_inv_den(p, j);
-    return r;
-}
-__constant__ LagInv c_lag_inv = make_lag_inv();
-
-// One Lagrange weight w_j(t) of compile-time degree P for a runtime node j.
-template <typename T, int P>
-__device__ __forceinline__ T lag1(T t, int j) {
-    T r = T(1), c = T(lag_inv_den(P, 0));
-#pragma unroll
-    for (int l = 0; l <= P; ++l) {
-        r *= (l == j) ? T(1) : (t - T(l));
-        if (l > 0) c = (l == j) ? T(lag_inv_den(P, l)) : c;
-    }
-    return r * c;
-}
-
-// One Lagrange weight w_j(t) of runtime degree p <= PIM_MAX_P.
-template <typename T>
-__device__ __forceinline__ T lag1_rt(int p, T t, int j) {
-    T r = T(1);
-#pragma unroll
-    for (int l = 0; l <= PIM_MAX_P; ++l) r *= (l == j || l > p) ? T(1) : (t - T(l));
-    return r * T(c_lag_inv.v[p][j]);
-}
-
-// Lagrange weights of runtime degree p <= PIM_MAX_P without divisions
-// (prefix/suffix products times the tabulated inverse denominators).
-template <typename T>
-__device__ __forceinline__ void lagrange_w_rt(int p, T t, T* w) {
-    T pre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1];
-    pre[0] = T(1);
-#pragma unroll
-    for (int j = 1; j <= PIM_MAX_P; ++j) pre[j] = pre[j - 1] * (t - T(j - 1));
-    suf[PIM_MAX_P] = T(1);
-#pragma unroll
-    for (int j = PIM_MAX_P - 1; j >= 0; --j) suf[j] = (j + 1 <= p) ? suf[j + 1] * (t - T(j + 1)) : T(1);
-#pragma unroll
-    for (int j = 0; j <= PIM_MAX_P; ++j) w[j] = j <= p ? pre[j] * suf[j] * T(c_lag_inv.v[p][j]) : T(0);
 }
 
 // Near-pair correction of one row, all lanes of the warp: entry q = lane,
