@@ -144,13 +144,22 @@ def gather_bytes(info, N, G, nf3):
     return info.nnz * per_nnz + (N + 1) * 8 + N * per_point + G * 8 + nf3 * 8
 
 
+def gather_source_hash():
+    """First 16 hex digits of the SHA-256 of the gather kernel's sources
+    (the kernel, the Lagrange helpers it inlines and the shared header)."""
+    csrc = os.path.join(ROOT, "paper_2312_02376_gb300", "csrc")
+    hs = hashlib.sha256()
+    for f in ("gather.cuh", "lagrange.cuh", "pim_internal.cuh"):
+        hs.update(open(os.path.join(csrc, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
 def profile_traffic():
     """DRAM bytes per launch of the gather kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
     try:
         txt = open(PROFILE_SUMMARY).read()
-        src = open(os.path.join(ROOT, "paper_2312_02376_gb300", "csrc", "apply.cu"), "rb").read()
-        h = hashlib.sha256(src).hexdigest()[:16]
+        h = gather_source_hash()
         m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
         t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
         if m and t and m.group(1) == h:
@@ -171,6 +180,8 @@ def run_gpu(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     W = workload(args.workload)
+    if args.corr_radius is not None:
+        W.b = args.corr_radius
     plan = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
                     pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
     plan.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
@@ -445,6 +456,9 @@ def main():
                     help="helmholtz2d_65k: the same recipe, smaller, for profiler captures; "
                          "helmholtz1d_batch: 16 sets x 64 right-hand sides, batched graph; "
                          "coulomb3d_1m: forward + adjoint + position gradient")
+    ap.add_argument("--corr-radius", type=int, default=None,
+                    help="override the correction radius of the helmholtz2d workloads (for profiler captures "
+                         "of the stages that do not depend on it; the line then states the radius used)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -4,6 +4,7 @@ Each translation unit is compiled by its own nvcc process in parallel, then
 linked as a shared library.  Output: paper_2312_02376_gb300/_build/libpim.so.
 """
 import concurrent.futures
+import glob
 import os
 import subprocess
 import sys
@@ -38,8 +39,8 @@ def _compile(unit, verbose):
 
 def build(verbose=False, force=False):
     os.makedirs(OUT, exist_ok=True)
-    deps = [os.path.join(SRC, u) for u in UNITS] + [os.path.join(SRC, "pim_internal.cuh"),
-                                                    os.path.join(ROOT, "include", "pim.h")]
+    deps = ([os.path.join(SRC, u) for u in UNITS] + glob.glob(os.path.join(SRC, "*.cuh")) +
+            [os.path.join(ROOT, "include", "pim.h")])
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps):
         return LIB
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
