@@ -189,9 +189,18 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
 // rows are in flight together.
 struct LineArgs {
     int n[3], nb[3];
+    int ncopy;           // copies of the line in shared memory (1, 2 or 4)
     const int* rsp;      // first slot of each box row
     const int* blist;    // box id of each slot
 };
+
+// Shared-memory layout of one warp's line: ncopy copies, each a real and an
+// imaginary array of line_ld(nx) words; copy c starts 8c words past a
+// multiple of 32, so that equal x in different copies fall in different
+// banks.  Consecutive box rows of a chunk add into different copies, so the
+// atomics of one instruction rarely share an address.
+__host__ __device__ __forceinline__ int line_ld(int nx) { return ((nx + 31) & ~31) + 16; }
+__host__ __device__ __forceinline__ int line_words(int nx, int ncopy) { return ncopy * (2 * line_ld(nx) + 8); }
 
 template <int P>
 __device__ __forceinline__ int sclamp(int b, int n) {
@@ -205,11 +214,12 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nx = a.n[0];
-    T* L = reinterpret_cast<T*>(smem_raw) + 2 * (size_t)wid * nx;
+    const int ld = line_ld(nx), cw = 2 * ld + 8;
+    T* L = reinterpret_cast<T*>(smem_raw) + (size_t)wid * line_words(nx, a.ncopy);
     const long long line = (long long)blockIdx.x * (blockDim.x >> 5) + wid;
     if (line >= (long long)a.n[1] * a.n[2]) return;
     const int y = (int)(line % a.n[1]), z = (int)(line / a.n[1]);
-    for (int i = lane; i < 2 * nx; i += 32) L[i] = T(0);
+    for (int i = lane; i < line_words(nx, a.ncopy); i += 32) L[i] = T(0);
     __syncwarp();
     int ylo, yhi, zlo, zhi;
     covering_boxes<P>(y, a.n[1], a.nb[1], ylo, yhi);
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
         const int moff = (jz * NP + jy) * NP;
         for (int t0 = 0; t0 < total; t0 += 64) {
             // two list entries per lane, all loads issued before the adds
-            int slot[2], off[2], bx[2];
+            int slot[2], off[2], bx[2], cp[2];
             bool ok[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -250,6 +260,7 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
                 ok[h] = t < total;
                 slot[h] = __shfl_sync(0xffffffffu, s0, k) + (t - __shfl_sync(0xffffffffu, excl, k));
                 off[h] = __shfl_sync(0xffffffffu, moff, k);
+                cp[h] = (k % a.ncopy) * cw;
                 bx[h] = ok[h] ? a.blist[slot[h]] : 0;
             }
             cplx<T> v[2][NP];
@@ -264,16 +275,24 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
                 if (!ok[h]) continue;
                 const int sx = sclamp<P>(bx[h] % a.nb[0], nx);
 #pragma unroll
+                T* Lr = L + cp[h];
                 for (int j = 0; j < NP; ++j) {
-                    atomicAdd(L + 2 * (sx + j), v[h][j].x);
-                    atomicAdd(L + 2 * (sx + j) + 1, v[h][j].y);
+                    atomicAdd(Lr + sx + j, v[h][j].x);
+                    atomicAdd(Lr + ld + sx + j, v[h][j].y);
                 }
             }
         }
     }
     __syncwarp();
     cplx<T>* out = Q + ((long long)z * a.n[1] + y) * nx;
-    for (int x = lane; x < nx; x += 32) out[x] = mk<T>(L[2 * x], L[2 * x + 1]);
+    for (int x = lane; x < nx; x += 32) {
+        T re = L[x], im = L[ld + x];
+        for (int c = 1; c < a.ncopy; ++c) {
+            re += L[c * cw + x];
+            im += L[c * cw + ld + x];
+        }
+        out[x] = mk<T>(re, im);
+    }
 }
 
 template <typename T, int P>
@@ -292,7 +311,10 @@ pim_status spread_two_phase(pim_plan P_, const cplx<T>* qs, cplx<T>* Q, cudaStre
     la.rsp = d.rsp;
     la.blist = d.blist;
     const long long nlines = (long long)P_->n[1] * P_->n[2];
-    const size_t sm = 8 * 2 * sizeof(T) * (size_t)P_->n[0];
+    // as many line copies as fit in 96 KB per CTA of 8 warps
+    la.ncopy = 4;
+    while (la.ncopy > 1 && 8 * sizeof(T) * (size_t)line_words(P_->n[0], la.ncopy) > 96 * 1024) la.ncopy /= 2;
+    const size_t sm = 8 * sizeof(T) * (size_t)line_words(P_->n[0], la.ncopy);
     PIM_CK(cudaFuncSetAttribute(line_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     line_kernel<T, P><<<(unsigned)((nlines + 7) / 8), 256, sm, s>>>(la, (const cplx<T>*)d.mom, Q);
     PIM_CK(cudaGetLastError());
