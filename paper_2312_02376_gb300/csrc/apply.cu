@@ -483,8 +483,10 @@ struct GradArgs {
     const double* ftd;
     const int64_t* row_ptr;
     const uint32_t* col;
-    const double2* dval;
+    const double2* dval;      // 3 per entry, FP64
+    const float4* dvaldf;     // 3 per entry, double-float (double-float correction mode)
     const double2* phase;
+    const float4* phasedf;
 };
 
 // One warp per sorted point k:
@@ -492,8 +494,12 @@ struct GradArgs {
 //          + Re[q_k conj(grad w_k . V + grad w^s_k . v_f)]
 //          + sum over row k: Re[conj(g_k) ph_i D q_n] + Re[q_k conj(g_n) conj(ph_i) D]
 // with U, u_f the forward grid potentials of q, V, v_f the adjoint ones of g
-// and D = d d_i(k, n) / d r_k from the correction list (FP64).
-template <typename T, int P>
+// and D = d d_i(k, n) / d r_k from the correction list.  In both stencil
+// gathers lane (jy, jz) takes one x-row: with A = sum_x w'_x U, B = sum_x w_x U
+// the row adds (w_y w_z A, w'_y w_z B, w_y w'_z B) to the three components.
+// Grid sums accumulate in T; the list in FP64 (DF = false) or in
+// double-float on the FP32 pipes (DF = true, T = float).
+template <typename T, int P, bool DF>
 __global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __restrict__ U,
                                                    const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ uf,
                                                    const cplx<T>* __restrict__ vf, const cplx<T>* __restrict__ qs,
@@ -501,108 +507,193 @@ __global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __
     const int lane = threadIdx.x & 31;
     const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (m >= a.N) return;
-    constexpr int NP = P + 1, NP3 = NP * NP * NP;
-    int s[3];
-    unpack3(a.ns[m], s[0], s[1], s[2]);
-    T w[3][NP], dw[3][NP];
+    constexpr int NP = P + 1;
+    // obs[d]: observer-side sums (U, u_f), src[d]: source-side sums (V, v_f)
+    cplx<T> obs[3], src[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-        lagrange_w<T, P>(tt, w[d]);
-        lagrange_dw<T, P>(tt, dw[d]);
-#pragma unroll
-        for (int j = 0; j < NP; ++j) dw[d][j] *= T(1.0 / a.h[d]);
-    }
-    // obs[d], src[d]: complex, accumulated in FP64 across the four sums
-    double2 obs[3], src[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) obs[d] = src[d] = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int k = 0; k < (NP3 + 31) / 32; ++k) {
-        const int idx = lane + 32 * k;
-        if (idx >= NP3) break;
-        const int jx = idx % NP, jy = (idx / NP) % NP, jz = idx / (NP * NP);
-        const T wx = pick<NP>(w[0], jx), wy = pick<NP>(w[1], jy), wz = pick<NP>(w[2], jz);
-        const T gx = pick<NP>(dw[0], jx) * wy * wz, gy = wx * pick<NP>(dw[1], jy) * wz, gz = wx * wy * pick<NP>(dw[2], jz);
-        const long long node = ((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + (s[0] + jx);
-        const cplx<T> u = U[node], v = V[node];
-        const T gw[3] = {gx, gy, gz};
+    for (int d = 0; d < 3; ++d) obs[d] = src[d] = mk<T>(T(0), T(0));
+    if (lane < NP * NP) {
+        const int jy = lane % NP, jz = lane / NP;
+        int s[3];
+        unpack3(a.ns[m], s[0], s[1], s[2]);
+        T w[3][NP], dw[3][NP];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            obs[d].x += (double)(gw[d] * u.x);
-            obs[d].y += (double)(gw[d] * u.y);
-            src[d].x += (double)(gw[d] * v.x);
-            src[d].y += (double)(gw[d] * v.y);
+            const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+            lagrange_wdw<T, P>(tt, w[d], dw[d]);
+            const T ih = T(1.0 / a.h[d]);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) dw[d][j] *= ih;
         }
+        const T wy = pick<NP>(w[1], jy), dwy = pick<NP>(dw[1], jy);
+        const T wz = pick<NP>(w[2], jz), dwz = pick<NP>(dw[2], jz);
+        const long long row = ((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + s[0];
+        cplx<T> A = mk<T>(T(0), T(0)), B = A, C = A, D = A;
+#pragma unroll
+        for (int jx = 0; jx < NP; ++jx) {
+            const cplx<T> u = U[row + jx], v = V[row + jx];
+            A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
+            B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
+            C.x += dw[0][jx] * v.x; C.y += dw[0][jx] * v.y;
+            D.x += w[0][jx] * v.x;  D.y += w[0][jx] * v.y;
+        }
+        obs[0] = cscale(A, wy * wz);
+        obs[1] = cscale(B, dwy * wz);
+        obs[2] = cscale(B, wy * dwz);
+        src[0] = cscale(C, wy * wz);
+        src[1] = cscale(D, dwy * wz);
+        src[2] = cscale(D, wy * dwz);
     }
     if (a.has_far) {
-        // observer grid for U_far, source grid for V_far
+        // observer grid for u_f, source grid for v_f
+        const int np = a.pf + 1;
         for (int side = 0; side < 2; ++side) {
-            int f[3];
-            unpack3(side == 0 ? a.fo[m] : a.fs[m], f[0], f[1], f[2]);
-            const int toff = side == 0 ? 3 : 0;
-            T wf[3][PIM_MAX_P + 1], dwf[3][PIM_MAX_P + 1];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + toff + d] : (T)a.ft[6 * m + toff + d];
-                lagrange_weights_rt<T>(a.pf, tt, wf[d]);
-                lagrange_dw_rt<T>(a.pf, tt, dwf[d]);
-            }
-            const cplx<T>* grid = side == 0 ? uf : vf;
-            const int np = a.pf + 1, np3 = np * np * np;
-            for (int idx = lane; idx < np3; idx += 32) {
-                const int jx = idx % np, jy = (idx / np) % np, jz = idx / (np * np);
-                const T wx = pick<PIM_MAX_P + 1>(wf[0], jx), wy = pick<PIM_MAX_P + 1>(wf[1], jy),
-                        wz = pick<PIM_MAX_P + 1>(wf[2], jz);
-                const T gw[3] = {pick<PIM_MAX_P + 1>(dwf[0], jx) * wy * wz * T(1.0 / a.df[0]),
-                                 wx * pick<PIM_MAX_P + 1>(dwf[1], jy) * wz * T(1.0 / a.df[1]),
-                                 wx * wy * pick<PIM_MAX_P + 1>(dwf[2], jz) * T(1.0 / a.df[2])};
-                const cplx<T> v = grid[((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + (f[0] + jx)];
+            for (int l = lane; l < np * np; l += 32) {
+                const int jy = l % np, jz = l / np;
+                int f[3];
+                unpack3(side == 0 ? a.fo[m] : a.fs[m], f[0], f[1], f[2]);
+                const int toff = side == 0 ? 3 : 0;
+                T w[3][PIM_MAX_P + 1], dw[3][PIM_MAX_P + 1];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    double2& acc = side == 0 ? obs[d] : src[d];
-                    acc.x += (double)(gw[d] * v.x);
-                    acc.y += (double)(gw[d] * v.y);
+                    const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + toff + d] : (T)a.ft[6 * m + toff + d];
+                    lagrange_wdw_rt<T>(a.pf, tt, w[d], dw[d]);
+                    const T id = T(1.0 / a.df[d]);
+#pragma unroll
+                    for (int j = 0; j <= PIM_MAX_P; ++j) dw[d][j] *= id;
                 }
+                const T wy = pick<PIM_MAX_P + 1>(w[1], jy), dwy = pick<PIM_MAX_P + 1>(dw[1], jy);
+                const T wz = pick<PIM_MAX_P + 1>(w[2], jz), dwz = pick<PIM_MAX_P + 1>(dw[2], jz);
+                const cplx<T>* grid = side == 0 ? uf : vf;
+                const cplx<T>* rowp = grid + ((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
+                cplx<T> A = mk<T>(T(0), T(0)), B = A;
+#pragma unroll
+                for (int jx = 0; jx <= PIM_MAX_P; ++jx) {
+                    if (jx < np) {
+                        const cplx<T> u = rowp[jx];
+                        A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
+                        B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
+                    }
+                }
+                cplx<T>* acc = side == 0 ? obs : src;
+                acc[0] = cadd(acc[0], cscale(A, wy * wz));
+                acc[1] = cadd(acc[1], cscale(B, dwy * wz));
+                acc[2] = cadd(acc[2], cscale(B, wy * dwz));
             }
         }
     }
-    // correction list
+    // correction list: c1[d] = sum ph D q_n, c2[d] = sum conj(ph) D conj(g_n)
+    const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
     double2 c1[3], c2[3];
+    float4 e1[3], e2[3];  // double-float accumulators (re hi, re lo, im hi, im lo)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) c1[d] = c2[d] = make_double2(0.0, 0.0);
-    for (long long q = a.row_ptr[m] + lane; q < a.row_ptr[m + 1]; q += 32) {
-        const uint32_t c = a.col[q];
+    for (int d = 0; d < 3; ++d) {
+        c1[d] = c2[d] = make_double2(0.0, 0.0);
+        e1[d] = e2[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (long long q = r0 + lane; q < r1; q += 32) {
+        const uint32_t c = __ldcs(a.col + q);
         const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
         const cplx<T> xq = qs[n], xg = gs[n];
-        const double2 ph = a.phase[ii];
-        const double2 pq = cmul(ph, make_double2((double)xq.x, (double)xq.y));         // ph q_n
-        const double2 pg = cmul(cconj(ph), make_double2((double)xg.x, -(double)xg.y));  // conj(ph) conj(g_n)
+        if constexpr (DF) {
+            float4 D[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const double2 D = a.dval[3 * q + d];
-            c1[d] = cadd(c1[d], cmul(D, pq));
-            c2[d] = cadd(c2[d], cmul(D, pg));
+            for (int d = 0; d < 3; ++d) D[d] = __ldcs(a.dvaldf + 3 * q + d);
+            if (ii != a.self_img) {
+                const float4 ph = a.phasedf[ii];
+                const float4 phc = make_float4(ph.x, ph.y, -ph.z, -ph.w);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float4 d1 = df_cmul(ph, D[d]), d2 = df_cmul(phc, D[d]);
+                    df_cmac(e1[d].x, e1[d].y, e1[d].z, e1[d].w, d1, (float)xq.x, (float)xq.y);
+                    df_cmac(e2[d].x, e2[d].y, e2[d].z, e2[d].w, d2, (float)xg.x, -(float)xg.y);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    df_cmac(e1[d].x, e1[d].y, e1[d].z, e1[d].w, D[d], (float)xq.x, (float)xq.y);
+                    df_cmac(e2[d].x, e2[d].y, e2[d].z, e2[d].w, D[d], (float)xg.x, -(float)xg.y);
+                }
+            }
+        } else {
+            const double2 ph = a.phase[ii];
+            const double2 pq = cmul(ph, make_double2((double)xq.x, (double)xq.y));         // ph q_n
+            const double2 pg = cmul(cconj(ph), make_double2((double)xg.x, -(double)xg.y));  // conj(ph) conj(g_n)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double2 Dd = a.dval[3 * q + d];
+                c1[d] = cadd(c1[d], cmul(Dd, pq));
+                c2[d] = cadd(c2[d], cmul(Dd, pg));
+            }
         }
     }
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
         for (int o = 16; o > 0; o >>= 1) {
             obs[d].x += __shfl_xor_sync(0xffffffffu, obs[d].x, o);
             obs[d].y += __shfl_xor_sync(0xffffffffu, obs[d].y, o);
             src[d].x += __shfl_xor_sync(0xffffffffu, src[d].x, o);
             src[d].y += __shfl_xor_sync(0xffffffffu, src[d].y, o);
-            c1[d].x += __shfl_xor_sync(0xffffffffu, c1[d].x, o);
-            c1[d].y += __shfl_xor_sync(0xffffffffu, c1[d].y, o);
-            c2[d].x += __shfl_xor_sync(0xffffffffu, c2[d].x, o);
-            c2[d].y += __shfl_xor_sync(0xffffffffu, c2[d].y, o);
         }
+        if constexpr (DF) {
+            df_warp_sum(e1[d].x, e1[d].y);
+            df_warp_sum(e1[d].z, e1[d].w);
+            df_warp_sum(e2[d].x, e2[d].y);
+            df_warp_sum(e2[d].z, e2[d].w);
+        } else {
+            for (int o = 16; o > 0; o >>= 1) {
+                c1[d].x += __shfl_xor_sync(0xffffffffu, c1[d].x, o);
+                c1[d].y += __shfl_xor_sync(0xffffffffu, c1[d].y, o);
+                c2[d].x += __shfl_xor_sync(0xffffffffu, c2[d].x, o);
+                c2[d].y += __shfl_xor_sync(0xffffffffu, c2[d].y, o);
+            }
+        }
+    }
+    if constexpr (DF) {
+        // in FP32 arithmetic: the real part of the three products as a
+        // double-float sum (exact products by fma, TwoSum for the leading
+        // parts), converted to FP64 once
+        if (lane == 0) {
+            const float qx = (float)qs[m].x, qy = (float)qs[m].y, gx = (float)gs[m].x, gy = (float)gs[m].y;
+            for (int d = 0; d < 3; ++d) {
+                float h = 0.f, l = 0.f;
+                // X = obs + c1 (double-float per component)
+                float xr, xre, xi, xie;
+                two_sum((float)obs[d].x, e1[d].x, xr, xre);
+                two_sum((float)obs[d].y, e1[d].z, xi, xie);
+                xre += e1[d].y;
+                xie += e1[d].w;
+                // terms a b with a float, b = b_hi + b_lo: exact a b_hi, then a b_lo
+                const float tb[5] = {xr, xi, (float)src[d].x, (float)src[d].y, 0.f};
+                const float ta[4] = {gx, gy, qx, qy};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float p = ta[t] * tb[t], e = fmaf(ta[t], tb[t], -p);
+                    two_sum_acc(h, l, p);
+                    l += e;
+                }
+                l += gx * xre + gy * xie;
+                // Re(q c2) = qx c2r - qy c2i
+                const float p1 = qx * e2[d].x, f1 = fmaf(qx, e2[d].x, -p1);
+                const float p2 = qy * e2[d].z, f2 = fmaf(qy, e2[d].z, -p2);
+                two_sum_acc(h, l, p1);
+                two_sum_acc(h, l, -p2);
+                l += (f1 - f2) + (qx * e2[d].y - qy * e2[d].w);
+                const double v = (double)h + (double)l;
+                const long long o = 3LL * a.perm[m] + d;
+                grad[o] = a.first ? v : grad[o] + v;
+            }
+        }
+        return;
+    }
     if (lane == 0) {
         const double2 qm = make_double2((double)qs[m].x, (double)qs[m].y);
         const double2 gm = make_double2((double)gs[m].x, (double)gs[m].y);
         for (int d = 0; d < 3; ++d) {
-            const double2 t1 = cmul(cconj(gm), cadd(obs[d], c1[d]));   // conj(g_k) (...)
-            const double2 t2 = cmul(qm, cconj(src[d]));                 // q_k conj(...)
+            const double2 od = make_double2((double)obs[d].x, (double)obs[d].y);
+            const double2 sd = make_double2((double)src[d].x, (double)src[d].y);
+            const double2 t1 = cmul(cconj(gm), cadd(od, c1[d]));   // conj(g_k) (...)
+            const double2 t2 = cmul(qm, cconj(sd));                 // q_k conj(...)
             const double2 t3 = cmul(qm, c2[d]);
             const double v = t1.x + t2.x + t3.x;
             const long long o = 3LL * a.perm[m] + d;
@@ -1019,10 +1110,25 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
         ga.row_ptr = d.row_ptr;
         ga.col = d.col;
         ga.dval = d.dval;
+        ga.dvaldf = reinterpret_cast<const float4*>(d.dval);
         ga.phase = P->dphase;
-        if (N > 0)
-            grad_kernel<T, PP><<<(unsigned)((N * 32 + 255) / 256), 256, 0, s>>>(
-                ga, gA, gD, (const cplx<T>*)P->fU, (const cplx<T>*)P->fV, qs, gs, grad);
+        ga.phasedf = P->dphasedf;
+        for (int i = 0; i < P->nimg; ++i)
+            if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) ga.self_img = i;
+        const unsigned nbk = (unsigned)((N * 32 + 255) / 256);
+        if (N > 0) {
+            if constexpr (sizeof(T) == 4) {
+                if (P->corr_mode == PIM_CORR_DOUBLE_FLOAT)
+                    grad_kernel<T, PP, true><<<nbk, 256, 0, s>>>(ga, gA, gD, (const cplx<T>*)P->fU,
+                                                                 (const cplx<T>*)P->fV, qs, gs, grad);
+                else
+                    grad_kernel<T, PP, false><<<nbk, 256, 0, s>>>(ga, gA, gD, (const cplx<T>*)P->fU,
+                                                                  (const cplx<T>*)P->fV, qs, gs, grad);
+            } else {
+                grad_kernel<T, PP, false><<<nbk, 256, 0, s>>>(ga, gA, gD, (const cplx<T>*)P->fU,
+                                                              (const cplx<T>*)P->fV, qs, gs, grad);
+            }
+        }
         PIM_CK(cudaGetLastError());
     }
     return PIM_OK;

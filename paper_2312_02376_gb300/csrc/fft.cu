@@ -122,11 +122,11 @@ struct PassArgs {
 };
 
 // FFT along a strided axis: CTA = (plane, group of B consecutive columns).
-// Every thread issues all of its global loads (and, in the z pass, its
-// spectrum loads) before it stores to shared memory, so their latencies
-// overlap instead of forming a chain.
+// Every thread issues its global loads in groups (up to 8) before it stores
+// them to shared memory, so that their latencies overlap instead of forming
+// a chain.
 template <typename T, int L, int B, int NBS>
-__global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, cplx<T>* out,
+__global__ void __launch_bounds__(B* NBS, sizeof(T) == 4 ? (B* NBS >= 512 ? 2 : (B* NBS >= 256 ? 3 : 1)) : 1) fft_strided_kernel(const cplx<T>* in, cplx<T>* out,
                                                               PassArgs a, const cplx<T>* __restrict__ tw,
                                                               const cplx<T>* __restrict__ spec) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,23 +141,31 @@ __global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, 
     const cplx<T> zero = mk<T>(T(0), T(0));
     const cplx<T>* ib = in + plane * a.in_plane + c0;
     const bool cok = c0 + col < a.width;   // i % B == col for every i = tid + k NT
-    cplx<T> v[EPT];
+    // loads in groups of at most 8 per thread, all of a group issued before
+    // its shared-memory stores; the z pass also prefetches its spectrum
+    // tile into registers when a thread holds at most 8 elements
+    constexpr int G = EPT < 8 ? EPT : 8;
+    constexpr bool PREF = EPT <= 8;
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-        const int r = (tid + k * NT) / B;
-        v[k] = (r < a.n_in && cok) ? ib[r * a.in_row + col] : zero;
+    for (int k0 = 0; k0 < EPT; k0 += G) {
+        cplx<T> v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int r = (tid + (k0 + g) * NT) / B;
+            v[g] = (r < a.n_in && cok) ? ib[(long long)r * a.in_row + col] : zero;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) s[((tid + (k0 + g) * NT) / B) * LD + col] = v[g];
     }
-    cplx<T> sp[EPT];
-    if (a.mode >= 2) {
-        const cplx<T>* spb = spec + plane * a.spec_plane + c0;
+    const cplx<T>* spb = spec + plane * a.spec_plane + c0;
+    cplx<T> sp[PREF ? EPT : 1];
+    if (PREF && a.mode >= 2) {
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
+        for (int k = 0; k < (PREF ? EPT : 1); ++k) {
             const int r = (tid + k * NT) / B;
-            sp[k] = cok ? spb[r * a.spec_row + col] : zero;
+            sp[k] = cok ? spb[(long long)r * a.spec_row + col] : zero;
         }
     }
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) s[((tid + k * NT) / B) * LD + col] = v[k];
     __syncthreads();
     if (a.mode == 1) {
         fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
@@ -168,7 +176,9 @@ __global__ void __launch_bounds__(B* NBS) fft_strided_kernel(const cplx<T>* in, 
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const int r = (tid + k * NT) / B;
-            cplx<T> w = sp[k];
+            cplx<T> w;
+            if constexpr (PREF) w = sp[k];
+            else w = cok ? spb[(long long)r * a.spec_row + col] : zero;
             if (a.mode == 3) w.y = -w.y;
             s[r * LD + col] = cmul(s[r * LD + col], w);
         }
@@ -228,6 +238,15 @@ template <> struct TileCfg<float> {
 template <> struct TileCfg<double> {
     static constexpr int B(int L) { return L <= 128 ? 16 : (L == 256 ? 8 : 4); }
 };
+// strided passes: narrower column groups at the long lengths, so that a
+// thread holds at most 8 elements (registers) and two CTAs fit on an SM
+template <typename T> struct TileCfgS;
+template <> struct TileCfgS<float> {
+    static constexpr int B(int L) { return L <= 64 ? 32 : (L <= 512 ? 16 : 8); }
+};
+template <> struct TileCfgS<double> {
+    static constexpr int B(int L) { return L <= 128 ? 16 : (L == 256 ? 8 : 4); }
+};
 
 template <typename T, int L>
 pim_status launch_len(const cplx<T>* in, cplx<T>* out, PassArgs a, const cplx<T>* tw, cudaStream_t s) {
@@ -247,7 +266,7 @@ pim_status launch_len(const cplx<T>* in, cplx<T>* out, PassArgs a, const cplx<T>
 template <typename T, int L>
 pim_status launch_strided_len(const cplx<T>* in, cplx<T>* out, PassArgs a, int nplanes, const cplx<T>* tw,
                               const cplx<T>* spec, cudaStream_t s) {
-    constexpr int B = TileCfg<T>::B(L);
+    constexpr int B = TileCfgS<T>::B(L);
     constexpr int NBS0 = L / 8 > 0 ? L / 8 : 1;
     constexpr int NBS = NBS0 * B > 512 ? 512 / B : NBS0;
     constexpr int NT = B * NBS;

@@ -247,18 +247,28 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
         df_warp_sum(ih, il);
     }
     if (lane == 0) {
-        if (CM == PIM_CORR_DOUBLE_FLOAT || CM == PIM_CORR_FP32) {
-            accd.x = (double)rh + (double)rl;
-            accd.y = (double)ih + (double)il;
+        T re, im;
+        if constexpr (sizeof(T) == 4 && CM != PIM_CORR_FP64) {
+            // FP32 output: grid part + correction rounded once, without the
+            // FP64 pipe (TwoSum of the leading parts, then the tails)
+            float s, e;
+            ih *= fs;  // undo the conjugation of the adjoint sum
+            il *= fs;
+            two_sum(acc.x, rh, s, e);
+            re = s + (e + rl);
+            two_sum(acc.y, ih, s, e);
+            im = s + (e + il);
+        } else {
+            accd.y *= (double)fs;  // undo the conjugation of the adjoint sum
+            re = (T)((double)acc.x + accd.x);
+            im = (T)((double)acc.y + accd.y);
         }
-        accd.y *= (double)fs;  // undo the conjugation of the adjoint sum
-        const double re = (double)acc.x + accd.x, im = (double)acc.y + accd.y;
         if (a.sorted_out) {
-            ((cplx<T>*)out)[m] = mk<T>((T)re, (T)im);
+            ((cplx<T>*)out)[m] = mk<T>(re, im);
         } else {
             const long long o = (long long)a.perm[m] * a.nrhs + a.r;
-            if (a.real_out) ((T*)out)[o] = (T)re;
-            else ((cplx<T>*)out)[o] = mk<T>((T)re, (T)im);
+            if (a.real_out) ((T*)out)[o] = re;
+            else ((cplx<T>*)out)[o] = mk<T>(re, im);
         }
     }
 }

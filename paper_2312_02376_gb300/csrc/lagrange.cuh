@@ -124,4 +124,58 @@ __device__ __forceinline__ void lagrange_dw_rt(int p, T t, T* dw) {
     }
 }
 
+// Weights and their t-derivatives together, O(P) per node: prefix and suffix
+// products of (t - l) and, by the product rule, their derivatives.
+template <typename T, int P>
+__device__ __forceinline__ void lagrange_wdw(T t, T* w, T* dw) {
+    T pre[P + 1], dpre[P + 1], suf[P + 1], dsuf[P + 1];
+    pre[0] = T(1);
+    dpre[0] = T(0);
+#pragma unroll
+    for (int j = 1; j <= P; ++j) {
+        pre[j] = pre[j - 1] * (t - T(j - 1));
+        dpre[j] = dpre[j - 1] * (t - T(j - 1)) + pre[j - 1];
+    }
+    suf[P] = T(1);
+    dsuf[P] = T(0);
+#pragma unroll
+    for (int j = P - 1; j >= 0; --j) {
+        suf[j] = suf[j + 1] * (t - T(j + 1));
+        dsuf[j] = dsuf[j + 1] * (t - T(j + 1)) + suf[j + 1];
+    }
+#pragma unroll
+    for (int j = 0; j <= P; ++j) {
+        const T c = T(lag_inv_den(P, j));
+        w[j] = pre[j] * suf[j] * c;
+        dw[j] = (dpre[j] * suf[j] + pre[j] * dsuf[j]) * c;
+    }
+}
+
+// The same for a runtime degree p <= PIM_MAX_P (entries above p are zero).
+template <typename T>
+__device__ __forceinline__ void lagrange_wdw_rt(int p, T t, T* w, T* dw) {
+    T pre[PIM_MAX_P + 1], dpre[PIM_MAX_P + 1], suf[PIM_MAX_P + 1], dsuf[PIM_MAX_P + 1];
+    pre[0] = T(1);
+    dpre[0] = T(0);
+#pragma unroll
+    for (int j = 1; j <= PIM_MAX_P; ++j) {
+        pre[j] = pre[j - 1] * (t - T(j - 1));
+        dpre[j] = dpre[j - 1] * (t - T(j - 1)) + pre[j - 1];
+    }
+    suf[PIM_MAX_P] = T(1);
+    dsuf[PIM_MAX_P] = T(0);
+#pragma unroll
+    for (int j = PIM_MAX_P - 1; j >= 0; --j) {
+        const bool in = j + 1 <= p;
+        suf[j] = in ? suf[j + 1] * (t - T(j + 1)) : T(1);
+        dsuf[j] = in ? dsuf[j + 1] * (t - T(j + 1)) + suf[j + 1] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j <= PIM_MAX_P; ++j) {
+        const T c = j <= p ? T(c_lag_inv.v[p][j]) : T(0);
+        w[j] = pre[j] * suf[j] * c;
+        dw[j] = (dpre[j] * suf[j] + pre[j] * dsuf[j]) * c;
+    }
+}
+
 }  // namespace pim_k

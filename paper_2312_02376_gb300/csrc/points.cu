@@ -409,6 +409,20 @@ __device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32
     return csub(exact, grid);
 }
 
+// position derivatives of a value: FP64, or double-float splits in the same
+// 16-byte slots when the apply accumulates in double-float
+__device__ __forceinline__ void store_grad(const FillArgs& a, long long q, const double2* gr, double2* dval) {
+    for (int k = 0; k < 3; ++k) {
+        if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
+            const float rh = (float)gr[k].x, ih = (float)gr[k].y;
+            reinterpret_cast<float4*>(dval)[3 * q + k] =
+                make_float4(rh, (float)(gr[k].x - (double)rh), ih, (float)(gr[k].y - (double)ih));
+        } else {
+            dval[3 * q + k] = gr[k];
+        }
+    }
+}
+
 __device__ __forceinline__ void store_value(const FillArgs& a, long long q, double2 d, double2* val, float4* valdf,
                                             float2* valf) {
     val[q] = d;
@@ -438,7 +452,7 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
                     double2 gr[3];
                     const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
                     store_value(a, q, d, val, valdf, valf);
-                    for (int k = 0; k < 3; ++k) dval[3 * q + k] = gr[k];
+                    store_grad(a, q, gr, dval);
                 } else {
                     const double2 d = corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr);
                     store_value(a, q, d, val, valdf, valf);
@@ -465,7 +479,7 @@ __global__ void pair_refill_kernel(const double* pos, const uint32_t* ns, const 
                 double2 gr[3];
                 const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
                 store_value(a, q, d, val, valdf, valf);
-                for (int k = 0; k < 3; ++k) dval[3 * q + k] = gr[k];
+                store_grad(a, q, gr, dval);
             } else {
                 store_value(a, q, corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr), val, valdf, valf);
             }

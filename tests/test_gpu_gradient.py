@@ -67,6 +67,31 @@ def test_position_grad_matches_oracle(name):
     pl.close()
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", ["double_float", "fp64"])
+def test_position_grad_fp32_matches_oracle(name, mode):
+    # FP32 bulk (grid sums in FP32); the correction list in double-float or
+    # FP64: rel-L2 within the FP32 path's bound
+    c = CASES[name]
+    P, _, pts, q, g, real = setup(name)
+    cm = pim.PIM_CORR_DOUBLE_FLOAT if mode == "double_float" else pim.PIM_CORR_FP64
+    pl = pim.Plan(c["D"], c["pdims"], c["k"], c["k0"], c["n"], p=c["p"], layers=1, precision="fp32", b=c["b"],
+                  nf=c["nf"], pf=c["pf"], corr_mode=cm, with_gradient=True)
+    pl.set_points(torch.tensor(pts, device="cuda"))
+    if real:
+        qd = torch.tensor(np.real(q), dtype=torch.float32, device="cuda")
+        gd = torch.tensor(np.real(g), dtype=torch.float32, device="cuda")
+    else:
+        qd = torch.tensor(q, dtype=torch.complex64, device="cuda")
+        gd = torch.tensor(g, dtype=torch.complex64, device="cuda")
+    G = pl.position_grad(qd, gd).cpu().numpy()
+    qo = qd.cpu().numpy().astype(complex)
+    go = gd.cpu().numpy().astype(complex)
+    Go = opim.Plan(P, pts).position_grad(qo, go)
+    assert rel(G, Go) < 2e-5, rel(G, Go)
+    pl.close()
+
+
 @pytest.mark.parametrize("name", ["helmholtz2d_bloch", "npsp3d"])
 def test_update_positions_is_frozen_topology_apply(name):
     P, pl, pts, q, g, real = setup(name)
