@@ -489,18 +489,96 @@ struct GradArgs {
     const float4* phasedf;
 };
 
+// One stencil's contribution to a point's gradient, lane (jy, jz) taking
+// the x-row: adds Re[conj(g_k) (grad w . U)] + Re[q_k conj(grad w . V)] to
+// part[0..2], with the weights of degree PF (compile time) at local
+// coordinates t (grid steps) and 1/h the inverse spacings.
+template <typename T, int PF>
+__device__ __forceinline__ void grad_stencil(const T* t, const double* h, int jy, int jz, const cplx<T>* rowU,
+                                             const cplx<T>* rowV, cplx<T> gm, cplx<T> qm, T* part) {
+    constexpr int NP = PF + 1;
+    T w[3][NP], dw[3][NP];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lagrange_wdw<T, PF>(t[d], w[d], dw[d]);
+        const T ih = T(1.0 / h[d]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) dw[d][j] *= ih;
+    }
+    const T wy = pick<NP>(w[1], jy), dwy = pick<NP>(dw[1], jy);
+    const T wz = pick<NP>(w[2], jz), dwz = pick<NP>(dw[2], jz);
+    // A = sum w'_x U, B = sum w_x U (C, D the same for V); the row adds
+    // (w_y w_z A, w'_y w_z B, w_y w'_z B) to the three gradient components
+    cplx<T> A = mk<T>(T(0), T(0)), B = A, C = A, D = A;
+#pragma unroll
+    for (int jx = 0; jx < NP; ++jx) {
+        if (rowU) {
+            const cplx<T> u = rowU[jx];
+            A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
+            B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
+        }
+        if (rowV) {
+            const cplx<T> v = rowV[jx];
+            C.x += dw[0][jx] * v.x; C.y += dw[0][jx] * v.y;
+            D.x += w[0][jx] * v.x;  D.y += w[0][jx] * v.y;
+        }
+    }
+    // Re[conj(g) X] = g.x X.x + g.y X.y and Re[q conj(Y)] = q.x Y.x + q.y Y.y
+    const T ra = gm.x * A.x + gm.y * A.y + qm.x * C.x + qm.y * C.y;
+    const T rb = gm.x * B.x + gm.y * B.y + qm.x * D.x + qm.y * D.y;
+    part[0] += wy * wz * ra;
+    part[1] += dwy * wz * rb;
+    part[2] += wy * dwz * rb;
+}
+
+// The same for a runtime far degree p <= PIM_MAX_P.
+template <typename T>
+__device__ __forceinline__ void grad_stencil_rt(int p, const T* t, const double* h, int jy, int jz,
+                                                const cplx<T>* rowU, const cplx<T>* rowV, cplx<T> gm, cplx<T> qm,
+                                                T* part) {
+    T w[3][PIM_MAX_P + 1], dw[3][PIM_MAX_P + 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lagrange_wdw_rt<T>(p, t[d], w[d], dw[d]);
+        const T ih = T(1.0 / h[d]);
+#pragma unroll
+        for (int j = 0; j <= PIM_MAX_P; ++j) dw[d][j] *= ih;
+    }
+    const T wy = pick<PIM_MAX_P + 1>(w[1], jy), dwy = pick<PIM_MAX_P + 1>(dw[1], jy);
+    const T wz = pick<PIM_MAX_P + 1>(w[2], jz), dwz = pick<PIM_MAX_P + 1>(dw[2], jz);
+    cplx<T> A = mk<T>(T(0), T(0)), B = A, C = A, D = A;
+#pragma unroll
+    for (int jx = 0; jx <= PIM_MAX_P; ++jx) {
+        if (jx > p) break;
+        if (rowU) {
+            const cplx<T> u = rowU[jx];
+            A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
+            B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
+        }
+        if (rowV) {
+            const cplx<T> v = rowV[jx];
+            C.x += dw[0][jx] * v.x; C.y += dw[0][jx] * v.y;
+            D.x += w[0][jx] * v.x;  D.y += w[0][jx] * v.y;
+        }
+    }
+    const T ra = gm.x * A.x + gm.y * A.y + qm.x * C.x + qm.y * C.y;
+    const T rb = gm.x * B.x + gm.y * B.y + qm.x * D.x + qm.y * D.y;
+    part[0] += wy * wz * ra;
+    part[1] += dwy * wz * rb;
+    part[2] += wy * dwz * rb;
+}
+
 // One warp per sorted point k:
 //   grad_k = Re[conj(g_k) (grad w_k . U + grad w^o_k . u_f)]
 //          + Re[q_k conj(grad w_k . V + grad w^s_k . v_f)]
-//          + sum over row k: Re[conj(g_k) ph_i D q_n] + Re[q_k conj(g_n) conj(ph_i) D]
+//          + sum over row k of Re[D w_n],  w_n = conj(g_k) ph_i q_n + q_k conj(ph_i g_n)
 // with U, u_f the forward grid potentials of q, V, v_f the adjoint ones of g
-// and D = d d_i(k, n) / d r_k from the correction list.  In both stencil
-// gathers lane (jy, jz) takes one x-row: with A = sum_x w'_x U, B = sum_x w_x U
-// the row adds (w_y w_z A, w'_y w_z B, w_y w'_z B) to the three components.
-// Grid sums accumulate in T; the list in FP64 (DF = false) or in
-// double-float on the FP32 pipes (DF = true, T = float).
+// and D = d d_i(k, n) / d r_k from the correction list.  The row constants
+// q_k, g_k are folded in per lane, so only three real sums per point are
+// reduced over the warp.  Grid sums accumulate in T; the list in FP64
+// (DF = false) or in double-float on the FP32 pipes (DF = true, T = float).
 template <typename T, int P, bool DF>
-__global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __restrict__ U,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) grad_kernel(GradArgs a, const cplx<T>* __restrict__ U,
                                                    const cplx<T>* __restrict__ V, const cplx<T>* __restrict__ uf,
                                                    const cplx<T>* __restrict__ vf, const cplx<T>* __restrict__ qs,
                                                    const cplx<T>* __restrict__ gs, double* grad) {
@@ -508,89 +586,43 @@ __global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __
     const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (m >= a.N) return;
     constexpr int NP = P + 1;
-    // obs[d]: observer-side sums (U, u_f), src[d]: source-side sums (V, v_f)
-    cplx<T> obs[3], src[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) obs[d] = src[d] = mk<T>(T(0), T(0));
+    const cplx<T> qm = qs[m], gm = gs[m];
+    T part[3] = {T(0), T(0), T(0)};
     if (lane < NP * NP) {
         const int jy = lane % NP, jz = lane / NP;
         int s[3];
         unpack3(a.ns[m], s[0], s[1], s[2]);
-        T w[3][NP], dw[3][NP];
+        T t[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const T tt = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
-            lagrange_wdw<T, P>(tt, w[d], dw[d]);
-            const T ih = T(1.0 / a.h[d]);
-#pragma unroll
-            for (int j = 0; j < NP; ++j) dw[d][j] *= ih;
-        }
-        const T wy = pick<NP>(w[1], jy), dwy = pick<NP>(dw[1], jy);
-        const T wz = pick<NP>(w[2], jz), dwz = pick<NP>(dw[2], jz);
+        for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
         const long long row = ((long long)(s[2] + jz) * a.n[1] + (s[1] + jy)) * a.n[0] + s[0];
-        cplx<T> A = mk<T>(T(0), T(0)), B = A, C = A, D = A;
-#pragma unroll
-        for (int jx = 0; jx < NP; ++jx) {
-            const cplx<T> u = U[row + jx], v = V[row + jx];
-            A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
-            B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
-            C.x += dw[0][jx] * v.x; C.y += dw[0][jx] * v.y;
-            D.x += w[0][jx] * v.x;  D.y += w[0][jx] * v.y;
-        }
-        obs[0] = cscale(A, wy * wz);
-        obs[1] = cscale(B, dwy * wz);
-        obs[2] = cscale(B, wy * dwz);
-        src[0] = cscale(C, wy * wz);
-        src[1] = cscale(D, dwy * wz);
-        src[2] = cscale(D, wy * dwz);
+        grad_stencil<T, P>(t, a.h, jy, jz, U + row, V + row, gm, qm, part);
     }
     if (a.has_far) {
         // observer grid for u_f, source grid for v_f
         const int np = a.pf + 1;
         for (int side = 0; side < 2; ++side) {
+            int f[3];
+            unpack3(side == 0 ? a.fo[m] : a.fs[m], f[0], f[1], f[2]);
+            const int toff = side == 0 ? 3 : 0;
+            T t[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ftd[6 * m + toff + d] : (T)a.ft[6 * m + toff + d];
+            const cplx<T>* gridp = side == 0 ? uf : vf;
             for (int l = lane; l < np * np; l += 32) {
                 const int jy = l % np, jz = l / np;
-                int f[3];
-                unpack3(side == 0 ? a.fo[m] : a.fs[m], f[0], f[1], f[2]);
-                const int toff = side == 0 ? 3 : 0;
-                T w[3][PIM_MAX_P + 1], dw[3][PIM_MAX_P + 1];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T tt = sizeof(T) == 8 ? (T)a.ftd[6 * m + toff + d] : (T)a.ft[6 * m + toff + d];
-                    lagrange_wdw_rt<T>(a.pf, tt, w[d], dw[d]);
-                    const T id = T(1.0 / a.df[d]);
-#pragma unroll
-                    for (int j = 0; j <= PIM_MAX_P; ++j) dw[d][j] *= id;
-                }
-                const T wy = pick<PIM_MAX_P + 1>(w[1], jy), dwy = pick<PIM_MAX_P + 1>(dw[1], jy);
-                const T wz = pick<PIM_MAX_P + 1>(w[2], jz), dwz = pick<PIM_MAX_P + 1>(dw[2], jz);
-                const cplx<T>* grid = side == 0 ? uf : vf;
-                const cplx<T>* rowp = grid + ((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
-                cplx<T> A = mk<T>(T(0), T(0)), B = A;
-#pragma unroll
-                for (int jx = 0; jx <= PIM_MAX_P; ++jx) {
-                    if (jx < np) {
-                        const cplx<T> u = rowp[jx];
-                        A.x += dw[0][jx] * u.x; A.y += dw[0][jx] * u.y;
-                        B.x += w[0][jx] * u.x;  B.y += w[0][jx] * u.y;
-                    }
-                }
-                cplx<T>* acc = side == 0 ? obs : src;
-                acc[0] = cadd(acc[0], cscale(A, wy * wz));
-                acc[1] = cadd(acc[1], cscale(B, dwy * wz));
-                acc[2] = cadd(acc[2], cscale(B, wy * dwz));
+                const cplx<T>* rowp = gridp + ((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
+                const cplx<T>* rU = side == 0 ? rowp : nullptr;
+                const cplx<T>* rV = side == 0 ? nullptr : rowp;
+                if (a.pf == P) grad_stencil<T, P>(t, a.df, jy, jz, rU, rV, gm, qm, part);
+                else grad_stencil_rt<T>(a.pf, t, a.df, jy, jz, rU, rV, gm, qm, part);
             }
         }
     }
-    // correction list: c1[d] = sum ph D q_n, c2[d] = sum conj(ph) D conj(g_n)
+    // correction list
     const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
-    double2 c1[3], c2[3];
-    float4 e1[3], e2[3];  // double-float accumulators (re hi, re lo, im hi, im lo)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        c1[d] = c2[d] = make_double2(0.0, 0.0);
-        e1[d] = e2[d] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    float hh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};  // double-float sums (DF)
+    double acc[3] = {0.0, 0.0, 0.0};                         // FP64 sums
     for (long long q = r0 + lane; q < r1; q += 32) {
         const uint32_t c = __ldcs(a.col + q);
         const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
@@ -599,103 +631,59 @@ __global__ void __launch_bounds__(256) grad_kernel(GradArgs a, const cplx<T>* __
             float4 D[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) D[d] = __ldcs(a.dvaldf + 3 * q + d);
+            float ax = (float)xq.x, ay = (float)xq.y, bx = (float)xg.x, by = (float)xg.y;
             if (ii != a.self_img) {
                 const float4 ph = a.phasedf[ii];
-                const float4 phc = make_float4(ph.x, ph.y, -ph.z, -ph.w);
+                const float px = ph.x + ph.y, py = ph.z + ph.w;
+                const float tx = px * ax - py * ay, ty = px * ay + py * ax;
+                const float ux = px * bx - py * by, uy = px * by + py * bx;
+                ax = tx; ay = ty; bx = ux; by = uy;
+            }
+            const float gx = (float)gm.x, gy = (float)gm.y, qx = (float)qm.x, qy = (float)qm.y;
+            const float wr = gx * ax + gy * ay + qx * bx + qy * by;
+            const float wi = gx * ay - gy * ax + qy * bx - qx * by;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float4 d1 = df_cmul(ph, D[d]), d2 = df_cmul(phc, D[d]);
-                    df_cmac(e1[d].x, e1[d].y, e1[d].z, e1[d].w, d1, (float)xq.x, (float)xq.y);
-                    df_cmac(e2[d].x, e2[d].y, e2[d].z, e2[d].w, d2, (float)xg.x, -(float)xg.y);
-                }
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    df_cmac(e1[d].x, e1[d].y, e1[d].z, e1[d].w, D[d], (float)xq.x, (float)xq.y);
-                    df_cmac(e2[d].x, e2[d].y, e2[d].z, e2[d].w, D[d], (float)xg.x, -(float)xg.y);
-                }
+            for (int d = 0; d < 3; ++d) {
+                // Re(D w) = D.re w.re - D.im w.im with exact leading products
+                const float p1 = D[d].x * wr, e1 = fmaf(D[d].x, wr, -p1);
+                const float p2 = D[d].z * wi, e2 = fmaf(D[d].z, wi, -p2);
+                two_sum_acc(hh[d], ll[d], p1);
+                two_sum_acc(hh[d], ll[d], -p2);
+                ll[d] += (e1 - e2) + (D[d].y * wr - D[d].w * wi);
             }
         } else {
             const double2 ph = a.phase[ii];
-            const double2 pq = cmul(ph, make_double2((double)xq.x, (double)xq.y));         // ph q_n
-            const double2 pg = cmul(cconj(ph), make_double2((double)xg.x, -(double)xg.y));  // conj(ph) conj(g_n)
+            const double2 pq = cmul(ph, make_double2((double)xq.x, (double)xq.y));  // ph q_n
+            const double2 pg = cmul(ph, make_double2((double)xg.x, (double)xg.y));  // ph g_n
+            const double2 gmd = make_double2((double)gm.x, (double)gm.y), qmd = make_double2((double)qm.x, (double)qm.y);
+            const double2 w = cadd(cmul(cconj(gmd), pq), cmul(qmd, cconj(pg)));
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double2 Dd = a.dval[3 * q + d];
-                c1[d] = cadd(c1[d], cmul(Dd, pq));
-                c2[d] = cadd(c2[d], cmul(Dd, pg));
+                acc[d] += Dd.x * w.x - Dd.y * w.y;
             }
         }
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        for (int o = 16; o > 0; o >>= 1) {
-            obs[d].x += __shfl_xor_sync(0xffffffffu, obs[d].x, o);
-            obs[d].y += __shfl_xor_sync(0xffffffffu, obs[d].y, o);
-            src[d].x += __shfl_xor_sync(0xffffffffu, src[d].x, o);
-            src[d].y += __shfl_xor_sync(0xffffffffu, src[d].y, o);
-        }
+        for (int o = 16; o > 0; o >>= 1) part[d] += __shfl_xor_sync(0xffffffffu, part[d], o);
         if constexpr (DF) {
-            df_warp_sum(e1[d].x, e1[d].y);
-            df_warp_sum(e1[d].z, e1[d].w);
-            df_warp_sum(e2[d].x, e2[d].y);
-            df_warp_sum(e2[d].z, e2[d].w);
+            df_warp_sum(hh[d], ll[d]);
         } else {
-            for (int o = 16; o > 0; o >>= 1) {
-                c1[d].x += __shfl_xor_sync(0xffffffffu, c1[d].x, o);
-                c1[d].y += __shfl_xor_sync(0xffffffffu, c1[d].y, o);
-                c2[d].x += __shfl_xor_sync(0xffffffffu, c2[d].x, o);
-                c2[d].y += __shfl_xor_sync(0xffffffffu, c2[d].y, o);
-            }
+            for (int o = 16; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
         }
-    }
-    if constexpr (DF) {
-        // in FP32 arithmetic: the real part of the three products as a
-        // double-float sum (exact products by fma, TwoSum for the leading
-        // parts), converted to FP64 once
-        if (lane == 0) {
-            const float qx = (float)qs[m].x, qy = (float)qs[m].y, gx = (float)gs[m].x, gy = (float)gs[m].y;
-            for (int d = 0; d < 3; ++d) {
-                float h = 0.f, l = 0.f;
-                // X = obs + c1 (double-float per component)
-                float xr, xre, xi, xie;
-                two_sum((float)obs[d].x, e1[d].x, xr, xre);
-                two_sum((float)obs[d].y, e1[d].z, xi, xie);
-                xre += e1[d].y;
-                xie += e1[d].w;
-                // terms a b with a float, b = b_hi + b_lo: exact a b_hi, then a b_lo
-                const float tb[5] = {xr, xi, (float)src[d].x, (float)src[d].y, 0.f};
-                const float ta[4] = {gx, gy, qx, qy};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float p = ta[t] * tb[t], e = fmaf(ta[t], tb[t], -p);
-                    two_sum_acc(h, l, p);
-                    l += e;
-                }
-                l += gx * xre + gy * xie;
-                // Re(q c2) = qx c2r - qy c2i
-                const float p1 = qx * e2[d].x, f1 = fmaf(qx, e2[d].x, -p1);
-                const float p2 = qy * e2[d].z, f2 = fmaf(qy, e2[d].z, -p2);
-                two_sum_acc(h, l, p1);
-                two_sum_acc(h, l, -p2);
-                l += (f1 - f2) + (qx * e2[d].y - qy * e2[d].w);
-                const double v = (double)h + (double)l;
-                const long long o = 3LL * a.perm[m] + d;
-                grad[o] = a.first ? v : grad[o] + v;
-            }
-        }
-        return;
     }
     if (lane == 0) {
-        const double2 qm = make_double2((double)qs[m].x, (double)qs[m].y);
-        const double2 gm = make_double2((double)gs[m].x, (double)gs[m].y);
         for (int d = 0; d < 3; ++d) {
-            const double2 od = make_double2((double)obs[d].x, (double)obs[d].y);
-            const double2 sd = make_double2((double)src[d].x, (double)src[d].y);
-            const double2 t1 = cmul(cconj(gm), cadd(od, c1[d]));   // conj(g_k) (...)
-            const double2 t2 = cmul(qm, cconj(sd));                 // q_k conj(...)
-            const double2 t3 = cmul(qm, c2[d]);
-            const double v = t1.x + t2.x + t3.x;
+            double v;
+            if constexpr (DF) {
+                // part + hh + ll in FP32 (TwoSum), one conversion
+                float s, e;
+                two_sum((float)part[d], hh[d], s, e);
+                v = (double)s + (double)(e + ll[d]);
+            } else {
+                v = (double)part[d] + acc[d];
+            }
             const long long o = 3LL * a.perm[m] + d;
             grad[o] = a.first ? v : grad[o] + v;
         }
@@ -1054,18 +1042,12 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
             permute_kernel<T, false><<<1024, 256, 0, s>>>(g, d.perm, N, nrhs, r, nullptr, gs);
         }
         PIM_CK(cudaGetLastError());
-        // near grid potentials: U = K * Q(q), V = K^H * Q(g)
-        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
-        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, false, s)) !=
-            PIM_OK)
-            return st;
-        if ((st = spread_two_phase<T, PP>(P, gs, gD, s)) != PIM_OK) return st;
-        if ((st = fft3_conv<T>(P, P->ng, gD, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, true, s)) !=
-            PIM_OK)
-            return st;
         // far grid potentials: u_f from the source-grid projection of q, v_f
-        // (adjoint) from the observer-grid projection of g
+        // (adjoint) from the observer-grid projection of g, on the far
+        // stream while the near grids are built
         if (P->has_far) {
+            PIM_CK(cudaEventRecord(P->ev_fork, s));
+            PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
             for (int side = 0; side < 2; ++side) {
                 FarSpreadArgs fa{};
                 for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
@@ -1077,16 +1059,27 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
                 fa.ftd = d.ftd;
                 fa.toff = side == 0 ? 0 : 3;
                 const size_t sm = 2 * sizeof(T) * G;
-                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, s, fa, side == 0 ? qs : gs,
+                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, P->s_far, fa, side == 0 ? qs : gs,
                                                (cplx<T>*)P->fpart)) != PIM_OK)
                     return st;
                 double2* fq = side == 0 ? P->fA : P->fD;
-                far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, s>>>((const cplx<T>*)P->fpart, P->far_chunks, G, fq);
-                if ((st = fft3_conv<double>(P, P->fg, fq, P->fB, P->fC, P->fspec, side == 1, s)) != PIM_OK) return st;
-                far_convert_kernel<T><<<(G + 255) / 256, 256, 0, s>>>(fq, (cplx<T>*)(side == 0 ? P->fU : P->fV), G);
+                far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks, G, fq);
+                if ((st = fft3_conv<double>(P, P->fg, fq, P->fB, P->fC, P->fspec, side == 1, P->s_far)) != PIM_OK) return st;
+                far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(fq, (cplx<T>*)(side == 0 ? P->fU : P->fV), G);
                 PIM_CK(cudaGetLastError());
             }
+            PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
+        // near grid potentials: U = K * Q(q), V = K^H * Q(g)
+        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
+        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, false, s)) !=
+            PIM_OK)
+            return st;
+        if ((st = spread_two_phase<T, PP>(P, gs, gD, s)) != PIM_OK) return st;
+        if ((st = fft3_conv<T>(P, P->ng, gD, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, true, s)) !=
+            PIM_OK)
+            return st;
+        if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
         GradArgs ga{};
         for (int i = 0; i < 3; ++i) {
             ga.n[i] = P->n[i];
