@@ -537,10 +537,29 @@ class Plan:
     def apply_rows(self, q, rows):
         """u_m for m in rows only; the grid potential is summed only at the
         stencil nodes of those rows (for large inputs)."""
+        return self.rows_from(self.rows_prepare(q), rows)
+
+    def rows_prepare(self, q):
+        """The part of apply_rows shared by all rows: the regularised sources,
+        the near grid charges (step 1) and the far grid potentials (Eq. 8)."""
         P = self.P
-        rows = np.asarray(rows, np.int64)
         q = self.regularise(q)
         Q = spread(tuple(P.n), self.s, self.w, P.p, q)
+        ug = None
+        if len(P.pdims):
+            nf = tuple(P.nf)
+            qg = spread(nf, self.ss, self.ws, P.pf, q)
+            A = far_matrix(P, self.F)
+            ug = (A @ qg.ravel()).reshape(nf)
+        return q, Q, ug
+
+    def rows_from(self, state, rows):
+        """The per-row part of apply_rows: the grid potential at the rows'
+        stencil nodes (step 2), the gather (step 3), the correction (step 4)
+        and the far gather."""
+        P = self.P
+        q, Q, ug = state
+        rows = np.asarray(rows, np.int64)
         idx, wt = _stencil_nodes(self.s[rows], self.w[rows], P.p)
         flat = idx.reshape(-1, 3)
         uniq, inv = np.unique(flat, axis=0, return_inverse=True)
@@ -551,11 +570,7 @@ class Plan:
         pos = {int(r): t for t, r in enumerate(rows)}
         for mm, v in zip(m, c * q[n]):
             u[pos[int(mm)]] += v
-        if len(P.pdims):
-            nf = tuple(P.nf)
-            qg = spread(nf, self.ss, self.ws, P.pf, q)
-            A = far_matrix(P, self.F)
-            ug = (A @ qg.ravel()).reshape(nf)
+        if ug is not None:
             u += gather(ug, self.so[rows], self.wo[rows], P.pf)
         return u
 
