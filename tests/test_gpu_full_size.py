@@ -1,0 +1,145 @@
+"""Full-size workloads through the C ABI, in the launch configuration that
+bench.py times: sampled rows against the FP64 oracle (or, where the oracle
+cannot evaluate the workload, against the committed Ewald ground truth) and
+properties that hold at any size."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import pim as opim  # noqa: E402
+from paper_2312_02376_gb300 import inputs, pim  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+METHOD_TOL = 1e-4   # stated method error at p = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def read_rows(name):
+    rows, vals = [], []
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        m, re_, im_ = line.split()
+        rows.append(int(m))
+        vals.append(float(re_) + 1j * float(im_))
+    return np.array(rows), np.array(vals)
+
+
+@pytest.fixture(scope="module")
+def coulomb_1m():
+    W = inputs.coulomb3d_big()
+    pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
+                  pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT, with_gradient=True)
+    x0 = torch.tensor(W.points, dtype=torch.float64, device="cuda")
+    pl.set_points(x0)
+    yield W, pl, x0
+    pl.close()
+
+
+def test_coulomb3d_1m_rows_vs_ewald(coulomb_1m):
+    # 3D static Coulomb, N = 10^6, grid 256^3, FP32 bulk: 16 rows of the
+    # Ewald ground truth (tin-foil; the constant cancels for neutral charges)
+    W, pl, _ = coulomb_1m
+    rows, ue = read_rows("coulomb3d_1m_ewald_rows.txt")
+    u = pl.apply(torch.tensor(W.q, device="cuda")).cpu().numpy().astype(np.float64)
+    assert rel(u[rows], ue.real) < METHOD_TOL, rel(u[rows], ue.real)
+
+
+def test_coulomb3d_1m_adjoint_identity(coulomb_1m):
+    # <g, A q> = <A^H g, q> for the discrete operator (real data: A^H = A^T)
+    W, pl, _ = coulomb_1m
+    rng = np.random.default_rng(11)
+    q = rng.standard_normal(W.N)
+    g = rng.standard_normal(W.N)
+    q -= q.mean()
+    g -= g.mean()
+    qd = torch.tensor(q, dtype=torch.float32, device="cuda")
+    gd = torch.tensor(g, dtype=torch.float32, device="cuda")
+    a = torch.dot(gd.double(), pl.apply(qd).double()).item()
+    b = torch.dot(pl.apply_adjoint(gd).double(), qd.double()).item()
+    assert abs(a - b) < 1e-5 * abs(a), (a, b)
+
+
+def test_coulomb3d_1m_gradient_directional_derivative(coulomb_1m):
+    # E(x) = 1/2 q^T A(x) q: the derivative of E along a displacement field
+    # delta (all points move, frozen topology) by central differences equals
+    # 1/2 sum_k grad_k . delta_k from pim_position_grad(q, q)
+    # (points with a neighbour closer than 20 eps stay put: the expansion of
+    # E in eps is then dominated by its linear term)
+    from scipy.spatial import cKDTree
+    W, pl, x0 = coulomb_1m
+    q = torch.tensor(W.q, device="cuda")
+    grad = pl.position_grad(q, q).cpu().numpy()
+    x = W.points
+    eps = 1e-5
+    dnn = cKDTree(x, boxsize=1.0).query(x, k=2)[0][:, 1]
+    move = np.all((x > 4 * eps) & (x < 1 - 4 * eps), axis=1) & (dnn > 20 * eps)
+    delta = np.sign(grad) * move[:, None]
+    an = 0.5 * float(np.sum(grad * delta))
+    E = []
+    for s in (1, -1):
+        pl.update_positions(torch.tensor(x + s * eps * delta, device="cuda"))
+        E.append(0.5 * torch.dot(q.double(), pl.apply(q).double()).item())
+    pl.update_positions(x0)
+    fd = (E[0] - E[1]) / (2 * eps)
+    assert abs(fd - an) < 1e-3 * abs(an), (fd, an)
+
+
+def test_helmholtz1d_batch_largest_set_rows():
+    # the largest set of the batched 1D-periodic workload (64 right-hand
+    # sides, FP32 bulk, double-float correction): sampled rows of two
+    # right-hand sides against the oracle
+    sets = inputs.helmholtz1d_batch()
+    W = max(sets, key=lambda s: s.N)
+    pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, pf=W.pf,
+                  corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
+    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    u = pl.apply(torch.tensor(W.q, device="cuda")).cpu().numpy()
+    info = pl.info()
+    P = opim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b,
+                    nf=tuple(info.nf), pf=W.pf)
+    o = opim.Plan(P, W.points)
+    rows = np.random.default_rng(6).choice(W.N, 6, replace=False)
+    for r in (0, W.nrhs - 1):
+        ue = o.apply_rows(W.q[:, r].astype(np.complex128), rows)
+        assert rel(u[rows, r], ue) < FP32_TOL, (r, rel(u[rows, r], ue))
+    pl.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_helmholtz3d_spheres_recipe_rows(precision, tol):
+    # the 3D-periodic Helmholtz + Bloch recipe (3/4 uniform, 1/4 on 8 small
+    # spheres, k = 2 pi 2, k0 = (0.2k, 0.2k, 0)) at N = 40000 on a 48^3 grid:
+    # sampled rows against the oracle (at the full size of 1.6e7 points the
+    # correction list does not fit in device memory)
+    W = inputs.helmholtz3d(N=40000, n=48, nf=12)
+    pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=precision, b=W.b, nf=W.nf,
+                  pf=W.pf)
+    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    u = pl.apply(torch.tensor(W.q, dtype=dt, device="cuda")).cpu().numpy()
+    P = opim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b, nf=W.nf, pf=W.pf)
+    o = opim.Plan(P, W.points)
+    rows = np.concatenate([np.random.default_rng(7).choice(30000, 4, replace=False),
+                           30000 + np.random.default_rng(8).choice(10000, 4, replace=False)])
+    ue = o.apply_rows(W.q.astype(np.complex128), rows)
+    assert rel(u[rows], ue) < tol, rel(u[rows], ue)
+    pl.close()
