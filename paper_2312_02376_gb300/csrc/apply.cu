@@ -333,15 +333,17 @@ struct FarSpreadArgs {
 };
 
 // Per-CTA partial far-grid charges (Eq. projection) in shared memory.  Each
-// warp walks a contiguous run of (spatially sorted) points with lanes owning
-// stencil nodes; consecutive points mostly share a far stencil, so sums stay
-// in registers until the stencil start changes.
+// warp walks a contiguous run of (spatially sorted) points; lane (jy, jz)
+// owns one x-row of the far stencil and keeps its P+1 sums in registers
+// while consecutive points share a stencil start, adding them to shared
+// memory when the start changes (the lanes of one flush write distinct
+// rows, so their atomics do not collide).
 template <typename T, int PF>
 __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const cplx<T>* __restrict__ qs,
                                                          cplx<T>* part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
-    constexpr int NP = PF + 1, NP3 = NP * NP * NP, KPL = (NP3 + 31) / 32;
+    constexpr int NP = PF + 1, KP = (NP * NP + 31) / 32;  // (jy, jz) rows per lane
     const int G = a.nf[0] * a.nf[1] * a.nf[2];
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
     __syncthreads();
@@ -350,24 +352,29 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long per = (m1 - m0 + nw - 1) / nw;
     const long long w0 = m0 + wid * per, w1 = min(m1, w0 + per);
-    int jx[KPL], jy[KPL], jz[KPL];
+    bool act[KP];
+    int jy[KP], jz[KP], base[KP];
+    cplx<T> sum[KP][NP];
 #pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-        const int o = lane + 32 * k;
-        jx[k] = o % NP;
-        jy[k] = (o / NP) % NP;
-        jz[k] = o / (NP * NP);
+    for (int k = 0; k < KP; ++k) {
+        const int l = lane + 32 * k;
+        act[k] = l < NP * NP;
+        jy[k] = act[k] ? l % NP : 0;
+        jz[k] = act[k] ? l / NP : 0;
+        base[k] = 0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sum[k][i] = mk<T>(T(0), T(0));
     }
     uint32_t cur = 0xffffffffu;
-    int loc[KPL];
-    cplx<T> sum[KPL];
     auto flush = [&]() {
-        if (cur == 0xffffffffu) return;
 #pragma unroll
-        for (int k = 0; k < KPL; ++k)
-            if (loc[k] >= 0) {
-                atomicAdd(acc + 2 * loc[k], sum[k].x);
-                atomicAdd(acc + 2 * loc[k] + 1, sum[k].y);
+        for (int k = 0; k < KP; ++k)
+            if (act[k]) {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    atomicAdd(acc + 2 * (base[k] + i), sum[k][i].x);
+                    atomicAdd(acc + 2 * (base[k] + i) + 1, sum[k][i].y);
+                }
             }
     };
     for (long long b0 = w0; b0 < w1; b0 += 32) {
@@ -386,30 +393,35 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
         for (int j = 0; j < cnt; ++j) {
             const uint32_t sm = __shfl_sync(0xffffffffu, sl, j);
             if (sm != cur) {
-                flush();
+                if (cur != 0xffffffffu) flush();
                 cur = sm;
-                int s[3];
-                unpack3(sm, s[0], s[1], s[2]);
+                int s3[3];
+                unpack3(sm, s3[0], s3[1], s3[2]);
 #pragma unroll
-                for (int k = 0; k < KPL; ++k) {
-                    loc[k] = jz[k] < NP ? ((s[2] + jz[k]) * a.nf[1] + (s[1] + jy[k])) * a.nf[0] + s[0] + jx[k] : -1;
-                    sum[k] = mk<T>(T(0), T(0));
+                for (int k = 0; k < KP; ++k) {
+                    base[k] = ((s3[2] + jz[k]) * a.nf[1] + (s3[1] + jy[k])) * a.nf[0] + s3[0];
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) sum[k][i] = mk<T>(T(0), T(0));
                 }
             }
-            T w[3][NP];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) lagrange_w<T, PF>(__shfl_sync(0xffffffffu, tl[d], j), w[d]);
+            const T tx = __shfl_sync(0xffffffffu, tl[0], j), ty = __shfl_sync(0xffffffffu, tl[1], j),
+                    tz = __shfl_sync(0xffffffffu, tl[2], j);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+            T wx[NP];
+            lagrange_w<T, PF>(tx, wx);
 #pragma unroll
-            for (int k = 0; k < KPL; ++k)
-                if (jz[k] < NP) {
-                    const T ww = pick<NP>(w[0], jx[k]) * pick<NP>(w[1], jy[k]) * pick<NP>(w[2], jz[k]);
-                    sum[k].x += ww * qx;
-                    sum[k].y += ww * qy;
+            for (int k = 0; k < KP; ++k) {
+                const T wyz = lag1<T, PF>(ty, jy[k]) * lag1<T, PF>(tz, jz[k]);
+                const T cx = wyz * qx, cy = wyz * qy;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    sum[k][i].x += wx[i] * cx;
+                    sum[k][i].y += wx[i] * cy;
                 }
+            }
         }
     }
-    flush();
+    if (cur != 0xffffffffu) flush();
     __syncthreads();
     cplx<T>* out = part + (long long)blockIdx.x * G;
     for (int i = threadIdx.x; i < G; i += blockDim.x) out[i] = mk<T>(acc[2 * i], acc[2 * i + 1]);
