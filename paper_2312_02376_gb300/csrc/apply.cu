@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
     const long long s0 = a.wbeg[w], s1 = a.wbeg[w + 1];
     const bool act = lane < NP * NP;
     const int jy = lane % NP, jz = lane / NP;
+    const int wd = min(lane / NP, 2), wj = lane % NP;  // the weight this lane evaluates
     // a warp's boxes start inside one 32-point block, so there are at most
     // 32 of them: lane b keeps the first point of box s0 + b
     const int nbw = (int)(s1 - s0);
@@ -158,12 +159,17 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
                 const int nx = __shfl_sync(0xffffffffu, bs, (slot + 1) & 31);
                 next = slot + 1 < nbw ? nx : m1;
             }
+            // lane l < 3(P+1) evaluates the one weight w_{l % (P+1)} of axis
+            // l / (P+1); every lane then fetches the weights it needs
             const T tx = __shfl_sync(0xffffffffu, tl[0], j), ty = __shfl_sync(0xffffffffu, tl[1], j),
                     tz = __shfl_sync(0xffffffffu, tl[2], j);
+            const T t = wd == 0 ? tx : (wd == 1 ? ty : tz);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+            const T wl = lag1<T, P>(t, wj);
             T wx[NP];
-            lagrange_w<T, P>(tx, wx);
-            const T wyz = lag1<T, P>(ty, jy) * lag1<T, P>(tz, jz);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) wx[i] = __shfl_sync(0xffffffffu, wl, i);
+            const T wyz = __shfl_sync(0xffffffffu, wl, NP + jy) * __shfl_sync(0xffffffffu, wl, 2 * NP + jz);
             const T cx = wyz * qx, cy = wyz * qy;
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
@@ -344,6 +350,7 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
     constexpr int NP = PF + 1, KP = (NP * NP + 31) / 32;  // (jy, jz) rows per lane
+    static_assert(3 * NP <= 32, "one lane per weight");
     const int G = a.nf[0] * a.nf[1] * a.nf[2];
     for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
     __syncthreads();
@@ -352,6 +359,7 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long per = (m1 - m0 + nw - 1) / nw;
     const long long w0 = m0 + wid * per, w1 = min(m1, w0 + per);
+    const int wd = min(lane / NP, 2), wj = lane % NP;  // the weight this lane evaluates
     bool act[KP];
     int jy[KP], jz[KP], base[KP];
     cplx<T> sum[KP][NP];
@@ -407,11 +415,15 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
             const T tx = __shfl_sync(0xffffffffu, tl[0], j), ty = __shfl_sync(0xffffffffu, tl[1], j),
                     tz = __shfl_sync(0xffffffffu, tl[2], j);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
+            // lane l < 3(P+1) evaluates the one weight w_{l % (P+1)} of axis
+            // l / (P+1); every lane then fetches the weights it needs
+            const T wl = lag1<T, PF>(wd == 0 ? tx : (wd == 1 ? ty : tz), wj);
             T wx[NP];
-            lagrange_w<T, PF>(tx, wx);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) wx[i] = __shfl_sync(0xffffffffu, wl, i);
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
-                const T wyz = lag1<T, PF>(ty, jy[k]) * lag1<T, PF>(tz, jz[k]);
+                const T wyz = __shfl_sync(0xffffffffu, wl, NP + jy[k]) * __shfl_sync(0xffffffffu, wl, 2 * NP + jz[k]);
                 const T cx = wyz * qx, cy = wyz * qy;
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
