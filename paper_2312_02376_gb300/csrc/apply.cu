@@ -85,12 +85,14 @@ __global__ void permute_kernel(const void* q, const int* perm, long long N, int 
 // ------------------------------- near spread -------------------------------
 
 
-// Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1) in two atomic-free phases.
-// Every point of a box shares the box's stencil start s_b, so
-//   Q(a) = sum_{boxes b whose stencil covers a} M_b(a - s_b),
-//   M_b(j) = sum_{n in b} w_n(j) q_n         (the box's (p+1)^3 moments).
-// Phase 1: one warp per non-empty box, lanes own stencil offsets, the box's
-// points are loaded 32 at a time and walked by shuffles.
+// Q(a) = sum_n w_n(a) q_n (Sec. 3.3 step 1) without global atomics.
+// Every point of a box shares the box's stencil start s_b, so the points of
+// a box with many points are first summed into the box's (p+1)^3 moments
+//   M_b(j) = sum_{n in b} w_n(j) q_n,        Q(a) = sum_b M_b(a - s_b),
+// while the points of the other boxes are added one by one.  Phase 1 forms
+// the moments of the dense boxes; phase 2 builds every grid line (y, z) in
+// shared memory from the "entries" (a dense box or a single point) of the box
+// rows whose stencils cover the line.
 template <int P>
 __device__ __forceinline__ void covering_boxes(int a, int n, int nb, int& lo, int& hi) {
     constexpr int LO = (P & 1) ? (P - 1) / 2 : P / 2;
@@ -101,37 +103,30 @@ __device__ __forceinline__ void covering_boxes(int a, int n, int nb, int& lo, in
 }
 
 struct MomentArgs {
-    long long nne, nmw;
+    long long nd;
+    const int* dslot;    // slot of each dense box
     const int* bstart;   // nne + 1 point offsets of the non-empty boxes
-    const int* wbeg;     // nmw + 1 first slot of each warp (about 32 points each)
     const float* nt;
     const double* ntd;
 };
 
-// A warp walks the points of the boxes [wbeg[w], wbeg[w+1]) (contiguous in
-// the sorted order), 32 at a time (coalesced loads, then shuffles).  Lane l
-// < (P+1)^2 owns the stencil offsets (jx = 0..P, jy = l % (P+1),
-// jz = l / (P+1)); a box's moment row is written when the walk leaves it
-// (lane l writes P+1 consecutive values, the warp one contiguous row).
+// Phase 1: one warp per dense box.  Lane l < (P+1)^2 owns the stencil
+// offsets (jx = 0..P, jy = l % (P+1), jz = l / (P+1)); the box's points are
+// loaded 32 at a time and walked by shuffles; for each point, lane l < 3(P+1)
+// evaluates the one weight w_{l % (P+1)} along axis l / (P+1) and the others
+// fetch it.  The row of moments is written once (lane l: P+1 consecutive
+// values, the warp one contiguous row).
 template <typename T, int P>
 __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>* __restrict__ qs, cplx<T>* mom) {
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
     static_assert(NP * NP <= 32, "one lane per (jy, jz) pair");
     const int lane = threadIdx.x & 31;
-    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (w >= a.nmw) return;
-    const long long s0 = a.wbeg[w], s1 = a.wbeg[w + 1];
-    const bool act = lane < NP * NP;
+    const long long dbox = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (dbox >= a.nd) return;
     const int jy = lane % NP, jz = lane / NP;
     const int wd = min(lane / NP, 2), wj = lane % NP;  // the weight this lane evaluates
-    // a warp's boxes start inside one 32-point block, so there are at most
-    // 32 of them: lane b keeps the first point of box s0 + b
-    const int nbw = (int)(s1 - s0);
-    const int bs = lane < nbw ? a.bstart[s0 + lane] : 0;
-    const int m1 = a.bstart[s1];
-    const int m0 = __shfl_sync(0xffffffffu, bs, 0);
-    int slot = 0;  // box s0 + slot
-    int next = nbw > 1 ? __shfl_sync(0xffffffffu, bs, 1) : m1;
+    const int slot = a.dslot[dbox];
+    const int m0 = a.bstart[slot], m1 = a.bstart[slot + 1];
     cplx<T> sum[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) sum[j] = mk<T>(T(0), T(0));
@@ -146,26 +141,10 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
             ql = qs[ml];
         }
         for (int j = 0; j < cnt; ++j) {
-            const int m = b0 + j;
-            while (m >= next) {  // the walk leaves box s0 + slot: write its row
-                if (act) {
-                    cplx<T>* out = mom + (s0 + slot) * NP3 + lane * NP;
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) out[i] = sum[i];
-                }
-#pragma unroll
-                for (int i = 0; i < NP; ++i) sum[i] = mk<T>(T(0), T(0));
-                ++slot;
-                const int nx = __shfl_sync(0xffffffffu, bs, (slot + 1) & 31);
-                next = slot + 1 < nbw ? nx : m1;
-            }
-            // lane l < 3(P+1) evaluates the one weight w_{l % (P+1)} of axis
-            // l / (P+1); every lane then fetches the weights it needs
             const T tx = __shfl_sync(0xffffffffu, tl[0], j), ty = __shfl_sync(0xffffffffu, tl[1], j),
                     tz = __shfl_sync(0xffffffffu, tl[2], j);
-            const T t = wd == 0 ? tx : (wd == 1 ? ty : tz);
             const T qx = __shfl_sync(0xffffffffu, ql.x, j), qy = __shfl_sync(0xffffffffu, ql.y, j);
-            const T wl = lag1<T, P>(t, wj);
+            const T wl = lag1<T, P>(wd == 0 ? tx : (wd == 1 ? ty : tz), wj);
             T wx[NP];
 #pragma unroll
             for (int i = 0; i < NP; ++i) wx[i] = __shfl_sync(0xffffffffu, wl, i);
@@ -178,26 +157,28 @@ __global__ void __launch_bounds__(256) moment_kernel(MomentArgs a, const cplx<T>
             }
         }
     }
-    if (act) {
-        cplx<T>* out = mom + (s0 + slot) * NP3 + lane * NP;
+    if (lane < NP * NP) {
+        cplx<T>* out = mom + dbox * NP3 + lane * NP;
 #pragma unroll
         for (int i = 0; i < NP; ++i) out[i] = sum[i];
     }
 }
 
-// Phase 2: one warp per grid line (y, z) along x.  The line gathers the
-// moments of the (<= (P+1)^2 in the interior) box rows whose stencils cover
-// (y, z); each non-empty box of a row adds its P+1 contiguous moments
-// M_b(jz, jy, 0..P) at x = s_x(b)..s_x(b)+P of the line, kept in shared
-// memory.  No global atomics; every node written once.  The candidate rows
-// go to lanes and their non-empty boxes are enumerated as one flat list
-// (a warp prefix sum of the row counts), so that the dependent loads of all
-// rows are in flight together.
+// Phase 2: one warp per grid line (y, z) along x, the line kept in shared
+// memory.  The box rows whose stencils cover (y, z) (<= (P+1)^2 in the
+// interior) go to lanes, and their entries are enumerated as one flat list
+// (a warp prefix sum of the row counts), so that the loads of all rows are
+// in flight together.  An entry adds P+1 values at x = s_x..s_x+P of the
+// line: a dense box its moments M_b(0..P, jy, jz), a point
+// w_x(0..P) w_y(jy) w_z(jz) q_n.
 struct LineArgs {
     int n[3], nb[3];
-    int ncopy;           // copies of the line in shared memory (1, 2 or 4)
-    const int* rsp;      // first slot of each box row
-    const int* blist;    // box id of each slot
+    int ncopy;             // copies of the line in shared memory (1, 2 or 4)
+    const int* eptr;       // first entry of each box row
+    const uint32_t* ent;   // entries: dense box (bit 31 | dense index) or point
+    const uint16_t* esx;   // stencil start along x of each entry
+    const float* nt;
+    const double* ntd;
 };
 
 // Shared-memory layout of one warp's line: ncopy copies, each a real and an
@@ -215,7 +196,8 @@ __device__ __forceinline__ int sclamp(int b, int n) {
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __restrict__ mom, cplx<T>* Q) {
+__global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __restrict__ mom,
+                                                   const cplx<T>* __restrict__ qs, cplx<T>* Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NP = P + 1, NP3 = NP * NP * NP;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -232,15 +214,15 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
     covering_boxes<P>(z, a.n[2], a.nb[2], zlo, zhi);
     const int nyc = yhi - ylo + 1, ncand = nyc * (zhi - zlo + 1);
     for (int c0 = 0; c0 < ncand; c0 += 32) {
-        // lane: one candidate box row (by, bz) and its slot range
+        // lane: one candidate box row (by, bz) and its entry range
         const int c = c0 + lane;
         const int by = ylo + c % nyc, bz = zlo + c / nyc;
         const int jy = y - sclamp<P>(by, a.n[1]), jz = z - sclamp<P>(bz, a.n[2]);
         int s0 = 0, cnt = 0;
         if (c < ncand && (unsigned)jy <= (unsigned)P && (unsigned)jz <= (unsigned)P) {
             const long long r = (long long)bz * a.nb[1] + by;
-            s0 = a.rsp[r];
-            cnt = a.rsp[r + 1] - s0;
+            s0 = a.eptr[r];
+            cnt = a.eptr[r + 1] - s0;
         }
         int incl = cnt;
 #pragma unroll
@@ -249,10 +231,10 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
             if (lane >= o) incl += v;
         }
         const int excl = incl - cnt, total = __shfl_sync(0xffffffffu, incl, 31);
-        const int moff = (jz * NP + jy) * NP;
+        const int jyz = jz * NP + jy;
         for (int t0 = 0; t0 < total; t0 += 64) {
-            // two list entries per lane, all loads issued before the adds
-            int slot[2], off[2], bx[2], cp[2];
+            // two entries per lane, all loads issued before the adds
+            int e[2], rjyz[2], cp[2];
             bool ok[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -260,31 +242,51 @@ __global__ void __launch_bounds__(256) line_kernel(LineArgs a, const cplx<T>* __
                 int k = 0;  // owner: the last lane whose range starts at or before t
 #pragma unroll
                 for (int st = 16; st > 0; st >>= 1) {
-                    const int e = __shfl_sync(0xffffffffu, excl, k + st);
-                    if (e <= t) k += st;
+                    const int ex = __shfl_sync(0xffffffffu, excl, k + st);
+                    if (ex <= t) k += st;
                 }
                 ok[h] = t < total;
-                slot[h] = __shfl_sync(0xffffffffu, s0, k) + (t - __shfl_sync(0xffffffffu, excl, k));
-                off[h] = __shfl_sync(0xffffffffu, moff, k);
+                e[h] = __shfl_sync(0xffffffffu, s0, k) + (t - __shfl_sync(0xffffffffu, excl, k));
+                rjyz[h] = __shfl_sync(0xffffffffu, jyz, k);
                 cp[h] = (k % a.ncopy) * cw;
-                bx[h] = ok[h] ? a.blist[slot[h]] : 0;
+            }
+            uint32_t desc[2];
+            int sx[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                desc[h] = ok[h] ? a.ent[e[h]] : 0u;
+                sx[h] = ok[h] ? (int)a.esx[e[h]] : 0;
             }
             cplx<T> v[2][NP];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const cplx<T>* src = mom + (long long)slot[h] * NP3 + off[h];
+                if (desc[h] & 0x80000000u) {
+                    const cplx<T>* src = mom + (long long)(desc[h] & 0x7fffffffu) * NP3 + rjyz[h] * NP;
 #pragma unroll
-                for (int j = 0; j < NP; ++j) v[h][j] = ok[h] ? src[j] : mk<T>(T(0), T(0));
+                    for (int j = 0; j < NP; ++j) v[h][j] = src[j];
+                } else {
+                    // a single point: w_x(0..P) w_y(jy) w_z(jz) q_n
+                    const long long m = desc[h];
+                    T t[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+                    const cplx<T> q = ok[h] ? qs[m] : mk<T>(T(0), T(0));
+                    T wx[NP];
+                    lagrange_w<T, P>(t[0], wx);
+                    const T wyz = lag1<T, P>(t[1], rjyz[h] % NP) * lag1<T, P>(t[2], rjyz[h] / NP);
+                    const T cx = wyz * q.x, cy = wyz * q.y;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) v[h][j] = mk<T>(wx[j] * cx, wx[j] * cy);
+                }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
-                const int sx = sclamp<P>(bx[h] % a.nb[0], nx);
-#pragma unroll
                 T* Lr = L + cp[h];
+#pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    atomicAdd(Lr + sx + j, v[h][j].x);
-                    atomicAdd(Lr + ld + sx + j, v[h][j].y);
+                    atomicAdd(Lr + sx[h] + j, v[h][j].x);
+                    atomicAdd(Lr + ld + sx[h] + j, v[h][j].y);
                 }
             }
         }
@@ -305,24 +307,26 @@ template <typename T, int P>
 pim_status spread_two_phase(pim_plan P_, const cplx<T>* qs, cplx<T>* Q, cudaStream_t s) {
     const PointsData& d = P_->pts;
     MomentArgs ma{};
-    ma.nne = d.nne;
-    ma.nmw = d.nmw;
+    ma.nd = d.nd;
+    ma.dslot = d.dslot;
     ma.bstart = d.bstart;
-    ma.wbeg = d.wbeg;
     ma.nt = d.nt;
     ma.ntd = d.ntd;
-    if (d.nmw > 0) moment_kernel<T, P><<<(unsigned)((d.nmw * 32 + 255) / 256), 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
+    if (d.nd > 0) moment_kernel<T, P><<<(unsigned)((d.nd * 32 + 255) / 256), 256, 0, s>>>(ma, qs, (cplx<T>*)d.mom);
     LineArgs la{};
     for (int i = 0; i < 3; ++i) { la.n[i] = P_->n[i]; la.nb[i] = P_->nb[i]; }
-    la.rsp = d.rsp;
-    la.blist = d.blist;
+    la.eptr = d.eptr;
+    la.ent = d.ent;
+    la.esx = d.esx;
+    la.nt = d.nt;
+    la.ntd = d.ntd;
     const long long nlines = (long long)P_->n[1] * P_->n[2];
     // as many line copies as fit in 96 KB per CTA of 8 warps
     la.ncopy = 4;
     while (la.ncopy > 1 && 8 * sizeof(T) * (size_t)line_words(P_->n[0], la.ncopy) > 96 * 1024) la.ncopy /= 2;
     const size_t sm = 8 * sizeof(T) * (size_t)line_words(P_->n[0], la.ncopy);
     PIM_CK(cudaFuncSetAttribute(line_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    line_kernel<T, P><<<(unsigned)((nlines + 7) / 8), 256, sm, s>>>(la, (const cplx<T>*)d.mom, Q);
+    line_kernel<T, P><<<(unsigned)((nlines + 7) / 8), 256, sm, s>>>(la, (const cplx<T>*)d.mom, qs, Q);
     PIM_CK(cudaGetLastError());
     return PIM_OK;
 }
@@ -936,7 +940,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, s)) != PIM_OK)
             return st;
         prof_mark(P, PIM_STAGE_FFT, 1, s);
-        P->launches += (d.nne > 0 ? 2 : 1) + 5;
+        P->launches += (d.nd > 0 ? 2 : 1) + 5;
         // 5. gather + correction + far gather
         if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
         GatherArgs ga{};

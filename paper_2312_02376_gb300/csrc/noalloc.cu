@@ -79,7 +79,7 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
     const size_t GB = (size_t)P->n[2] * P->n[1] * P->ng.L[0];
     const size_t GC = (size_t)P->n[2] * P->ng.L[1] * P->ng.L[0];
     const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
-    const size_t mom = (size_t)(P->pts.nne > 0 ? P->pts.nne : 1) * np3 * ge;
+    const size_t mom = (size_t)(P->pts.nd > 0 ? P->pts.nd : 1) * np3 * ge;
     size_t Gf = 0, fB = 0, fC = 0;
     if (P->has_far) {
         Gf = (size_t)P->nf[0] * P->nf[1] * P->nf[2];

@@ -25,6 +25,9 @@ void pim_set_error(const std::string& msg);
 constexpr int PIM_COL_BITS = 25;
 constexpr uint32_t PIM_COL_MASK = (1u << PIM_COL_BITS) - 1u;
 constexpr int PIM_MAX_IMAGES = 125;
+// boxes with at least this many points are spread through their moments,
+// the points of the others one by one
+constexpr int PIM_DENSE_MIN = 4;
 constexpr int PIM_MAX_P = 6;
 
 // device-side status flags (bit set)
@@ -157,10 +160,15 @@ struct PointsData {
     int* bstart = nullptr;        // nne + 1: first sorted point of each non-empty box
     int* rsp = nullptr;           // nrows + 1: first slot of each box row (y, z)
     long long nrows = 0;
-    int* wbeg = nullptr;          // nmw + 1: first slot of each moment-kernel warp
-    long long nmw = 0;
     int64_t nne = 0;              // non-empty boxes
-    void* mom = nullptr;          // nne x (p+1)^3 box moments, complex<T> (apply scratch)
+    int* dslot = nullptr;         // nd: slot of each dense box (PIM_DENSE_MIN points or more)
+    int64_t nd = 0;
+    int* eptr = nullptr;          // nrows + 1: first spread entry of each box row
+    uint32_t* ent = nullptr;      // ne spread entries in box-row order: a dense box (bit 31 | dense
+                                  // index) or, for the other boxes, each point (sorted index)
+    uint16_t* esx = nullptr;      // ne: stencil start along x of each entry
+    int64_t ne = 0;
+    void* mom = nullptr;          // nd x (p+1)^3 moments of the dense boxes, complex<T> (apply scratch)
     int64_t* row_ptr = nullptr;   // N + 1
     uint32_t* col = nullptr;      // nnz
     double2* val = nullptr;       // nnz: G0 - G_grid (FP64)

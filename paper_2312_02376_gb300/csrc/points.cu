@@ -152,17 +152,51 @@ __global__ void row_slots_kernel(const int* pos, long long nrows, int nbx, int* 
         rsp[r] = pos[r * nbx];
 }
 
-// warp boundaries of the moment kernel: a warp starts at every slot whose
-// first point crosses a multiple of K points (work balanced by points)
-__global__ void warp_flags_kernel(const int* bstart, long long nne, int K, int* flag) {
+// dense boxes (PIM_DENSE_MIN points or more) and their compact index
+__global__ void dense_flags_kernel(const int* bstart, long long nne, int* flag) {
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x)
-        flag[s] = (s == 0 || bstart[s] / K != bstart[s - 1] / K) ? 1 : 0;
+        flag[s] = bstart[s + 1] - bstart[s] >= PIM_DENSE_MIN ? 1 : 0;
 }
 
-__global__ void warp_begin_kernel(const int* flag, const int* pos, long long nne, int* wbeg) {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x)
-        if (flag[s]) wbeg[pos[s]] = (int)s;
-    if (blockIdx.x == 0 && threadIdx.x == 0) wbeg[pos[nne]] = (int)nne;
+__global__ void dense_slots_kernel(const int* flag, const int* pos, long long nne, int* dix, int* dslot) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x) {
+        if (flag[s]) {
+            dix[s] = pos[s];
+            dslot[pos[s]] = (int)s;
+        } else {
+            dix[s] = -1;
+        }
+    }
+}
+
+// spread entries per box row: one for a dense box, one per point otherwise
+__global__ void row_entries_kernel(const int* rsp, const int* bstart, const int* dix, long long nrows, int* cnt) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows; r += (long long)gridDim.x * blockDim.x) {
+        int c = 0;
+        for (int s = rsp[r]; s < rsp[r + 1]; ++s) c += dix[s] >= 0 ? 1 : bstart[s + 1] - bstart[s];
+        cnt[r] = c;
+    }
+}
+
+__global__ void row_fill_kernel(const int* rsp, const int* bstart, const int* dix, const int* blist, long long nrows,
+                                int nb0, int nx, int p, const int* eptr, uint32_t* ent, uint16_t* esx) {
+    const int lo = (p & 1) ? (p - 1) / 2 : p / 2;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows; r += (long long)gridDim.x * blockDim.x) {
+        int e = eptr[r];
+        for (int s = rsp[r]; s < rsp[r + 1]; ++s) {
+            const int bx = blist[s] % nb0;
+            const uint16_t sx = (uint16_t)min(max(bx - lo, 0), nx - 1 - p);
+            if (dix[s] >= 0) {
+                ent[e] = 0x80000000u | (uint32_t)dix[s];
+                esx[e++] = sx;
+            } else {
+                for (int m = bstart[s]; m < bstart[s + 1]; ++m) {
+                    ent[e] = (uint32_t)m;
+                    esx[e++] = sx;
+                }
+            }
+        }
+    }
 }
 
 // order each box's points by caller index (deterministic layout)
@@ -644,11 +678,14 @@ void points_free(pim_plan P) {
     pim_free(P, d.blist, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
     pim_free(P, d.bstart, (size_t)(d.nne + 1) * sizeof(int));
     pim_free(P, d.rsp, (size_t)(d.nrows + 1) * sizeof(int));
-    pim_free(P, d.wbeg, (size_t)(d.nmw + 1) * sizeof(int));
+    pim_free(P, d.dslot, (size_t)std::max<int64_t>(1, d.nd) * sizeof(int));
+    pim_free(P, d.eptr, (size_t)(d.nrows + 1) * sizeof(int));
+    pim_free(P, d.ent, (size_t)std::max<int64_t>(1, d.ne) * sizeof(uint32_t));
+    pim_free(P, d.esx, (size_t)std::max<int64_t>(1, d.ne) * sizeof(uint16_t));
     {
         const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
         const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
-        pim_free(P, d.mom, (size_t)std::max<int64_t>(1, d.nne) * np3 * ge);
+        pim_free(P, d.mom, (size_t)std::max<int64_t>(1, d.nd) * np3 * ge);
     }
     pim_free(P, d.row_ptr, (N + 1) * sizeof(int64_t));
     pim_free(P, d.col, d.nnz * sizeof(uint32_t));
@@ -709,26 +746,40 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         if ((st = pim_alloc(P, (void**)&d.bstart, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
         box_slots_kernel<<<1024, 256, 0, s>>>(cursor, pos, d.box_ptr, nboxes, d.bslot, d.blist, d.bstart);
         PIM_CK(cudaGetLastError());
-        const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
-        const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
-        if ((st = pim_alloc(P, &d.mom, (size_t)std::max(1, nne) * np3 * ge)) != PIM_OK) return st;
         // row slot pointers
         d.nrows = (long long)P->nb[1] * P->nb[2];
         if ((st = pim_alloc(P, (void**)&d.rsp, (d.nrows + 1) * sizeof(int))) != PIM_OK) return st;
         row_slots_kernel<<<256, 256, 0, s>>>(pos, d.nrows, P->nb[0], d.rsp);
-        // point-balanced warp boundaries for the moment kernel
-        int* wpos = nullptr;
-        if ((st = pim_alloc(P, (void**)&wpos, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
-        if (nne > 0) warp_flags_kernel<<<1024, 256, 0, s>>>(d.bstart, nne, 32, cursor);
-        if ((st = scan<int>(P, cursor, wpos, nne, s)) != PIM_OK) return st;
-        int nwarps = 0;
-        PIM_CK(cudaMemcpy(&nwarps, wpos + nne, sizeof(int), cudaMemcpyDeviceToHost));
-        d.nmw = nwarps;
-        if ((st = pim_alloc(P, (void**)&d.wbeg, (size_t)(nwarps + 1) * sizeof(int))) != PIM_OK) return st;
-        warp_begin_kernel<<<1024, 256, 0, s>>>(cursor, wpos, nne, d.wbeg);
+        // dense boxes
+        int *dix = nullptr, *dpos = nullptr;
+        if ((st = pim_alloc(P, (void**)&dix, (size_t)std::max(1, nne) * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&dpos, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
+        if (nne > 0) dense_flags_kernel<<<1024, 256, 0, s>>>(d.bstart, nne, cursor);
+        if ((st = scan<int>(P, cursor, dpos, nne, s)) != PIM_OK) return st;
+        int nd = 0;
+        PIM_CK(cudaMemcpy(&nd, dpos + nne, sizeof(int), cudaMemcpyDeviceToHost));
+        d.nd = nd;
+        if ((st = pim_alloc(P, (void**)&d.dslot, (size_t)std::max(1, nd) * sizeof(int))) != PIM_OK) return st;
+        if (nne > 0) dense_slots_kernel<<<1024, 256, 0, s>>>(cursor, dpos, nne, dix, d.dslot);
+        const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
+        const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+        if ((st = pim_alloc(P, &d.mom, (size_t)std::max(1, nd) * np3 * ge)) != PIM_OK) return st;
+        // spread entries by box row
+        if ((st = pim_alloc(P, (void**)&d.eptr, (d.nrows + 1) * sizeof(int))) != PIM_OK) return st;
+        if (d.nrows > 0) row_entries_kernel<<<256, 256, 0, s>>>(d.rsp, d.bstart, dix, d.nrows, cursor);
+        if ((st = scan<int>(P, cursor, d.eptr, d.nrows, s)) != PIM_OK) return st;
+        int ne = 0;
+        PIM_CK(cudaMemcpy(&ne, d.eptr + d.nrows, sizeof(int), cudaMemcpyDeviceToHost));
+        d.ne = ne;
+        if ((st = pim_alloc(P, (void**)&d.ent, (size_t)std::max(1, ne) * sizeof(uint32_t))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.esx, (size_t)std::max(1, ne) * sizeof(uint16_t))) != PIM_OK) return st;
+        if (d.nrows > 0)
+            row_fill_kernel<<<256, 256, 0, s>>>(d.rsp, d.bstart, dix, d.blist, d.nrows, P->nb[0], P->n[0], P->p, d.eptr,
+                                                d.ent, d.esx);
         PIM_CK(cudaGetLastError());
         PIM_CK(cudaStreamSynchronize(s));
-        pim_free(P, wpos, (size_t)(nne + 1) * sizeof(int));
+        pim_free(P, dix, (size_t)std::max(1, nne) * sizeof(int));
+        pim_free(P, dpos, (size_t)(nne + 1) * sizeof(int));
         pim_free(P, pos, (nboxes + 1) * sizeof(int));
     }
     // per-point data in sorted order

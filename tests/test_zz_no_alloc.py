@@ -49,7 +49,8 @@ def test_noalloc_matches_apply_on_two_calls_in_a_row(precision, tol):
 
 
 def test_noalloc_rejects_plans_beyond_the_limit_and_host_buffers():
-    W = inputs.helmholtz2d(N=65536, n=(64, 64, 32), nf=(12, 12, 8), b=3)
+    # FP64 grids of 96 x 96 x 48 nodes: the padded FFT work grids alone exceed the 32 MiB scratch
+    W = inputs.helmholtz2d(N=65536, n=(96, 96, 48), nf=(12, 12, 8), b=3)
     pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=4, layers=1, precision="fp64", b=W.b, nf=W.nf, pf=4)
     pl.set_points(torch.tensor(W.points, device="cuda"))
     q = torch.tensor(W.q, dtype=torch.complex128, device="cuda")
