@@ -119,7 +119,7 @@ void pim_destroy(pim_plan P) {
     points_free(P);
     const size_t ge = grid_elem(P);
     const long long G = (long long)P->n[0] * P->n[1] * P->n[2];
-    const long long Gs = (long long)P->ng.L[0] * P->ng.L[1] * P->ng.L[2];
+    const long long Gs = (long long)P->ng.S[0] * P->ng.S[1] * P->ng.S[2];
     pim_free(P, P->spec, Gs * ge);
     pim_free(P, P->gA, G * ge);
     pim_free(P, P->gB, (long long)P->n[2] * P->n[1] * P->ng.L[0] * ge);

@@ -117,6 +117,8 @@ struct PassArgs {
     long long in_row, out_row;       // stride between FFT rows (strided) / between lines (contig)
     long long in_plane, out_plane;   // stride between planes (strided pass)
     long long spec_row, spec_plane;  // spectrum strides (z pass)
+    int spec_fold;                   // z pass: bit 0/1/2 = stored spectrum folded along columns/planes/rows
+    int Lc, Lp;                      // z pass: full lengths along columns and planes (for the folding)
     int ngroups;     // column groups per plane
     int mode;        // 0 forward, 1 inverse, 2 forward*spec*inverse, 3 forward*conj(spec)*inverse
 };
@@ -157,13 +159,19 @@ __global__ void __launch_bounds__(B* NBS, sizeof(T) == 4 ? (B* NBS >= 512 ? 2 : 
 #pragma unroll
         for (int g = 0; g < G; ++g) s[((tid + (k0 + g) * NT) / B) * LD + col] = v[g];
     }
-    const cplx<T>* spb = spec + plane * a.spec_plane + c0;
+    // spectrum element of (row r, this plane, this column), folded along the
+    // axes where only frequencies 0..L/2 are stored
+    const int xc = c0 + col, pl = plane;
+    const int fxc = (a.spec_fold & 1) ? min(xc, a.Lc - xc) : xc;
+    const int fpl = (a.spec_fold & 2) ? min(pl, a.Lp - pl) : pl;
+    const cplx<T>* spb = spec + fpl * a.spec_plane + fxc;
+    auto srow = [&](int r) { return (long long)((a.spec_fold & 4) ? min(r, L - r) : r) * a.spec_row; };
     cplx<T> sp[PREF ? EPT : 1];
     if (PREF && a.mode >= 2) {
 #pragma unroll
         for (int k = 0; k < (PREF ? EPT : 1); ++k) {
             const int r = (tid + k * NT) / B;
-            sp[k] = cok ? spb[(long long)r * a.spec_row + col] : zero;
+            sp[k] = cok ? spb[srow(r)] : zero;
         }
     }
     __syncthreads();
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(B* NBS, sizeof(T) == 4 ? (B* NBS >= 512 ? 2 : 
             const int r = (tid + k * NT) / B;
             cplx<T> w;
             if constexpr (PREF) w = sp[k];
-            else w = cok ? spb[(long long)r * a.spec_row + col] : zero;
+            else w = cok ? spb[srow(r)] : zero;
             if (a.mode == 3) w.y = -w.y;
             s[r * LD + col] = cmul(s[r * LD + col], w);
         }
@@ -358,7 +366,13 @@ pim_status fft3_conv(pim_plan P, const FftGeom& g, cplx<T>* A, cplx<T>* B, cplx<
     // z forward * spectrum * inverse: planes y' (stride Lx), rows z (stride Ly Lx)
     a = PassArgs{};
     a.n_in = nz; a.n_keep = nz; a.width = Lx; a.in_row = (long long)Ly * Lx; a.out_row = (long long)Ly * Lx;
-    a.in_plane = Lx; a.out_plane = Lx; a.spec_row = (long long)Ly * Lx; a.spec_plane = Lx;
+    a.in_plane = Lx; a.out_plane = Lx;
+    if (g.fold || g.S[0]) {
+        a.spec_row = (long long)g.S[1] * g.S[0]; a.spec_plane = g.S[0];
+        a.spec_fold = g.fold; a.Lc = Lx; a.Lp = Ly;
+    } else {
+        a.spec_row = (long long)Ly * Lx; a.spec_plane = Lx;
+    }
     a.mode = conj_spec ? 3 : 2;
     if ((st = pass_strided<T>(Lz, C, C, a, Ly, tw, spec, s)) != PIM_OK) return st;
     // y inverse: keep ny rows

@@ -138,6 +138,10 @@ __host__ __device__ __forceinline__ void unpack3(uint32_t v, int& a, int& b, int
 struct FftGeom {
     int n[3];   // data nodes per axis
     int L[3];   // padded FFT length per axis
+    // stored spectrum: along an axis in `fold` (bit d) the kernel is even, so
+    // its spectrum is too and only frequencies 0..L/2 are kept (S = L/2 + 1)
+    int fold = 0;
+    int S[3] = {0, 0, 0};
 };
 
 // ---------------------------------------------------------------------------

@@ -67,6 +67,17 @@ __global__ void scale_convert_kernel(const double2* in, cplx<T>* out, long long 
     }
 }
 
+// the kept part [Sz][Sy][Sx] of a full spectrum [Lz][Ly][Lx], scaled
+template <typename T>
+__global__ void fold_convert_kernel(const double2* in, cplx<T>* out, int Lx, int Ly, int Sx, int Sy, int Sz, double s) {
+    const long long tot = (long long)Sx * Sy * Sz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Sx), y = (int)((i / Sx) % Sy), z = (int)(i / ((long long)Sx * Sy));
+        const double2 v = in[((long long)z * Ly + y) * Lx + x];
+        out[i] = mk<T>((T)(v.x * s), (T)(v.y * s));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // special functions (FP64)
 // ---------------------------------------------------------------------------
@@ -330,9 +341,23 @@ pim_status build_near_spectrum(pim_plan P, cudaStream_t s) {
     if ((st = fft3_forward_full<double>(P, g, X, nullptr, s)) != PIM_OK) return st;
     const double scale = 1.0 / (double)tot;
     const size_t esz = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
-    if ((st = pim_alloc(P, &P->spec, tot * esz)) != PIM_OK) return st;
-    if (P->prec == PIM_FP64) scale_convert_kernel<double><<<1024, 256, 0, s>>>(X, (double2*)P->spec, tot, scale);
-    else scale_convert_kernel<float><<<1024, 256, 0, s>>>(X, (float2*)P->spec, tot, scale);
+    // K(delta) is even along a non-periodic axis (no images there) and along
+    // a periodic axis without phase shift (images i and -i weigh the same),
+    // and so is its spectrum: keep frequencies 0..L/2 of those axes
+    g.fold = 0;
+    for (int d = 0; d < 3; ++d) {
+        const bool even = !((P->pmask >> d) & 1u) || P->k0[d] == 0.0;
+        if (even) g.fold |= 1 << d;
+        g.S[d] = even ? g.L[d] / 2 + 1 : g.L[d];
+    }
+    const long long stot = (long long)g.S[0] * g.S[1] * g.S[2];
+    if ((st = pim_alloc(P, &P->spec, stot * esz)) != PIM_OK) return st;
+    if (P->prec == PIM_FP64)
+        fold_convert_kernel<double><<<1024, 256, 0, s>>>(X, (double2*)P->spec, g.L[0], g.L[1], g.S[0], g.S[1], g.S[2],
+                                                         scale);
+    else
+        fold_convert_kernel<float><<<1024, 256, 0, s>>>(X, (float2*)P->spec, g.L[0], g.L[1], g.S[0], g.S[1], g.S[2],
+                                                        scale);
     PIM_CK(cudaGetLastError());
     PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, X, tot * sizeof(double2));
