@@ -71,7 +71,35 @@ template <typename T, int R, bool INV> __device__ __forceinline__ void dftR(cplx
 }
 
 // One Stockham stage of radix R at sub-transform size Ns, then recurse.
-template <typename T, int L, int B, int NBS, int Ns, bool INV>
+// PIN: the transform's input is zero in rows >= L/2 (the padding), so the
+// first stage reads and transforms only its first R/2 inputs.  POUT: only
+// rows < L/2 of the result are kept, so the last stage computes and stores
+// only its first R/2 outputs.  Twiddles: W^r for r = 1, 2, 4 come from the
+// table, the others are products of those.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void twiddle(cplx<T>* v, const cplx<T>* __restrict__ tw, int base) {
+    auto cj = [](cplx<T> x) {
+        if (INV) x.y = -x.y;
+        return x;
+    };
+    const cplx<T> w1 = cj(tw[base]);
+    v[1] = cmul(v[1], w1);
+    if constexpr (R >= 4) {
+        const cplx<T> w2 = cj(tw[2 * base]);
+        const cplx<T> w3 = cmul(w1, w2);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        if constexpr (R >= 8) {
+            const cplx<T> w4 = cj(tw[4 * base]);
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], cmul(w1, w4));
+            v[6] = cmul(v[6], cmul(w2, w4));
+            v[7] = cmul(v[7], cmul(w3, w4));
+        }
+    }
+}
+
+template <typename T, int L, int B, int NBS, int Ns, bool INV, bool PIN = false, bool POUT = false>
 __device__ __forceinline__ void fft_stages(cplx<T>* s, const cplx<T>* __restrict__ tw, int col, int bslot) {
     if constexpr (Ns < L) {
         constexpr int REM = L / Ns;
@@ -80,21 +108,17 @@ __device__ __forceinline__ void fft_stages(cplx<T>* s, const cplx<T>* __restrict
         constexpr int PER = NBF / NBS;      // butterflies per thread
         static_assert(PER >= 1 && PER * NBS == NBF, "butterfly split");
         constexpr int LD = B + 1;
+        constexpr bool FIRST_HALF = PIN && Ns == 1 && R >= 2;     // inputs r >= R/2 are zero
+        constexpr bool LAST_HALF = POUT && Ns * R == L && R >= 2;  // outputs r >= R/2 unused
+        constexpr int RIN = FIRST_HALF ? R / 2 : R, ROUT = LAST_HALF ? R / 2 : R;
         cplx<T> v[PER][R];
 #pragma unroll
         for (int b = 0; b < PER; ++b) {
             const int j = bslot + b * NBS;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = s[(j + r * NBF) * LD + col];
-            if constexpr (Ns > 1) {
-                const int kk = j % Ns;
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    cplx<T> w = tw[(r * kk) * (LMAX / (Ns * R))];
-                    if (INV) w.y = -w.y;
-                    v[b][r] = cmul(v[b][r], w);
-                }
-            }
+            for (int r = 0; r < R; ++r)
+                v[b][r] = r < RIN ? s[(j + r * NBF) * LD + col] : mk<T>(T(0), T(0));
+            if constexpr (Ns > 1) twiddle<T, R, INV>(v[b], tw, (j % Ns) * (LMAX / (Ns * R)));
             dftR<T, R, INV>(v[b]);
         }
         __syncthreads();
@@ -103,11 +127,21 @@ __device__ __forceinline__ void fft_stages(cplx<T>* s, const cplx<T>* __restrict
             const int j = bslot + b * NBS;
             const int idx = (j / Ns) * Ns * R + (j % Ns);
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[(idx + r * Ns) * LD + col] = v[b][r];
+            for (int r = 0; r < ROUT; ++r) s[(idx + r * Ns) * LD + col] = v[b][r];
         }
         __syncthreads();
-        fft_stages<T, L, B, NBS, Ns * R, INV>(s, tw, col, bslot);
+        fft_stages<T, L, B, NBS, Ns * R, INV, false, POUT>(s, tw, col, bslot);
     }
+}
+
+// A full transform with the pruning flags chosen at run time.
+template <typename T, int L, int B, int NBS, bool INV>
+__device__ __forceinline__ void fft_run(cplx<T>* s, const cplx<T>* __restrict__ tw, int col, int bslot, bool pin,
+                                        bool pout) {
+    if (pin && pout) fft_stages<T, L, B, NBS, 1, INV, true, true>(s, tw, col, bslot);
+    else if (pin) fft_stages<T, L, B, NBS, 1, INV, true, false>(s, tw, col, bslot);
+    else if (pout) fft_stages<T, L, B, NBS, 1, INV, false, true>(s, tw, col, bslot);
+    else fft_stages<T, L, B, NBS, 1, INV, false, false>(s, tw, col, bslot);
 }
 
 struct PassArgs {
@@ -127,7 +161,7 @@ struct PassArgs {
 // Every thread issues its global loads in groups (up to 8) before it stores
 // them to shared memory, so that their latencies overlap instead of forming
 // a chain.
-template <typename T, int L, int B, int NBS>
+template <typename T, int L, int B, int NBS, bool Z>
 __global__ void __launch_bounds__(B* NBS, sizeof(T) == 4 ? (B* NBS >= 512 ? 2 : (B* NBS >= 256 ? 3 : 1)) : 1) fft_strided_kernel(const cplx<T>* in, cplx<T>* out,
                                                               PassArgs a, const cplx<T>* __restrict__ tw,
                                                               const cplx<T>* __restrict__ spec) {
@@ -166,32 +200,34 @@ __global__ void __launch_bounds__(B* NBS, sizeof(T) == 4 ? (B* NBS >= 512 ? 2 : 
     const int fpl = (a.spec_fold & 2) ? min(pl, a.Lp - pl) : pl;
     const cplx<T>* spb = spec + fpl * a.spec_plane + fxc;
     auto srow = [&](int r) { return (long long)((a.spec_fold & 4) ? min(r, L - r) : r) * a.spec_row; };
-    cplx<T> sp[PREF ? EPT : 1];
-    if (PREF && a.mode >= 2) {
+    cplx<T> sp[PREF && Z ? EPT : 1];
+    if constexpr (PREF && Z) {
 #pragma unroll
-        for (int k = 0; k < (PREF ? EPT : 1); ++k) {
+        for (int k = 0; k < EPT; ++k) {
             const int r = (tid + k * NT) / B;
             sp[k] = cok ? spb[srow(r)] : zero;
         }
     }
     __syncthreads();
-    if (a.mode == 1) {
-        fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
+    const bool half_in = 2 * a.n_in <= L, half_out = 2 * a.n_keep <= L;
+    if (!Z && a.mode == 1) {
+        fft_run<T, L, B, NBS, true>(s, tw, col, bslot, false, half_out);
     } else {
-        fft_stages<T, L, B, NBS, 1, false>(s, tw, col, bslot);
+        // forward: the z pass keeps the whole spectrum for the product
+        fft_run<T, L, B, NBS, false>(s, tw, col, bslot, half_in, !Z && half_out);
     }
-    if (a.mode >= 2) {
+    if constexpr (Z) {
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const int r = (tid + k * NT) / B;
             cplx<T> w;
-            if constexpr (PREF) w = sp[k];
+            if constexpr (PREF && Z) w = sp[k];
             else w = cok ? spb[srow(r)] : zero;
             if (a.mode == 3) w.y = -w.y;
             s[r * LD + col] = cmul(s[r * LD + col], w);
         }
         __syncthreads();
-        fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
+        fft_run<T, L, B, NBS, true>(s, tw, col, bslot, false, half_out);
     }
     cplx<T>* ob = out + plane * a.out_plane + c0;
     if (cok) {
@@ -229,8 +265,9 @@ __global__ void __launch_bounds__(B* NBS) fft_contig_kernel(const cplx<T>* in, c
         s[(i % L) * LD + i / L] = v[k];
     }
     __syncthreads();
-    if (a.mode == 1) fft_stages<T, L, B, NBS, 1, true>(s, tw, col, bslot);
-    else fft_stages<T, L, B, NBS, 1, false>(s, tw, col, bslot);
+    const bool half_in = 2 * a.n_in <= L, half_out = 2 * a.n_keep <= L;
+    if (a.mode == 1) fft_run<T, L, B, NBS, true>(s, tw, col, bslot, false, half_out);
+    else fft_run<T, L, B, NBS, false>(s, tw, col, bslot, half_in, half_out);
     for (int i = tid; i < a.n_keep * B; i += NT) {
         const int c = i / a.n_keep, x = i % a.n_keep;
         if (l0 + c < a.width) out[(long long)(l0 + c) * a.out_row + x] = s[x * LD + c];
@@ -279,7 +316,7 @@ pim_status launch_strided_len(const cplx<T>* in, cplx<T>* out, PassArgs a, int n
     constexpr int NBS = NBS0 * B > 512 ? 512 / B : NBS0;
     constexpr int NT = B * NBS;
     const size_t smem = (size_t)L * (B + 1) * sizeof(cplx<T>);
-    auto k = fft_strided_kernel<T, L, B, NBS>;
+    auto k = a.mode >= 2 ? fft_strided_kernel<T, L, B, NBS, true> : fft_strided_kernel<T, L, B, NBS, false>;
     PIM_CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     a.ngroups = (a.width + B - 1) / B;
     const long long grid = (long long)a.ngroups * nplanes;
