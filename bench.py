@@ -136,12 +136,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gather_bytes(info, N, G, nf3):
-    """Algorithmic bytes of one gather + correction launch (FP32 grid, FP64-
-    class correction values of 16 B and a 4 B column per entry)."""
+def gather_bytes(info, N, G, nf3, fp64=False):
+    """Algorithmic bytes of one gather + correction launch: FP64-class
+    correction values of 16 B and a 4 B column per entry; per point the
+    stencil starts, local coordinates, permutation, sorted source, output,
+    far stencil and far coordinates; the near and far grids once."""
     per_nnz = 16 + 4
-    per_point = 4 + 12 + 4 + 8 + 8 + 4 + 12   # stencil, coords, perm, q (sorted), u out, far stencil, far coords
-    return info.nnz * per_nnz + (N + 1) * 8 + N * per_point + G * 8 + nf3 * 8
+    c, r = (16, 8) if fp64 else (8, 4)        # complex and real element sizes
+    per_point = 4 + 3 * r + 4 + c + c + 4 + 3 * r
+    return info.nnz * per_nnz + (N + 1) * 8 + N * per_point + G * c + nf3 * c
 
 
 def gather_source_hash():
@@ -182,11 +185,13 @@ def run_gpu(args):
     W = workload(args.workload)
     if args.corr_radius is not None:
         W.b = args.corr_radius
-    plan = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
-                    pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
+    fp64 = args.precision == "fp64"
+    cdt = torch.complex128 if fp64 else torch.complex64
+    plan = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=args.precision, b=W.b,
+                    nf=W.nf, pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_DOUBLE_FLOAT)
     plan.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     info = plan.info()
-    q = torch.tensor(W.q, dtype=torch.complex64, device="cuda")
+    q = torch.tensor(W.q, dtype=cdt, device="cuda")
     u = torch.empty_like(q)
     w = torch.empty_like(q)
     stream = torch.cuda.current_stream()
@@ -230,7 +235,7 @@ def run_gpu(args):
     value = 2.0 * W.N * world / (ms_step * 1e-3) / 1e6
 
     # end to end through the C ABI with pinned host buffers (copies timed)
-    qh = torch.tensor(W.q, dtype=torch.complex64).pin_memory()
+    qh = torch.tensor(W.q, dtype=cdt).pin_memory()
     uh = torch.empty_like(qh).pin_memory()
     wh = torch.empty_like(qh).pin_memory()
     for _ in range(2):
@@ -245,23 +250,24 @@ def run_gpu(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = allmax(1e3 * float(np.mean(e2e_t)), world)
     e2e_val = 2.0 * W.N * world / (e2e_ms * 1e-3) / 1e6
-    elem = 8
+    elem = 16 if fp64 else 8
     result = None
     if rank == 0:
         peak, peak_kind = measured_peaks()
         G = int(np.prod(W.n))
         nf3 = int(np.prod(W.nf))
-        gb = gather_bytes(info, W.N, G, nf3)
+        gb = gather_bytes(info, W.N, G, nf3, fp64)
         g_ms = stage_ms["gather_correct"] / max(1, napplies)
         achieved = gb / (g_ms * 1e-3) / 1e9
         apply_ms = stage_ms["apply"] / max(1, napplies)
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "c128" if fp64 else "c64+f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": W.N, "grid": list(W.n), "p": W.p, "near_layers": W.layers,
                        "corr_radius_steps": W.b, "far_grid": list(W.nf), "far_p": W.pf, "nnz": int(info.nnz),
-                       "precision": "complex64 bulk, FP64 far series/grid sum, FP64 correction values "
+                       "precision": "FP64 throughout" if fp64 else
+                                    "complex64 bulk, FP64 far series/grid sum, FP64 correction values "
                                     "(double-float accumulation)",
                        "rel_l2_vs_ewald_ground_truth": err_truth,
                        "ground_truth_rows": 16,
@@ -269,7 +275,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": "gather_kernel (near gather + CSR correction + far gather)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "traffic": profile_traffic(), "algorithmic_bytes_per_launch": gb,
+                         "traffic": None if fp64 else profile_traffic(), "algorithmic_bytes_per_launch": gb,
                          "kernel_ms": round(g_ms, 4)},
             "stages_ms_per_apply": {k: round(v / max(1, napplies), 4) for k, v in stage_ms.items()},
             "apply_ms": round(apply_ms, 4),
@@ -489,6 +495,8 @@ def main():
                     help="helmholtz2d_65k: the same recipe, smaller, for profiler captures; "
                          "helmholtz1d_batch: 16 sets x 64 right-hand sides, batched graph; "
                          "coulomb3d_1m: forward + adjoint + position gradient")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp64: the plain FP64 apply of the same workload, for comparison with the FP32-bulk path")
     ap.add_argument("--corr-radius", type=int, default=None,
                     help="override the correction radius of the helmholtz2d workloads (for profiler captures "
                          "of the stages that do not depend on it; the line then states the radius used)")

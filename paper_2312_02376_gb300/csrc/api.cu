@@ -116,6 +116,8 @@ void pim_destroy(pim_plan P) {
     if (!P) return;
     cudaDeviceSynchronize();
     batch_forget(P);
+    lanes_free(P);
+    if (P->lane_fork) cudaEventDestroy(P->lane_fork);
     points_free(P);
     const size_t ge = grid_elem(P);
     const long long G = (long long)P->n[0] * P->n[1] * P->n[2];
@@ -335,6 +337,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     const double t0 = now_ms();
     cudaDeviceSynchronize();
     batch_forget(P);
+    lanes_free(P);  // their sizes depend on the points
     const size_t ge = grid_elem(P);
     if (P->pts.N > 0 || P->pts.box_ptr) {
         free_grad_buffers(P);

@@ -882,24 +882,50 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         }
         if (!P->dmeans && (st = pim_alloc(P, (void**)&P->dmeans, 2 * 128 * sizeof(double))) != PIM_OK) return st;
     }
+    // the right-hand sides of a multi-RHS apply go round-robin to lanes with
+    // their own scratch and streams, so that several run at once
+    // (not for the neutral static case, whose per-RHS means share one scratch)
+    const int K = multi && !P->npsp ? std::min(nrhs, (int)pim_plan_s::RHS_LANES) : 1;
+    if (K > 1) {
+        if ((st = lanes_prepare(P, K)) != PIM_OK) return st;
+        PIM_CK(cudaEventRecord(P->lane_fork, s));
+        for (int k = 1; k < K; ++k) PIM_CK(cudaStreamWaitEvent(P->lane[k].sm, P->lane_fork, 0));
+    }
+    const pim_plan_s::Lane own{P->qs, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC,
+                               s, P->s_far, P->ev_fork, P->ev_join, nullptr};
+    auto use_lane = [&](const pim_plan_s::Lane& l) {
+        P->qs = l.qs; P->gA = l.gA; P->gB = l.gB; P->gC = l.gC; P->pts.mom = l.mom; P->fpart = l.fpart;
+        P->fA = l.fA; P->fB = l.fB; P->fC = l.fC; P->s_far = l.sf; P->ev_fork = l.fork; P->ev_join = l.join;
+    };
+    // the plan's own scratch is back in place on every way out
+    struct Restore {
+        decltype(use_lane)& f;
+        const pim_plan_s::Lane& l;
+        ~Restore() { f(l); }
+    } restore{use_lane, own};
     for (int r = 0; r < nrhs; ++r) {
-        prof_mark(P, PIM_STAGE_APPLY, 0, s);
-        prof_mark(P, PIM_STAGE_PERMUTE, 0, s);
+        const int lk = r % K;
+        use_lane(lk == 0 ? own : P->lane[lk]);
+        const cudaStream_t sr = lk == 0 ? s : P->lane[lk].sm;
+        qs = (cplx<T>*)P->qs;
+        gA = (cplx<T>*)P->gA;
+        prof_mark(P, PIM_STAGE_APPLY, 0, sr);
+        prof_mark(P, PIM_STAGE_PERMUTE, 0, sr);
         // 1. sorted, regularised sources (Eq. neutral)
         const double* mean = nullptr;
         if (P->npsp && !adj) {
-            if ((st = mean_of<T>(P, q, false, N, nrhs, r, true, s)) != PIM_OK) return st;
+            if ((st = mean_of<T>(P, q, false, N, nrhs, r, true, sr)) != PIM_OK) return st;
             mean = P->dsum;
-            if (multi) copy_mean_kernel<<<1, 1, 0, s>>>(P->dsum, P->dmeans + 2 * r);
+            if (multi) copy_mean_kernel<<<1, 1, 0, sr>>>(P->dsum, P->dmeans + 2 * r);
         }
-        if (P->real_data) permute_kernel<T, true><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
-        else permute_kernel<T, false><<<1024, 256, 0, s>>>(q, d.perm, N, nrhs, r, mean, qs);
+        if (P->real_data) permute_kernel<T, true><<<1024, 256, 0, sr>>>(q, d.perm, N, nrhs, r, mean, qs);
+        else permute_kernel<T, false><<<1024, 256, 0, sr>>>(q, d.perm, N, nrhs, r, mean, qs);
         PIM_CK(cudaGetLastError());
         P->launches += 1 + (mean ? 2 : 0);
-        prof_mark(P, PIM_STAGE_PERMUTE, 1, s);
+        prof_mark(P, PIM_STAGE_PERMUTE, 1, sr);
         // 2. far zone on the second stream
         if (P->has_far) {
-            PIM_CK(cudaEventRecord(P->ev_fork, s));
+            PIM_CK(cudaEventRecord(P->ev_fork, sr));
             PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
             prof_mark(P, PIM_STAGE_FAR, 0, P->s_far);
             FarSpreadArgs fa{};
@@ -933,16 +959,16 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
         // 3. near spread (two phases), 4. FFT convolution
-        prof_mark(P, PIM_STAGE_SPREAD, 0, s);
-        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
-        prof_mark(P, PIM_STAGE_SPREAD, 1, s);
-        prof_mark(P, PIM_STAGE_FFT, 0, s);
-        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, s)) != PIM_OK)
+        prof_mark(P, PIM_STAGE_SPREAD, 0, sr);
+        if ((st = spread_two_phase<T, PP>(P, qs, gA, sr)) != PIM_OK) return st;
+        prof_mark(P, PIM_STAGE_SPREAD, 1, sr);
+        prof_mark(P, PIM_STAGE_FFT, 0, sr);
+        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, sr)) != PIM_OK)
             return st;
-        prof_mark(P, PIM_STAGE_FFT, 1, s);
+        prof_mark(P, PIM_STAGE_FFT, 1, sr);
         P->launches += (d.nd > 0 ? 2 : 1) + 5;
         // 5. gather + correction + far gather
-        if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
+        if (P->has_far) PIM_CK(cudaStreamWaitEvent(sr, P->ev_join, 0));
         GatherArgs ga{};
         for (int i = 0; i < 3; ++i) { ga.n[i] = P->n[i]; ga.nf[i] = P->nf[i]; }
         ga.pf = P->pf;
@@ -976,26 +1002,33 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
-        prof_mark(P, PIM_STAGE_GATHER, 0, s);
+        prof_mark(P, PIM_STAGE_GATHER, 0, sr);
         if (N > 0) {
             const unsigned nb = (unsigned)((threads + 255) / 256);
-            if (P->tune_ev[0]) PIM_CK(cudaEventRecord(P->tune_ev[0], s));
-            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, s, ga, gA, ufar, qs, dst)) != PIM_OK)
+            if (P->tune_ev[0]) PIM_CK(cudaEventRecord(P->tune_ev[0], sr));
+            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, sr, ga, gA, ufar, qs, dst)) != PIM_OK)
                 return st;
-            if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], s));
+            if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], sr));
         }
         PIM_CK(cudaGetLastError());
-        prof_mark(P, PIM_STAGE_GATHER, 1, s);
+        prof_mark(P, PIM_STAGE_GATHER, 1, sr);
         P->launches += N > 0 ? 1 : 0;
         if (post_mean) {
-            if ((st = mean_of<T>(P, P->us, true, N, 1, 0, false, s)) != PIM_OK) return st;
-            unpermute_kernel<T><<<1024, 256, 0, s>>>((const cplx<T>*)P->us, d.perm, N, nrhs, r, P->dsum,
+            if ((st = mean_of<T>(P, P->us, true, N, 1, 0, false, sr)) != PIM_OK) return st;
+            unpermute_kernel<T><<<1024, 256, 0, sr>>>((const cplx<T>*)P->us, d.perm, N, nrhs, r, P->dsum,
                                                      P->real_data ? 1 : 0, u);
             PIM_CK(cudaGetLastError());
             P->launches += 3;
         }
-        prof_mark(P, PIM_STAGE_APPLY, 1, s);
+        prof_mark(P, PIM_STAGE_APPLY, 1, sr);
         if (P->prof_on && P->prof_next < pim_plan_s::PROF_RING) P->prof_next++;
+    }
+    use_lane(own);
+    qs = (cplx<T>*)P->qs;
+    gA = (cplx<T>*)P->gA;
+    for (int k = 1; k < K; ++k) {
+        PIM_CK(cudaEventRecord(P->lane[k].done, P->lane[k].sm));
+        PIM_CK(cudaStreamWaitEvent(s, P->lane[k].done, 0));
     }
     if (multi) {
         cplx<T>* qsall = (cplx<T>*)P->qsall;
@@ -1194,11 +1227,84 @@ pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {
 
 // Allocates what an apply with these arguments would allocate on first use
 // (the multi-RHS source buffer), so that the apply itself can be captured.
+// Scratch sizes of one right-hand-side lane (the per-RHS buffers of an apply).
+static void lane_sizes(pim_plan P, size_t* sz) {
+    const size_t ge = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t N = (size_t)P->pts.N;
+    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const size_t GB = (size_t)P->n[2] * P->n[1] * P->ng.L[0];
+    const size_t GC = (size_t)P->n[2] * P->ng.L[1] * P->ng.L[0];
+    const size_t np3 = (size_t)(P->p + 1) * (P->p + 1) * (P->p + 1);
+    size_t Gf = 0, fB = 0, fC = 0;
+    if (P->has_far) {
+        Gf = (size_t)P->nf[0] * P->nf[1] * P->nf[2];
+        fB = (size_t)P->nf[2] * P->nf[1] * P->fg.L[0];
+        fC = (size_t)P->nf[2] * P->fg.L[1] * P->fg.L[0];
+    }
+    sz[0] = N * ge;
+    sz[1] = G * ge;
+    sz[2] = GB * ge;
+    sz[3] = GC * ge;
+    sz[4] = (size_t)(P->pts.nd > 0 ? P->pts.nd : 1) * np3 * ge;
+    sz[5] = (size_t)P->far_chunks * Gf * ge;
+    sz[6] = Gf * sizeof(double2);
+    sz[7] = fB * sizeof(double2);
+    sz[8] = fC * sizeof(double2);
+}
+
+void lanes_free(pim_plan P) {
+    size_t sz[9];
+    lane_sizes(P, sz);
+    for (int k = 1; k < P->nlanes; ++k) {
+        pim_plan_s::Lane& l = P->lane[k];
+        void* b[9] = {l.qs, l.gA, l.gB, l.gC, l.mom, l.fpart, l.fA, l.fB, l.fC};
+        for (int i = 0; i < 9; ++i) pim_free(P, b[i], sz[i]);
+        if (l.sm) cudaStreamDestroy(l.sm);
+        if (l.sf) cudaStreamDestroy(l.sf);
+        if (l.fork) cudaEventDestroy(l.fork);
+        if (l.join) cudaEventDestroy(l.join);
+        if (l.done) cudaEventDestroy(l.done);
+        l = pim_plan_s::Lane{};
+    }
+    P->nlanes = 1;
+}
+
+pim_status lanes_prepare(pim_plan P, int nl) {
+    nl = std::min(nl, (int)pim_plan_s::RHS_LANES);
+    if (P->nlanes >= nl) return PIM_OK;
+    if (!P->lane_fork && cudaEventCreateWithFlags(&P->lane_fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        pim_set_error("event creation failed");
+        return PIM_ERR_CUDA;
+    }
+    size_t sz[9];
+    lane_sizes(P, sz);
+    for (int k = P->nlanes; k < nl; ++k) {
+        pim_plan_s::Lane& l = P->lane[k];
+        void** b[9] = {&l.qs, &l.gA, &l.gB, &l.gC, &l.mom, &l.fpart, (void**)&l.fA, (void**)&l.fB, (void**)&l.fC};
+        pim_status st;
+        for (int i = 0; i < 9; ++i)
+            if (sz[i] && (st = pim_alloc(P, b[i], sz[i])) != PIM_OK) return st;
+        if (cudaStreamCreateWithFlags(&l.sm, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&l.sf, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            pim_set_error("stream or event creation failed");
+            return PIM_ERR_CUDA;
+        }
+        P->nlanes = k + 1;
+    }
+    return PIM_OK;
+}
+
 pim_status apply_prepare(pim_plan P, int nrhs, bool adj) {
     const long long N = P->pts.N;
     const bool multi = nrhs > 1 && nrhs <= 128 && !P->no_multi && !(P->npsp && adj) && N > 0;
     if (!multi) return PIM_OK;
     pim_status st;
+    if (!P->npsp && (st = lanes_prepare(P, std::min(nrhs, (int)pim_plan_s::RHS_LANES))) != PIM_OK) return st;
     const size_t el = P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t need = (size_t)N * nrhs * el;
     if (P->qsall_bytes < need) {

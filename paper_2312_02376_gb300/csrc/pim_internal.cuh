@@ -252,6 +252,25 @@ struct pim_plan_s {
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double plan_ms = 0, points_ms = 0;
+    // extra lanes of a multi-RHS apply: right-hand side r runs its per-RHS
+    // stages on lane r % nlanes, each lane with its own scratch and streams
+    // (lane 0 is the plan's own scratch above)
+    static constexpr int RHS_LANES = 4;
+    struct Lane {
+        void* qs = nullptr;
+        void* gA = nullptr;
+        void* gB = nullptr;
+        void* gC = nullptr;
+        void* mom = nullptr;
+        void* fpart = nullptr;
+        double2* fA = nullptr;
+        double2* fB = nullptr;
+        double2* fC = nullptr;
+        cudaStream_t sm = nullptr, sf = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
+    } lane[RHS_LANES];
+    int nlanes = 1;                // lanes allocated (1: none extra)
+    cudaEvent_t lane_fork = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -287,6 +306,8 @@ pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
 pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
+pim_status lanes_prepare(pim_plan P, int nlanes);
+void lanes_free(pim_plan P);
 
 // batch.cu
 void batch_forget(pim_plan P);
