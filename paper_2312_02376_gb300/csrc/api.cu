@@ -118,6 +118,13 @@ void pim_destroy(pim_plan P) {
     batch_forget(P);
     lanes_free(P);
     if (P->lane_fork) cudaEventDestroy(P->lane_fork);
+    {
+        const size_t gq = grid_elem(P) * (size_t)P->pts.N;
+        pim_free(P, P->qs, gq);
+        pim_free(P, P->us, gq);
+        pim_free(P, P->hq, P->stage_bytes);
+        pim_free(P, P->hu, P->stage_bytes);
+    }
     points_free(P);
     const size_t ge = grid_elem(P);
     const long long G = (long long)P->n[0] * P->n[1] * P->n[2];
