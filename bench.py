@@ -61,12 +61,16 @@ def workload(name=WORKLOAD):
     return inputs.helmholtz2d()
 
 
-def dist_init(n_gpus):
+def dist_init(n_gpus, backend="nccl"):
+    """Ranks from the launcher's environment; one process group over all
+    ranks for the barrier and the max of the step times (replicas: no
+    collective on the data path)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        if not dist.is_initialized():
+            dist.init_process_group(backend, init_method="env://")
     return rank, world
 
 
@@ -77,13 +81,21 @@ def barrier(world):
 
 
 def allmax(x, world):
+    """The maximum of x over the ranks (the slowest replica sets the time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(n_points, world, ms_step):
+    """Whole-job Mpts/s of a step of one forward and one adjoint apply on
+    every replica."""
+    return 2.0 * n_points * world / (ms_step * 1e-3) / 1e6
 
 
 class ClockSampler:
@@ -232,7 +244,7 @@ def run_gpu(args):
         err_truth = float(np.linalg.norm(uu - ref) / np.linalg.norm(ref))
     launches = plan.info().launches - launches0
     ms_step = allmax(float(np.mean(times)), world)
-    value = 2.0 * W.N * world / (ms_step * 1e-3) / 1e6
+    value = replica_value(W.N, world, ms_step)
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     qh = torch.tensor(W.q, dtype=cdt).pin_memory()
