@@ -98,6 +98,11 @@ typedef struct {
     int with_gradient;   /* 1: pim_set_points also stores the position derivatives of
                             the correction values (48 B per entry), which
                             pim_position_grad needs                                    */
+    int gather_variant;  /* -1: launch shape of the gather kernel chosen by autotune
+                            (shape 0 without it); v >= 0 forces shape v, which must be
+                            below pim_info.gather_variants (which depends on the
+                            precision and correction mode; else pim_set_points
+                            returns PIM_ERR_ARG)                                       */
 } pim_options;
 
 typedef struct {
@@ -110,7 +115,8 @@ typedef struct {
     double plan_ms;      /* wall time of pim_plan_create                               */
     double points_ms;    /* wall time of the last pim_set_points                       */
     int64_t launches;    /* kernels launched by this plan's applies so far             */
-    int gather_variant;  /* launch shape of the gather kernel chosen by the autotuner  */
+    int gather_variant;  /* launch shape of the gather kernel in use                   */
+    int gather_variants; /* launch shapes available to this plan                       */
 } pim_info;
 
 /* Stages timed by the profiling ring (pim_set_profiling). */

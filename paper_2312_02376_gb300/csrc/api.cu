@@ -93,6 +93,7 @@ void pim_options_default(pim_options* o) {
     o->mem_cap = 0;
     o->autotune = 1;
     o->with_gradient = 0;
+    o->gather_variant = -1;
 }
 
 const char* pim_status_string(pim_status s) {
@@ -201,6 +202,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->mem_cap = o.mem_cap;
     P->autotune = o.autotune ? 1 : 0;
     P->with_gradient = o.with_gradient ? 1 : 0;
+    P->force_variant = o.gather_variant;
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
@@ -373,7 +375,12 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     if ((st = pim_alloc(P, &P->qs, (size_t)N * ge)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &P->us, (size_t)N * ge)) != PIM_OK) return st;
     P->gather_variant = 0;
-    if (P->autotune && N > 0 && (st = apply_autotune(P, 0)) != PIM_OK) return st;
+    if (P->force_variant >= 0) {
+        if (P->force_variant >= gather_variant_count(P)) return PIM_ERR_ARG;
+        P->gather_variant = P->force_variant;
+    } else if (P->autotune && N > 0 && (st = apply_autotune(P, 0)) != PIM_OK) {
+        return st;
+    }
     PIM_CK(cudaDeviceSynchronize());
     P->points_ms = now_ms() - t0;
     return PIM_OK;
@@ -534,6 +541,7 @@ pim_status pim_plan_info(pim_plan P, pim_info* info) {
     info->points_ms = P->points_ms;
     info->launches = P->launches;
     info->gather_variant = P->gather_variant;
+    info->gather_variants = gather_variant_count(P);
     return PIM_OK;
 }
 

@@ -1318,6 +1318,10 @@ pim_status apply_prepare(pim_plan P, int nrhs, bool adj) {
     return PIM_OK;
 }
 
+// Launch shapes of the gather kernel: (unroll depth of the row loop, minimum
+// resident CTAs), the same set for every precision and correction mode.
+int gather_variant_count(const pim_plan_s*) { return GATHER_VARIANTS; }
+
 // Times every gather variant on a forward apply of zero sources and keeps
 // the fastest (the other stages do not depend on the variant).
 pim_status apply_autotune(pim_plan P, cudaStream_t s) {
@@ -1337,7 +1341,8 @@ pim_status apply_autotune(pim_plan P, cudaStream_t s) {
     const bool prof = P->prof_on;
     P->prof_on = false;
     const int64_t launches = P->launches;
-    for (int v = 0; v < GATHER_VARIANTS; ++v) {
+    const int nvar = gather_variant_count(P);
+    for (int v = 0; v < nvar; ++v) {
         P->gather_variant = v;
         if ((st = apply_run(P, q, u, 1, false, s)) != PIM_OK) return st;  // warm-up
         float tot = 0.f;

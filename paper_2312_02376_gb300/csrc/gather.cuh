@@ -117,17 +117,11 @@ __device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __re
     }
 }
 
-// One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
-// correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
-// written in the caller's order.  In both gathers lane (jy, jz) takes one
-// x-row of the stencil.
-template <typename T, int P, int CM, int UNR, int MINB>
-__global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
-                                                     const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
-                                                     void* out) {
-    const int lane = threadIdx.x & 31;
-    const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (m >= a.N) return;
+// Near gather (Sec. 3.3 step 3) and far gather (Eq. interpolation) of point m,
+// this lane's share: lane (jy, jz) takes one x-row of each stencil.
+template <typename T, int P>
+__device__ __forceinline__ cplx<T> grid_part(const GatherArgs& a, long long m, int lane, const cplx<T>* __restrict__ U,
+                                             const cplx<T>* __restrict__ uf) {
     constexpr int NP = P + 1;
     cplx<T> acc = mk<T>(T(0), T(0));
     // near gather
@@ -180,6 +174,21 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
             acc.y += wyz * r.y;
         }
     }
+    return acc;
+}
+
+// One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
+// correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
+// written in the caller's order.  In both gathers lane (jy, jz) takes one
+// x-row of the stencil.
+template <typename T, int P, int CM, int UNR, int MINB>
+__global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
+                                                     const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
+                                                     void* out) {
+    const int lane = threadIdx.x & 31;
+    const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (m >= a.N) return;
+    cplx<T> acc = grid_part<T, P>(a, m, lane, U, uf);
     // near-pair correction: exp(-j k0.(i o L)) d q_n (forward) or
     // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  The adjoint is summed as the
     // conjugate of sum conj(phase) d conj(v_n), so that the values are used

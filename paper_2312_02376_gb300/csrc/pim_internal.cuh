@@ -235,6 +235,7 @@ struct pim_plan_s {
     unsigned char prof_mask[512];    // stages recorded per ring slot
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
+    int force_variant = -1;       // >= 0: launch shape fixed by the options
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // around the gather launch while autotuning
     void* qsall = nullptr;        // sorted sources of every right-hand side (multi-RHS correction)
     size_t qsall_bytes = 0;
@@ -304,6 +305,7 @@ constexpr int PIM_RED_BLOCKS = 608;
 pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s);
 pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
+int gather_variant_count(const pim_plan_s* P);
 pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
 pim_status lanes_prepare(pim_plan P, int nlanes);

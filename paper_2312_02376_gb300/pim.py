@@ -31,7 +31,8 @@ class pim_options(ctypes.Structure):
     _fields_ = [("far_n", ctypes.c_int * 3), ("far_p", ctypes.c_int), ("corr_radius", ctypes.c_int),
                 ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
-                ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int),
+                ("gather_variant", ctypes.c_int)]
 
 
 class pim_info(ctypes.Structure):
@@ -39,7 +40,8 @@ class pim_info(ctypes.Structure):
                 ("corr_radius", ctypes.c_int), ("precision", ctypes.c_int), ("corr_mode", ctypes.c_int),
                 ("periodic_mask", ctypes.c_int), ("near_layers", ctypes.c_int), ("N", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double),
-                ("points_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("gather_variant", ctypes.c_int)]
+                ("points_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("gather_variant", ctypes.c_int),
+                ("gather_variants", ctypes.c_int)]
 
 
 class PimError(RuntimeError):
@@ -246,7 +248,7 @@ class Plan:
 
     def __init__(self, D, pdims, k, k0, n, p=4, layers=1, precision="fp32", b=None, nf=None, pf=None,
                  corr_mode=None, cube=False, tile=None, neutral_tol=None, mem_cap=0, autotune=None,
-                 with_gradient=False, stream=None):
+                 with_gradient=False, gather_variant=None, stream=None):
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
         self.pdims = tuple(pdims)
@@ -272,6 +274,8 @@ class Plan:
         if autotune is not None:
             opt.autotune = 1 if autotune else 0
         opt.with_gradient = 1 if with_gradient else 0
+        if gather_variant is not None:
+            opt.gather_variant = int(gather_variant)
         opt.mem_cap = int(mem_cap)
         mask = sum(1 << d for d in self.pdims)
         h = self.D / (self.n - 1)

@@ -50,6 +50,8 @@ def to_dev(x, precision, real):
 CASES = {
     # name: (D, pdims, k, k0, n, N, b, nf, pf)
     "helmholtz2d_bloch": ((1, 1, 0.5), (0, 1), 2 * np.pi * 0.8, (1.5, 0.5, 0.0), (17, 17, 9), 700, 4, (10, 10, 6), 4),
+    "helmholtz2d_dense": ((1, 1, 0.5), (0, 1), 2 * np.pi * 0.8, (1.5, 0.5, 0.0), (17, 17, 9), 1600, 4, (10, 10, 6),
+                          4),
     "helmholtz3d_bloch": ((1, 1, 1), (0, 1, 2), 2 * np.pi * 0.7, (0.9, 0.9, 0.0), (13, 13, 13), 500, 4, (8, 8, 8), 3),
     "helmholtz1d_z": ((1, 0.5, 0.5), (2,), 2 * np.pi * 0.5, (0, 0, 0.0), (9, 9, 17), 500, 3, (6, 6, 10), 3),
     "helmholtz1d_x_phase": ((1, 0.5, 0.5), (0,), 3.0, (1.2, 0, 0), (17, 9, 9), 400, 3, (10, 6, 6), 3),
@@ -108,6 +110,36 @@ def test_fp32_mixed_forward_and_adjoint(name, mode, oracle_cache):
     assert rel(u, ue) < FP32_TOL, rel(u, ue)
     assert rel(w, we) < FP32_TOL, rel(w, we)
     pl.close()
+
+
+@pytest.mark.parametrize("precision,mode", [("fp32", pim.PIM_CORR_DOUBLE_FLOAT), ("fp32", pim.PIM_CORR_FP32),
+                                            ("fp64", pim.PIM_CORR_FP64)])
+@pytest.mark.parametrize("name", ["helmholtz2d_dense", "npsp3d"])
+def test_every_gather_launch_shape(name, precision, mode, oracle_cache):
+    """Each launch shape of the gather kernel the autotuner may pick, forced
+    through the options, on rows long enough for every unrolled trip count
+    and tail."""
+    W, o, ue, we = oracle_results(name, oracle_cache)
+    real = W.k == 0 and not any(W.k0)
+    tol = FP64_TOL if precision == "fp64" else FP32_TOL
+    nvar = None
+    v = 0
+    while nvar is None or v < nvar:
+        pl = gpu_plan(W, precision, corr_mode=mode, gather_variant=v)
+        info = pl.info()
+        nvar = info.gather_variants
+        assert info.gather_variant == v
+        q = to_dev(W.q, precision, real)
+        u = pl.apply(q).cpu().numpy()
+        w = pl.apply_adjoint(q).cpu().numpy()
+        assert pl.device_status() == pim.PIM_OK
+        assert rel(u, ue) < tol, (v, rel(u, ue))
+        assert rel(w, we) < tol, (v, rel(w, we))
+        pl.close()
+        v += 1
+    assert nvar == 5
+    with pytest.raises(Exception):
+        gpu_plan(W, precision, corr_mode=mode, gather_variant=nvar)
 
 
 def test_stage_parity_far_table_spread_and_correction(oracle_cache):
