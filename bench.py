@@ -4,8 +4,9 @@ Workload: 2D-periodic (x, y) Helmholtz with a Bloch phase shift, cell
 1 x 1 x 0.5, k = 2 pi 0.8, k0 = (0.3k, 0.1k, 0), N = 262144 points (half
 uniform, half on a sphere of radius 0.2 at the cell centre), complex64
 sources CN(0, 1), near grid 128 x 128 x 64, p = 4, FP32 bulk with FP64 far
-series, far grid sum and near-pair correction (double-float accumulation of
-FP64 values).  A step is one forward apply plus one adjoint apply (every row
+series, far grid sum and near-pair correction (values computed in FP64; per
+row the entries above 2^-10 of its largest stored as an FP32 head and a bf16
+tail and summed in double-float, the others as complex64 summed in FP32).  A step is one forward apply plus one adjoint apply (every row
 of the hot path).  Metric: Mpts/s per apply (fwd+adjoint) = 2 N / t_step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -148,15 +149,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gather_bytes(info, N, G, nf3, fp64=False):
-    """Algorithmic bytes of one gather + correction launch: FP64-class
-    correction values of 16 B and a 4 B column per entry; per point the
-    stencil starts, local coordinates, permutation, sorted source, output,
-    far stencil and far coordinates; the near and far grids once."""
-    per_nnz = 16 + 4
+VALUE_BYTES = {0: 16, 1: 16, 2: 8, 3: 8}   # per correction value, by pim_corr_mode
+
+
+def gather_bytes(info, N, G, nf3, fp64=False, nbig=0):
+    """Algorithmic bytes of one gather + correction launch: the correction
+    value (16 B FP64 or double-float, 8 B FP32 or compact, plus a 4 B tail
+    for the nbig compact entries summed in double-float) and a 4 B column per
+    entry; per point the stencil starts, local coordinates, permutation,
+    sorted source, output, far stencil and far coordinates (and the compact
+    row split); the near and far grids once."""
+    compact = int(info.corr_mode) == 3
+    per_nnz = VALUE_BYTES[int(info.corr_mode)] + 4
     c, r = (16, 8) if fp64 else (8, 4)        # complex and real element sizes
-    per_point = 4 + 3 * r + 4 + c + c + 4 + 3 * r
-    return info.nnz * per_nnz + (N + 1) * 8 + N * per_point + G * c + nf3 * c
+    per_point = 4 + 3 * r + 4 + c + c + 4 + 3 * r + (4 if compact else 0)
+    return info.nnz * per_nnz + 4 * nbig + (N + 1) * 8 + N * per_point + G * c + nf3 * c
 
 
 def gather_source_hash():
@@ -200,7 +207,7 @@ def run_gpu(args):
     fp64 = args.precision == "fp64"
     cdt = torch.complex128 if fp64 else torch.complex64
     plan = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=args.precision, b=W.b,
-                    nf=W.nf, pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_DOUBLE_FLOAT)
+                    nf=W.nf, pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_COMPACT)
     plan.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     info = plan.info()
     q = torch.tensor(W.q, dtype=cdt, device="cuda")
@@ -268,7 +275,8 @@ def run_gpu(args):
         peak, peak_kind = measured_peaks()
         G = int(np.prod(W.n))
         nf3 = int(np.prod(W.nf))
-        gb = gather_bytes(info, W.N, G, nf3, fp64)
+        nbig = int(plan.debug(7).astype(np.int64).sum()) if int(info.corr_mode) == 3 else 0
+        gb = gather_bytes(info, W.N, G, nf3, fp64, nbig)
         g_ms = stage_ms["gather_correct"] / max(1, napplies)
         achieved = gb / (g_ms * 1e-3) / 1e9
         apply_ms = stage_ms["apply"] / max(1, napplies)
@@ -278,9 +286,12 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "c128" if fp64 else "c64+f64", "data": "synthetic",
             "config": {"workload": args.workload, "N": W.N, "grid": list(W.n), "p": W.p, "near_layers": W.layers,
                        "corr_radius_steps": W.b, "far_grid": list(W.nf), "far_p": W.pf, "nnz": int(info.nnz),
+                       "nnz_double_float": nbig if int(info.corr_mode) == 3 else None,
                        "precision": "FP64 throughout" if fp64 else
-                                    "complex64 bulk, FP64 far series/grid sum, FP64 correction values "
-                                    "(double-float accumulation)",
+                                    "complex64 bulk, FP64 far series/grid sum, correction values computed "
+                                    "in FP64; per row the entries above 2^-10 of its largest as FP32 head + "
+                                    "bf16 tail summed in double-float, the rest complex64 summed in FP32 "
+                                    "(every stored value within 2^-33 of the row's largest)",
                        "rel_l2_vs_ewald_ground_truth": err_truth,
                        "ground_truth_rows": 16,
                        "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"},
@@ -398,7 +409,7 @@ def run_batch(args):
     t0 = time.perf_counter()
     for W in sets:
         pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, pf=W.pf,
-                      corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
+                      corr_mode=pim.PIM_CORR_COMPACT)
         pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
         plans.append(pl)
         qs.append(torch.tensor(W.q, device="cuda"))
@@ -453,7 +464,7 @@ def run_coulomb_grad(args):
     W = inputs.coulomb3d_big()
     t0 = time.perf_counter()
     pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
-                  pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT, with_gradient=True)
+                  pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT, with_gradient=True)
     pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     t_plan = time.perf_counter() - t0
     q = torch.tensor(W.q, device="cuda")

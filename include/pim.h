@@ -78,8 +78,14 @@ typedef enum {
     PIM_CORR_FP64 = 0,        /* correction values FP64, FP64 accumulation */
     PIM_CORR_DOUBLE_FLOAT = 1,/* values as FP64 split into two floats, compensated
                                  (double-float) accumulation on the FP32 pipes */
-    PIM_CORR_FP32 = 2         /* values rounded to complex64 after the FP64
+    PIM_CORR_FP32 = 2,        /* values rounded to complex64 after the FP64
                                  cancellation, FP32 accumulation */
+    PIM_CORR_COMPACT = 3      /* the default.  Each row holds first the entries with
+                                 |d| > 2^-corr_split max_row |d|, as FP64 split into an FP32
+                                 head and a bf16 tail per component (12 B, relative
+                                 rounding <= 2^-33) summed in double-float, then the others
+                                 as complex64 (8 B) summed in FP32: every stored value is
+                                 within 2^-33 max_row |d| of its FP64 value */
 } pim_corr_mode;
 
 typedef struct {
@@ -98,6 +104,9 @@ typedef struct {
     int with_gradient;   /* 1: pim_set_points also stores the position derivatives of
                             the correction values (48 B per entry), which
                             pim_position_grad needs                                    */
+    int corr_split;      /* PIM_CORR_COMPACT: the exponent s of the 2^-s max_row |d|
+                            threshold above; 0 keeps every entry in the 12-byte form;
+                            default 10; 0 <= s <= 30 (else PIM_ERR_ARG)                */
     int gather_variant;  /* -1: launch shape of the gather kernel chosen by autotune
                             (shape 0 without it); v >= 0 forces shape v, which must be
                             below pim_info.gather_variants (which depends on the
@@ -319,7 +328,9 @@ const char* pim_stage_name(int stage);
  *   3 sort permutation (int32, sorted slot -> caller index), N entries;
  *   4 correction row pointers (int64, N+1) in sorted order;
  *   5 correction columns (uint32, nnz): sorted column | image index << 25;
- *   6 correction values (complex128 FP64, nnz): G0 - G_grid before the phase.
+ *   6 correction values (complex128 FP64, nnz): G0 - G_grid before the phase;
+ *   7 entries at the head of each row summed in double-float (int32, N;
+ *     PIM_CORR_COMPACT plans only, PIM_ERR_STATE otherwise).
  * `bytes` must be at least the size of the table; PIM_ERR_ARG otherwise.
  */
 pim_status pim_debug_copy(pim_plan plan, int what, void* host_out, size_t bytes);

@@ -87,12 +87,13 @@ void pim_options_default(pim_options* o) {
     o->far_p = -1;
     o->corr_radius = -1;
     o->corr_cube = 0;
-    o->corr_mode = PIM_CORR_DOUBLE_FLOAT;
+    o->corr_mode = PIM_CORR_COMPACT;
     o->neutral_tol = 1e-6;
     o->series_tol = 1e-16;
     o->mem_cap = 0;
     o->autotune = 1;
     o->with_gradient = 0;
+    o->corr_split = 10;
     o->gather_variant = -1;
 }
 
@@ -238,10 +239,15 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->b = o.corr_radius >= 0 ? o.corr_radius : p + 1;
     P->cube = o.corr_cube ? 1 : 0;
     P->corr_mode = prec == PIM_FP64 ? PIM_CORR_FP64 : o.corr_mode;
-    if (P->corr_mode < 0 || P->corr_mode > 2) {
+    if (P->corr_mode < 0 || P->corr_mode > 3) {
         pim_set_error("invalid correction mode");
         return fail(PIM_ERR_ARG);
     }
+    if (o.corr_split < 0 || o.corr_split > 30) {
+        pim_set_error("corr_split outside [0, 30]");
+        return fail(PIM_ERR_ARG);
+    }
+    P->corr_split = o.corr_split;
     // near images (Eq. 4)
     P->nimg = 0;
     const int Lr = near_layers;
@@ -608,6 +614,11 @@ pim_status pim_debug_copy(pim_plan P, int what, void* host, size_t bytes) {
         case 4: src = P->pts.row_ptr; need = (N + 1) * sizeof(int64_t); break;
         case 5: src = P->pts.col; need = (size_t)P->pts.nnz * sizeof(uint32_t); break;
         case 6: src = P->pts.val; need = (size_t)P->pts.nnz * sizeof(double2); break;
+        case 7:
+            if (P->corr_mode != PIM_CORR_COMPACT) return PIM_ERR_STATE;
+            src = P->pts.nbig;
+            need = N * sizeof(int);
+            break;
         default: return PIM_ERR_ARG;
     }
     if (bytes < need) {

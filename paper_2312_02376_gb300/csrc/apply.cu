@@ -745,6 +745,8 @@ struct CorrMultiArgs {
     const double2* val;
     const float4* valdf;
     const float2* valf;
+    const uint32_t* valt;
+    const int* nbig;
     const double2* phase;
     const float4* phasedf;
 };
@@ -763,12 +765,17 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
         rh[k] = rl[k] = ih[k] = il[k] = 0.f;
     }
     const double cs = a.adj ? -1.0 : 1.0;
-    for (long long q = a.row_ptr[m]; q < a.row_ptr[m + 1]; ++q) {
+    const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
+    // compact mode: entries [r0, rb) in double-float, the rest in FP32 (their
+    // sums go to the low words)
+    const long long rb = CM == PIM_CORR_COMPACT ? r0 + a.nbig[m] : r1;
+    for (long long q = r0; q < r1; ++q) {
         const uint32_t c = __ldg(a.col + q);
         const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
         const cplx<T>* xr = qsall + (long long)n * R;
-        if (CM == PIM_CORR_DOUBLE_FLOAT) {
-            const float4 d = __ldg(a.valdf + q);
+        if (corr_df(CM) && q < rb) {
+            const float4 d = CM == PIM_CORR_COMPACT ? compact_value(__ldg(a.valf + q), __ldg(a.valt + q))
+                                                    : __ldg(a.valdf + q);
             const float fs = (float)cs;
             float4 v = make_float4(d.x, d.y, fs * d.z, fs * d.w);
             if (ii != a.self_img) v = df_cmul(a.phasedf[ii], v);
@@ -779,7 +786,7 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
                 const cplx<T> xv = xr[r];
                 df_cmac(rh[k], rl[k], ih[k], il[k], v, (float)xv.x, (float)xv.y);
             }
-        } else if (CM == PIM_CORR_FP32) {
+        } else if (CM == PIM_CORR_FP32 || CM == PIM_CORR_COMPACT) {
             const float2 d = __ldg(a.valf + q);
             float2 dd = make_float2(d.x, (float)cs * d.y);
             if (ii != a.self_img) {
@@ -791,8 +798,15 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
                 const int r = lane + 32 * k;
                 if (r >= R) break;
                 const cplx<T> xv = xr[r];
-                rh[k] += dd.x * (float)xv.x - dd.y * (float)xv.y;
-                ih[k] += dd.x * (float)xv.y + dd.y * (float)xv.x;
+                const float tr = dd.x * (float)xv.x - dd.y * (float)xv.y;
+                const float ti = dd.x * (float)xv.y + dd.y * (float)xv.x;
+                if (CM == PIM_CORR_COMPACT) {
+                    rl[k] += tr;
+                    il[k] += ti;
+                } else {
+                    rh[k] += tr;
+                    ih[k] += ti;
+                }
             }
         } else {
             double2 d = __ldg(a.val + q);
@@ -997,6 +1011,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ga.val = d.val;
         ga.valdf = d.valdf;
         ga.valf = d.valf;
+        ga.valt = d.valt;
+        ga.nbig = d.nbig;
         ga.phase = P->dphase;
         ga.phasedf = P->dphasedf;
         const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
@@ -1049,6 +1065,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ca.val = d.val;
         ca.valdf = d.valdf;
         ca.valf = d.valf;
+        ca.valt = d.valt;
+        ca.nbig = d.nbig;
         ca.phase = P->dphase;
         ca.phasedf = P->dphasedf;
         const int cm = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
@@ -1059,7 +1077,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         else if (nrhs <= 64) corr_multi_kernel<T, CMV, 2><<<nb, 256, 0, s>>>(ca, qsall, u);                 \
         else corr_multi_kernel<T, CMV, 4><<<nb, 256, 0, s>>>(ca, qsall, u);                                 \
     } while (0)
-        if (cm == PIM_CORR_DOUBLE_FLOAT) PIM_CM_LAUNCH(PIM_CORR_DOUBLE_FLOAT);
+        if (cm == PIM_CORR_COMPACT) PIM_CM_LAUNCH(PIM_CORR_COMPACT);
+        else if (cm == PIM_CORR_DOUBLE_FLOAT) PIM_CM_LAUNCH(PIM_CORR_DOUBLE_FLOAT);
         else if (cm == PIM_CORR_FP32) PIM_CM_LAUNCH(PIM_CORR_FP32);
         else PIM_CM_LAUNCH(PIM_CORR_FP64);
 #undef PIM_CM_LAUNCH
@@ -1172,7 +1191,7 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
         const unsigned nbk = (unsigned)((N * 32 + 255) / 256);
         if (N > 0) {
             if constexpr (sizeof(T) == 4) {
-                if (P->corr_mode == PIM_CORR_DOUBLE_FLOAT)
+                if (corr_df(P->corr_mode))
                     grad_kernel<T, PP, true><<<nbk, 256, 0, s>>>(ga, gA, gD, (const cplx<T>*)P->fU,
                                                                  (const cplx<T>*)P->fV, qs, gs, grad);
                 else

@@ -25,6 +25,8 @@ struct GatherArgs {
     const double2* val;
     const float4* valdf;
     const float2* valf;
+    const uint32_t* valt;
+    const int* nbig;
     const double2* phase;
     const float4* phasedf;
 };
@@ -76,6 +78,12 @@ __device__ __forceinline__ float4 df_cmul(const float4 p, const float4 d) {
     return r;
 }
 
+// A compact value (FP32 head h, bf16 tails of re and im in t) as a
+// double-float complex: the tails are the high halves of FP32 words.
+__device__ __forceinline__ float4 compact_value(float2 h, uint32_t t) {
+    return make_float4(h.x, __uint_as_float(t << 16), h.y, __uint_as_float(t & 0xffff0000u));
+}
+
 // sum of a double-float over the warp (lane 0 holds the result)
 __device__ __forceinline__ void df_warp_sum(float& h, float& l) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -90,11 +98,12 @@ __device__ __forceinline__ void df_warp_sum(float& h, float& l) {
 // Near-pair correction of one row, all lanes of the warp: entry q = lane,
 // lane + 32, ... of [0, len).  Full trips take UNR entries per lane with every
 // column and value load issued before the dependent source loads and no
-// bounds tests; the tail takes one entry per lane.  body(c, d, x) gets the
-// column word, the value and the source q_n.
-template <int UNR, typename V, typename C, typename F>
-__device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __restrict__ colr,
-                                         const V* __restrict__ valr, const C* __restrict__ qs, F&& body) {
+// bounds tests; the tail takes one entry per lane.  load(q) reads the value
+// of entry q; body(c, d, x) gets the column word, the value and the source q_n.
+template <int UNR, typename C, typename L, typename F>
+__device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __restrict__ colr, L&& load,
+                                         const C* __restrict__ qs, F&& body) {
+    using V = decltype(load(0));
     int q = lane;
     for (; q + 32 * (UNR - 1) < len; q += 32 * UNR) {
         uint32_t c[UNR];
@@ -102,7 +111,7 @@ __device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __re
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             c[u] = __ldcs(colr + q + 32 * u);
-            d[u] = __ldcs(valr + q + 32 * u);
+            d[u] = load(q + 32 * u);
         }
         C x[UNR];
 #pragma unroll
@@ -112,7 +121,7 @@ __device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __re
     }
     for (; q < len; q += 32) {
         const uint32_t c = __ldcs(colr + q);
-        const V d = __ldcs(valr + q);
+        const V d = load(q);
         body(c, d, qs[c & PIM_COL_MASK]);
     }
 }
@@ -200,7 +209,9 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
     double2 accd = make_double2(0.0, 0.0);
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     if (CM == PIM_CORR_FP64) {
-        corr_row<UNR>(lane, len, colr, a.val + r0, qs, [&](uint32_t c, const double2& d, const cplx<T>& x) {
+        const double2* vr = a.val + r0;
+        corr_row<UNR>(lane, len, colr, [=](int e) { return __ldcs(vr + e); }, qs,
+                      [&](uint32_t c, const double2& d, const cplx<T>& x) {
             const double xr = (double)x.x, xi = (double)fs * (double)x.y;
             double2 t = make_double2(d.x * xr - d.y * xi, d.x * xi + d.y * xr);
             const int ii = (int)(c >> PIM_COL_BITS);
@@ -210,11 +221,11 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
             }
             accd = cadd(accd, t);
         });
-    } else if (CM == PIM_CORR_DOUBLE_FLOAT) {
+    } else if (corr_df(CM)) {
         // FP32 arithmetic throughout: values of other images are multiplied by
         // their phase in double-float, every entry is added by df_cmac and the
         // warp sum is double-float too
-        corr_row<UNR>(lane, len, colr, a.valdf + r0, qs, [&](uint32_t c, const float4& d, const cplx<T>& x) {
+        auto body = [&](uint32_t c, const float4& d, const cplx<T>& x) {
             const int ii = (int)(c >> PIM_COL_BITS);
             float4 v = d;
             if (ii != a.self_img) {
@@ -224,9 +235,39 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
                 v = df_cmul(ph, v);
             }
             df_cmac(rh, rl, ih, il, v, (float)x.x, fs * (float)x.y);
-        });
+        };
+        if (CM == PIM_CORR_COMPACT) {
+            // the row's large entries (double-float), then its small ones
+            // (complex64 values, FP32 sums folded in once per lane)
+            const int nb = a.nbig[m];
+            const float2* hr = a.valf + r0;
+            const uint32_t* tr = a.valt + r0;
+            corr_row<UNR>(lane, nb, colr, [=](int e) { return compact_value(__ldcs(hr + e), __ldcs(tr + e)); }, qs,
+                          body);
+            float sr = 0.f, si = 0.f;
+            corr_row<UNR>(lane, len - nb, colr + nb, [=](int e) { return __ldcs(hr + nb + e); }, qs,
+                          [&](uint32_t c, const float2& d, const cplx<T>& x) {
+                              const float xr = (float)x.x, xi = fs * (float)x.y;
+                              float2 t = make_float2(d.x * xr - d.y * xi, d.x * xi + d.y * xr);
+                              const int ii = (int)(c >> PIM_COL_BITS);
+                              if (ii != a.self_img) {
+                                  const float4 ph = a.phasedf[ii];
+                                  const float pr = ph.x, pi = fs * ph.z;
+                                  t = make_float2(pr * t.x - pi * t.y, pr * t.y + pi * t.x);
+                              }
+                              sr += t.x;
+                              si += t.y;
+                          });
+            two_sum_acc(rh, rl, sr);
+            two_sum_acc(ih, il, si);
+        } else {
+            const float4* vr = a.valdf + r0;
+            corr_row<UNR>(lane, len, colr, [=](int e) { return __ldcs(vr + e); }, qs, body);
+        }
     } else if (CM == PIM_CORR_FP32) {
-        corr_row<UNR>(lane, len, colr, a.valf + r0, qs, [&](uint32_t c, const float2& d, const cplx<T>& x) {
+        const float2* vr = a.valf + r0;
+        corr_row<UNR>(lane, len, colr, [=](int e) { return __ldcs(vr + e); }, qs,
+                      [&](uint32_t c, const float2& d, const cplx<T>& x) {
             const float xr = (float)x.x, xi = fs * (float)x.y;
             float2 t = make_float2(d.x * xr - d.y * xi, d.x * xi + d.y * xr);
             const int ii = (int)(c >> PIM_COL_BITS);
@@ -251,7 +292,7 @@ __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const c
             ih += __shfl_xor_sync(0xffffffffu, ih, o);
         }
     }
-    if (CM == PIM_CORR_DOUBLE_FLOAT) {
+    if (corr_df(CM)) {
         df_warp_sum(rh, rl);
         df_warp_sum(ih, il);
     }
@@ -312,6 +353,7 @@ pim_status launch_gather(int cm, int v, unsigned nb, cudaStream_t s, const Gathe
     if constexpr (sizeof(T) == 8) {
         return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
     } else {
+        if (cm == PIM_CORR_COMPACT) return launch_gather_cm<T, PP, PIM_CORR_COMPACT>(v, nb, s, ga, U, uf, qs, dst);
         if (cm == PIM_CORR_DOUBLE_FLOAT)
             return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
         if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);

@@ -30,6 +30,11 @@ constexpr int PIM_MAX_IMAGES = 125;
 constexpr int PIM_DENSE_MIN = 4;
 constexpr int PIM_MAX_P = 6;
 
+// correction modes whose sums run in double-float on the FP32 pipes
+__host__ __device__ constexpr bool corr_df(int mode) {
+    return mode == PIM_CORR_DOUBLE_FLOAT || mode == PIM_CORR_COMPACT;
+}
+
 // device-side status flags (bit set)
 enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2, PIM_DEV_COINCIDENT = 4 };
 
@@ -177,7 +182,9 @@ struct PointsData {
     uint32_t* col = nullptr;      // nnz
     double2* val = nullptr;       // nnz: G0 - G_grid (FP64)
     float4* valdf = nullptr;      // nnz: double-float split (re_hi, re_lo, im_hi, im_lo)
-    float2* valf = nullptr;       // nnz: complex64
+    float2* valf = nullptr;       // nnz: complex64 (FP32 mode), or the FP32 heads (compact mode)
+    uint32_t* valt = nullptr;     // nnz: bf16 tails of re (low half) and im (high half), compact mode
+    int* nbig = nullptr;          // N: compact mode, entries at the head of each row summed in double-float
     double2* dval = nullptr;      // 3 nnz: d/dr_m of the values (with_gradient)
     int64_t nnz = 0;
 };
@@ -236,6 +243,7 @@ struct pim_plan_s {
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
     int force_variant = -1;       // >= 0: launch shape fixed by the options
+    int corr_split = 10;          // compact mode: threshold 2^-corr_split of the row's largest |d|
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // around the gather launch while autotuning
     void* qsall = nullptr;        // sorted sources of every right-hand side (multi-RHS correction)
     size_t qsall_bytes = 0;

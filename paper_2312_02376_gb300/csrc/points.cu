@@ -5,6 +5,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "pim_internal.cuh"
 
 namespace {
@@ -447,7 +449,7 @@ __device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32
 // 16-byte slots when the apply accumulates in double-float
 __device__ __forceinline__ void store_grad(const FillArgs& a, long long q, const double2* gr, double2* dval) {
     for (int k = 0; k < 3; ++k) {
-        if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
+        if (corr_df(a.corr_mode)) {
             const float rh = (float)gr[k].x, ih = (float)gr[k].y;
             reinterpret_cast<float4*>(dval)[3 * q + k] =
                 make_float4(rh, (float)(gr[k].x - (double)rh), ih, (float)(gr[k].y - (double)ih));
@@ -457,20 +459,28 @@ __device__ __forceinline__ void store_grad(const FillArgs& a, long long q, const
     }
 }
 
+// bf16 bits of x, rounded to nearest even
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
 __device__ __forceinline__ void store_value(const FillArgs& a, long long q, double2 d, double2* val, float4* valdf,
-                                            float2* valf) {
+                                            float2* valf, uint32_t* valt) {
     val[q] = d;
+    const float rh = (float)d.x, ih = (float)d.y;
     if (a.corr_mode == PIM_CORR_DOUBLE_FLOAT) {
-        const float rh = (float)d.x, ih = (float)d.y;
         valdf[q] = make_float4(rh, (float)(d.x - (double)rh), ih, (float)(d.y - (double)ih));
     } else if (a.corr_mode == PIM_CORR_FP32) {
-        valf[q] = make_float2((float)d.x, (float)d.y);
+        valf[q] = make_float2(rh, ih);
+    } else if (a.corr_mode == PIM_CORR_COMPACT) {
+        // head rounded to FP32, tail (the FP64 remainder) rounded to bf16:
+        // |d - head - tail| <= 2^-9 |tail| <= 2^-33 |d| per component
+        valf[q] = make_float2(rh, ih);
+        valt[q] = bf16_bits((float)(d.x - (double)rh)) | (bf16_bits((float)(d.y - (double)ih)) << 16);
     }
 }
 
 __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
                                  const int* box_ptr, const int64_t* row_ptr, uint32_t* col, double2* val,
-                                 float4* valdf, float2* valf, double2* dval, int* status) {
+                                 float4* valdf, float2* valf, uint32_t* valt, double2* dval, int* status) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -485,11 +495,11 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
                 if (dval) {
                     double2 gr[3];
                     const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
-                    store_value(a, q, d, val, valdf, valf);
+                    store_value(a, q, d, val, valdf, valf, valt);
                     store_grad(a, q, gr, dval);
                 } else {
                     const double2 d = corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr);
-                    store_value(a, q, d, val, valdf, valf);
+                    store_value(a, q, d, val, valdf, valf, valt);
                 }
             }
             off += hi - lo;
@@ -500,7 +510,7 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
 // Recomputes the values of an existing correction list (frozen topology).
 __global__ void pair_refill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
                                    const int64_t* row_ptr, const uint32_t* col, double2* val, float4* valdf,
-                                   float2* valf, double2* dval, int* status) {
+                                   float2* valf, uint32_t* valt, double2* dval, int* status) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -512,12 +522,71 @@ __global__ void pair_refill_kernel(const double* pos, const uint32_t* ns, const 
             if (dval) {
                 double2 gr[3];
                 const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
-                store_value(a, q, d, val, valdf, valf);
+                store_value(a, q, d, val, valdf, valf, valt);
                 store_grad(a, q, gr, dval);
             } else {
-                store_value(a, q, corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr), val, valdf, valf);
+                store_value(a, q, corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr), val, valdf, valf,
+                            valt);
             }
         }
+    }
+}
+
+// Compact correction mode: reorders every row into [entries with |d| >
+// 2^-split max_row |d|] [the others], each part in its former order, into
+// fresh arrays, and sets nbig[m] to the size of the first part.  One warp
+// per row: the row maximum, the count, then a ballot-ranked scatter.
+__global__ void split_rows_kernel(long long N, const int64_t* row_ptr, int split, const uint32_t* col,
+                                  const double2* val, const float2* valf, const uint32_t* valt, const double2* dval,
+                                  uint32_t* col2, double2* val2, float2* valf2, uint32_t* valt2, double2* dval2,
+                                  int* nbig) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long m = warp; m < N; m += nwarps) {
+        const long long r0 = row_ptr[m], r1 = row_ptr[m + 1];
+        double mx = 0.0;  // largest |d|^2 of the row
+        for (long long q = r0 + lane; q < r1; q += 32) {
+            const double2 d = val[q];
+            mx = fmax(mx, d.x * d.x + d.y * d.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const double thr = split > 0 ? ldexp(mx, -2 * split) : -1.0;
+        int nb = 0;
+        for (long long q0 = r0; q0 < r1; q0 += 32) {
+            const long long q = q0 + lane;
+            bool big = false;
+            if (q < r1) {
+                const double2 d = val[q];
+                big = d.x * d.x + d.y * d.y > thr;
+            }
+            nb += __popc(__ballot_sync(0xffffffffu, big));
+        }
+        long long ob = r0, os = r0 + nb;
+        for (long long q0 = r0; q0 < r1; q0 += 32) {
+            const long long q = q0 + lane;
+            const bool in = q < r1;
+            bool big = false;
+            double2 d = make_double2(0.0, 0.0);
+            if (in) {
+                d = val[q];
+                big = d.x * d.x + d.y * d.y > thr;
+            }
+            const unsigned mb = __ballot_sync(0xffffffffu, big), ms = __ballot_sync(0xffffffffu, in && !big);
+            if (in) {
+                const long long t = big ? ob + __popc(mb & below) : os + __popc(ms & below);
+                col2[t] = col[q];
+                val2[t] = d;
+                valf2[t] = valf[q];
+                valt2[t] = valt[q];
+                if (dval)
+                    for (int k = 0; k < 3; ++k) dval2[3 * t + k] = dval[3 * q + k];
+            }
+            ob += __popc(mb);
+            os += __popc(ms);
+        }
+        if (lane == 0) nbig[m] = nb;
     }
 }
 
@@ -598,6 +667,49 @@ FillArgs fill_args(pim_plan P, const PairArgs& pr) {
 }  // namespace
 
 // New positions for the current points with the discrete structure kept.
+// Splits every row of a compact-mode list (split_rows_kernel) out of place.
+static pim_status split_rows(pim_plan P, cudaStream_t s) {
+    PointsData& d = P->pts;
+    pim_status st;
+    const int64_t N = d.N, nnz = d.nnz;
+    if (!d.nbig && (st = pim_alloc(P, (void**)&d.nbig, (size_t)std::max<int64_t>(1, N) * sizeof(int))) != PIM_OK)
+        return st;
+    if (N == 0) return PIM_OK;
+    if (nnz == 0) {
+        PIM_CK(cudaMemsetAsync(d.nbig, 0, (size_t)N * sizeof(int), s));
+        return PIM_OK;
+    }
+    uint32_t *col2 = nullptr, *valt2 = nullptr;
+    double2 *val2 = nullptr, *dval2 = nullptr;
+    float2* valf2 = nullptr;
+    if ((st = pim_alloc(P, (void**)&col2, nnz * sizeof(uint32_t))) != PIM_OK ||
+        (st = pim_alloc(P, (void**)&val2, nnz * sizeof(double2))) != PIM_OK ||
+        (st = pim_alloc(P, (void**)&valf2, nnz * sizeof(float2))) != PIM_OK ||
+        (st = pim_alloc(P, (void**)&valt2, nnz * sizeof(uint32_t))) != PIM_OK ||
+        (d.dval && (st = pim_alloc(P, (void**)&dval2, 3 * nnz * sizeof(double2))) != PIM_OK)) {
+        pim_free(P, col2, nnz * sizeof(uint32_t));
+        pim_free(P, val2, nnz * sizeof(double2));
+        pim_free(P, valf2, nnz * sizeof(float2));
+        pim_free(P, valt2, nnz * sizeof(uint32_t));
+        return st;
+    }
+    split_rows_kernel<<<152 * 16, 256, 0, s>>>(N, d.row_ptr, P->corr_split, d.col, d.val, d.valf, d.valt, d.dval, col2,
+                                               val2, valf2, valt2, dval2, d.nbig);
+    PIM_CK(cudaGetLastError());
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, d.col, nnz * sizeof(uint32_t));
+    pim_free(P, d.val, nnz * sizeof(double2));
+    pim_free(P, d.valf, nnz * sizeof(float2));
+    pim_free(P, d.valt, nnz * sizeof(uint32_t));
+    pim_free(P, d.dval, 3 * nnz * sizeof(double2));
+    d.col = col2;
+    d.val = val2;
+    d.valf = valf2;
+    d.valt = valt2;
+    d.dval = dval2;
+    return PIM_OK;
+}
+
 pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
     PointsData& d = P->pts;
     const long long N = d.N;
@@ -643,7 +755,7 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
     fa.gtab = gtab;
     if (N > 0 && d.nnz > 0)
         pair_refill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.row_ptr, d.col, d.val, d.valdf,
-                                                     d.valf, d.dval, P->dstatus);
+                                                     d.valf, d.valt, d.dval, P->dstatus);
     PIM_CK(cudaGetLastError());
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     PIM_CK(cudaStreamSynchronize(s));
@@ -657,6 +769,7 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
         pim_set_error("internal bounds check tripped while updating the correction values");
         return PIM_ERR_DEVICE;
     }
+    if (P->corr_mode == PIM_CORR_COMPACT) return split_rows(P, s);
     return PIM_OK;
 }
 
@@ -692,7 +805,9 @@ void points_free(pim_plan P) {
     pim_free(P, d.val, d.nnz * sizeof(double2));
     pim_free(P, d.valdf, d.nnz * sizeof(float4));
     pim_free(P, d.valf, d.nnz * sizeof(float2));
+    pim_free(P, d.valt, d.nnz * sizeof(uint32_t));
     pim_free(P, d.dval, 3 * d.nnz * sizeof(double2));
+    pim_free(P, d.nbig, (size_t)std::max<int64_t>(1, d.N) * sizeof(int));
     d = PointsData{};
 }
 
@@ -829,8 +944,10 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     if ((st = pim_alloc(P, (void**)&d.val, nnz * sizeof(double2))) != PIM_OK) return st;
     if (P->corr_mode == PIM_CORR_DOUBLE_FLOAT)
         if ((st = pim_alloc(P, (void**)&d.valdf, nnz * sizeof(float4))) != PIM_OK) return st;
-    if (P->corr_mode == PIM_CORR_FP32)
+    if (P->corr_mode == PIM_CORR_FP32 || P->corr_mode == PIM_CORR_COMPACT)
         if ((st = pim_alloc(P, (void**)&d.valf, nnz * sizeof(float2))) != PIM_OK) return st;
+    if (P->corr_mode == PIM_CORR_COMPACT)
+        if ((st = pim_alloc(P, (void**)&d.valt, nnz * sizeof(uint32_t))) != PIM_OK) return st;
     if (P->with_gradient)
         if ((st = pim_alloc(P, (void**)&d.dval, 3 * nnz * sizeof(double2))) != PIM_OK) return st;
     // table of g over the offsets a correction can reach
@@ -842,7 +959,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     fa.gtab = gtab;
     if (N > 0 && nnz > 0)
         pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.row_ptr, d.col, d.val,
-                                                   d.valdf, d.valf, d.dval, P->dstatus);
+                                                   d.valdf, d.valf, d.valt, d.dval, P->dstatus);
     PIM_CK(cudaGetLastError());
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     PIM_CK(cudaStreamSynchronize(s));
@@ -860,5 +977,6 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         pim_set_error("internal bounds check tripped while building the correction list");
         return PIM_ERR_DEVICE;
     }
+    if (P->corr_mode == PIM_CORR_COMPACT) return split_rows(P, s);
     return PIM_OK;
 }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpim.so")
 PIM_OK, PIM_ERR_ARG, PIM_ERR_UNSUPPORTED, PIM_ERR_ANOMALY, PIM_ERR_NOT_NEUTRAL, PIM_ERR_OUT_OF_CELL, \
     PIM_ERR_STATE, PIM_ERR_OOM, PIM_ERR_CUDA, PIM_ERR_TIMEOUT, PIM_ERR_DEVICE = range(11)
 PIM_FP64, PIM_FP32_MIXED = 0, 1
-PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32 = 0, 1, 2
+PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32, PIM_CORR_COMPACT = 0, 1, 2, 3
 
 # symbols declared in include/pim.h
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
@@ -31,7 +31,7 @@ class pim_options(ctypes.Structure):
     _fields_ = [("far_n", ctypes.c_int * 3), ("far_p", ctypes.c_int), ("corr_radius", ctypes.c_int),
                 ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
-                ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int), ("corr_split", ctypes.c_int),
                 ("gather_variant", ctypes.c_int)]
 
 
@@ -248,7 +248,7 @@ class Plan:
 
     def __init__(self, D, pdims, k, k0, n, p=4, layers=1, precision="fp32", b=None, nf=None, pf=None,
                  corr_mode=None, cube=False, tile=None, neutral_tol=None, mem_cap=0, autotune=None,
-                 with_gradient=False, gather_variant=None, stream=None):
+                 with_gradient=False, gather_variant=None, corr_split=None, stream=None):
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
         self.pdims = tuple(pdims)
@@ -276,6 +276,8 @@ class Plan:
         opt.with_gradient = 1 if with_gradient else 0
         if gather_variant is not None:
             opt.gather_variant = int(gather_variant)
+        if corr_split is not None:
+            opt.corr_split = int(corr_split)
         opt.mem_cap = int(mem_cap)
         mask = sum(1 << d for d in self.pdims)
         h = self.D / (self.n - 1)
@@ -359,6 +361,8 @@ class Plan:
             out = np.empty(info.nnz, np.uint32)
         elif what == 6:
             out = np.empty(info.nnz, np.complex128)
+        elif what == 7:
+            out = np.empty(info.N, np.int32)
         else:
             raise ValueError(what)
         pim_debug_copy(self._h, what, out)

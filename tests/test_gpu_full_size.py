@@ -47,7 +47,7 @@ def read_rows(name):
 def coulomb_1m():
     W = inputs.coulomb3d_big()
     pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
-                  pf=W.pf, corr_mode=pim.PIM_CORR_DOUBLE_FLOAT, with_gradient=True)
+                  pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT, with_gradient=True)
     x0 = torch.tensor(W.points, dtype=torch.float64, device="cuda")
     pl.set_points(x0)
     yield W, pl, x0
@@ -105,12 +105,12 @@ def test_coulomb3d_1m_gradient_directional_derivative(coulomb_1m):
 
 def test_helmholtz1d_batch_largest_set_rows():
     # the largest set of the batched 1D-periodic workload (64 right-hand
-    # sides, FP32 bulk, double-float correction): sampled rows of two
+    # sides, FP32 bulk, compact correction values): sampled rows of two
     # right-hand sides against the oracle
     sets = inputs.helmholtz1d_batch()
     W = max(sets, key=lambda s: s.N)
     pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, pf=W.pf,
-                  corr_mode=pim.PIM_CORR_DOUBLE_FLOAT)
+                  corr_mode=pim.PIM_CORR_COMPACT)
     pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     u = pl.apply(torch.tensor(W.q, device="cuda")).cpu().numpy()
     info = pl.info()

@@ -68,13 +68,13 @@ def test_position_grad_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("mode", ["double_float", "fp64"])
+@pytest.mark.parametrize("mode", ["double_float", "compact", "fp64"])
 def test_position_grad_fp32_matches_oracle(name, mode):
-    # FP32 bulk (grid sums in FP32); the correction list in double-float or
-    # FP64: rel-L2 within the FP32 path's bound
+    # FP32 bulk (grid sums in FP32); the correction list in double-float,
+    # compact or FP64: rel-L2 within the FP32 path's bound
     c = CASES[name]
     P, _, pts, q, g, real = setup(name)
-    cm = pim.PIM_CORR_DOUBLE_FLOAT if mode == "double_float" else pim.PIM_CORR_FP64
+    cm = {"double_float": pim.PIM_CORR_DOUBLE_FLOAT, "compact": pim.PIM_CORR_COMPACT, "fp64": pim.PIM_CORR_FP64}[mode]
     pl = pim.Plan(c["D"], c["pdims"], c["k"], c["k0"], c["n"], p=c["p"], layers=1, precision="fp32", b=c["b"],
                   nf=c["nf"], pf=c["pf"], corr_mode=cm, with_gradient=True)
     pl.set_points(torch.tensor(pts, device="cuda"))

@@ -98,7 +98,8 @@ def test_fp64_forward_and_adjoint(name, oracle_cache):
     pl.close()
 
 
-@pytest.mark.parametrize("mode", [pim.PIM_CORR_FP64, pim.PIM_CORR_DOUBLE_FLOAT, pim.PIM_CORR_FP32])
+@pytest.mark.parametrize("mode", [pim.PIM_CORR_FP64, pim.PIM_CORR_DOUBLE_FLOAT, pim.PIM_CORR_FP32,
+                                  pim.PIM_CORR_COMPACT])
 @pytest.mark.parametrize("name", ["helmholtz2d_bloch", "npsp3d", "helmholtz1d_z"])
 def test_fp32_mixed_forward_and_adjoint(name, mode, oracle_cache):
     W, o, ue, we = oracle_results(name, oracle_cache)
@@ -113,7 +114,7 @@ def test_fp32_mixed_forward_and_adjoint(name, mode, oracle_cache):
 
 
 @pytest.mark.parametrize("precision,mode", [("fp32", pim.PIM_CORR_DOUBLE_FLOAT), ("fp32", pim.PIM_CORR_FP32),
-                                            ("fp64", pim.PIM_CORR_FP64)])
+                                            ("fp32", pim.PIM_CORR_COMPACT), ("fp64", pim.PIM_CORR_FP64)])
 @pytest.mark.parametrize("name", ["helmholtz2d_dense", "npsp3d"])
 def test_every_gather_launch_shape(name, precision, mode, oracle_cache):
     """Each launch shape of the gather kernel the autotuner may pick, forced
@@ -181,6 +182,46 @@ def test_stage_parity_far_table_spread_and_correction(oracle_cache):
             worst = max(worst, abs(ph[img] * val[t] - cc))
     assert worst < 1e-12 * scale
     pl.close()
+
+
+@pytest.mark.parametrize("split", [0, 10, 20])
+def test_compact_rows_split_by_magnitude(split, oracle_cache):
+    """Compact mode: each row starts with its entries above 2^-split of the
+    row's largest |d| (summed in double-float), the rest follow; the pairs and
+    their FP64 values are those of the FP64 plan, and the apply matches the
+    oracle."""
+    W, o, ue, we = oracle_results("helmholtz2d_dense", oracle_cache)
+    ref = gpu_plan(W, "fp64")
+    rp, col, val = ref.debug(4), ref.debug(5), ref.debug(6)
+    pl = gpu_plan(W, "fp32", corr_mode=pim.PIM_CORR_COMPACT, corr_split=split)
+    assert np.array_equal(pl.debug(4), rp)
+    col2, val2, nb = pl.debug(5), pl.debug(6), pl.debug(7)
+    thr = 2.0 ** -split
+    nsmall = 0
+    for r in range(len(rp) - 1):
+        a, b = rp[r], rp[r + 1]
+        order = np.argsort(col[a:b], kind="stable")
+        order2 = np.argsort(col2[a:b], kind="stable")
+        assert np.array_equal(col[a:b][order], col2[a:b][order2])
+        assert np.array_equal(val[a:b][order], val2[a:b][order2])
+        mag = np.abs(val2[a:b])
+        if b > a:
+            big = mag > thr * mag.max() if split > 0 else np.ones(b - a, bool)
+            assert nb[r] == big.sum()
+            assert big[:nb[r]].all() and not big[nb[r]:].any()
+            nsmall += (b - a) - nb[r]
+    if split == 0:
+        assert nsmall == 0
+    else:
+        assert nsmall > 0
+    real = W.k == 0 and not any(W.k0)
+    q = to_dev(W.q, "fp32", real)
+    assert rel(pl.apply(q).cpu().numpy(), ue) < FP32_TOL
+    assert rel(pl.apply_adjoint(q).cpu().numpy(), we) < FP32_TOL
+    with pytest.raises(Exception):
+        gpu_plan(W, "fp32", corr_mode=pim.PIM_CORR_COMPACT, corr_split=31)
+    pl.close()
+    ref.close()
 
 
 def test_multiple_rhs_and_host_pointers(oracle_cache):

@@ -36,6 +36,6 @@ def test_library_builds_loads_and_exports_all_symbols():
 
 def test_struct_layouts_match_header():
     from paper_2312_02376_gb300 import pim
-    # pim_options: 3+1+1+1+1+3 ints (40 B), 2 doubles, size_t, 3 ints (76 B) padded to 80 B
+    # pim_options: 3+1+1+1+1+3 ints (40 B), 2 doubles, size_t, 4 ints -> 80 B
     assert ctypes.sizeof(pim.pim_options) == 80
     assert pim.pim_options.neutral_tol.offset == 40
