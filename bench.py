@@ -156,14 +156,14 @@ def gather_bytes(info, N, G, nf3, fp64=False, nbig=0):
     """Algorithmic bytes of one gather + correction launch: the correction
     value (16 B FP64 or double-float, 8 B FP32 or compact, plus a 4 B tail
     for the nbig compact entries summed in double-float) and a 4 B column per
-    entry; per point the stencil starts, local coordinates, permutation,
-    sorted source, output, far stencil and far coordinates (and the compact
-    row split); the near and far grids once."""
+    entry; per point the stencil start, local coordinates, permutation,
+    sorted source and output (and the compact row split); the near grid
+    once.  (The far interpolation is a separate kernel on the far stream.)"""
     compact = int(info.corr_mode) == 3
     per_nnz = VALUE_BYTES[int(info.corr_mode)] + 4
     c, r = (16, 8) if fp64 else (8, 4)        # complex and real element sizes
-    per_point = 4 + 3 * r + 4 + c + c + 4 + 3 * r + (4 if compact else 0)
-    return info.nnz * per_nnz + 4 * nbig + (N + 1) * 8 + N * per_point + G * c + nf3 * c
+    per_point = 4 + 3 * r + 4 + c + c + (4 if compact else 0)
+    return info.nnz * per_nnz + 4 * nbig + (N + 1) * 8 + N * per_point + G * c
 
 
 def gather_source_hash():
@@ -295,7 +295,7 @@ def run_gpu(args):
                        "rel_l2_vs_ewald_ground_truth": err_truth,
                        "ground_truth_rows": 16,
                        "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"},
-            "roofline": {"bound": "hbm", "kernel": "gather_kernel (near gather + CSR correction + far gather)",
+            "roofline": {"bound": "hbm", "kernel": "gather_kernel (near gather + CSR correction)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": None if fp64 else profile_traffic(), "algorithmic_bytes_per_launch": gb,

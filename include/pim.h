@@ -133,8 +133,9 @@ typedef enum {
     PIM_STAGE_PERMUTE = 0,   /* regularise (Eq. neutral) and reorder the sources        */
     PIM_STAGE_SPREAD = 1,    /* near step 1: anterpolation onto the grid                */
     PIM_STAGE_FFT = 2,       /* near step 2: the five pruned FFT passes                 */
-    PIM_STAGE_GATHER = 3,    /* near steps 3-4 and far step 3: gather, correction, sum  */
-    PIM_STAGE_FAR = 4,       /* far steps 1-2: projection and grid sum (second stream)  */
+    PIM_STAGE_GATHER = 3,    /* near steps 3-4: gather and correction                   */
+    PIM_STAGE_FAR = 4,       /* far steps 1-3: projection, grid sum, interpolation
+                                (second stream; added to u after the gather)            */
     PIM_STAGE_APPLY = 5,     /* the whole apply, first to last launch                   */
     PIM_NUM_STAGES = 6
 } pim_stage;

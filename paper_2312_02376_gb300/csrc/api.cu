@@ -33,6 +33,15 @@ size_t data_elem(pim_plan P) {
 
 void pim_set_error(const std::string& msg) { g_last_error = msg; }
 
+int far_stream_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
+}
+
 pim_status pim_alloc(pim_plan P, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return PIM_OK;
@@ -124,6 +133,7 @@ void pim_destroy(pim_plan P) {
         const size_t gq = grid_elem(P) * (size_t)P->pts.N;
         pim_free(P, P->qs, gq);
         pim_free(P, P->us, gq);
+        pim_free(P, P->ufp, gq);
         pim_free(P, P->hq, P->stage_bytes);
         pim_free(P, P->hu, P->stage_bytes);
     }
@@ -284,7 +294,10 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     for (int d = 0; d < 3; ++d) P->tile[d] = o.tile[d] > 0 ? o.tile[d] : (d == 0 ? 16 : 8);
     cudaStream_t s = (cudaStream_t)stream;
     pim_status st;
-    if (cudaStreamCreateWithFlags(&P->s_far, cudaStreamNonBlocking) != cudaSuccess ||
+    // the far zone's stream takes the highest priority: its short chain ends
+    // with the far interpolation, which then runs ahead of the pending blocks
+    // of the near gather instead of after them
+    if (cudaStreamCreateWithPriority(&P->s_far, cudaStreamNonBlocking, far_stream_priority()) != cudaSuccess ||
         cudaStreamCreateWithFlags(&P->s_main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -361,7 +374,8 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
         P->qsall_bytes = 0;
         pim_free(P, P->qs, (size_t)P->pts.N * ge);
         pim_free(P, P->us, (size_t)P->pts.N * ge);
-        P->qs = P->us = nullptr;
+        pim_free(P, P->ufp, (size_t)P->pts.N * ge);
+        P->qs = P->us = P->ufp = nullptr;
         points_free(P);
     }
     const double* dx = xyz;
@@ -380,6 +394,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     }
     if ((st = pim_alloc(P, &P->qs, (size_t)N * ge)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &P->us, (size_t)N * ge)) != PIM_OK) return st;
+    if (P->has_far && (st = pim_alloc(P, &P->ufp, (size_t)N * ge)) != PIM_OK) return st;
     P->gather_variant = 0;
     if (P->force_variant >= 0) {
         if (P->force_variant >= gather_variant_count(P)) return PIM_ERR_ARG;

@@ -905,11 +905,12 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         PIM_CK(cudaEventRecord(P->lane_fork, s));
         for (int k = 1; k < K; ++k) PIM_CK(cudaStreamWaitEvent(P->lane[k].sm, P->lane_fork, 0));
     }
-    const pim_plan_s::Lane own{P->qs, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC,
+    const pim_plan_s::Lane own{P->qs, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC, P->ufp,
                                s, P->s_far, P->ev_fork, P->ev_join, nullptr};
     auto use_lane = [&](const pim_plan_s::Lane& l) {
         P->qs = l.qs; P->gA = l.gA; P->gB = l.gB; P->gC = l.gC; P->pts.mom = l.mom; P->fpart = l.fpart;
-        P->fA = l.fA; P->fB = l.fB; P->fC = l.fC; P->s_far = l.sf; P->ev_fork = l.fork; P->ev_join = l.join;
+        P->fA = l.fA; P->fB = l.fB; P->fC = l.fC; P->ufp = l.ufp; P->s_far = l.sf; P->ev_fork = l.fork;
+        P->ev_join = l.join;
     };
     // the plan's own scratch is back in place on every way out
     struct Restore {
@@ -968,7 +969,21 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
                 far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)P->fB, G);
                 PIM_CK(cudaGetLastError());
             }
-            P->launches += 2 + 5 + (sizeof(T) == 4 ? 1 : 0);
+            // far gather of every point (Eq. interpolation), while the near
+            // path and its gather run on the main stream
+            if (N > 0) {
+                GatherArgs fg{};
+                for (int i = 0; i < 3; ++i) fg.nf[i] = P->nf[i];
+                fg.pf = P->pf;
+                fg.N = N;
+                fg.fst = adj ? d.fs : d.fo;
+                fg.ft = d.ft;
+                fg.ftd = d.ftd;
+                fg.toff = adj ? 0 : 3;
+                const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
+                if ((st = launch_far_interp<T>(P->pf, N, P->s_far, fg, ufar, (cplx<T>*)P->ufp)) != PIM_OK) return st;
+            }
+            P->launches += 2 + 5 + (sizeof(T) == 4 ? 1 : 0) + (N > 0 ? 1 : 0);
             prof_mark(P, PIM_STAGE_FAR, 1, P->s_far);
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
@@ -981,8 +996,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             return st;
         prof_mark(P, PIM_STAGE_FFT, 1, sr);
         P->launches += (d.nd > 0 ? 2 : 1) + 5;
-        // 5. gather + correction + far gather
-        if (P->has_far) PIM_CK(cudaStreamWaitEvent(sr, P->ev_join, 0));
+        // 5. gather + correction, then the far part once both streams joined
         GatherArgs ga{};
         for (int i = 0; i < 3; ++i) { ga.n[i] = P->n[i]; ga.nf[i] = P->nf[i]; }
         ga.pf = P->pf;
@@ -1015,20 +1029,28 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ga.nbig = d.nbig;
         ga.phase = P->dphase;
         ga.phasedf = P->dphasedf;
-        const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
         prof_mark(P, PIM_STAGE_GATHER, 0, sr);
         if (N > 0) {
             const unsigned nb = (unsigned)((threads + 255) / 256);
             if (P->tune_ev[0]) PIM_CK(cudaEventRecord(P->tune_ev[0], sr));
-            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, sr, ga, gA, ufar, qs, dst)) != PIM_OK)
+            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, sr, ga, gA, qs, dst)) != PIM_OK)
                 return st;
             if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], sr));
         }
         PIM_CK(cudaGetLastError());
         prof_mark(P, PIM_STAGE_GATHER, 1, sr);
         P->launches += N > 0 ? 1 : 0;
+        if (P->has_far) {
+            PIM_CK(cudaStreamWaitEvent(sr, P->ev_join, 0));
+            if (N > 0) {
+                far_add_kernel<T><<<(unsigned)std::min<long long>((N + 255) / 256, 152 * 8), 256, 0, sr>>>(
+                    ga, (const cplx<T>*)P->ufp, dst);
+                PIM_CK(cudaGetLastError());
+                P->launches += 1;
+            }
+        }
         if (post_mean) {
             if ((st = mean_of<T>(P, P->us, true, N, 1, 0, false, sr)) != PIM_OK) return st;
             unpermute_kernel<T><<<1024, 256, 0, sr>>>((const cplx<T>*)P->us, d.perm, N, nrhs, r, P->dsum,
@@ -1269,15 +1291,16 @@ static void lane_sizes(pim_plan P, size_t* sz) {
     sz[6] = Gf * sizeof(double2);
     sz[7] = fB * sizeof(double2);
     sz[8] = fC * sizeof(double2);
+    sz[9] = P->has_far ? N * ge : 0;
 }
 
 void lanes_free(pim_plan P) {
-    size_t sz[9];
+    size_t sz[10];
     lane_sizes(P, sz);
     for (int k = 1; k < P->nlanes; ++k) {
         pim_plan_s::Lane& l = P->lane[k];
-        void* b[9] = {l.qs, l.gA, l.gB, l.gC, l.mom, l.fpart, l.fA, l.fB, l.fC};
-        for (int i = 0; i < 9; ++i) pim_free(P, b[i], sz[i]);
+        void* b[10] = {l.qs, l.gA, l.gB, l.gC, l.mom, l.fpart, l.fA, l.fB, l.fC, l.ufp};
+        for (int i = 0; i < 10; ++i) pim_free(P, b[i], sz[i]);
         if (l.sm) cudaStreamDestroy(l.sm);
         if (l.sf) cudaStreamDestroy(l.sf);
         if (l.fork) cudaEventDestroy(l.fork);
@@ -1296,16 +1319,17 @@ pim_status lanes_prepare(pim_plan P, int nl) {
         pim_set_error("event creation failed");
         return PIM_ERR_CUDA;
     }
-    size_t sz[9];
+    size_t sz[10];
     lane_sizes(P, sz);
     for (int k = P->nlanes; k < nl; ++k) {
         pim_plan_s::Lane& l = P->lane[k];
-        void** b[9] = {&l.qs, &l.gA, &l.gB, &l.gC, &l.mom, &l.fpart, (void**)&l.fA, (void**)&l.fB, (void**)&l.fC};
+        void** b[10] = {&l.qs, &l.gA, &l.gB, &l.gC, &l.mom, &l.fpart, (void**)&l.fA, (void**)&l.fB, (void**)&l.fC,
+                        &l.ufp};
         pim_status st;
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < 10; ++i)
             if (sz[i] && (st = pim_alloc(P, b[i], sz[i])) != PIM_OK) return st;
         if (cudaStreamCreateWithFlags(&l.sm, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&l.sf, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&l.sf, cudaStreamNonBlocking, far_stream_priority()) != cudaSuccess ||
             cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&l.join, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess) {

@@ -1,6 +1,7 @@
-// The fused gather of the apply (Sec. 3.3 steps 3-4, Eq. interpolation):
-// near-grid interpolation, CSR near-pair correction and far-grid
-// interpolation, one warp per point, plus its launch-shape variants.
+// The gathers of the apply (Sec. 3.3 steps 3-4, Eq. interpolation): the
+// fused near-grid interpolation and CSR near-pair correction, one warp per
+// point, with its launch-shape variants; the far-grid interpolation and the
+// final far-zone sum.
 #pragma once
 #include "lagrange.cuh"
 #include "pim_internal.cuh"
@@ -126,14 +127,12 @@ __device__ __forceinline__ void corr_row(int lane, int len, const uint32_t* __re
     }
 }
 
-// Near gather (Sec. 3.3 step 3) and far gather (Eq. interpolation) of point m,
-// this lane's share: lane (jy, jz) takes one x-row of each stencil.
+// Near gather (Sec. 3.3 step 3) of point m, this lane's share: lane (jy, jz)
+// takes one x-row of the stencil.
 template <typename T, int P>
-__device__ __forceinline__ cplx<T> grid_part(const GatherArgs& a, long long m, int lane, const cplx<T>* __restrict__ U,
-                                             const cplx<T>* __restrict__ uf) {
+__device__ __forceinline__ cplx<T> near_part(const GatherArgs& a, long long m, int lane, const cplx<T>* __restrict__ U) {
     constexpr int NP = P + 1;
     cplx<T> acc = mk<T>(T(0), T(0));
-    // near gather
     if (lane < NP * NP) {
         const int jy = lane % NP, jz = lane / NP;
         int s[3];
@@ -155,49 +154,97 @@ __device__ __forceinline__ cplx<T> grid_part(const GatherArgs& a, long long m, i
         acc.x = wyz * r.x;
         acc.y = wyz * r.y;
     }
-    // far gather
-    if (a.has_far) {
-        const int np = a.pf + 1;
-        for (int l = lane; l < np * np; l += 32) {
-            const int jy = l % np, jz = l / np;
-            int f[3];
-            unpack3(a.fst[m], f[0], f[1], f[2]);
-            T t[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                t[d] = sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d];
-            const T wyz = lag1_rt<T>(a.pf, t[1], jy) * lag1_rt<T>(a.pf, t[2], jz);
-            T wx[PIM_MAX_P + 1];
-            lagrange_w_rt<T>(a.pf, t[0], wx);
-            const cplx<T>* row = uf + ((f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
-            cplx<T> r = mk<T>(T(0), T(0));
-#pragma unroll
-            for (int jx = 0; jx <= PIM_MAX_P; ++jx) {
-                if (jx < np) {
-                    const cplx<T> v = row[jx];
-                    r.x += wx[jx] * v.x;
-                    r.y += wx[jx] * v.y;
-                }
-            }
-            acc.x += wyz * r.x;
-            acc.y += wyz * r.y;
-        }
-    }
     return acc;
 }
 
-// One warp per sorted point: near gather (Sec. 3.3 step 3), near-pair
-// correction (step 4, Eq. er) and far gather (Eq. interpolation), summed and
-// written in the caller's order.  In both gathers lane (jy, jz) takes one
+// Far gather (Eq. interpolation) of every point into ufp (sorted order), one
+// thread per point: its (PF+1)^3 observer-stencil weights once, then the
+// stencil's x-rows of the far grid (small, cache-resident).  Runs on the far
+// stream while the near gather runs on the main one.
+template <typename T, int PF>
+__global__ void __launch_bounds__(256) far_interp_kernel(GatherArgs a, const cplx<T>* __restrict__ uf,
+                                                         cplx<T>* __restrict__ ufp) {
+    constexpr int NP = PF + 1;
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= a.N) return;
+    int f[3];
+    unpack3(a.fst[m], f[0], f[1], f[2]);
+    T w[3][NP];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        lagrange_w<T, PF>(sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d], w[d]);
+    cplx<T> acc = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int jz = 0; jz < NP; ++jz) {
+        cplx<T> az = mk<T>(T(0), T(0));
+#pragma unroll
+        for (int jy = 0; jy < NP; ++jy) {
+            const cplx<T>* row = uf + ((long long)(f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
+            cplx<T> r = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int jx = 0; jx < NP; ++jx) {
+                const cplx<T> v = __ldg(row + jx);
+                r.x += w[0][jx] * v.x;
+                r.y += w[0][jx] * v.y;
+            }
+            az.x += w[1][jy] * r.x;
+            az.y += w[1][jy] * r.y;
+        }
+        acc.x += w[2][jz] * az.x;
+        acc.y += w[2][jz] * az.y;
+    }
+    ufp[m] = acc;
+}
+
+template <typename T>
+pim_status launch_far_interp(int pf, long long N, cudaStream_t s, const GatherArgs& fg, const cplx<T>* uf,
+                             cplx<T>* ufp) {
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    switch (pf) {
+        case 2: far_interp_kernel<T, 2><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
+        case 3: far_interp_kernel<T, 3><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
+        case 4: far_interp_kernel<T, 4><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
+        case 5: far_interp_kernel<T, 5><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
+        case 6: far_interp_kernel<T, 6><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
+        default: pim_set_error("far degree must be 2..6"); return PIM_ERR_UNSUPPORTED;
+    }
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+// u += far part, in the gather's output order (the sum of Eq. 5's near and
+// far zones, after both streams have joined).
+template <typename T>
+__global__ void far_add_kernel(GatherArgs a, const cplx<T>* __restrict__ ufp, void* out) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.N;
+         m += (long long)gridDim.x * blockDim.x) {
+        const cplx<T> f = ufp[m];
+        if (a.sorted_out) {
+            cplx<T>* u = (cplx<T>*)out + m;
+            *u = mk<T>(u->x + f.x, u->y + f.y);
+        } else {
+            const long long o = (long long)a.perm[m] * a.nrhs + a.r;
+            if (a.real_out) {
+                ((T*)out)[o] += f.x;
+            } else {
+                cplx<T>* u = (cplx<T>*)out + o;
+                *u = mk<T>(u->x + f.x, u->y + f.y);
+            }
+        }
+    }
+}
+
+// One warp per sorted point: near gather (Sec. 3.3 step 3) and near-pair
+// correction (step 4, Eq. er), summed and written in the caller's order (the
+// far part is added by far_add_kernel).  In the gather lane (jy, jz) takes one
 // x-row of the stencil.
 template <typename T, int P, int CM, int UNR, int MINB>
 __global__ void __launch_bounds__(256, MINB) gather_kernel(GatherArgs a, const cplx<T>* __restrict__ U,
-                                                     const cplx<T>* __restrict__ uf, const cplx<T>* __restrict__ qs,
-                                                     void* out) {
+                                                     const cplx<T>* __restrict__ qs, void* out) {
     const int lane = threadIdx.x & 31;
     const long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (m >= a.N) return;
-    cplx<T> acc = grid_part<T, P>(a, m, lane, U, uf);
+    cplx<T> acc = near_part<T, P>(a, m, lane, U);
     // near-pair correction: exp(-j k0.(i o L)) d q_n (forward) or
     // exp(-j k0.(i o L)) conj(d) v_n (adjoint).  The adjoint is summed as the
     // conjugate of sum conj(phase) d conj(v_n), so that the values are used
@@ -329,13 +376,13 @@ constexpr int GATHER_VARIANTS = 5;
 
 template <typename T, int PP, int CM>
 pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
-                            const cplx<T>* uf, const cplx<T>* qs, void* dst) {
+                            const cplx<T>* qs, void* dst) {
     switch (v) {
-        case 0: gather_kernel<T, PP, CM, 2, 6><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 1: gather_kernel<T, PP, CM, 4, 4><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 2: gather_kernel<T, PP, CM, 3, 5><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        case 3: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
-        default: gather_kernel<T, PP, CM, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst); break;
+        case 0: gather_kernel<T, PP, CM, 2, 6><<<nb, 256, 0, s>>>(ga, U, qs, dst); break;
+        case 1: gather_kernel<T, PP, CM, 4, 4><<<nb, 256, 0, s>>>(ga, U, qs, dst); break;
+        case 2: gather_kernel<T, PP, CM, 3, 5><<<nb, 256, 0, s>>>(ga, U, qs, dst); break;
+        case 3: gather_kernel<T, PP, CM, 2, 8><<<nb, 256, 0, s>>>(ga, U, qs, dst); break;
+        default: gather_kernel<T, PP, CM, 1, 8><<<nb, 256, 0, s>>>(ga, U, qs, dst); break;
     }
     PIM_CK(cudaGetLastError());
     return PIM_OK;
@@ -343,21 +390,21 @@ pim_status launch_gather_cm(int v, unsigned nb, cudaStream_t s, const GatherArgs
 
 template <typename T, int PP>
 pim_status launch_gather(int cm, int v, unsigned nb, cudaStream_t s, const GatherArgs& ga, const cplx<T>* U,
-                         const cplx<T>* uf, const cplx<T>* qs, void* dst) {
+                         const cplx<T>* qs, void* dst) {
     if (cm < 0) {
         // near and far gathers only (the correction runs in the multi-RHS kernel)
-        gather_kernel<T, PP, -1, 1, 8><<<nb, 256, 0, s>>>(ga, U, uf, qs, dst);
+        gather_kernel<T, PP, -1, 1, 8><<<nb, 256, 0, s>>>(ga, U, qs, dst);
         PIM_CK(cudaGetLastError());
         return PIM_OK;
     }
     if constexpr (sizeof(T) == 8) {
-        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, qs, dst);
     } else {
-        if (cm == PIM_CORR_COMPACT) return launch_gather_cm<T, PP, PIM_CORR_COMPACT>(v, nb, s, ga, U, uf, qs, dst);
+        if (cm == PIM_CORR_COMPACT) return launch_gather_cm<T, PP, PIM_CORR_COMPACT>(v, nb, s, ga, U, qs, dst);
         if (cm == PIM_CORR_DOUBLE_FLOAT)
-            return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, uf, qs, dst);
-        if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, uf, qs, dst);
-        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, uf, qs, dst);
+            return launch_gather_cm<T, PP, PIM_CORR_DOUBLE_FLOAT>(v, nb, s, ga, U, qs, dst);
+        if (cm == PIM_CORR_FP32) return launch_gather_cm<T, PP, PIM_CORR_FP32>(v, nb, s, ga, U, qs, dst);
+        return launch_gather_cm<T, PP, PIM_CORR_FP64>(v, nb, s, ga, U, qs, dst);
     }
 }
 

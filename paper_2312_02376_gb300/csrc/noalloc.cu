@@ -86,8 +86,9 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         fB = (size_t)P->nf[2] * P->nf[1] * P->fg.L[0];
         fC = (size_t)P->nf[2] * P->fg.L[1] * P->fg.L[0];
     }
-    const size_t sizes[10] = {N * ge,  N * ge,  G * ge, GB * ge, GC * ge, mom, (size_t)P->far_chunks * Gf * ge,
-                              Gf * sizeof(double2), fB * sizeof(double2), fC * sizeof(double2)};
+    const size_t sizes[11] = {N * ge,  N * ge,  G * ge, GB * ge, GC * ge, mom, (size_t)P->far_chunks * Gf * ge,
+                              Gf * sizeof(double2), fB * sizeof(double2), fC * sizeof(double2),
+                              P->has_far ? N * ge : 0};
     size_t need = 0;
     for (size_t b : sizes) need += up256(b);
     if (need > NOALLOC_BYTES) {
@@ -96,13 +97,13 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         return PIM_ERR_ARG;
     }
     unsigned char* cur = static_cast<unsigned char*>(base);
-    void* ptrs[10];
-    for (int i = 0; i < 10; ++i) {
+    void* ptrs[11];
+    for (int i = 0; i < 11; ++i) {
         ptrs[i] = sizes[i] ? cur : nullptr;
         cur += up256(sizes[i]);
     }
     // run the apply with the plan's scratch fields pointing into the array
-    void* save[10] = {P->qs, P->us, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC};
+    void* save[11] = {P->qs, P->us, P->gA, P->gB, P->gC, P->pts.mom, P->fpart, P->fA, P->fB, P->fC, P->ufp};
     P->qs = ptrs[0];
     P->us = ptrs[1];
     P->gA = ptrs[2];
@@ -114,6 +115,7 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         P->fA = (double2*)ptrs[7];
         P->fB = (double2*)ptrs[8];
         P->fC = (double2*)ptrs[9];
+        P->ufp = ptrs[10];
     }
     const bool no_multi = P->no_multi;
     P->no_multi = true;  // the multi-RHS path would allocate its source buffer
@@ -129,5 +131,6 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
     P->fA = (double2*)save[7];
     P->fB = (double2*)save[8];
     P->fC = (double2*)save[9];
+    P->ufp = save[10];
     return st;
 }

@@ -227,6 +227,7 @@ struct pim_plan_s {
     PointsData pts;
     void* qs = nullptr;           // sorted sources, complex<T>, N
     void* us = nullptr;           // staging for host pointers
+    void* ufp = nullptr;          // far part of every point (sorted order), complex<T>, N (with a far zone)
     size_t stage_bytes = 0;
     void* hq = nullptr;           // device staging of caller buffers (host pointers)
     void* hu = nullptr;
@@ -275,6 +276,7 @@ struct pim_plan_s {
         double2* fA = nullptr;
         double2* fB = nullptr;
         double2* fC = nullptr;
+        void* ufp = nullptr;
         cudaStream_t sm = nullptr, sf = nullptr;
         cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
     } lane[RHS_LANES];
@@ -313,6 +315,7 @@ constexpr int PIM_RED_BLOCKS = 608;
 pim_status apply_run(pim_plan P, const void* q, void* u, int nrhs, bool adjoint, cudaStream_t s);
 pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
+int far_stream_priority();  // the device's highest stream priority
 int gather_variant_count(const pim_plan_s* P);
 pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
