@@ -1,7 +1,6 @@
-// The gathers of the apply (Sec. 3.3 steps 3-4, Eq. interpolation): the
-// fused near-grid interpolation and CSR near-pair correction, one warp per
-// point, with its launch-shape variants; the far-grid interpolation and the
-// final far-zone sum.
+// The gather of the apply (Sec. 3.3 steps 3-4): the fused near-grid
+// interpolation and CSR near-pair correction, one warp per point, with its
+// launch-shape variants.
 #pragma once
 #include "lagrange.cuh"
 #include "pim_internal.cuh"
@@ -155,83 +154,6 @@ __device__ __forceinline__ cplx<T> near_part(const GatherArgs& a, long long m, i
         acc.y = wyz * r.y;
     }
     return acc;
-}
-
-// Far gather (Eq. interpolation) of every point into ufp (sorted order), one
-// thread per point: its (PF+1)^3 observer-stencil weights once, then the
-// stencil's x-rows of the far grid (small, cache-resident).  Runs on the far
-// stream while the near gather runs on the main one.
-template <typename T, int PF>
-__global__ void __launch_bounds__(256) far_interp_kernel(GatherArgs a, const cplx<T>* __restrict__ uf,
-                                                         cplx<T>* __restrict__ ufp) {
-    constexpr int NP = PF + 1;
-    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (m >= a.N) return;
-    int f[3];
-    unpack3(a.fst[m], f[0], f[1], f[2]);
-    T w[3][NP];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-        lagrange_w<T, PF>(sizeof(T) == 8 ? (T)a.ftd[6 * m + a.toff + d] : (T)a.ft[6 * m + a.toff + d], w[d]);
-    cplx<T> acc = mk<T>(T(0), T(0));
-#pragma unroll
-    for (int jz = 0; jz < NP; ++jz) {
-        cplx<T> az = mk<T>(T(0), T(0));
-#pragma unroll
-        for (int jy = 0; jy < NP; ++jy) {
-            const cplx<T>* row = uf + ((long long)(f[2] + jz) * a.nf[1] + (f[1] + jy)) * a.nf[0] + f[0];
-            cplx<T> r = mk<T>(T(0), T(0));
-#pragma unroll
-            for (int jx = 0; jx < NP; ++jx) {
-                const cplx<T> v = __ldg(row + jx);
-                r.x += w[0][jx] * v.x;
-                r.y += w[0][jx] * v.y;
-            }
-            az.x += w[1][jy] * r.x;
-            az.y += w[1][jy] * r.y;
-        }
-        acc.x += w[2][jz] * az.x;
-        acc.y += w[2][jz] * az.y;
-    }
-    ufp[m] = acc;
-}
-
-template <typename T>
-pim_status launch_far_interp(int pf, long long N, cudaStream_t s, const GatherArgs& fg, const cplx<T>* uf,
-                             cplx<T>* ufp) {
-    const unsigned nb = (unsigned)((N + 255) / 256);
-    switch (pf) {
-        case 2: far_interp_kernel<T, 2><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
-        case 3: far_interp_kernel<T, 3><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
-        case 4: far_interp_kernel<T, 4><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
-        case 5: far_interp_kernel<T, 5><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
-        case 6: far_interp_kernel<T, 6><<<nb, 256, 0, s>>>(fg, uf, ufp); break;
-        default: pim_set_error("far degree must be 2..6"); return PIM_ERR_UNSUPPORTED;
-    }
-    PIM_CK(cudaGetLastError());
-    return PIM_OK;
-}
-
-// u += far part, in the gather's output order (the sum of Eq. 5's near and
-// far zones, after both streams have joined).
-template <typename T>
-__global__ void far_add_kernel(GatherArgs a, const cplx<T>* __restrict__ ufp, void* out) {
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < a.N;
-         m += (long long)gridDim.x * blockDim.x) {
-        const cplx<T> f = ufp[m];
-        if (a.sorted_out) {
-            cplx<T>* u = (cplx<T>*)out + m;
-            *u = mk<T>(u->x + f.x, u->y + f.y);
-        } else {
-            const long long o = (long long)a.perm[m] * a.nrhs + a.r;
-            if (a.real_out) {
-                ((T*)out)[o] += f.x;
-            } else {
-                cplx<T>* u = (cplx<T>*)out + o;
-                *u = mk<T>(u->x + f.x, u->y + f.y);
-            }
-        }
-    }
 }
 
 // One warp per sorted point: near gather (Sec. 3.3 step 3) and near-pair
