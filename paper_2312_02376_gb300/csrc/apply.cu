@@ -830,6 +830,18 @@ struct CorrMultiArgs {
     const float4* phasedf;
 };
 
+// a value of lane `src`, for the broadcast of list values inside a warp
+__device__ __forceinline__ float2 shfl_value(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float4 shfl_value(float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+__device__ __forceinline__ double2 shfl_value(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 template <typename T, int CM, int RPL>
 __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const cplx<T>* __restrict__ qsall, void* out) {
     const int lane = threadIdx.x & 31;
@@ -844,62 +856,84 @@ __global__ void __launch_bounds__(256) corr_multi_kernel(CorrMultiArgs a, const 
         rh[k] = rl[k] = ih[k] = il[k] = 0.f;
     }
     const double cs = a.adj ? -1.0 : 1.0;
+    const float fs = (float)cs;
     const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
-    // compact mode: entries [r0, rb) in double-float, the rest in FP32 (their
-    // sums go to the low words)
-    const long long rb = CM == PIM_CORR_COMPACT ? r0 + a.nbig[m] : r1;
-    for (long long q = r0; q < r1; ++q) {
-        const uint32_t c = __ldg(a.col + q);
-        const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
-        const cplx<T>* xr = qsall + (long long)n * R;
-        if (corr_df(CM) && q < rb) {
-            const float4 d = CM == PIM_CORR_COMPACT ? compact_value(__ldg(a.valf + q), __ldg(a.valt + q))
-                                                    : __ldg(a.valdf + q);
-            const float fs = (float)cs;
-            float4 v = make_float4(d.x, d.y, fs * d.z, fs * d.w);
-            if (ii != a.self_img) v = df_cmul(a.phasedf[ii], v);
+    // The row in groups of 32 entries: lane j loads entry j's column and
+    // value and applies its image phase, then the warp walks the group's
+    // entries with the column and value broadcast by shuffles; the source
+    // loads of consecutive entries are independent, so several are in flight.
+    auto group = [&](long long s0, long long s1, auto load_v, auto mac) {
+        for (long long q0 = s0; q0 < s1; q0 += 32) {
+            const long long q = q0 + lane < s1 ? q0 + lane : s1 - 1;
+            const int cnt = (int)(s1 - q0 < 32 ? s1 - q0 : 32);
+            const uint32_t c = __ldg(a.col + q);
+            const int nl = (int)(c & PIM_COL_MASK);
+            const auto v = load_v(q, (int)(c >> PIM_COL_BITS));
+#pragma unroll 4
+            for (int e = 0; e < cnt; ++e) {
+                const int n = __shfl_sync(0xffffffffu, nl, e);
+                const auto ve = shfl_value(v, e);
+                const cplx<T>* xr = qsall + (long long)n * R;
 #pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int r = lane + 32 * k;
-                if (r >= R) break;
-                const cplx<T> xv = xr[r];
-                df_cmac(rh[k], rl[k], ih[k], il[k], v, (float)xv.x, (float)xv.y);
-            }
-        } else if (CM == PIM_CORR_FP32 || CM == PIM_CORR_COMPACT) {
-            const float2 d = __ldg(a.valf + q);
-            float2 dd = make_float2(d.x, (float)cs * d.y);
-            if (ii != a.self_img) {
-                const double2 ph = a.phase[ii];
-                dd = make_float2((float)ph.x * dd.x - (float)ph.y * dd.y, (float)ph.x * dd.y + (float)ph.y * dd.x);
-            }
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int r = lane + 32 * k;
-                if (r >= R) break;
-                const cplx<T> xv = xr[r];
-                const float tr = dd.x * (float)xv.x - dd.y * (float)xv.y;
-                const float ti = dd.x * (float)xv.y + dd.y * (float)xv.x;
-                if (CM == PIM_CORR_COMPACT) {
-                    rl[k] += tr;
-                    il[k] += ti;
-                } else {
-                    rh[k] += tr;
-                    ih[k] += ti;
+                for (int k = 0; k < RPL; ++k) {
+                    const int r = lane + 32 * k;
+                    if (r < R) mac(k, ve, xr[r]);
                 }
             }
-        } else {
-            double2 d = __ldg(a.val + q);
-            d.y *= cs;
-            if (ii != a.self_img) d = cmul(a.phase[ii], d);
-#pragma unroll
-            for (int k = 0; k < RPL; ++k) {
-                const int r = lane + 32 * k;
-                if (r >= R) break;
-                const cplx<T> xv = xr[r];
-                acc[k].x += d.x * (double)xv.x - d.y * (double)xv.y;
-                acc[k].y += d.x * (double)xv.y + d.y * (double)xv.x;
-            }
         }
+    };
+    // double-float entries: all of them, or a compact row's leading ones
+    const long long rb = CM == PIM_CORR_COMPACT ? r0 + a.nbig[m] : r1;
+    if (corr_df(CM)) {
+        group(r0, rb,
+              [&](long long q, int ii) {
+                  const float4 d = CM == PIM_CORR_COMPACT ? compact_value(__ldg(a.valf + q), __ldg(a.valt + q))
+                                                          : __ldg(a.valdf + q);
+                  float4 v = make_float4(d.x, d.y, fs * d.z, fs * d.w);
+                  if (ii != a.self_img) v = df_cmul(a.phasedf[ii], v);
+                  return v;
+              },
+              [&](int k, const float4& v, const cplx<T>& xv) {
+                  df_cmac(rh[k], rl[k], ih[k], il[k], v, (float)xv.x, (float)xv.y);
+              });
+    }
+    // complex64 entries: all of them, or a compact row's trailing ones (their
+    // sums go to the low words)
+    if (CM == PIM_CORR_FP32 || CM == PIM_CORR_COMPACT) {
+        group(CM == PIM_CORR_COMPACT ? rb : r0, r1,
+              [&](long long q, int ii) {
+                  const float2 d = __ldg(a.valf + q);
+                  float2 dd = make_float2(d.x, fs * d.y);
+                  if (ii != a.self_img) {
+                      const double2 ph = a.phase[ii];
+                      dd = make_float2((float)ph.x * dd.x - (float)ph.y * dd.y, (float)ph.x * dd.y + (float)ph.y * dd.x);
+                  }
+                  return dd;
+              },
+              [&](int k, const float2& dd, const cplx<T>& xv) {
+                  const float tr = dd.x * (float)xv.x - dd.y * (float)xv.y;
+                  const float ti = dd.x * (float)xv.y + dd.y * (float)xv.x;
+                  if (CM == PIM_CORR_COMPACT) {
+                      rl[k] += tr;
+                      il[k] += ti;
+                  } else {
+                      rh[k] += tr;
+                      ih[k] += ti;
+                  }
+              });
+    }
+    if (CM == PIM_CORR_FP64) {
+        group(r0, r1,
+              [&](long long q, int ii) {
+                  double2 d = __ldg(a.val + q);
+                  d.y *= cs;
+                  if (ii != a.self_img) d = cmul(a.phase[ii], d);
+                  return d;
+              },
+              [&](int k, const double2& d, const cplx<T>& xv) {
+                  acc[k].x += d.x * (double)xv.x - d.y * (double)xv.y;
+                  acc[k].y += d.x * (double)xv.y + d.y * (double)xv.x;
+              });
     }
     const long long o = (long long)a.perm[m] * R;
 #pragma unroll

@@ -105,6 +105,34 @@ def test_update_positions_is_frozen_topology_apply(name):
     pl.close()
 
 
+@pytest.mark.parametrize("name", ["helmholtz2d_bloch", "npsp3d"])
+def test_update_positions_compact_fp32(name):
+    # FP32 plan with compact rows: the refilled values are split again by
+    # magnitude; the apply at the moved points matches the frozen-topology
+    # oracle within the FP32 path's bound
+    c = CASES[name]
+    P, _, pts, q, g, real = setup(name)
+    pl = pim.Plan(c["D"], c["pdims"], c["k"], c["k0"], c["n"], p=c["p"], layers=1, precision="fp32", b=c["b"],
+                  nf=c["nf"], pf=c["pf"], corr_mode=pim.PIM_CORR_COMPACT, corr_split=4)
+    pl.set_points(torch.tensor(pts, device="cuda"))
+    base = opim.Plan(P, pts)
+    moved = pts + 1e-3 * np.random.default_rng(1).standard_normal(pts.shape) * np.asarray(P.D)
+    moved = np.clip(moved, 0, np.asarray(P.D))
+    pl.update_positions(torch.tensor(moved, device="cuda"))
+    rp, val, nb = pl.debug(4), pl.debug(6), pl.debug(7)
+    for r in range(len(rp) - 1):
+        a, b = rp[r], rp[r + 1]
+        if b > a:
+            mag = np.abs(val[a:b])
+            big = mag > 2.0 ** -4 * mag.max()
+            assert nb[r] == big.sum() and big[:nb[r]].all()
+    qd = torch.tensor(np.real(q) if real else q, dtype=torch.float32 if real else torch.complex64, device="cuda")
+    u = pl.apply(qd).cpu().numpy()
+    uo = opim.Plan(P, moved, K=base.K, F=base.F, frozen=base).apply(qd.cpu().numpy().astype(complex))
+    assert rel(u, uo) < 2e-5, rel(u, uo)
+    pl.close()
+
+
 def test_position_grad_finite_differences_on_gpu():
     # central differences of Re <g, A q> through pim_update_positions (FP64)
     P, pl, pts, q, g, real = setup("helmholtz2d_bloch", N=200)
