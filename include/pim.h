@@ -236,6 +236,23 @@ pim_status pim_apply_adjoint(pim_plan plan, const void* v, void* w, int nrhs, vo
 pim_status pim_position_grad(pim_plan plan, const void* q, const void* g, double* grad_xyz, int nrhs, void* stream);
 
 /*
+ * pim_position_grad_reuse -- pim_position_grad for one right-hand side that
+ * reuses the near and far grid potentials of the plan's last single-RHS
+ * pim_apply (U = K Q(q), u_f) and last single-RHS pim_apply_adjoint
+ * (V = K^H Q(g), v_f) instead of recomputing them: the position-gradient
+ * kernel alone, after a forward and an adjoint apply (the backward pass of
+ * a differentiable apply).  Not part of the paper.
+ *   q, g      [N], the very arrays those two applies read (the caller's
+ *             guarantee: the plan cannot check their contents); device or host.
+ *   grad_xyz  N x 3 FP64, written, as in pim_position_grad.
+ * Both applies must have run on a with_gradient plan since the last
+ * pim_set_points or pim_update_positions, with no multi-RHS apply,
+ * pim_apply_noalloc or pim_position_grad after them (PIM_ERR_STATE
+ * otherwise); issue it on their stream or after they completed.
+ */
+pim_status pim_position_grad_reuse(pim_plan plan, const void* q, const void* g, double* grad_xyz, void* stream);
+
+/*
  * pim_update_positions -- moves the points of the last pim_set_points to new
  * positions (N x 3 FP64, caller order, device or host) while keeping the
  * discrete structure: the box order, every stencil start, the box of every

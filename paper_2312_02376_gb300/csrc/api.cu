@@ -78,12 +78,33 @@ static void free_grad_buffers(pim_plan P) {
     const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
     const size_t Gf = P->has_far ? (size_t)P->nf[0] * P->nf[1] * P->nf[2] : 0;
     pim_free(P, P->gD, G * ge);
-    pim_free(P, P->gsrt, (size_t)P->pts.N * ge);
+    pim_free(P, P->gsrt, (size_t)std::max<int64_t>(1, P->pts.N) * ge);
     pim_free(P, P->fD, Gf * sizeof(double2));
     pim_free(P, P->fU, Gf * ge);
     pim_free(P, P->fV, Gf * ge);
     P->gD = P->gsrt = P->fU = P->fV = nullptr;
     P->fD = nullptr;
+}
+
+static pim_status position_grad(pim_plan P, const void* q, const void* g, double* grad, int nrhs, void* stream,
+                                bool reuse);
+
+// Buffers of the position gradient: V, the sorted g, the far charges and
+// both far potentials (kept between applies for pim_position_grad_reuse).
+pim_status alloc_grad_buffers(pim_plan P) {
+    if (P->gsrt) return PIM_OK;
+    const size_t ge = grid_elem(P);
+    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const size_t Gf = P->has_far ? (size_t)P->nf[0] * P->nf[1] * P->nf[2] : 0;
+    pim_status st;
+    if ((st = pim_alloc(P, &P->gD, G * ge)) != PIM_OK) return st;
+    if ((st = pim_alloc(P, &P->gsrt, (size_t)std::max<int64_t>(1, P->pts.N) * ge)) != PIM_OK) return st;
+    if (Gf) {
+        if ((st = pim_alloc(P, (void**)&P->fD, Gf * sizeof(double2))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, &P->fU, Gf * ge)) != PIM_OK) return st;
+        if ((st = pim_alloc(P, &P->fV, Gf * ge)) != PIM_OK) return st;
+    }
+    return PIM_OK;
 }
 
 extern "C" {
@@ -386,6 +407,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
         PIM_CK(cudaMemcpy(tmp, xyz, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
         dx = tmp;
     }
+    P->pot_valid = 0;
     st = points_build(P, N, dx, 0);
     if (tmp) pim_free(P, tmp, 3 * N * sizeof(double));
     if (st != PIM_OK) {
@@ -395,6 +417,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     if ((st = pim_alloc(P, &P->qs, (size_t)N * ge)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &P->us, (size_t)N * ge)) != PIM_OK) return st;
     if (P->has_far && (st = pim_alloc(P, &P->ufp, (size_t)N * ge)) != PIM_OK) return st;
+    if (P->with_gradient && (st = alloc_grad_buffers(P)) != PIM_OK) return st;
     P->gather_variant = 0;
     if (P->force_variant >= 0) {
         if (P->force_variant >= gather_variant_count(P)) return PIM_ERR_ARG;
@@ -402,6 +425,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     } else if (P->autotune && N > 0 && (st = apply_autotune(P, 0)) != PIM_OK) {
         return st;
     }
+    P->pot_valid = 0;  // the autotuner's applies are not the caller's
     PIM_CK(cudaDeviceSynchronize());
     P->points_ms = now_ms() - t0;
     return PIM_OK;
@@ -460,20 +484,32 @@ pim_status pim_position_grad(pim_plan P, const void* q, const void* g, double* g
         pim_set_error("position gradient needs pim_set_points on a plan created with with_gradient = 1");
         return PIM_ERR_STATE;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t ge = grid_elem(P);
-    const size_t G = (size_t)P->n[0] * P->n[1] * P->n[2];
-    const size_t Gf = P->has_far ? (size_t)P->nf[0] * P->nf[1] * P->nf[2] : 0;
-    pim_status st;
-    if (!P->gsrt) {
-        if ((st = pim_alloc(P, &P->gD, G * ge)) != PIM_OK) return st;
-        if ((st = pim_alloc(P, &P->gsrt, (size_t)P->pts.N * ge)) != PIM_OK) return st;
-        if (Gf) {
-            if ((st = pim_alloc(P, (void**)&P->fD, Gf * sizeof(double2))) != PIM_OK) return st;
-            if ((st = pim_alloc(P, &P->fU, Gf * ge)) != PIM_OK) return st;
-            if ((st = pim_alloc(P, &P->fV, Gf * ge)) != PIM_OK) return st;
-        }
+    return position_grad(P, q, g, grad, nrhs, stream, false);
+}
+
+pim_status pim_position_grad_reuse(pim_plan P, const void* q, const void* g, double* grad, void* stream) {
+    if (!P || !q || !g || !grad) {
+        pim_set_error("invalid argument");
+        return PIM_ERR_ARG;
     }
+    if (!P->pts.box_ptr || !P->with_gradient || !P->pts.dval) {
+        pim_set_error("position gradient needs pim_set_points on a plan created with with_gradient = 1");
+        return PIM_ERR_STATE;
+    }
+    if (P->pot_valid != 3) {
+        pim_set_error("no single-RHS forward and adjoint applies on record since the points were last set");
+        return PIM_ERR_STATE;
+    }
+    return position_grad(P, q, g, grad, 1, stream, true);
+}
+
+}  // extern "C"
+
+static pim_status position_grad(pim_plan P, const void* q, const void* g, double* grad, int nrhs, void* stream,
+                                bool reuse) {
+    cudaStream_t s = (cudaStream_t)stream;
+    pim_status st;
+    if ((st = alloc_grad_buffers(P)) != PIM_OK) return st;
     const size_t bytes = (size_t)P->pts.N * nrhs * data_elem(P);
     const size_t gbytes = (size_t)P->pts.N * 3 * sizeof(double);
     const bool hq = !is_device_ptr(q), hg = !is_device_ptr(g), hd = !is_device_ptr(grad);
@@ -494,7 +530,7 @@ pim_status pim_position_grad(pim_plan P, const void* q, const void* g, double* g
         if ((st = pim_alloc(P, &tgr, gbytes)) != PIM_OK) return st;
         dgr = (double*)tgr;
     }
-    st = grad_run(P, dq, dg, dgr, nrhs, s);
+    st = grad_run(P, dq, dg, dgr, nrhs, s, reuse);
     if (st == PIM_OK && hd) PIM_CK(cudaMemcpyAsync(grad, dgr, gbytes, cudaMemcpyDeviceToHost, s));
     if (hq || hg || hd) PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, tq, bytes);
@@ -502,6 +538,8 @@ pim_status pim_position_grad(pim_plan P, const void* q, const void* g, double* g
     pim_free(P, tgr, gbytes);
     return st;
 }
+
+extern "C" {
 
 pim_status pim_update_positions(pim_plan P, const double* xyz) {
     if (!P || (P->pts.N > 0 && !xyz)) {
@@ -522,6 +560,7 @@ pim_status pim_update_positions(pim_plan P, const double* xyz) {
         PIM_CK(cudaMemcpy(tmp, xyz, 3 * N * sizeof(double), cudaMemcpyHostToDevice));
         dx = tmp;
     }
+    P->pot_valid = 0;
     st = points_update(P, dx, 0);
     pim_free(P, tmp, 3 * N * sizeof(double));
     return st;

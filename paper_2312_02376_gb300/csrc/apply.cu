@@ -1013,6 +1013,11 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
     // their own scratch and streams, so that several run at once
     // (not for the neutral static case, whose per-RHS means share one scratch)
     const int K = multi && !P->npsp ? std::min(nrhs, (int)pim_plan_s::RHS_LANES) : 1;
+    // plans with the position gradient keep the grid potentials of their last
+    // single-RHS forward (near in gA, far in fU) and adjoint (gD, fV) applies
+    const bool keep = P->with_gradient && nrhs == 1 && !multi && !P->keep_off && P->gD;
+    const int kept = P->pot_valid;
+    P->pot_valid = 0;  // until this apply has been issued in full
     if (K > 1) {
         if ((st = lanes_prepare(P, K)) != PIM_OK) return st;
         PIM_CK(cudaEventRecord(P->lane_fork, s));
@@ -1037,6 +1042,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         const cudaStream_t sr = lk == 0 ? s : P->lane[lk].sm;
         qs = (cplx<T>*)P->qs;
         gA = (cplx<T>*)P->gA;
+        cplx<T>* gN = keep && adj ? (cplx<T>*)P->gD : gA;  // the near grid of this apply
         prof_mark(P, PIM_STAGE_APPLY, 0, sr);
         prof_mark(P, PIM_STAGE_PERMUTE, 0, sr);
         // 1. sorted, regularised sources (Eq. neutral)
@@ -1082,6 +1088,11 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
                 far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)P->fB, G);
                 PIM_CK(cudaGetLastError());
             }
+            if (keep) {
+                far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)(adj ? P->fV : P->fU), G);
+                PIM_CK(cudaGetLastError());
+                P->launches += 1;
+            }
             // far gather of every point (Eq. interpolation), while the near
             // path and its gather run on the main stream
             if (N > 0) {
@@ -1103,10 +1114,10 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         }
         // 3. near spread (two phases), 4. FFT convolution
         prof_mark(P, PIM_STAGE_SPREAD, 0, sr);
-        if ((st = spread_two_phase<T, PP>(P, qs, gA, sr)) != PIM_OK) return st;
+        if ((st = spread_two_phase<T, PP>(P, qs, gN, sr)) != PIM_OK) return st;
         prof_mark(P, PIM_STAGE_SPREAD, 1, sr);
         prof_mark(P, PIM_STAGE_FFT, 0, sr);
-        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, sr)) != PIM_OK)
+        if ((st = fft3_conv<T>(P, P->ng, gN, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, sr)) != PIM_OK)
             return st;
         prof_mark(P, PIM_STAGE_FFT, 1, sr);
         P->launches += (d.nd > 0 ? 2 : 1) + 5;
@@ -1149,7 +1160,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         if (N > 0) {
             const unsigned nb = (unsigned)((threads + 255) / 256);
             if (P->tune_ev[0]) PIM_CK(cudaEventRecord(P->tune_ev[0], sr));
-            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, sr, ga, gA, qs, dst)) != PIM_OK)
+            if ((st = launch_gather<T, PP>(ga.cmode, P->gather_variant, nb, sr, ga, gN, qs, dst)) != PIM_OK)
                 return st;
             if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], sr));
         }
@@ -1221,6 +1232,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         PIM_CK(cudaGetLastError());
         P->launches += 2;
     }
+    if (keep) P->pot_valid = kept | (adj ? 2 : 1);
     return PIM_OK;
 }
 
@@ -1235,7 +1247,8 @@ pim_status run_p(pim_plan P, const void* q, void* u, int nrhs, bool adj, cudaStr
 }
 
 template <typename T, int PP>
-pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
+pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s,
+                      bool reuse) {
     const PointsData& d = P->pts;
     const long long N = d.N;
     cplx<T>* qs = (cplx<T>*)P->qs;
@@ -1260,8 +1273,9 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
         PIM_CK(cudaGetLastError());
         // far grid potentials: u_f from the source-grid projection of q, v_f
         // (adjoint) from the observer-grid projection of g, on the far
-        // stream while the near grids are built
-        if (P->has_far) {
+        // stream while the near grids are built (reuse: those the last
+        // forward and adjoint applies left in fU, fV, gA and gD)
+        if (P->has_far && !reuse) {
             PIM_CK(cudaEventRecord(P->ev_fork, s));
             PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
             for (int side = 0; side < 2; ++side) {
@@ -1287,15 +1301,18 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
         }
         // near grid potentials: U = K * Q(q), V = K^H * Q(g)
-        if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
-        if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, false, s)) !=
-            PIM_OK)
-            return st;
-        if ((st = spread_two_phase<T, PP>(P, gs, gD, s)) != PIM_OK) return st;
-        if ((st = fft3_conv<T>(P, P->ng, gD, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, true, s)) !=
-            PIM_OK)
-            return st;
-        if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
+        if (!reuse) {
+            P->pot_valid = 0;  // gA and gD no longer hold the applies' potentials
+            if ((st = spread_two_phase<T, PP>(P, qs, gA, s)) != PIM_OK) return st;
+            if ((st = fft3_conv<T>(P, P->ng, gA, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, false,
+                                   s)) != PIM_OK)
+                return st;
+            if ((st = spread_two_phase<T, PP>(P, gs, gD, s)) != PIM_OK) return st;
+            if ((st = fft3_conv<T>(P, P->ng, gD, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, true,
+                                   s)) != PIM_OK)
+                return st;
+            if (P->has_far) PIM_CK(cudaStreamWaitEvent(s, P->ev_join, 0));
+        }
         GradArgs ga{};
         for (int i = 0; i < 3; ++i) {
             ga.n[i] = P->n[i];
@@ -1344,11 +1361,11 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
 }
 
 template <typename T>
-pim_status grad_p(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
+pim_status grad_p(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s, bool reuse) {
     switch (P->p) {
-        case 2: return grad_typed<T, 2>(P, q, g, grad, nrhs, s);
-        case 3: return grad_typed<T, 3>(P, q, g, grad, nrhs, s);
-        case 4: return grad_typed<T, 4>(P, q, g, grad, nrhs, s);
+        case 2: return grad_typed<T, 2>(P, q, g, grad, nrhs, s, reuse);
+        case 3: return grad_typed<T, 3>(P, q, g, grad, nrhs, s, reuse);
+        case 4: return grad_typed<T, 4>(P, q, g, grad, nrhs, s, reuse);
         default: return PIM_ERR_UNSUPPORTED;
     }
 }
@@ -1370,9 +1387,9 @@ pim_status debug_spread_p(pim_plan P, void* out, cudaStream_t s) {
 
 }  // namespace
 
-pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s) {
-    if (P->prec == PIM_FP64) return grad_p<double>(P, q, g, grad, nrhs, s);
-    return grad_p<float>(P, q, g, grad, nrhs, s);
+pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s, bool reuse) {
+    if (P->prec == PIM_FP64) return grad_p<double>(P, q, g, grad, nrhs, s, reuse);
+    return grad_p<float>(P, q, g, grad, nrhs, s, reuse);
 }
 
 pim_status apply_debug_spread(pim_plan P, void* out, cudaStream_t s) {

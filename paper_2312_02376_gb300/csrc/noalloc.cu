@@ -119,8 +119,10 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
     }
     const bool no_multi = P->no_multi;
     P->no_multi = true;  // the multi-RHS path would allocate its source buffer
+    P->keep_off = true;  // the grid potentials live in the borrowed scratch
     const pim_status st = apply_run(P, q, u, nrhs, adjoint != 0, (cudaStream_t)stream);
     P->no_multi = no_multi;
+    P->keep_off = false;
     P->qs = save[0];
     P->us = save[1];
     P->gA = save[2];

@@ -244,6 +244,11 @@ struct pim_plan_s {
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
     int force_variant = -1;       // >= 0: launch shape fixed by the options
+    // grid potentials kept for pim_position_grad_reuse (with_gradient plans):
+    // bit 1: gA and fU hold those of the last single-RHS forward apply; bit 2:
+    // gD and fV those of the last single-RHS adjoint apply
+    int pot_valid = 0;
+    bool keep_off = false;        // an apply on borrowed scratch (pim_apply_noalloc) keeps nothing
     int corr_split = 10;          // compact mode: threshold 2^-corr_split of the row's largest |d|
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};  // around the gather launch while autotuning
     void* qsall = nullptr;        // sorted sources of every right-hand side (multi-RHS correction)
@@ -317,7 +322,9 @@ pim_status apply_debug_spread(pim_plan P, void* out_dev, cudaStream_t s);
 pim_status apply_autotune(pim_plan P, cudaStream_t s);
 int far_stream_priority();  // the device's highest stream priority
 int gather_variant_count(const pim_plan_s* P);
-pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s);
+pim_status grad_run(pim_plan P, const void* q, const void* g, double* grad, int nrhs, cudaStream_t s,
+                    bool reuse = false);
+pim_status alloc_grad_buffers(pim_plan P);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
 pim_status lanes_prepare(pim_plan P, int nlanes);
 void lanes_free(pim_plan P);

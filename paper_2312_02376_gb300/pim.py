@@ -22,7 +22,8 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32, PIM_CORR_COMPACT = 0, 1, 2,
 # symbols declared in include/pim.h
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
            "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
-           "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_update_positions", "pim_apply_noalloc",
+           "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_position_grad_reuse", "pim_update_positions",
+           "pim_apply_noalloc",
            "pim_apply_batched", "pim_debug_copy", "pim_destroy"]
 STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
@@ -94,6 +95,8 @@ def load(path=LIB_PATH):
     lib.pim_stage_name.restype = ctypes.c_char_p
     lib.pim_position_grad.argtypes = [vp, vp, vp, vp, i32, vp]
     lib.pim_position_grad.restype = i32
+    lib.pim_position_grad_reuse.argtypes = [vp, vp, vp, vp, vp]
+    lib.pim_position_grad_reuse.restype = i32
     lib.pim_update_positions.argtypes = [vp, vp]
     lib.pim_update_positions.restype = i32
     lib.pim_apply_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32, vp]
@@ -199,6 +202,11 @@ def pim_stage_name(stage):
 def pim_position_grad(plan, q, g, grad_xyz, nrhs=1, stream=None):
     _check(load().pim_position_grad(plan, _ptr(q), _ptr(g), _ptr(grad_xyz), int(nrhs), _stream_ptr(stream)),
            "pim_position_grad")
+
+
+def pim_position_grad_reuse(plan, q, g, grad_xyz, stream=None):
+    _check(load().pim_position_grad_reuse(plan, _ptr(q), _ptr(g), _ptr(grad_xyz), _stream_ptr(stream)),
+           "pim_position_grad_reuse")
 
 
 def pim_update_positions(plan, xyz):
@@ -309,6 +317,8 @@ class Plan:
                 out = np.empty_like(q)
         f = pim_apply_adjoint if adjoint else pim_apply
         f(self._h, q, out, nrhs, stream)
+        if not adjoint:
+            self.forward_applies = getattr(self, "forward_applies", 0) + 1
         return out
 
     def apply_adjoint(self, v, out=None, stream=None):
@@ -325,6 +335,19 @@ class Plan:
             else:
                 out = np.empty((self.N, 3), np.float64)
         pim_position_grad(self._h, q, g, out, nrhs, stream)
+        return out
+
+    def position_grad_reuse(self, q, g, out=None, stream=None):
+        """position_grad for one right-hand side after apply(q) and
+        apply_adjoint(g) on this plan, reusing their grid potentials (q and g
+        must be the arrays those applies read)."""
+        if out is None:
+            if hasattr(q, "data_ptr") and not isinstance(q, np.ndarray):
+                import torch
+                out = torch.empty((self.N, 3), dtype=torch.float64, device=q.device)
+            else:
+                out = np.empty((self.N, 3), np.float64)
+        pim_position_grad_reuse(self._h, q, g, out, stream)
         return out
 
     def update_positions(self, xyz):

@@ -133,6 +133,44 @@ def test_update_positions_compact_fp32(name):
     pl.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["helmholtz2d_bloch", "npsp3d", "helmholtz3d"])
+def test_position_grad_reuse_equals_full(name, precision):
+    # after apply(q) and apply_adjoint(g) the gradient kernel alone, on the
+    # potentials those applies kept, equals the full gradient; the state
+    # rules: none before both applies, none after a multi-RHS apply or new points
+    c = CASES[name]
+    P, _, pts, q, g, real = setup(name)
+    pl = pim.Plan(c["D"], c["pdims"], c["k"], c["k0"], c["n"], p=c["p"], layers=1, precision=precision, b=c["b"],
+                  nf=c["nf"], pf=c["pf"], with_gradient=True)
+    pl.set_points(torch.tensor(pts, device="cuda"))
+    if precision == "fp64":
+        qd, gd = dev(q, real), dev(g, real)
+    else:
+        dt = torch.float32 if real else torch.complex64
+        qd = torch.tensor(np.real(q) if real else q, dtype=dt, device="cuda")
+        gd = torch.tensor(np.real(g) if real else g, dtype=dt, device="cuda")
+    with pytest.raises(pim.PimError):
+        pl.position_grad_reuse(qd, gd)
+    pl.apply(qd)
+    with pytest.raises(pim.PimError):
+        pl.position_grad_reuse(qd, gd)
+    pl.apply_adjoint(gd)
+    G1 = pl.position_grad_reuse(qd, gd).cpu().numpy()
+    G0 = pl.position_grad(qd, gd).cpu().numpy()
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert rel(G1, G0) < tol, rel(G1, G0)
+    with pytest.raises(pim.PimError):      # the full gradient replaced the kept potentials
+        pl.position_grad_reuse(qd, gd)
+    pl.apply_adjoint(gd)
+    pl.apply(qd)
+    assert rel(pl.position_grad_reuse(qd, gd).cpu().numpy(), G0) < tol
+    pl.apply(torch.stack([qd, qd], dim=1).contiguous())
+    with pytest.raises(pim.PimError):
+        pl.position_grad_reuse(qd, gd)
+    pl.close()
+
+
 def test_position_grad_finite_differences_on_gpu():
     # central differences of Re <g, A q> through pim_update_positions (FP64)
     P, pl, pts, q, g, real = setup("helmholtz2d_bloch", N=200)
