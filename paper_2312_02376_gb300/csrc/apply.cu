@@ -577,6 +577,8 @@ __global__ void far_convert_kernel(const double2* in, cplx<T>* out, int G) {
 // ------------------------------- position gradient -------------------------
 struct GradArgs {
     int n[3], nf[3], pf;
+    const int* nbig;          // compact mode: the rows' double-float entries (else null: all of them)
+    const float2* dvalf;      // 3 per entry, FP32 heads of the derivatives (compact mode)
     double h[3], df[3];
     long long N;
     int has_far, self_img, first;
@@ -726,11 +728,36 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) grad_kernel(GradA
             }
         }
     }
-    // correction list
+    // correction list (compact rows: the double-float entries [r0, rb), then
+    // the complex64 ones with FP32 derivative heads, summed into the low words)
     const long long r0 = a.row_ptr[m], r1 = a.row_ptr[m + 1];
+    const long long rb = DF && a.nbig ? r0 + a.nbig[m] : r1;
     float hh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};  // double-float sums (DF)
     double acc[3] = {0.0, 0.0, 0.0};                         // FP64 sums
-    for (long long q = r0 + lane; q < r1; q += 32) {
+    if constexpr (DF) {
+        for (long long q = rb + lane; q < r1; q += 32) {
+            const uint32_t c = __ldcs(a.col + q);
+            const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
+            const cplx<T> xq = qs[n], xg = gs[n];
+            float2 D[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) D[d] = __ldcs(a.dvalf + 3 * q + d);
+            float ax = (float)xq.x, ay = (float)xq.y, bx = (float)xg.x, by = (float)xg.y;
+            if (ii != a.self_img) {
+                const float4 ph = a.phasedf[ii];
+                const float px = ph.x + ph.y, py = ph.z + ph.w;
+                const float tx = px * ax - py * ay, ty = px * ay + py * ax;
+                const float ux = px * bx - py * by, uy = px * by + py * bx;
+                ax = tx; ay = ty; bx = ux; by = uy;
+            }
+            const float gx = (float)gm.x, gy = (float)gm.y, qx = (float)qm.x, qy = (float)qm.y;
+            const float wr = gx * ax + gy * ay + qx * bx + qy * by;
+            const float wi = gx * ay - gy * ax + qy * bx - qx * by;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ll[d] += D[d].x * wr - D[d].y * wi;
+        }
+    }
+    for (long long q = r0 + lane; q < rb; q += 32) {
         const uint32_t c = __ldcs(a.col + q);
         const int n = (int)(c & PIM_COL_MASK), ii = (int)(c >> PIM_COL_BITS);
         const cplx<T> xq = qs[n], xg = gs[n];
@@ -1337,6 +1364,8 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
         ga.col = d.col;
         ga.dval = d.dval;
         ga.dvaldf = reinterpret_cast<const float4*>(d.dval);
+        ga.dvalf = d.dvalf;
+        ga.nbig = P->corr_mode == PIM_CORR_COMPACT ? d.nbig : nullptr;
         ga.phase = P->dphase;
         ga.phasedf = P->dphasedf;
         for (int i = 0; i < P->nimg; ++i)

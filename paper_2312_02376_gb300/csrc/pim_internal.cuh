@@ -186,6 +186,7 @@ struct PointsData {
     uint32_t* valt = nullptr;     // nnz: bf16 tails of re (low half) and im (high half), compact mode
     int* nbig = nullptr;          // N: compact mode, entries at the head of each row summed in double-float
     double2* dval = nullptr;      // 3 nnz: d/dr_m of the values (with_gradient)
+    float2* dvalf = nullptr;      // 3 nnz: their FP32 heads (compact mode; read for a row's complex64 part)
     int64_t nnz = 0;
 };
 

@@ -539,7 +539,7 @@ __global__ void pair_refill_kernel(const double* pos, const uint32_t* ns, const 
 __global__ void split_rows_kernel(long long N, const int64_t* row_ptr, int split, const uint32_t* col,
                                   const double2* val, const float2* valf, const uint32_t* valt, const double2* dval,
                                   uint32_t* col2, double2* val2, float2* valf2, uint32_t* valt2, double2* dval2,
-                                  int* nbig) {
+                                  float2* dvalf2, int* nbig) {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -581,7 +581,13 @@ __global__ void split_rows_kernel(long long N, const int64_t* row_ptr, int split
                 valf2[t] = valf[q];
                 valt2[t] = valt[q];
                 if (dval)
-                    for (int k = 0; k < 3; ++k) dval2[3 * t + k] = dval[3 * q + k];
+                    for (int k = 0; k < 3; ++k) {
+                        // double-float derivatives (re hi, re lo, im hi, im lo) and their heads
+                        const double2 g = dval[3 * q + k];
+                        dval2[3 * t + k] = g;
+                        const float4 gf = *reinterpret_cast<const float4*>(&g);
+                        dvalf2[3 * t + k] = make_float2(gf.x, gf.z);
+                    }
             }
             ob += __popc(mb);
             os += __popc(ms);
@@ -681,20 +687,22 @@ static pim_status split_rows(pim_plan P, cudaStream_t s) {
     }
     uint32_t *col2 = nullptr, *valt2 = nullptr;
     double2 *val2 = nullptr, *dval2 = nullptr;
-    float2* valf2 = nullptr;
+    float2 *valf2 = nullptr, *dvalf2 = nullptr;
     if ((st = pim_alloc(P, (void**)&col2, nnz * sizeof(uint32_t))) != PIM_OK ||
         (st = pim_alloc(P, (void**)&val2, nnz * sizeof(double2))) != PIM_OK ||
         (st = pim_alloc(P, (void**)&valf2, nnz * sizeof(float2))) != PIM_OK ||
         (st = pim_alloc(P, (void**)&valt2, nnz * sizeof(uint32_t))) != PIM_OK ||
-        (d.dval && (st = pim_alloc(P, (void**)&dval2, 3 * nnz * sizeof(double2))) != PIM_OK)) {
+        (d.dval && (st = pim_alloc(P, (void**)&dval2, 3 * nnz * sizeof(double2))) != PIM_OK) ||
+        (d.dval && (st = pim_alloc(P, (void**)&dvalf2, 3 * nnz * sizeof(float2))) != PIM_OK)) {
         pim_free(P, col2, nnz * sizeof(uint32_t));
         pim_free(P, val2, nnz * sizeof(double2));
         pim_free(P, valf2, nnz * sizeof(float2));
         pim_free(P, valt2, nnz * sizeof(uint32_t));
+        pim_free(P, dval2, 3 * nnz * sizeof(double2));
         return st;
     }
     split_rows_kernel<<<152 * 16, 256, 0, s>>>(N, d.row_ptr, P->corr_split, d.col, d.val, d.valf, d.valt, d.dval, col2,
-                                               val2, valf2, valt2, dval2, d.nbig);
+                                               val2, valf2, valt2, dval2, dvalf2, d.nbig);
     PIM_CK(cudaGetLastError());
     PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, d.col, nnz * sizeof(uint32_t));
@@ -702,11 +710,13 @@ static pim_status split_rows(pim_plan P, cudaStream_t s) {
     pim_free(P, d.valf, nnz * sizeof(float2));
     pim_free(P, d.valt, nnz * sizeof(uint32_t));
     pim_free(P, d.dval, 3 * nnz * sizeof(double2));
+    pim_free(P, d.dvalf, 3 * nnz * sizeof(float2));
     d.col = col2;
     d.val = val2;
     d.valf = valf2;
     d.valt = valt2;
     d.dval = dval2;
+    d.dvalf = dvalf2;
     return PIM_OK;
 }
 
@@ -807,6 +817,7 @@ void points_free(pim_plan P) {
     pim_free(P, d.valf, d.nnz * sizeof(float2));
     pim_free(P, d.valt, d.nnz * sizeof(uint32_t));
     pim_free(P, d.dval, 3 * d.nnz * sizeof(double2));
+    pim_free(P, d.dvalf, 3 * d.nnz * sizeof(float2));
     pim_free(P, d.nbig, (size_t)std::max<int64_t>(1, d.N) * sizeof(int));
     d = PointsData{};
 }
