@@ -95,7 +95,8 @@ typedef struct {
     int corr_cube;       /* 0: boxes within D^ER of the observer box (|r - r_m| <=
                             D^ER, Sec. 3.3 step 4); 1: Chebyshev box distance <= b     */
     int corr_mode;       /* pim_corr_mode; ignored (FP64) for PIM_FP64 plans           */
-    int tile[3];         /* spread node tile; 0 -> autotuned default                   */
+    int tile[3];         /* ignored: the two-phase spread (box moments, then grid lines)
+                            has no node tile; kept so that the layout stays stable     */
     double neutral_tol;  /* tau of the neutrality check; default 1e-6                  */
     double series_tol;   /* relative truncation of the far series; default 1e-16      */
     size_t mem_cap;      /* bytes; 0 = no cap.  Exceeding it -> PIM_ERR_OOM            */

@@ -273,7 +273,7 @@ class Plan:
             opt.far_p = int(pf)
         if corr_mode is not None:
             opt.corr_mode = int(corr_mode)
-        if tile is not None:
+        if tile is not None:  # ignored by the library (see pim_options.tile)
             for d in range(3):
                 opt.tile[d] = int(tile[d])
         if neutral_tol is not None:
