@@ -103,8 +103,10 @@ typedef struct {
     int autotune;        /* 1: pim_set_points times the gather kernel's launch shapes
                             and keeps the fastest; 0: default shape                    */
     int with_gradient;   /* 1: pim_set_points also stores the position derivatives of
-                            the correction values (48 B per entry), which
-                            pim_position_grad needs                                    */
+                            the correction values (48 B per entry, plus 24 B of FP32
+                            heads in compact mode), which pim_position_grad needs, and
+                            single-RHS applies keep their grid potentials (one more
+                            near grid) for pim_position_grad_reuse                   */
     int corr_split;      /* PIM_CORR_COMPACT: the exponent s of the 2^-s max_row |d|
                             threshold above; 0 keeps every entry in the 12-byte form;
                             default 10; 0 <= s <= 30 (else PIM_ERR_ARG)                */
