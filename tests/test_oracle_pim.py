@@ -127,6 +127,47 @@ def test_adjoint_is_conjugate_transpose(case):
         assert np.allclose(AH, A.conj().T, atol=1e-12 * np.abs(A).max())
 
 
+def _dense(pl, N):
+    E = np.eye(N, dtype=complex)
+    return np.array([pl.apply(E[:, j]) for j in range(N)]).T
+
+
+def test_reciprocity_free_space_is_exact():
+    # G0(r) = G0(-r) and the spread and gather share their weights, so the
+    # discrete free-space operator W K W^T + C is complex symmetric to
+    # round-off (reciprocity; a sign slip in the grid kernel's offsets or in
+    # the correction's pair order breaks it)
+    rng = np.random.default_rng(8)
+    N = 40
+    P = pim.Params(D=(1, 1, 0.5), pdims=(), k=5.0, k0=(0, 0, 0), n=(9, 9, 6), p=3, layers=0, b=2)
+    pts = rng.random((N, 3)) * P.D
+    A = _dense(pim.Plan(P, pts), N)
+    assert np.abs(A - A.T).max() < 1e-12 * np.abs(A).max()
+
+
+def test_reciprocity_bloch_swaps_the_phase():
+    # periodic with a Bloch phase: A(k0)^T = A(-k0) (the image phase
+    # exp(-j k0.(iL)) of pair (m, n) is that of (n, m) with -i).  The near
+    # part and the corrections satisfy it exactly; the far part, whose source
+    # and observer grids are half a step apart (Eq. grid), only up to its
+    # interpolation error, which falls as the far grid is refined.  A wrong
+    # phase sign would leave an O(1) difference.
+    N = 40
+    pts = np.random.default_rng(9).random((N, 3)) * np.array([1, 1, 0.5])
+
+    def asym(nf, pf):
+        kw = dict(D=(1, 1, 0.5), pdims=(0, 1), k=4.0, n=(9, 9, 6), p=3, layers=1, b=3, nf=nf, pf=pf)
+        A = _dense(pim.Plan(pim.Params(k0=(1.1, 0.5, 0.0), **kw), pts), N)
+        B = _dense(pim.Plan(pim.Params(k0=(-1.1, -0.5, 0.0), **kw), pts), N)
+        nA = np.linalg.norm(A)
+        return np.linalg.norm(A.T - B) / nA, np.linalg.norm(A.T - A) / nA
+
+    coarse, _ = asym((8, 8, 6), 3)
+    fine, unswapped = asym((16, 16, 10), 4)
+    assert fine < 1e-4 and fine < coarse / 20, (coarse, fine)
+    assert unswapped > 0.1
+
+
 def test_method_error_falls_with_order_lossy_periodic():
     # Sec. 4.1: the error falls with interpolation order; reference = Eq. 2
     # summed by brute force (converges for Im k < 0).
