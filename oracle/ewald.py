@@ -13,17 +13,26 @@ halves converge exponentially.  For a splitting parameter E:
   2D lattice (periodic x, y; z free; A = cell area, kz from Eq. pgf's branch):
            sum_{m,n} exp(-j kt.rho)/(4 j kz A)
                  * [e^{-j kz z} erfc(j kz/2E - zE) + e^{j kz z} erfc(j kz/2E + zE)]
+  1D lattice (periodic x; L = period; rho = transverse distance; k_x = kx0 + 2 pi m / L): the 1D
+           Fourier transform along x of the smooth complement G0 - f_E, written with the integral
+           representation of G0 over s in [0, E] and expanded in powers of rho,
+           (1/(4 pi L)) sum_m e^{-j k_x x} sum_q (-1)^q (rho E)^{2q} / q! E_{q+1}(-(k^2 - k_x^2)/4E^2)
+           with E_p the generalized exponential integral, continued from losses (Im k < 0), i.e. its
+           argument taken just above the negative real axis
   self     lim_{R->0} [f_E(R) - G0(R)] = jk erfc(jk/2E)/(4 pi) - E e^{k^2/4E^2}/(2 pi^{3/2})
 
 As E -> infinity the 2D spectral part reduces term by term to Eq. pgf_2 and
 the 3D one to the Fourier series of Eq. 2; the tests check independence of E
-and agreement with brute-force image sums for a lossy wavenumber.
+and agreement with brute-force image sums for a lossy wavenumber, and the 1D
+lattice against Eq. pgf_1 (the Hankel-function series) for a real one.
 
 For k = k0 = 0 on a 3D lattice the G = 0 term is dropped: this is the
 "tin-foil" periodic Green's function, which solves -lap G = delta - 1/V with
 zero cell mean.  Eq. lgf_3 solves the same equation, so the two differ by a
 constant that cancels for neutral charges (Eq. neutral).
 """
+import math
+
 import numpy as np
 from scipy import special
 
@@ -155,9 +164,48 @@ def potential(points, q, tgt, L, pdims, k, k0, E, tol=1e-15, chunk=2048):
                 br = exp_erfc(-1j * kz[None, :] * z, jkz[None, :] / (2 * E) - z * E) \
                     + exp_erfc(1j * kz[None, :] * z, jkz[None, :] / (2 * E) + z * E)
                 u[t] += np.sum(q[s0:s0 + chunk, None] * tph * br / (4j * kz[None, :] * A))
+    elif len(pd) == 1:
+        Lx = L[0]
+        Mx = int(np.ceil(Gc * Lx / (2 * np.pi))) + 1
+        kx = k0[0] + 2 * np.pi * np.arange(-Mx, Mx + 1) / Lx
+        # transverse extent fixes the number of powers of (rho E)^2 kept
+        rho_max = np.hypot(np.ptp(points[:, 1]), np.ptp(points[:, 2]))
+        Q = int(np.ceil(2.0 * (rho_max * E) ** 2 + 60))
+        Etab = expint_table(Q, -(k * k - kx * kx) / (4 * E * E))          # (Q, modes)
+        coef = np.array([(-1.0) ** qq / math.factorial(qq) for qq in range(Q)])
+        for t, m in enumerate(tgt):
+            for s0 in range(0, len(points), chunk):
+                d = points[m] - points[s0:s0 + chunk]
+                w = (d[:, 1] ** 2 + d[:, 2] ** 2) * E * E                 # (rho E)^2
+                pw = w[:, None] ** np.arange(Q)[None, :] * coef[None, :]   # (n, Q)
+                S = pw @ Etab                                             # (n, modes)
+                ph = np.exp(-1j * np.outer(d[:, 0], kx))
+                u[t] += np.sum(q[s0:s0 + chunk, None] * ph * S) / (FOUR_PI * Lx)
     else:
-        raise ValueError("Ewald ground truth implemented for 2D and 3D lattices")
+        raise ValueError("Ewald ground truth implemented for 1D, 2D and 3D lattices")
     return u
+
+
+def expint_table(Q, z):
+    """E_p(z) for p = 1..Q (rows) at the complex arguments z (columns), the
+    argument moved just above the negative real axis (the outgoing branch).
+    E_1 in arbitrary precision (mpmath), the higher orders by the recurrence
+    E_{p+1}(z) = (e^{-z} - z E_p(z)) / p carried at 80 digits, which absorbs
+    its growth of rounding errors (at most about e^{|z|}) for the |z| < 100
+    of the modes kept."""
+    import mpmath
+
+    z = np.atleast_1d(np.asarray(z, np.complex128))
+    out = np.empty((Q, len(z)), np.complex128)
+    with mpmath.workdps(80):
+        for j, zz in enumerate(z):
+            zm = mpmath.mpc(zz.real, zz.imag if zz.imag != 0 else 1e-300)
+            ez = mpmath.exp(-zm)
+            e = mpmath.expint(1, zm)
+            for p in range(1, Q + 1):
+                out[p - 1, j] = complex(e)
+                e = (ez - zm * e) / p
+    return out
 
 
 def greens_function(r, L, pdims, k, k0, E):

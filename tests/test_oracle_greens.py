@@ -117,6 +117,29 @@ def test_ewald2d_vs_lossy_image_sum_and_real_k_vs_pgf():
     assert np.max(np.abs(e - s)) / np.max(np.abs(s)) < 1e-13
 
 
+@pytest.mark.parametrize("pd", [(0,), (2,)])
+def test_ewald1d_vs_lossy_image_sum_and_real_k_vs_pgf1(pd):
+    # 1D lattice: the Ewald split with the exponential-integral spectral part
+    # against the brute-force image sum for a lossy k (any E), and against
+    # Eq. pgf_1 (the Hankel-function series) for real k
+    pytest.importorskip("mpmath")
+    L = np.array([0.5, 0.5, 0.5])
+    L[pd[0]] = 0.25
+    k = 3.0 - 2.0j
+    k0 = np.zeros(3, complex)
+    k0[pd[0]] = 0.7 - 0.1j
+    b = _brute(R, L, pd, k, k0, 80)
+    for E in (2.0, 3.5):
+        e = ewald.greens_function(R, L, pd, k, k0, E)
+        assert np.max(np.abs(b - e)) / np.max(np.abs(b)) < 1e-12
+    for k, kz in ((2 * np.pi * 0.5, 0.0), (3.0, 0.9)):
+        k0 = np.zeros(3)
+        k0[pd[0]] = kz
+        e = ewald.greens_function(R, L, pd, k, k0, 2.5)
+        s = greens.pgf(R, L, pd, k, k0)
+        assert np.max(np.abs(e - s)) / np.max(np.abs(s)) < 1e-12
+
+
 def test_madelung_nacl():
     ref = float(open(os.path.join(GOLDEN, "madelung_nacl.txt")).read().split("\n")[-2])
     pts = np.array([[0, 0, 0], [.5, .5, 0], [.5, 0, .5], [0, .5, .5],
