@@ -234,6 +234,24 @@ def test_coulomb3d_4k_recipe_vs_ewald_rows():
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-4
 
 
+def test_error_converges_in_near_image_layers():
+    # Sec. 3.3: the near kernel sums the images |i| <= i_d, the far series the
+    # rest (Eq. 4).  Against the Ewald sum the 2D Helmholtz recipe's error
+    # drops by more than an order of magnitude from i_d = 0 to 1 and then
+    # settles at the grid's level (convergence in image count)
+    W = inputs.helmholtz2d(N=3000, n=(24, 24, 12), nf=(14, 14, 8), b=5)
+    q = W.q.astype(complex)
+    rows = np.random.default_rng(5).choice(W.N, 24, replace=False)
+    ref = ewald.potential(W.points, q, rows, W.D, W.pdims, W.k, W.k0, 4.0)
+    err = []
+    for layers in (0, 1, 2):
+        P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=4, layers=layers, b=W.b, nf=W.nf, pf=4)
+        u = pim.Plan(P, W.points).apply_rows(q, rows)
+        err.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    assert err[1] < err[0] / 10, err
+    assert abs(err[2] - err[1]) < 0.3 * err[1] and err[2] < 1e-3, err
+
+
 def test_far_table_against_ewald():
     # F(delta) = G^p - G_near at delta*Delta + Delta/2, checked pointwise
     # against the Ewald sum minus the same near images.
