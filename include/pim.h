@@ -63,7 +63,8 @@ typedef enum {
     PIM_ERR_STATE = 6,        /* apply before pim_set_points */
     PIM_ERR_OOM = 7,          /* device allocation failed or mem_cap exceeded */
     PIM_ERR_CUDA = 8,         /* a CUDA runtime call failed */
-    PIM_ERR_TIMEOUT = 9,      /* a bounded device wait ran out */
+    PIM_ERR_TIMEOUT = 9,      /* a bounded device wait ran out (reserved: no kernel of this
+                                 version waits on another)                                */
     PIM_ERR_DEVICE = 10       /* a device-side bounds check tripped */
 } pim_status;
 
