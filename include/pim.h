@@ -96,8 +96,6 @@ typedef struct {
     int corr_cube;       /* 0: boxes within D^ER of the observer box (|r - r_m| <=
                             D^ER, Sec. 3.3 step 4); 1: Chebyshev box distance <= b     */
     int corr_mode;       /* pim_corr_mode; ignored (FP64) for PIM_FP64 plans           */
-    int tile[3];         /* ignored: the two-phase spread (box moments, then grid lines)
-                            has no node tile; kept so that the layout stays stable     */
     double neutral_tol;  /* tau of the neutrality check; default 1e-6                  */
     double series_tol;   /* relative truncation of the far series; default 1e-16      */
     size_t mem_cap;      /* bytes; 0 = no cap.  Exceeding it -> PIM_ERR_OOM            */
@@ -116,6 +114,18 @@ typedef struct {
                             below pim_info.gather_variants (which depends on the
                             precision and correction mode; else pim_set_points
                             returns PIM_ERR_ARG)                                       */
+    int corr_listfree;   /* list-free correction (Sec. 3.3 step 4 without a stored
+                            list): a box whose points times its correction region's
+                            points is at least this value has its correction
+                            recomputed by every apply -- the exact kernel summed over
+                            the region's points minus the region's grid interaction,
+                            formed from the box moments on a local grid -- and keeps
+                            no stored entries.  The same operator as the stored list
+                            (to rounding).  -1: default (32768); 0: off (every
+                            correction stored).  Plans with with_gradient store every
+                            correction (the gradient reads the stored derivatives); a
+                            correction radius whose local grid exceeds 24 nodes per
+                            axis (2b + 2 floor(p/2) + p + 3 > 24) also stores all.   */
 } pim_options;
 
 typedef struct {
@@ -130,6 +140,9 @@ typedef struct {
     int64_t launches;    /* kernels launched by this plan's applies so far             */
     int gather_variant;  /* launch shape of the gather kernel in use                   */
     int gather_variants; /* launch shapes available to this plan                       */
+    int64_t lf_boxes;    /* boxes corrected list-free (corr_listfree)                  */
+    int64_t lf_points;   /* points in those boxes                                      */
+    int64_t lf_pairs;    /* (observer, source, image) pairs they sum per apply         */
 } pim_info;
 
 /* Stages timed by the profiling ring (pim_set_profiling). */
@@ -304,12 +317,18 @@ pim_status pim_apply_batched(int nplans, pim_plan const* plans, const void* cons
  *            required size in pim_last_error().
  *   Set-up   the first call on a device looks up the array's device address
  *            (cudaGetSymbolAddress) with that device current; make that first
- *            call before any stream capture.
+ *            call before any stream capture.  The address is cached per device
+ *            and per CUDA context: after the context is destroyed and created
+ *            again (cudaDeviceReset) the next call looks it up again, so that
+ *            call, too, belongs before any capture.
  *   Sharing  every call on a device uses the same array, which keeps the last
  *            call's contents (the apply writes every scratch word before it
  *            reads it, so nothing needs clearing); calls whose device work
  *            overlaps -- on different streams or from different threads --
- *            race.  Order them on one stream.
+ *            race.  Order them on one stream.  Calls on one plan from two
+ *            threads at once also corrupt the plan itself (a call points the
+ *            plan's scratch at the array for its duration): a plan is not
+ *            thread safe.
  */
 pim_status pim_apply_noalloc(pim_plan plan, const void* q, void* u, int nrhs, int adjoint, void* stream);
 

@@ -125,6 +125,7 @@ void pim_options_default(pim_options* o) {
     o->with_gradient = 0;
     o->corr_split = 10;
     o->gather_variant = -1;
+    o->corr_listfree = -1;
 }
 
 const char* pim_status_string(pim_status s) {
@@ -235,6 +236,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->autotune = o.autotune ? 1 : 0;
     P->with_gradient = o.with_gradient ? 1 : 0;
     P->force_variant = o.gather_variant;
+    P->lf_min_work = P->with_gradient ? 0 : (o.corr_listfree < 0 ? 32768 : o.corr_listfree);
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
@@ -312,7 +314,6 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
         pim_set_error("far degree must be 2..6");
         return fail(PIM_ERR_UNSUPPORTED);
     }
-    for (int d = 0; d < 3; ++d) P->tile[d] = o.tile[d] > 0 ? o.tile[d] : (d == 0 ? 16 : 8);
     cudaStream_t s = (cudaStream_t)stream;
     pim_status st;
     // the far zone's stream takes the highest priority: its short chain ends
@@ -602,6 +603,9 @@ pim_status pim_plan_info(pim_plan P, pim_info* info) {
     info->launches = P->launches;
     info->gather_variant = P->gather_variant;
     info->gather_variants = gather_variant_count(P);
+    info->lf_boxes = P->pts.nlf;
+    info->lf_points = P->pts.lf_points;
+    info->lf_pairs = P->pts.lf_pairs;
     return PIM_OK;
 }
 

@@ -1,0 +1,792 @@
+// List-free near-pair correction (Sec. 3.3 step 4, Eq. er) for observer boxes
+// that hold many points and many correction partners.
+//
+// For every observer box A the correction region (the boxes within D^ER of
+// A, per near image i, as for the stored list) is the same for all points of
+// A, and all points of a box share one interpolation stencil.  The correction
+// of Eq. er summed over the region,
+//
+//   c_m = sum_{(n,i) in region(A)} exp(-j k0.(i o L))
+//           [ G0(r_m - r_n - i o L) - sum_a sum_c w_m(a) w_n(c) g(a - c - i o (n-1)) ],
+//
+// splits into an exact part (a direct sum over the region's points) and a
+// grid part w_m . V_A with
+//
+//   V_A(a) = sum_c g(a - c) Q_A(c),
+//   Q_A    = sum_{(B,i) in region(A)} exp(-j k0.(i o L)) M_B placed at s_B + i o (n-1),
+//
+// where M_B(c) = sum_{n in B} w_n(c) q_n are the box moments of step 1 (the
+// spread forms them for boxes with >= PIM_DENSE_MIN points; the others are
+// added point by point) and g(e) = G0(|e o h|), g(0) = 0, is the grid kernel
+// of the image-i component (an image shift moves a box by whole periods of
+// n - 1 grid steps, so g is the free-space kernel on the unrolled grid).  Q_A
+// lives on a local grid of E^3 nodes around A in shared memory, so the grid
+// part costs one small convolution per box instead of one 729-term sum per
+// pair, and nothing is stored between applies.  The adjoint uses conj(G0),
+// conj(g) and the same image phases (the region is symmetric), as the stored
+// list does.
+//
+// Local grid frame of box A (per axis): origin A - R - 2c; a box B' = B +
+// i (n-1) of the region has |B' - A| <= R and its clamped stencil start s_B
+// differs from B - c by at most c, so s_B' - origin lies in [0, 2R + 2c] and
+// its stencil in [0, E - 1], E = 2R + 2c + p + 1; A's own stencil starts at
+// X0 = s_A - origin in [R, R + 2c]; the offsets a - c reach |e| <= H = R + 2c + p.
+#include <algorithm>
+#include <cmath>
+
+#include "lagrange.cuh"
+#include "pim_internal.cuh"
+
+namespace {
+using namespace pim_k;
+
+constexpr double PI = 3.141592653589793238462643383279502884;
+constexpr int LF_NT = 256;      // threads of the exact-part kernel
+constexpr int LF_CH = 2048;     // region points staged per chunk
+constexpr int LF_OB = 8;        // observers per register group
+constexpr int LF_MAXOBS = 512;  // observers per pass over the region
+constexpr int LF_GNT = 512;     // threads of the grid-part kernel
+constexpr int LF_MAXNT = 8;     // polynomial terms
+
+struct LfArgs {
+    const int* lfslot;
+    const int64_t* segptr;
+    const int4* seg;
+    const int* bstart;
+    const int* blist;
+    const int* dix;
+    const float4* lfp;
+    const double* pos;
+    const float* nt;
+    const double* ntd;
+    const int* perm;
+    const double2* phase;   // exp(-j k0.(i o L)) per near image
+    int nb[3], nL[3], n[3];
+    int p, c, R, E, H;
+    int nimg, self_img;
+    int img[PIM_MAX_IMAGES][3];
+    double h[3], D[3];
+    float hf[3];
+    double k;
+    float pc[LF_MAXNT], ps[LF_MAXNT];  // cos and sinc polynomial coefficients (x 1/(4 pi)), in s = r^2
+    long long nlf;
+    int nrhs, r, real_out, sorted_out;
+    int* status;
+};
+
+__device__ __forceinline__ void box_xyz(int b, const int* nb, int* B) {
+    B[0] = b % nb[0];
+    B[1] = (b / nb[0]) % nb[1];
+    B[2] = b / (nb[0] * nb[1]);
+}
+
+// stencil start of box B along one axis: clamp(B - c, 0, n - 1 - p)
+__device__ __forceinline__ int box_stencil(int B, int c, int n, int p) { return min(max(B - c, 0), n - 1 - p); }
+
+// dst[m] += v in the layout of the apply's output (caller order with the
+// right-hand-side stride, real or complex, or the sorted scratch)
+template <typename T>
+__device__ __forceinline__ void add_out(const LfArgs& a, void* out, long long m, cplx<T> v) {
+    if (a.sorted_out) {
+        cplx<T>* u = (cplx<T>*)out + m;
+        *u = mk<T>(u->x + v.x, u->y + v.y);
+        return;
+    }
+    const long long o = (long long)a.perm[m] * a.nrhs + a.r;
+    if (a.real_out) {
+        ((T*)out)[o] += v.x;
+    } else {
+        cplx<T>* u = (cplx<T>*)out + o;
+        *u = mk<T>(u->x + v.x, u->y + v.y);
+    }
+}
+
+// Reduce-scatter of 16 values over the warp: afterwards lane l holds the
+// warp sum of value (l >> 1) & 15 (lanes 2v and 2v + 1 both hold value v).
+__device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
+#pragma unroll
+    for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// ------------------------------ exact part --------------------------------
+// One CTA per list-free box.  The region's points are staged in shared
+// memory LF_CH at a time, each as its position relative to A's centre (FP32,
+// physical units: integer box offset plus the box-centred local coordinate,
+// so that close pairs keep their relative precision) and its source
+// strength times the image phase.  Warps split the staged points, lanes take
+// every 32nd of a warp's share, and each lane sums LF_OB observers at once;
+// the observers' sums are reduced over the warp and added in shared memory.
+//
+// MODE 0: forward, 1: adjoint (conj(G0)), 2: check only (flags points that
+// coincide modulo the lattice, or that FP32 coordinates cannot tell apart).
+// G0(r) = exp(-j k r)/(4 pi r) = [cos(k r) - j k sinc(k r)] / (4 pi r), with
+// cos and sinc as polynomials in s = r^2 of NT terms (Maclaurin series,
+// NT chosen on the host for the region's largest k r); NT = 0: sincosf.
+template <int MODE, int NT>
+__global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __restrict__ qs, void* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* sX = (float4*)smem;                          // LF_CH
+    float2* sQ = (float2*)(sX + LF_CH);                  // LF_CH
+    float4* sO = (float4*)(sQ + LF_CH);                  // LF_MAXOBS
+    float* sAcc = (float*)(sO + LF_MAXOBS);              // 2 LF_MAXOBS
+    int* sIdx = (int*)(sAcc + 2 * LF_MAXOBS);            // LF_CH (check mode)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = LF_NT / 32;
+    for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
+        const int sA = a.lfslot[j];
+        const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
+        int A[3];
+        box_xyz(a.blist[sA], a.nb, A);
+        const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        const int4 last = a.seg[g1 - 1];
+        const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
+        for (int o0 = 0; o0 < nA; o0 += LF_MAXOBS) {
+            const int no = min(LF_MAXOBS, nA - o0);
+            __syncthreads();
+            for (int i = tid; i < no; i += LF_NT) {
+                const float4 L = a.lfp[m0 + o0 + i];
+                sO[i] = make_float4(L.x * a.hf[0], L.y * a.hf[1], L.z * a.hf[2], 0.f);
+                sAcc[2 * i] = 0.f;
+                sAcc[2 * i + 1] = 0.f;
+            }
+            for (int f0 = 0; f0 < total; f0 += LF_CH) {
+                const int cnt = min(LF_CH, total - f0);
+                __syncthreads();
+                // stage: warp w copies the segments w, w + NW, ... that meet [f0, f0 + cnt)
+                for (int64_t g = g0 + warp; g < g1; g += NW) {
+                    const int4 sg = a.seg[g];
+                    const int p0 = a.bstart[sg.x], len = a.bstart[sg.y] - p0;
+                    const int lo = max(sg.w, f0), hi = min(sg.w + len, f0 + cnt);
+                    if (lo >= hi) continue;
+                    const int ii = sg.z & 255;
+                    const double2 phd = a.phase[ii];
+                    const float2 ph = make_float2((float)phd.x, (float)phd.y);
+                    for (int f = lo + lane; f < hi; f += 32) {
+                        const int nn = p0 + (f - sg.w);
+                        const float4 L = a.lfp[nn];
+                        int Bn[3];
+                        unpack3(__float_as_uint(L.w), Bn[0], Bn[1], Bn[2]);
+                        const float x = ((float)(Bn[0] + a.img[ii][0] * a.nL[0] - A[0]) + L.x) * a.hf[0];
+                        const float y = ((float)(Bn[1] + a.img[ii][1] * a.nL[1] - A[1]) + L.y) * a.hf[1];
+                        const float z = ((float)(Bn[2] + a.img[ii][2] * a.nL[2] - A[2]) + L.z) * a.hf[2];
+                        sX[f - f0] = make_float4(x, y, z, 0.f);
+                        if (MODE == 2) {
+                            sIdx[f - f0] = ii == a.self_img ? nn : -1;
+                        } else {
+                            const float2 q = qs[nn];
+                            sQ[f - f0] = make_float2(q.x * ph.x - q.y * ph.y, q.x * ph.y + q.y * ph.x);
+                        }
+                    }
+                }
+                __syncthreads();
+                if (MODE == 2) {
+                    for (int w = tid; w < no * cnt; w += LF_NT) {
+                        const int i = w / cnt, s = w - i * cnt;
+                        const float4 O = sO[i], X = sX[s];
+                        const float dx = O.x - X.x, dy = O.y - X.y, dz = O.z - X.z;
+                        if (dx * dx + dy * dy + dz * dz == 0.f && sIdx[s] != m0 + o0 + i)
+                            atomicOr(a.status, PIM_DEV_COINCIDENT);
+                    }
+                    continue;
+                }
+                const int ngr = (no + LF_OB - 1) / LF_OB;
+                for (int gi = 0; gi < ngr; ++gi) {
+                    float ox[LF_OB], oy[LF_OB], oz[LF_OB], ar[LF_OB], ai[LF_OB];
+#pragma unroll
+                    for (int k = 0; k < LF_OB; ++k) {
+                        const int i = gi * LF_OB + k;
+                        const float4 O = i < no ? sO[i] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
+                        ox[k] = O.x;
+                        oy[k] = O.y;
+                        oz[k] = O.z;
+                        ar[k] = 0.f;
+                        ai[k] = 0.f;
+                    }
+                    for (int s = warp * 32 + lane; s < cnt; s += LF_NT) {
+                        const float4 X = sX[s];
+                        const float2 q = sQ[s];
+#pragma unroll
+                        for (int k = 0; k < LF_OB; ++k) {
+                            const float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const bool nz = r2 > 0.f;
+                            const float ri = nz ? rsqrtf(r2) : 0.f;
+                            float gr, gim;
+                            if (NT > 0) {
+                                float pcv = a.pc[NT - 1], psv = a.ps[NT - 1];
+#pragma unroll
+                                for (int t = NT - 2; t >= 0; --t) {
+                                    pcv = fmaf(pcv, r2, a.pc[t]);
+                                    psv = fmaf(psv, r2, a.ps[t]);
+                                }
+                                gr = ri * pcv;
+                                gim = nz ? psv : 0.f;
+                            } else {
+                                float sn, cs;
+                                const float rr = r2 * ri;
+                                sincosf((float)a.k * rr, &sn, &cs);
+                                const float s4 = ri * (float)(0.25 / PI);
+                                gr = cs * s4;
+                                gim = -sn * s4;
+                            }
+                            if (MODE == 1) gim = -gim;
+                            ar[k] = fmaf(gr, q.x, fmaf(-gim, q.y, ar[k]));
+                            ai[k] = fmaf(gr, q.y, fmaf(gim, q.x, ai[k]));
+                        }
+                    }
+                    float v[2 * LF_OB];
+#pragma unroll
+                    for (int k = 0; k < LF_OB; ++k) {
+                        v[2 * k] = ar[k];
+                        v[2 * k + 1] = ai[k];
+                    }
+                    const float sum = reduce_scatter16(v, lane);
+                    const int vi = (lane >> 1) & 15;
+                    const int i = gi * LF_OB + (vi >> 1);
+                    if (!(lane & 1) && i < no) atomicAdd(&sAcc[2 * i + (vi & 1)], sum);
+                }
+            }
+            __syncthreads();
+            if (MODE != 2)
+                for (int i = tid; i < no; i += LF_NT)
+                    add_out<float>(a, out, m0 + o0 + i, make_float2(sAcc[2 * i], sAcc[2 * i + 1]));
+        }
+    }
+}
+
+// The same in FP64 from the FP64 positions (one source per lane, no staging of
+// observers in registers: FP64 plans are for accuracy, not speed).
+template <int MODE>
+__global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* __restrict__ qs, void* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double4* sX = (double4*)smem;                        // LF_CH
+    double2* sQ = (double2*)(sX + LF_CH);                // LF_CH
+    int* sIdx = (int*)(sQ + LF_CH);                      // LF_CH
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = LF_NT / 32;
+    for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
+        const int sA = a.lfslot[j];
+        const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
+        const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        const int4 last = a.seg[g1 - 1];
+        const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
+        // thread t sums observer t % nA over the staged points t / nA, + LF_NT / nA ...
+        const int per = max(1, LF_NT / max(nA, 1));
+        for (int o0 = 0; o0 < nA; o0 += LF_NT) {
+            const int no = min(nA - o0, LF_NT);
+            const int stride = no < LF_NT ? per : 1;
+            const int i = tid % no, part = tid / no;
+            const bool act = part < stride;
+            const long long m = m0 + o0 + i;
+            const double px = a.pos[3 * m], py = a.pos[3 * m + 1], pz = a.pos[3 * m + 2];
+            double2 acc = make_double2(0.0, 0.0);
+            for (int f0 = 0; f0 < total; f0 += LF_CH) {
+                const int cnt = min(LF_CH, total - f0);
+                __syncthreads();
+                for (int64_t g = g0 + warp; g < g1; g += NW) {
+                    const int4 sg = a.seg[g];
+                    const int p0 = a.bstart[sg.x], len = a.bstart[sg.y] - p0;
+                    const int lo = max(sg.w, f0), hi = min(sg.w + len, f0 + cnt);
+                    if (lo >= hi) continue;
+                    const int ii = sg.z & 255;
+                    const double2 ph = a.phase[ii];
+                    for (int f = lo + lane; f < hi; f += 32) {
+                        const int nn = p0 + (f - sg.w);
+                        sX[f - f0] = make_double4(a.pos[3 * nn] + a.img[ii][0] * a.D[0],
+                                                  a.pos[3 * nn + 1] + a.img[ii][1] * a.D[1],
+                                                  a.pos[3 * nn + 2] + a.img[ii][2] * a.D[2], 0.0);
+                        sIdx[f - f0] = ii == a.self_img ? nn : -1;
+                        if (MODE != 2) sQ[f - f0] = cmul(qs[nn], ph);
+                    }
+                }
+                __syncthreads();
+                if (!act) continue;
+                for (int s = part; s < cnt; s += stride) {
+                    const double4 X = sX[s];
+                    const double dx = px - X.x, dy = py - X.y, dz = pz - X.z;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 == 0.0) {
+                        if (MODE == 2 && sIdx[s] != m) atomicOr(a.status, PIM_DEV_COINCIDENT);
+                        continue;
+                    }
+                    if (MODE == 2) continue;
+                    const double R = sqrt(r2);
+                    double sn, cs;
+                    sincos(a.k * R, &sn, &cs);
+                    const double s4 = 1.0 / (4.0 * PI * R);
+                    const double2 G = make_double2(cs * s4, (MODE == 1 ? sn : -sn) * s4);
+                    acc = cadd(acc, cmul(G, sQ[s]));
+                }
+            }
+            __syncthreads();
+            // sum the parts of each observer in shared memory (reusing sQ)
+            if (MODE != 2) {
+                if (act) sQ[part * no + i] = acc;
+                __syncthreads();
+                if (tid < no) {
+                    double2 t = make_double2(0.0, 0.0);
+                    for (int k = 0; k < stride; ++k) t = cadd(t, sQ[k * no + tid]);
+                    add_out<double>(a, out, m0 + o0 + tid, t);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------ grid part ---------------------------------
+// One CTA per list-free box:
+//  1. the region's box moments (dense boxes) or points (other boxes), times
+//     their image phase, are added into the local grid Q_A (shared-memory
+//     atomics), work item = (region box, stencil row (jy, jz));
+//  2. V_A = g * Q_A at A's own (P+1)^3 stencil nodes: warps take the
+//     non-empty x-rows of Q_A, lane (ay, az) one output x-row; per input row
+//     the lane holds the g values of its x-offsets in registers and does
+//     (P+1) x EX complex multiply-adds;
+//  3. every point of A subtracts w_m . V_A from its output.
+// The kernel table g(|e|) is in shared memory (FP32) or read through the
+// cache (FP64).
+template <typename T, int P, int EX, bool ADJ>
+__global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>* __restrict__ qs,
+                                                       const cplx<T>* __restrict__ mom,
+                                                       const cplx<T>* __restrict__ gtab, void* out) {
+    constexpr int NP = P + 1, RW = NP * NP, NW = LF_GNT / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int E = a.E, H1 = a.H + 1;
+    const int ncell = E * E * EX;
+    T* Qr = (T*)smem;
+    T* Qi = Qr + ncell;
+    cplx<T>* Vp = (cplx<T>*)(Qi + ncell);                   // NW x NP^3
+    int* rowflag = (int*)(Vp + NW * NP * NP * NP);           // E^2
+    int* rows = rowflag + E * E;                             // E^2
+    int* nrows = rows + E * E;                               // 1
+    cplx<T>* gs = (cplx<T>*)(((uintptr_t)(nrows + 1) + 15) & ~(uintptr_t)15);  // H1^3 (FP32)
+    const cplx<T>* gt = sizeof(T) == 4 ? gs : gtab;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (sizeof(T) == 4)
+        for (int i = tid; i < H1 * H1 * H1; i += LF_GNT) gs[i] = gtab[i];
+    for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
+        const int sA = a.lfslot[j];
+        const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
+        int A[3], org[3], X0[3];
+        box_xyz(a.blist[sA], a.nb, A);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            org[d] = A[d] - a.R - 2 * a.c;
+            X0[d] = box_stencil(A[d], a.c, a.n[d], a.p) - org[d];
+        }
+        const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        __syncthreads();
+        for (int i = tid; i < ncell; i += LF_GNT) {
+            Qr[i] = T(0);
+            Qi[i] = T(0);
+        }
+        for (int i = tid; i < E * E; i += LF_GNT) rowflag[i] = 0;
+        __syncthreads();
+        // 1. local grid of the region's charges
+        const int4 last = a.seg[g1 - 1];
+        const int nslots = (last.z >> 8) + (last.y - last.x);
+        for (int w = tid; w < nslots * RW; w += LF_GNT) {
+            const int f = w / RW, rr = w - f * RW;
+            const int gy = rr % NP, gz = rr / NP;
+            int64_t lo = g0, hi = g1 - 1;  // last segment whose slot offset <= f
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if ((a.seg[mid].z >> 8) <= f) lo = mid;
+                else hi = mid - 1;
+            }
+            const int4 sg = a.seg[lo];
+            const int s = sg.x + (f - (sg.z >> 8));
+            const int ii = sg.z & 255;
+            int B[3], loc[3];
+            box_xyz(a.blist[s], a.nb, B);
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                loc[d] = box_stencil(B[d], a.c, a.n[d], a.p) + a.img[ii][d] * a.nL[d] - org[d];
+                ok = ok && loc[d] >= 0 && loc[d] + P < E;
+            }
+            if (!ok) {
+                atomicOr(a.status, PIM_DEV_BOUNDS);
+                continue;
+            }
+            cplx<T> v[NP];
+#pragma unroll
+            for (int jx = 0; jx < NP; ++jx) v[jx] = mk<T>(T(0), T(0));
+            const int di = a.dix[s];
+            if (di >= 0) {
+                const cplx<T>* mr = mom + (((long long)di * NP + gz) * NP + gy) * NP;
+#pragma unroll
+                for (int jx = 0; jx < NP; ++jx) v[jx] = mr[jx];
+            } else {
+                for (int nn = a.bstart[s]; nn < a.bstart[s + 1]; ++nn) {
+                    T t[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * nn + d] : (T)a.nt[3 * nn + d];
+                    T wx[NP];
+                    lagrange_w<T, P>(t[0], wx);
+                    const T wyz = lag1<T, P>(t[1], gy) * lag1<T, P>(t[2], gz);
+                    const cplx<T> q = qs[nn];
+#pragma unroll
+                    for (int jx = 0; jx < NP; ++jx) {
+                        v[jx].x += wx[jx] * wyz * q.x;
+                        v[jx].y += wx[jx] * wyz * q.y;
+                    }
+                }
+            }
+            const double2 phd = a.phase[ii];
+            const cplx<T> ph = mk<T>((T)phd.x, (T)phd.y);
+            const int row = (loc[2] + gz) * E + (loc[1] + gy);
+            T* qr = Qr + row * EX + loc[0];
+            T* qi = Qi + row * EX + loc[0];
+#pragma unroll
+            for (int jx = 0; jx < NP; ++jx) {
+                const cplx<T> x = cmul(v[jx], ph);
+                atomicAdd(qr + jx, x.x);
+                atomicAdd(qi + jx, x.y);
+            }
+            rowflag[row] = 1;
+        }
+        __syncthreads();
+        // non-empty rows, in order
+        if (warp == 0) {
+            int base = 0;
+            for (int r0 = 0; r0 < E * E; r0 += 32) {
+                const bool f = r0 + lane < E * E && rowflag[r0 + lane];
+                const unsigned b = __ballot_sync(0xffffffffu, f);
+                if (f) rows[base + __popc(b & ((1u << lane) - 1u))] = r0 + lane;
+                base += __popc(b);
+            }
+            if (lane == 0) *nrows = base;
+        }
+        __syncthreads();
+        // 2. V_A = g * Q_A at A's stencil nodes
+        {
+            cplx<T> acc[NP];
+#pragma unroll
+            for (int jx = 0; jx < NP; ++jx) acc[jx] = mk<T>(T(0), T(0));
+            const int ay = lane % NP, az = lane / NP;
+            const int oy = X0[1] + ay, oz = X0[2] + az;
+            const int nr = *nrows;
+            if (lane < RW) {
+                for (int ri = warp; ri < nr; ri += NW) {
+                    const int row = rows[ri];
+                    const int cy = row % E, cz = row / E;
+                    const cplx<T>* grow = gt + ((long long)abs(oz - cz) * H1 + abs(oy - cy)) * H1;
+                    const T* qr = Qr + row * EX;
+                    const T* qi = Qi + row * EX;
+                    // input nodes cb..cb+7: output jx and input cb + i are
+                    // e = X0 + jx - cb - i apart, held as gb[jx - i + 7]
+#pragma unroll 1
+                    for (int cb = 0; cb < EX; cb += 8) {
+                        cplx<T> gb[8 + P];
+#pragma unroll
+                        for (int k = 0; k < 8 + P; ++k) {
+                            gb[k] = grow[min(abs(X0[0] - cb - 7 + k), a.H)];
+                            if (ADJ) gb[k].y = -gb[k].y;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const T xr = qr[cb + i], xi = qi[cb + i];
+#pragma unroll
+                            for (int jx = 0; jx < NP; ++jx) {
+                                const cplx<T> g = gb[jx - i + 7];
+                                acc[jx].x += g.x * xr - g.y * xi;
+                                acc[jx].y += g.x * xi + g.y * xr;
+                            }
+                        }
+                    }
+                }
+                (void)oy;
+#pragma unroll
+                for (int jx = 0; jx < NP; ++jx) Vp[warp * NP * NP * NP + lane * NP + jx] = acc[jx];
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < NP * NP * NP; i += LF_GNT) {
+            cplx<T> t = Vp[i];
+            for (int w = 1; w < NW; ++w) t = cadd(t, Vp[w * NP * NP * NP + i]);
+            Vp[i] = t;
+        }
+        __syncthreads();
+        // 3. the grid part of every point of A
+        for (int i = tid; i < nA; i += LF_GNT) {
+            // V is re-read per point: hoisting its NP^3 values out of this
+            // loop would not fit in registers
+            asm volatile("" ::: "memory");
+            const long long m = m0 + i;
+            T t[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * m + d] : (T)a.nt[3 * m + d];
+            T wx[NP], wy[NP], wz[NP];
+            lagrange_w<T, P>(t[0], wx);
+            lagrange_w<T, P>(t[1], wy);
+            lagrange_w<T, P>(t[2], wz);
+            cplx<T> gsum = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int jz = 0; jz < NP; ++jz)
+#pragma unroll
+                for (int jy = 0; jy < NP; ++jy) {
+                    cplx<T> r = mk<T>(T(0), T(0));
+#pragma unroll
+                    for (int jx = 0; jx < NP; ++jx) {
+                        const cplx<T> vv = Vp[(jz * NP + jy) * NP + jx];
+                        r.x += wx[jx] * vv.x;
+                        r.y += wx[jx] * vv.y;
+                    }
+                    const T w = wy[jy] * wz[jz];
+                    gsum.x += w * r.x;
+                    gsum.y += w * r.y;
+                }
+            add_out<T>(a, out, m, mk<T>(-gsum.x, -gsum.y));
+        }
+    }
+}
+
+// g(|e|) on the offsets 0..H per axis: G0(|e o h|), g(0) = 0 (the grid
+// kernel of the near table at zero offset)
+template <typename T>
+__global__ void lf_table_kernel(cplx<T>* g, int H, double h0, double h1, double h2, double k) {
+    const int H1 = H + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H1 * H1 * H1; e += gridDim.x * blockDim.x) {
+        const int x = e % H1, y = (e / H1) % H1, z = e / (H1 * H1);
+        const double r = sqrt((x * h0) * (x * h0) + (y * h1) * (y * h1) + (z * h2) * (z * h2));
+        double sn = 0.0, cs = 0.0;
+        if (r > 0.0) sincos(k * r, &sn, &cs);
+        const double s4 = r > 0.0 ? 1.0 / (4.0 * PI * r) : 0.0;
+        g[e] = mk<T>((T)(cs * s4), (T)(-sn * s4));
+    }
+}
+
+LfArgs lf_args(pim_plan P, const LfGeom& G) {
+    const PointsData& d = P->pts;
+    LfArgs a{};
+    a.lfslot = d.lfslot;
+    a.segptr = d.segptr;
+    a.seg = d.seg;
+    a.bstart = d.bstart;
+    a.blist = d.blist;
+    a.dix = d.dix;
+    a.lfp = d.lfp;
+    a.pos = d.pos;
+    a.nt = d.nt;
+    a.ntd = d.ntd;
+    a.perm = d.perm;
+    a.phase = P->dphase;
+    for (int i = 0; i < 3; ++i) {
+        a.nb[i] = P->nb[i];
+        a.nL[i] = P->n[i] - 1;
+        a.n[i] = P->n[i];
+        a.h[i] = P->h[i];
+        a.D[i] = P->D[i];
+        a.hf[i] = (float)P->h[i];
+    }
+    a.p = P->p;
+    a.c = G.c;
+    a.R = G.R;
+    a.E = G.E;
+    a.H = G.H;
+    a.nimg = P->nimg;
+    a.self_img = -1;
+    for (int i = 0; i < P->nimg; ++i) {
+        for (int k = 0; k < 3; ++k) a.img[i][k] = P->img[i][k];
+        if (P->img[i][0] == 0 && P->img[i][1] == 0 && P->img[i][2] == 0) a.self_img = i;
+    }
+    a.k = P->k;
+    // cos(k r) / (4 pi) = sum_t (-k^2)^t s^t / ((2t)! 4 pi),
+    // -k sinc(k r) / (4 pi) = -k sum_t (-k^2)^t s^t / ((2t+1)! 4 pi)
+    double f2 = 1.0, f1 = 1.0, pw = 1.0;
+    for (int t = 0; t < LF_MAXNT; ++t) {
+        if (t > 0) {
+            f2 *= (2.0 * t - 1.0) * (2.0 * t);
+            f1 *= (2.0 * t) * (2.0 * t + 1.0);
+            pw *= -P->k * P->k;
+        }
+        a.pc[t] = (float)(pw / f2 / (4.0 * PI));
+        a.ps[t] = (float)(-P->k * pw / f1 / (4.0 * PI));
+    }
+    a.nlf = d.nlf;
+    a.status = P->dstatus;
+    return a;
+}
+
+size_t lf_exact_smem(bool f64) {
+    if (f64) return LF_CH * (sizeof(double4) + sizeof(double2) + sizeof(int));
+    return LF_CH * (sizeof(float4) + sizeof(float2) + sizeof(int)) + LF_MAXOBS * (sizeof(float4) + 2 * sizeof(float));
+}
+
+template <typename T, int P>
+size_t lf_grid_smem(const LfGeom& G) {
+    constexpr int NP = P + 1;
+    const size_t base = 2 * sizeof(T) * (size_t)G.E * G.E * G.EX + sizeof(cplx<T>) * (LF_GNT / 32) * NP * NP * NP +
+                        sizeof(int) * (2 * (size_t)G.E * G.E + 1) + 16;
+    const size_t H1 = (size_t)G.H + 1;
+    return base + (sizeof(T) == 4 ? sizeof(cplx<T>) * H1 * H1 * H1 : 0);
+}
+
+template <typename K>
+pim_status set_smem(K kern, size_t bytes) {
+    PIM_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return PIM_OK;
+}
+
+int lf_grid_blocks(long long nlf) { return (int)std::min<long long>(nlf, 152LL * 64); }
+
+template <int MODE>
+pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, void* dst, cudaStream_t s) {
+    const size_t sm = lf_exact_smem(false);
+    const int nb = lf_grid_blocks(a.nlf);
+    pim_status st;
+#define PIM_LF_EX(NTV)                                                                              \
+    do {                                                                                            \
+        if ((st = set_smem(lf_exact_f32<MODE, NTV>, sm)) != PIM_OK) return st;                      \
+        lf_exact_f32<MODE, NTV><<<nb, LF_NT, sm, s>>>(a, (const float2*)qs, dst);                   \
+    } while (0)
+    if (MODE == 2 || G.nterm == 0) PIM_LF_EX(0);
+    else if (G.nterm <= 4) PIM_LF_EX(4);
+    else if (G.nterm <= 6) PIM_LF_EX(6);
+    else PIM_LF_EX(8);
+#undef PIM_LF_EX
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <int MODE>
+pim_status launch_exact_f64(const LfArgs& a, const void* qs, void* dst, cudaStream_t s) {
+    const size_t sm = lf_exact_smem(true);
+    pim_status st;
+    if ((st = set_smem(lf_exact_f64<MODE>, sm)) != PIM_OK) return st;
+    lf_exact_f64<MODE><<<lf_grid_blocks(a.nlf), LF_NT, sm, s>>>(a, (const double2*)qs, dst);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <typename T, int P, int EX>
+pim_status launch_grid(const LfGeom& G, const LfArgs& a, bool adj, const void* qs, const void* mom, const void* gtab,
+                       void* dst, cudaStream_t s) {
+    const size_t sm = lf_grid_smem<T, P>(G);
+    pim_status st;
+    if (adj) {
+        if ((st = set_smem(lf_grid_kernel<T, P, EX, true>, sm)) != PIM_OK) return st;
+        lf_grid_kernel<T, P, EX, true><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(
+            a, (const cplx<T>*)qs, (const cplx<T>*)mom, (const cplx<T>*)gtab, dst);
+    } else {
+        if ((st = set_smem(lf_grid_kernel<T, P, EX, false>, sm)) != PIM_OK) return st;
+        lf_grid_kernel<T, P, EX, false><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(
+            a, (const cplx<T>*)qs, (const cplx<T>*)mom, (const cplx<T>*)gtab, dst);
+    }
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <typename T, int P>
+pim_status launch_grid_p(const LfGeom& G, const LfArgs& a, bool adj, const void* qs, const void* mom,
+                         const void* gtab, void* dst, cudaStream_t s) {
+    if (G.EX == 16) return launch_grid<T, P, 16>(G, a, adj, qs, mom, gtab, dst, s);
+    return launch_grid<T, P, 24>(G, a, adj, qs, mom, gtab, dst, s);
+}
+
+template <typename T>
+pim_status launch_grid_t(const LfGeom& G, const LfArgs& a, bool adj, const void* qs, const void* mom,
+                         const void* gtab, void* dst, cudaStream_t s) {
+    switch (a.p) {
+        case 2: return launch_grid_p<T, 2>(G, a, adj, qs, mom, gtab, dst, s);
+        case 3: return launch_grid_p<T, 3>(G, a, adj, qs, mom, gtab, dst, s);
+        default: return launch_grid_p<T, 4>(G, a, adj, qs, mom, gtab, dst, s);
+    }
+}
+
+}  // namespace
+
+LfGeom lf_geom(const pim_plan_s* P) {
+    LfGeom G{};
+    G.c = P->p / 2;
+    G.R = P->b + 1;
+    G.E = 2 * G.R + 2 * G.c + P->p + 1;
+    G.H = G.R + 2 * G.c + P->p;
+    G.EX = G.E <= 16 ? 16 : (G.E <= 24 ? 24 : 0);
+    // the largest k r between an observer of a box and a point of its region:
+    // box offsets up to R per axis plus half a box on each side
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) r2 += ((G.R + 1) * P->h[d]) * ((G.R + 1) * P->h[d]);
+    const double x = P->k * std::sqrt(r2);
+    // truncation of the cos series after t terms: x^(2t) / (2t)! (sinc: smaller)
+    G.nterm = 0;
+    double term = 1.0;
+    for (int t = 1; t <= LF_MAXNT; ++t) {
+        term *= x * x / ((2.0 * t - 1.0) * (2.0 * t));
+        if (term < 1.5e-8) {
+            G.nterm = std::max(t, 2);
+            break;
+        }
+    }
+    if (P->k == 0.0) G.nterm = 2;
+    if (G.EX) {
+        // the grid part's shared memory must fit one CTA
+        const size_t NP = P->p + 1, H1 = G.H + 1;
+        const size_t ts = P->prec == PIM_FP64 ? 8 : 4;
+        const size_t sm = 2 * ts * G.E * G.E * G.EX + 2 * ts * (LF_GNT / 32) * NP * NP * NP + 4 * (2 * G.E * G.E + 1) +
+                          16 + (ts == 4 ? 8 * H1 * H1 * H1 : 0);
+        if (sm > 227 * 1024) G.EX = 0;
+    }
+    return G;
+}
+
+pim_status lf_build_table(pim_plan P, cudaStream_t s) {
+    PointsData& d = P->pts;
+    const LfGeom G = lf_geom(P);
+    const size_t H1 = G.H + 1;
+    const size_t bytes = H1 * H1 * H1 * (P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2));
+    pim_status st;
+    if (!d.lfg && (st = pim_alloc(P, &d.lfg, bytes)) != PIM_OK) return st;
+    if (P->prec == PIM_FP64)
+        lf_table_kernel<double><<<64, 256, 0, s>>>((double2*)d.lfg, G.H, P->h[0], P->h[1], P->h[2], P->k);
+    else
+        lf_table_kernel<float><<<64, 256, 0, s>>>((float2*)d.lfg, G.H, P->h[0], P->h[1], P->h[2], P->k);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+// Flags pairs of list-free boxes that coincide (set-points check; the
+// stored list checks its own pairs when it computes their values).
+pim_status lf_check(pim_plan P, cudaStream_t s) {
+    if (P->pts.nlf == 0) return PIM_OK;
+    const LfGeom G = lf_geom(P);
+    const LfArgs a = lf_args(P, G);
+    if (P->prec == PIM_FP64) return launch_exact_f64<2>(a, nullptr, nullptr, s);
+    return launch_exact_f32<2>(G, a, nullptr, nullptr, s);
+}
+
+// Adds the list-free boxes' corrections to the apply's output: the exact
+// part, then minus the grid part (both read-modify-write dst after the
+// gather has written it).  qs: sorted sources of right-hand side r.
+pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
+                    cudaStream_t s) {
+    if (P->pts.nlf == 0) return PIM_OK;
+    const LfGeom G = lf_geom(P);
+    LfArgs a = lf_args(P, G);
+    a.nrhs = nrhs;
+    a.r = r;
+    a.real_out = P->real_data && !sorted_out ? 1 : 0;
+    a.sorted_out = sorted_out ? 1 : 0;
+    pim_status st;
+    if (P->prec == PIM_FP64) {
+        st = adj ? launch_exact_f64<1>(a, qs, dst, s) : launch_exact_f64<0>(a, qs, dst, s);
+        if (st != PIM_OK) return st;
+        st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    } else {
+        st = adj ? launch_exact_f32<1>(G, a, qs, dst, s) : launch_exact_f32<0>(G, a, qs, dst, s);
+        if (st != PIM_OK) return st;
+        st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    }
+    P->launches += 2;
+    return st;
+}

@@ -188,7 +188,30 @@ struct PointsData {
     double2* dval = nullptr;      // 3 nnz: d/dr_m of the values (with_gradient)
     float2* dvalf = nullptr;      // 3 nnz: their FP32 heads (compact mode; read for a row's complex64 part)
     int64_t nnz = 0;
+    int* dix = nullptr;           // nne: dense index of each non-empty box, -1 if not dense
+    // list-free correction: observer boxes whose correction is recomputed by
+    // every apply (exact sum over the region's points minus the region's grid
+    // interaction through a local grid of box moments); their rows of the
+    // stored list are empty
+    int64_t nlf = 0;              // list-free observer boxes
+    int* lfslot = nullptr;        // nlf: slot of each
+    int64_t* segptr = nullptr;    // nlf + 1: first region segment of each
+    int4* seg = nullptr;          // nseg: (first slot, end slot, image | slot offset << 8, point offset)
+    int64_t nseg = 0;
+    float4* lfp = nullptr;        // N: box-centred local coordinates (grid steps) and the packed box (w bits)
+    void* lfg = nullptr;          // (H+1)^3 grid kernel g(|e|) on the offsets of the local grid, plan precision
+    int64_t lf_points = 0;        // points in list-free boxes
+    int64_t lf_pairs = 0;         // (observer, source, image) pairs their correction sums per apply
 };
+
+// Geometry of the list-free correction's local grid (see listfree.cu): c =
+// floor(p/2), R = b + 1 the box reach of the correction region, E = 2R + 2c +
+// p + 1 nodes per axis, H = R + 2c + p the largest node offset.
+struct LfGeom {
+    int c, R, E, H, EX;           // EX: padded x-length of a local grid row (16 or 24), 0 if unsupported
+    int nterm;                    // terms of the exact kernel's cos / sinc polynomials; 0: sincos
+};
+LfGeom lf_geom(const pim_plan_s* P);
 
 struct pim_plan_s {
     // geometry and method parameters
@@ -196,7 +219,6 @@ struct pim_plan_s {
     unsigned pmask = 0;
     int npd = 0;                  // number of periodic axes
     int n[3], nb[3], p, layers, b, cube, nf[3], pf, prec, corr_mode;
-    int tile[3];
     bool npsp = false;
     bool real_data = false;
     double neutral_tol, series_tol;
@@ -258,6 +280,7 @@ struct pim_plan_s {
     bool no_multi = false;        // keep the fused per-RHS path (set by pim_apply_noalloc)
     int autotune = 1;
     int with_gradient = 0;
+    int lf_min_work = 0;          // list-free boxes: n_box x region points >= this (0: off)
     void* gD = nullptr;           // second full grid (adjoint potential of the gradient)
     void* gsrt = nullptr;         // sorted upstream gradient g, complex<T>, N
     double2* fD = nullptr;        // second far grid
@@ -329,6 +352,12 @@ pim_status alloc_grad_buffers(pim_plan P);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
 pim_status lanes_prepare(pim_plan P, int nlanes);
 void lanes_free(pim_plan P);
+
+// listfree.cu
+pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
+                    cudaStream_t s);
+pim_status lf_check(pim_plan P, cudaStream_t s);
+pim_status lf_build_table(pim_plan P, cudaStream_t s);
 
 // batch.cu
 void batch_forget(pim_plan P);

@@ -273,9 +273,10 @@ __device__ __forceinline__ int isqrt_floor(int r) {
 }
 
 // Visits every (image, source box row) of the correction region of the
-// point in box B: calls f(image, first sorted slot, end slot).
+// point in box B: calls f(image, box row, x0, x1, first sorted slot, end
+// slot) for the boxes x0..x1 of that row that hold points.
 template <typename F>
-__device__ __forceinline__ void for_each_region_row(const PairArgs& a, const int* box_ptr, const int B[3], F f) {
+__device__ __forceinline__ void for_each_region_span(const PairArgs& a, const int* box_ptr, const int B[3], F f) {
     const int R = a.b + 1;
     for (int ii = 0; ii < a.nimg; ++ii) {
         int cb[3];
@@ -303,9 +304,90 @@ __device__ __forceinline__ void for_each_region_row(const PairArgs& a, const int
                 if (x0 > x1) continue;
                 const long long row = ((long long)bz * a.nb[1] + by) * a.nb[0];
                 const int lo = box_ptr[row + x0], hi = box_ptr[row + x1 + 1];
-                if (hi > lo) f(ii, lo, hi);
+                if (hi > lo) f(ii, row, x0, x1, lo, hi);
             }
         }
+    }
+}
+
+// The same with f(image, first sorted slot, end slot).
+template <typename F>
+__device__ __forceinline__ void for_each_region_row(const PairArgs& a, const int* box_ptr, const int B[3], F f) {
+    for_each_region_span(a, box_ptr, B, [&](int ii, long long, int, int, int lo, int hi) { f(ii, lo, hi); });
+}
+
+// ------------------------------- list-free boxes ---------------------------
+// A non-empty box whose correction work (its points times its region's
+// points, the same for every point of the box) is at least thr is corrected
+// list-free by every apply; its points' rows of the stored list are emptied.
+__global__ void lf_flag_kernel(const int* bstart, long long nne, const int* rowlen, long long thr, int* flag,
+                               unsigned long long* tot) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x) {
+        const int m0 = bstart[s], nA = bstart[s + 1] - m0;
+        const long long work = (long long)nA * rowlen[m0];
+        const bool f = thr > 0 && work >= thr;
+        flag[s] = f ? 1 : 0;
+        if (f) {
+            atomicAdd(&tot[0], (unsigned long long)work);
+            atomicAdd(&tot[1], (unsigned long long)nA);
+        }
+    }
+}
+
+__global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, const int* bstart, int* lfslot,
+                               int* rowlen) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x) {
+        if (!flag[s]) continue;
+        lfslot[pos[s]] = (int)s;
+        for (int m = bstart[s]; m < bstart[s + 1]; ++m) rowlen[m] = 0;
+    }
+}
+
+// Region segments of every list-free box: one per (image, box row) span with
+// points, as (first slot, end slot, image | slot offset << 8, point offset),
+// the offsets counted from the box's first segment.  seg == nullptr: counts.
+__global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* lfslot,
+                              long long nlf, const int64_t* segptr, int* cnt, int4* seg) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nlf; j += (long long)gridDim.x * blockDim.x) {
+        const int b = blist[lfslot[j]];
+        const int B[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
+        int c = 0, soff = 0, ptoff = 0;
+        const int64_t o = seg ? segptr[j] : 0;
+        for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int lo, int hi) {
+            int fs = -1, ls = -1;
+            for (int x = x0; x <= x1; ++x) {
+                const int sl = bslot[row + x];
+                if (sl >= 0) {
+                    if (fs < 0) fs = sl;
+                    ls = sl;
+                }
+            }
+            if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
+            soff += ls + 1 - fs;
+            ptoff += hi - lo;
+            ++c;
+        });
+        if (!seg) cnt[j] = c;
+    }
+}
+
+// Box-centred local coordinates u - (B + 1/2 for odd p) in grid steps, FP32,
+// and the packed box (its bits in w).  old != nullptr keeps the boxes of an
+// earlier call (frozen topology).
+__global__ void lf_point_kernel(const double* pos, long long N, double h0, double h1, double h2, int nb0, int nb1,
+                                int nb2, int p, const float4* old, float4* lfp) {
+    const double h[3] = {h0, h1, h2};
+    const int nb[3] = {nb0, nb1, nb2};
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        int B[3];
+        if (old) unpack3(__float_as_uint(old[m].w), B[0], B[1], B[2]);
+        float c[3];
+        for (int d = 0; d < 3; ++d) {
+            const double u = pos[3 * m + d] / h[d];
+            if (!old) B[d] = box_of(u, nb[d], p);
+            c[d] = (float)(u - (B[d] + ((p & 1) ? 0.5 : 0.0)));
+        }
+        lfp[m] = make_float4(c[0], c[1], c[2], __uint_as_float(pack3(B[0], B[1], B[2])));
     }
 }
 
@@ -485,6 +567,9 @@ __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const do
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long m = warp; m < N; m += nwarps) {
+        // every stored row holds at least the point itself: an empty row is
+        // one of a list-free box
+        if (row_ptr[m + 1] == row_ptr[m]) continue;
         int B[3];
         for (int d = 0; d < 3; ++d) B[d] = box_of(pos[3 * m + d] / a.h[d], a.pa.nb[d], a.pa.p);
         long long off = row_ptr[m];
@@ -672,6 +757,60 @@ FillArgs fill_args(pim_plan P, const PairArgs& pr) {
 
 }  // namespace
 
+// Chooses the list-free boxes (lf_flag_kernel), empties their rows in
+// rowlen, and builds their region segments, box-centred coordinates and the
+// grid-kernel table of the local grid.
+static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaStream_t s) {
+    PointsData& d = P->pts;
+    d.nlf = d.nseg = d.lf_points = d.lf_pairs = 0;
+    const long long nne = d.nne;
+    if (P->lf_min_work <= 0 || d.N == 0 || nne == 0 || !lf_geom(P).EX) return PIM_OK;
+    pim_status st;
+    int *flag = nullptr, *pos = nullptr;
+    unsigned long long* tot = nullptr;
+    if ((st = pim_alloc(P, (void**)&flag, (size_t)nne * sizeof(int))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&pos, (size_t)(nne + 1) * sizeof(int))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&tot, 2 * sizeof(unsigned long long))) != PIM_OK) return st;
+    PIM_CK(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s));
+    lf_flag_kernel<<<1024, 256, 0, s>>>(d.bstart, nne, rowlen, P->lf_min_work, flag, tot);
+    PIM_CK(cudaGetLastError());
+    if ((st = scan<int>(P, flag, pos, nne, s)) != PIM_OK) return st;
+    int nlf = 0;
+    unsigned long long ht[2] = {0, 0};
+    PIM_CK(cudaMemcpy(&nlf, pos + nne, sizeof(int), cudaMemcpyDeviceToHost));
+    PIM_CK(cudaMemcpy(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost));
+    if (nlf > 0) {
+        if ((st = pim_alloc(P, (void**)&d.lfslot, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
+        lf_list_kernel<<<1024, 256, 0, s>>>(flag, pos, nne, d.bstart, d.lfslot, rowlen);
+        PIM_CK(cudaGetLastError());
+        int* cnt = flag;  // reuse (nlf <= nne)
+        const unsigned nb = (unsigned)std::min<long long>((nlf + 127) / 128, 152 * 16);
+        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.lfslot, nlf, nullptr, cnt, nullptr);
+        PIM_CK(cudaGetLastError());
+        if ((st = pim_alloc(P, (void**)&d.segptr, (size_t)(nlf + 1) * sizeof(int64_t))) != PIM_OK) return st;
+        if ((st = scan<int64_t>(P, cnt, d.segptr, nlf, s)) != PIM_OK) return st;
+        int64_t nseg = 0;
+        PIM_CK(cudaMemcpy(&nseg, d.segptr + nlf, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if ((st = pim_alloc(P, (void**)&d.seg, (size_t)nseg * sizeof(int4))) != PIM_OK) return st;
+        d.nseg = nseg;
+        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.lfslot, nlf, d.segptr, nullptr, d.seg);
+        PIM_CK(cudaGetLastError());
+        if ((st = pim_alloc(P, (void**)&d.lfp, (size_t)d.N * sizeof(float4))) != PIM_OK) return st;
+        lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, d.N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
+                                             nullptr, d.lfp);
+        PIM_CK(cudaGetLastError());
+        if ((st = lf_build_table(P, s)) != PIM_OK) return st;
+    }
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, flag, (size_t)nne * sizeof(int));
+    pim_free(P, pos, (size_t)(nne + 1) * sizeof(int));
+    pim_free(P, tot, 2 * sizeof(unsigned long long));
+    d.nlf = nlf;
+    d.lf_pairs = (int64_t)ht[0];
+    d.lf_points = (int64_t)ht[1];
+    return PIM_OK;
+}
+
 // New positions for the current points with the discrete structure kept.
 // Splits every row of a compact-mode list (split_rows_kernel) out of place.
 static pim_status split_rows(pim_plan P, cudaStream_t s) {
@@ -738,6 +877,9 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
     if (N > 0)
         point_update_kernel<<<1024, 256, 0, s>>>(xyz, d.perm, N, pa, dD, d.pos, d.ns, d.nt, d.ntd, d.fs, d.fo, d.ft,
                                                  d.ftd, P->dstatus);
+    if (N > 0 && d.lfp)
+        lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
+                                             d.lfp, d.lfp);
     PIM_CK(cudaGetLastError());
     int hstat = 0;
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -819,6 +961,16 @@ void points_free(pim_plan P) {
     pim_free(P, d.dval, 3 * d.nnz * sizeof(double2));
     pim_free(P, d.dvalf, 3 * d.nnz * sizeof(float2));
     pim_free(P, d.nbig, (size_t)std::max<int64_t>(1, d.N) * sizeof(int));
+    pim_free(P, d.dix, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
+    pim_free(P, d.lfslot, (size_t)d.nlf * sizeof(int));
+    pim_free(P, d.segptr, (size_t)(d.nlf + 1) * sizeof(int64_t));
+    pim_free(P, d.seg, (size_t)d.nseg * sizeof(int4));
+    pim_free(P, d.lfp, N * sizeof(float4));
+    if (d.lfg) {
+        const LfGeom G = lf_geom(P);
+        const size_t H1 = G.H + 1;
+        pim_free(P, d.lfg, H1 * H1 * H1 * (P->prec == PIM_FP64 ? sizeof(double2) : sizeof(float2)));
+    }
     d = PointsData{};
 }
 
@@ -904,7 +1056,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
                                                 d.ent, d.esx);
         PIM_CK(cudaGetLastError());
         PIM_CK(cudaStreamSynchronize(s));
-        pim_free(P, dix, (size_t)std::max(1, nne) * sizeof(int));
+        d.dix = dix;  // kept: the list-free correction reads the dense boxes' moments
         pim_free(P, dpos, (size_t)(nne + 1) * sizeof(int));
         pim_free(P, pos, (nboxes + 1) * sizeof(int));
     }
@@ -946,6 +1098,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     int* rowlen = key;  // reuse
     if (N > 0) pair_count_kernel<<<1024, 256, 0, s>>>(d.pos, N, dh, pr, d.box_ptr, rowlen);
     PIM_CK(cudaGetLastError());
+    if ((st = lf_classify(P, rowlen, pr, s)) != PIM_OK) return st;
     if ((st = pim_alloc(P, (void**)&d.row_ptr, (N + 1) * sizeof(int64_t))) != PIM_OK) return st;
     if ((st = scan<int64_t>(P, rowlen, d.row_ptr, N, s)) != PIM_OK) return st;
     int64_t nnz = 0;
@@ -972,6 +1125,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
         pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.row_ptr, d.col, d.val,
                                                    d.valdf, d.valf, d.valt, d.dval, P->dstatus);
     PIM_CK(cudaGetLastError());
+    if ((st = lf_check(P, s)) != PIM_OK) return st;
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, gtab, gsz);

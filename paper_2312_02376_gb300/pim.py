@@ -30,10 +30,10 @@ STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply"]
 
 class pim_options(ctypes.Structure):
     _fields_ = [("far_n", ctypes.c_int * 3), ("far_p", ctypes.c_int), ("corr_radius", ctypes.c_int),
-                ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int),
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
                 ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int), ("corr_split", ctypes.c_int),
-                ("gather_variant", ctypes.c_int)]
+                ("gather_variant", ctypes.c_int), ("corr_listfree", ctypes.c_int)]
 
 
 class pim_info(ctypes.Structure):
@@ -42,7 +42,8 @@ class pim_info(ctypes.Structure):
                 ("periodic_mask", ctypes.c_int), ("near_layers", ctypes.c_int), ("N", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double),
                 ("points_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("gather_variant", ctypes.c_int),
-                ("gather_variants", ctypes.c_int)]
+                ("gather_variants", ctypes.c_int), ("lf_boxes", ctypes.c_int64), ("lf_points", ctypes.c_int64),
+                ("lf_pairs", ctypes.c_int64)]
 
 
 class PimError(RuntimeError):
@@ -251,11 +252,11 @@ class Plan:
     n          near grid nodes per axis (h = D / (n - 1))
     p          near Lagrange degree; layers = near-image layers i_d
     precision  "fp64" or "fp32"
-    b, nf, pf, corr_mode, cube, tile: options (None = library default)
+    b, nf, pf, corr_mode, cube, listfree: options (None = library default)
     """
 
     def __init__(self, D, pdims, k, k0, n, p=4, layers=1, precision="fp32", b=None, nf=None, pf=None,
-                 corr_mode=None, cube=False, tile=None, neutral_tol=None, mem_cap=0, autotune=None,
+                 corr_mode=None, cube=False, listfree=None, neutral_tol=None, mem_cap=0, autotune=None,
                  with_gradient=False, gather_variant=None, corr_split=None, stream=None):
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
@@ -273,9 +274,8 @@ class Plan:
             opt.far_p = int(pf)
         if corr_mode is not None:
             opt.corr_mode = int(corr_mode)
-        if tile is not None:  # ignored by the library (see pim_options.tile)
-            for d in range(3):
-                opt.tile[d] = int(tile[d])
+        if listfree is not None:
+            opt.corr_listfree = int(listfree)
         if neutral_tol is not None:
             opt.neutral_tol = float(neutral_tol)
         opt.corr_cube = 1 if cube else 0

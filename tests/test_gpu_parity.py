@@ -272,7 +272,7 @@ def test_edge_cases_faces_single_box_and_tiny():
                         "fp64", len(pts), 1, pts, rng.standard_normal(len(pts)) + 1j * rng.standard_normal(len(pts)))
     o = oracle_plan(W)
     ue = o.apply(W.q)
-    pl = gpu_plan(W, "fp64", tile=(8, 4, 4))
+    pl = gpu_plan(W, "fp64")
     u = pl.apply(torch.tensor(W.q, device="cuda")).cpu().numpy()
     assert rel(u, ue) < FP64_TOL
     # a single point: only self images remain

@@ -34,8 +34,33 @@ def test_library_builds_loads_and_exports_all_symbols():
     assert pim.load().pim_status_string(pim.PIM_ERR_ANOMALY) == b"PIM_ERR_ANOMALY"
 
 
-def test_struct_layouts_match_header():
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of pim.h, as the C compiler lays it out."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pim.h"', "int main(void) {",
+             '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["pim_options", "pim_info"])
+def test_struct_layouts_match_header(name):
+    """The ctypes structures of the binding have the C layout of pim.h."""
     from paper_2312_02376_gb300 import pim
-    # pim_options: 3+1+1+1+1+3 ints (40 B), 2 doubles, size_t, 4 ints -> 80 B
-    assert ctypes.sizeof(pim.pim_options) == 80
-    assert pim.pim_options.neutral_tol.offset == 40
+    cls = getattr(pim, name)
+    fields = [f for f, _ in cls._fields_]
+    size, offs = _c_layout(name, fields)
+    assert ctypes.sizeof(cls) == size
+    for f, o in zip(fields, offs):
+        assert getattr(cls, f).offset == o, f
