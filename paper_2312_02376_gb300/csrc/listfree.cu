@@ -16,10 +16,13 @@
 //   Q_A    = sum_{(B,i) in region(A)} exp(-j k0.(i o L)) M_B placed at s_B + i o (n-1),
 //
 // where M_B(c) = sum_{n in B} w_n(c) q_n are the box moments of step 1 (the
-// spread forms them for boxes with >= PIM_DENSE_MIN points; the others are
-// added point by point) and g(e) = G0(|e o h|), g(0) = 0, is the grid kernel
+// spread forms them for the boxes with >= PIM_DENSE_MIN points) and g(e) =
+// G0(|e o h|), g(0) = 0, is the grid kernel
 // of the image-i component (an image shift moves a box by whole periods of
-// n - 1 grid steps, so g is the free-space kernel on the unrolled grid).  Q_A
+// n - 1 grid steps, so g is the free-space kernel on the unrolled grid).  Only
+// the region's boxes with moments take part here: the pairs of A's points with
+// the points of the region's other boxes stay in the stored list (few points,
+// each spread over a whole stencil, would fill the local grid).  Q_A
 // lives on a local grid of E^3 nodes around A in shared memory, so the grid
 // part costs one small convolution per box instead of one 729-term sum per
 // pair, and nothing is stored between applies.  The adjoint uses conj(G0),
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
         int A[3];
         box_xyz(a.blist[sA], a.nb, A);
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
         const int4 last = a.seg[g1 - 1];
         const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
         for (int o0 = 0; o0 < nA; o0 += LF_MAXOBS) {
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
         const int4 last = a.seg[g1 - 1];
         const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
         // thread t sums observer t % nA over the staged points t / nA, + LF_NT / nA ...
@@ -344,9 +349,9 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
 
 // ------------------------------ grid part ---------------------------------
 // One CTA per list-free box:
-//  1. the region's box moments (dense boxes) or points (other boxes), times
-//     their image phase, are added into the local grid Q_A (shared-memory
-//     atomics), work item = (region box, stencil row (jy, jz));
+//  1. the moments of the region's dense boxes, times their image phase, are
+//     added into the local grid Q_A (shared-memory atomics), work item =
+//     (region box, stencil row (jy, jz));
 //  2. V_A = g * Q_A at A's own (P+1)^3 stencil nodes: warps take the
 //     non-empty x-rows of Q_A, lane (ay, az) one output x-row; per input row
 //     the lane holds the g values of its x-offsets in registers and does
@@ -384,6 +389,7 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
             X0[d] = box_stencil(A[d], a.c, a.n[d], a.p) - org[d];
         }
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
+        if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
         __syncthreads();
         for (int i = tid; i < ncell; i += LF_GNT) {
             Qr[i] = T(0);
@@ -418,30 +424,16 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
                 atomicOr(a.status, PIM_DEV_BOUNDS);
                 continue;
             }
-            cplx<T> v[NP];
-#pragma unroll
-            for (int jx = 0; jx < NP; ++jx) v[jx] = mk<T>(T(0), T(0));
+            // the segments hold dense boxes only: their moments, row (gy, gz)
             const int di = a.dix[s];
-            if (di >= 0) {
-                const cplx<T>* mr = mom + (((long long)di * NP + gz) * NP + gy) * NP;
-#pragma unroll
-                for (int jx = 0; jx < NP; ++jx) v[jx] = mr[jx];
-            } else {
-                for (int nn = a.bstart[s]; nn < a.bstart[s + 1]; ++nn) {
-                    T t[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) t[d] = sizeof(T) == 8 ? (T)a.ntd[3 * nn + d] : (T)a.nt[3 * nn + d];
-                    T wx[NP];
-                    lagrange_w<T, P>(t[0], wx);
-                    const T wyz = lag1<T, P>(t[1], gy) * lag1<T, P>(t[2], gz);
-                    const cplx<T> q = qs[nn];
-#pragma unroll
-                    for (int jx = 0; jx < NP; ++jx) {
-                        v[jx].x += wx[jx] * wyz * q.x;
-                        v[jx].y += wx[jx] * wyz * q.y;
-                    }
-                }
+            if (di < 0) {
+                atomicOr(a.status, PIM_DEV_BOUNDS);
+                continue;
             }
+            cplx<T> v[NP];
+            const cplx<T>* mr = mom + (((long long)di * NP + gz) * NP + gy) * NP;
+#pragma unroll
+            for (int jx = 0; jx < NP; ++jx) v[jx] = mr[jx];
             const double2 phd = a.phase[ii];
             const cplx<T> ph = mk<T>((T)phd.x, (T)phd.y);
             const int row = (loc[2] + gz) * E + (loc[1] + gy);

@@ -22,7 +22,41 @@ static __device__ __align__(256) unsigned char pim_noalloc_scratch[NOALLOC_BYTES
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
+// per device: the address of the array in the context it was looked up in,
+// and that context's unique id (0: unknown, look it up again)
 void* g_addr[MAX_DEVICES] = {nullptr};
+unsigned long long g_ctx[MAX_DEVICES] = {0};
+
+// Unique id of the calling thread's current CUDA context (driver
+// cuCtxGetCurrent + cuCtxGetId, found through the runtime's entry-point
+// query), or 0 if it cannot be had.  A context that is destroyed and
+// created again -- cudaDeviceReset, a harness that resets between cases --
+// gets a new id, and its module a new copy of the array.
+unsigned long long current_context_id() {
+    using get_current_t = int (*)(void**);
+    using get_id_t = int (*)(void*, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (get_current_t)f1;
+            get_id = (get_id_t)f2;
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -50,7 +84,8 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         pim_set_error("pim_apply_noalloc takes device pointers only (host buffers would need staging memory)");
         return PIM_ERR_ARG;
     }
-    // one-time set-up per device: the device address of the scratch array
+    // set-up once per device and context: the device address of the scratch
+    // array in the current context (looked up again if the context changed)
     int dev = 0;
     PIM_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAX_DEVICES) {
@@ -60,7 +95,8 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
             void* ptr = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&ptr, pim_noalloc_scratch);
             if (e != cudaSuccess) {
@@ -69,6 +105,7 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
                 return PIM_ERR_CUDA;
             }
             g_addr[dev] = ptr;
+            g_ctx[dev] = ctx;
         }
         base = g_addr[dev];
     }

@@ -334,40 +334,62 @@ __global__ void lf_flag_kernel(const int* bstart, long long nne, const int* rowl
     }
 }
 
-__global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, const int* bstart, int* lfslot,
-                               int* rowlen) {
+__global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, int* lfslot, int* lfmark) {
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nne; s += (long long)gridDim.x * blockDim.x) {
-        if (!flag[s]) continue;
-        lfslot[pos[s]] = (int)s;
-        for (int m = bstart[s]; m < bstart[s + 1]; ++m) rowlen[m] = 0;
+        lfmark[s] = flag[s] ? pos[s] : -1;
+        if (flag[s]) lfslot[pos[s]] = (int)s;
     }
 }
 
-// Region segments of every list-free box: one per (image, box row) span with
-// points, as (first slot, end slot, image | slot offset << 8, point offset),
-// the offsets counted from the box's first segment.  seg == nullptr: counts.
-__global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* lfslot,
-                              long long nlf, const int64_t* segptr, int* cnt, int4* seg) {
+// Region segments of every list-free box: runs of consecutive dense boxes
+// (boxes with moments) inside one (image, box row) span, as (first slot, end
+// slot, image | slot offset << 8, point offset), the offsets counted from the
+// box's first segment.  The points of the region's other boxes stay in the
+// stored rows of the box's points; sparse[j] receives their number.
+// seg == nullptr: counts only.
+__global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* bstart,
+                              const int* dix, const int* lfslot, long long nlf, const int64_t* segptr, int* cnt,
+                              int* sparse, int4* seg) {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nlf; j += (long long)gridDim.x * blockDim.x) {
         const int b = blist[lfslot[j]];
         const int B[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
-        int c = 0, soff = 0, ptoff = 0;
+        int c = 0, soff = 0, ptoff = 0, nsp = 0;
         const int64_t o = seg ? segptr[j] : 0;
-        for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int lo, int hi) {
+        for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int, int) {
             int fs = -1, ls = -1;
+            auto close = [&]() {
+                if (fs < 0) return;
+                if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
+                soff += ls + 1 - fs;
+                ptoff += bstart[ls + 1] - bstart[fs];
+                ++c;
+                fs = ls = -1;
+            };
             for (int x = x0; x <= x1; ++x) {
                 const int sl = bslot[row + x];
-                if (sl >= 0) {
+                if (sl < 0) continue;
+                if (dix[sl] >= 0) {
                     if (fs < 0) fs = sl;
                     ls = sl;
+                } else {
+                    close();
+                    nsp += bstart[sl + 1] - bstart[sl];
                 }
             }
-            if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
-            soff += ls + 1 - fs;
-            ptoff += hi - lo;
-            ++c;
+            close();
         });
-        if (!seg) cnt[j] = c;
+        if (!seg) {
+            cnt[j] = c;
+            sparse[j] = nsp;
+        }
+    }
+}
+
+// the stored rows of a list-free box's points hold its sparse partners
+__global__ void lf_rowlen_kernel(const int* lfslot, long long nlf, const int* bstart, const int* sparse, int* rowlen) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nlf; j += (long long)gridDim.x * blockDim.x) {
+        const int s = lfslot[j];
+        for (int m = bstart[s]; m < bstart[s + 1]; ++m) rowlen[m] = sparse[j];
     }
 }
 
@@ -560,35 +582,60 @@ __device__ __forceinline__ void store_value(const FillArgs& a, long long q, doub
     }
 }
 
+// One warp per point: first the row's columns (the region's points, image
+// by image and box row by box row; for a point of a list-free box only the
+// points of boxes without moments), then the values with the lanes over the
+// whole row.
 __global__ void pair_fill_kernel(const double* pos, const uint32_t* ns, const double* ntd, long long N, FillArgs a,
-                                 const int* box_ptr, const int64_t* row_ptr, uint32_t* col, double2* val,
+                                 const int* box_ptr, const int* bslot, const int* bstart, const int* dix,
+                                 const int* lfmark, const int64_t* row_ptr, uint32_t* col, double2* val,
                                  float4* valdf, float2* valf, uint32_t* valt, double2* dval, int* status) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long m = warp; m < N; m += nwarps) {
-        // every stored row holds at least the point itself: an empty row is
-        // one of a list-free box
-        if (row_ptr[m + 1] == row_ptr[m]) continue;
+        const long long r0 = row_ptr[m], r1 = row_ptr[m + 1];
+        // every stored row of a box that is not list-free holds at least the
+        // point itself
+        if (r1 == r0) continue;
         int B[3];
         for (int d = 0; d < 3; ++d) B[d] = box_of(pos[3 * m + d] / a.h[d], a.pa.nb[d], a.pa.p);
-        long long off = row_ptr[m];
-        for_each_region_row(a.pa, box_ptr, B, [&](int ii, int lo, int hi) {
-            for (int n = lo + lane; n < hi; n += 32) {
-                const long long q = off + (n - lo);
-                col[q] = (uint32_t)n | ((uint32_t)ii << PIM_COL_BITS);
-                if (dval) {
-                    double2 gr[3];
-                    const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
-                    store_value(a, q, d, val, valdf, valf, valt);
-                    store_grad(a, q, gr, dval);
-                } else {
-                    const double2 d = corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr);
-                    store_value(a, q, d, val, valdf, valf, valt);
-                }
+        const long long bid = ((long long)B[2] * a.pa.nb[1] + B[1]) * a.pa.nb[0] + B[0];
+        const bool lf = lfmark && lfmark[bslot[bid]] >= 0;
+        long long off = r0;
+        for_each_region_span(a.pa, box_ptr, B, [&](int ii, long long row, int x0, int x1, int lo, int hi) {
+            if (!lf) {
+                for (int n = lo + lane; n < hi; n += 32) col[off + (n - lo)] = (uint32_t)n | ((uint32_t)ii << PIM_COL_BITS);
+                off += hi - lo;
+                return;
             }
-            off += hi - lo;
+            for (int x = x0; x <= x1; ++x) {
+                const int sl = bslot[row + x];
+                if (sl < 0 || dix[sl] >= 0) continue;
+                const int b0 = bstart[sl], b1 = bstart[sl + 1];
+                for (int n = b0 + lane; n < b1; n += 32) col[off + (n - b0)] = (uint32_t)n | ((uint32_t)ii << PIM_COL_BITS);
+                off += b1 - b0;
+            }
         });
+        if (off != r1) {
+            if (lane == 0) atomicOr(status, PIM_DEV_BOUNDS);
+            continue;
+        }
+        __syncwarp();
+        for (long long q = r0 + lane; q < r1; q += 32) {
+            const uint32_t c = col[q];
+            const long long n = c & PIM_COL_MASK;
+            const int ii = (int)(c >> PIM_COL_BITS);
+            if (dval) {
+                double2 gr[3];
+                const double2 d = corr_value<true>(a, pos, ns, ntd, m, n, ii, status, gr);
+                store_value(a, q, d, val, valdf, valf, valt);
+                store_grad(a, q, gr, dval);
+            } else {
+                store_value(a, q, corr_value<false>(a, pos, ns, ntd, m, n, ii, status, nullptr), val, valdf, valf,
+                            valt);
+            }
+        }
     }
 }
 
@@ -781,11 +828,16 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
     PIM_CK(cudaMemcpy(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost));
     if (nlf > 0) {
         if ((st = pim_alloc(P, (void**)&d.lfslot, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
-        lf_list_kernel<<<1024, 256, 0, s>>>(flag, pos, nne, d.bstart, d.lfslot, rowlen);
+        if ((st = pim_alloc(P, (void**)&d.lfmark, (size_t)nne * sizeof(int))) != PIM_OK) return st;
+        lf_list_kernel<<<1024, 256, 0, s>>>(flag, pos, nne, d.lfslot, d.lfmark);
         PIM_CK(cudaGetLastError());
-        int* cnt = flag;  // reuse (nlf <= nne)
+        int* cnt = flag;      // reuse (nlf <= nne)
+        int* sparse = pos;    // reuse
         const unsigned nb = (unsigned)std::min<long long>((nlf + 127) / 128, 152 * 16);
-        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.lfslot, nlf, nullptr, cnt, nullptr);
+        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, nullptr,
+                                         cnt, sparse, nullptr);
+        PIM_CK(cudaGetLastError());
+        lf_rowlen_kernel<<<nb, 128, 0, s>>>(d.lfslot, nlf, d.bstart, sparse, rowlen);
         PIM_CK(cudaGetLastError());
         if ((st = pim_alloc(P, (void**)&d.segptr, (size_t)(nlf + 1) * sizeof(int64_t))) != PIM_OK) return st;
         if ((st = scan<int64_t>(P, cnt, d.segptr, nlf, s)) != PIM_OK) return st;
@@ -793,7 +845,8 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         PIM_CK(cudaMemcpy(&nseg, d.segptr + nlf, sizeof(int64_t), cudaMemcpyDeviceToHost));
         if ((st = pim_alloc(P, (void**)&d.seg, (size_t)nseg * sizeof(int4))) != PIM_OK) return st;
         d.nseg = nseg;
-        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.lfslot, nlf, d.segptr, nullptr, d.seg);
+        lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, d.segptr,
+                                         nullptr, nullptr, d.seg);
         PIM_CK(cudaGetLastError());
         if ((st = pim_alloc(P, (void**)&d.lfp, (size_t)d.N * sizeof(float4))) != PIM_OK) return st;
         lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, d.N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
@@ -963,6 +1016,7 @@ void points_free(pim_plan P) {
     pim_free(P, d.nbig, (size_t)std::max<int64_t>(1, d.N) * sizeof(int));
     pim_free(P, d.dix, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
     pim_free(P, d.lfslot, (size_t)d.nlf * sizeof(int));
+    pim_free(P, d.lfmark, (size_t)(d.lfmark ? d.nne : 0) * sizeof(int));
     pim_free(P, d.segptr, (size_t)(d.nlf + 1) * sizeof(int64_t));
     pim_free(P, d.seg, (size_t)d.nseg * sizeof(int4));
     pim_free(P, d.lfp, N * sizeof(float4));
@@ -1122,8 +1176,9 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k);
     fa.gtab = gtab;
     if (N > 0 && nnz > 0)
-        pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.row_ptr, d.col, d.val,
-                                                   d.valdf, d.valf, d.valt, d.dval, P->dstatus);
+        pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.bslot, d.bstart, d.dix,
+                                                   d.lfmark, d.row_ptr, d.col, d.val, d.valdf, d.valf, d.valt, d.dval,
+                                                   P->dstatus);
     PIM_CK(cudaGetLastError());
     if ((st = lf_check(P, s)) != PIM_OK) return st;
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -175,3 +175,29 @@ def random_case(N, D, pdims, k, k0, n, p=4, layers=1, b=5, nf=(10, 10, 10), pf=4
         q = q[:, 0]
     return Workload("random_%d" % N, tuple(D), tuple(pdims), k, tuple(k0), tuple(n), p, layers, b,
                     tuple(nf), pf, precision, N, nrhs, pts, q)
+
+
+def random_clustered_case(N, D, pdims, k, k0, n, p=4, layers=1, b=5, nf=(10, 10, 10), pf=4, seed=0,
+                          complex_q=True, neutral=False, precision="fp64", nclusters=3, sigma_steps=0.4):
+    """A small case whose points are half uniform and half in nclusters
+    Gaussian clusters of standard deviation sigma_steps grid steps (boxes with
+    tens of points, as on the sphere surfaces of the 3D workload), clipped
+    into the closed cell."""
+    rng = _rng(200 + seed)
+    D = np.asarray(D, np.float64)
+    h = D / (np.asarray(n) - 1)
+    nu = N // 2
+    centres = rng.random((nclusters, 3)) * D
+    per = np.full(nclusters, (N - nu) // nclusters)
+    per[: (N - nu) - per.sum()] += 1
+    cl = [np.clip(c + sigma_steps * h * rng.standard_normal((cnt, 3)), 0.0, D) for c, cnt in zip(centres, per)]
+    pts = np.concatenate([rng.random((nu, 3)) * D] + cl)
+    if complex_q:
+        q = _cn(rng, N)
+    else:
+        q = rng.standard_normal(N)
+    if neutral:
+        q = q - q.mean()
+    return Workload("clustered_%d" % N, tuple(D), tuple(pdims), k, tuple(k0), tuple(n), p, layers, b,
+                    tuple(nf), pf, precision, N, 1, pts, q)
+

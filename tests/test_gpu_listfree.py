@@ -1,12 +1,14 @@
 """The list-free near-pair correction (Sec. 3.3 step 4, Eq. er, recomputed by
 every apply from the region's points and box moments instead of read from a
-stored list) against the FP64 oracle, through the C ABI.
+stored list) against the FP64 oracle, through the C ABI.  A list-free box
+sums its pairs with the region's boxes that have moments; its pairs with the
+other boxes stay in its points' stored rows.
 
 The oracle computes the correction pair by pair (oracle.pim.correction_values);
 the list-free kernels sum the same terms regrouped per observer box, so the
 bars are the method's: relative L2 <= 1e-12 for FP64 plans, <= 2e-5 for FP32
-plans.  `listfree=1` makes every box list-free (the stored list is empty);
-larger thresholds split the boxes between the two forms."""
+plans.  `listfree=1` makes every box list-free; larger thresholds split the
+boxes between the two forms."""
 import numpy as np
 import pytest
 
@@ -50,11 +52,14 @@ CASES = {
 
 
 def make_case(name, seed=0):
+    """Half the points uniform, half in three tight clusters: boxes with
+    moments (which the list-free kernels sum) and boxes without (whose pairs
+    stay in the stored rows)."""
     D, pdims, k, k0, n, N, b, nf, pf, p, layers = CASES[name]
     npsp = len(pdims) > 0 and k == 0 and not any(k0)
     real = k == 0 and not any(k0)
-    return inputs.random_case(N, D, pdims, k, k0, n, p=p, layers=layers, b=b, nf=nf, pf=pf, seed=seed + 11,
-                              complex_q=not real, neutral=npsp)
+    return inputs.random_clustered_case(N, D, pdims, k, k0, n, p=p, layers=layers, b=b, nf=nf, pf=pf,
+                                        seed=seed + 11, complex_q=not real, neutral=npsp)
 
 
 def oracle_plan(W):
@@ -97,7 +102,7 @@ def test_fp64_every_box_listfree(name, cache):
     W, ue, we = oracle_results(name, cache)
     pl = gpu_plan(W, "fp64", listfree=1)
     info = pl.info()
-    assert info.nnz == 0 and info.lf_points == W.N, (info.nnz, info.lf_points)
+    assert info.lf_points == W.N and info.lf_pairs > 0, (info.lf_points, info.lf_pairs)
     q = to_dev(W.q, "fp64", is_real(W))
     u = pl.apply(q).cpu().numpy()
     w = pl.apply_adjoint(q).cpu().numpy()
@@ -111,7 +116,7 @@ def test_fp64_every_box_listfree(name, cache):
 def test_fp32_every_box_listfree(name, cache):
     W, ue, we = oracle_results(name, cache)
     pl = gpu_plan(W, "fp32", listfree=1)
-    assert pl.info().nnz == 0
+    assert pl.info().lf_pairs > 0
     q = to_dev(W.q, "fp32", is_real(W))
     u = pl.apply(q).cpu().numpy()
     w = pl.apply_adjoint(q).cpu().numpy()
@@ -167,7 +172,7 @@ def test_listfree_equals_stored_list_fp64(clusters):
     q = to_dev(W.q, "fp64", False)
     a = gpu_plan(W, "fp64", listfree=0)
     b = gpu_plan(W, "fp64", listfree=1)
-    assert a.info().lf_boxes == 0 and b.info().nnz == 0
+    assert a.info().lf_boxes == 0 and b.info().lf_pairs > 0
     ua, ub = a.apply(q).cpu().numpy(), b.apply(q).cpu().numpy()
     wa, wb = a.apply_adjoint(q).cpu().numpy(), b.apply_adjoint(q).cpu().numpy()
     assert rel(ub, ua) < 1e-13 and rel(wb, wa) < 1e-13, (rel(ub, ua), rel(wb, wa))
