@@ -142,7 +142,8 @@ typedef struct {
     int gather_variants; /* launch shapes available to this plan                       */
     int64_t lf_boxes;    /* boxes corrected list-free (corr_listfree)                  */
     int64_t lf_points;   /* points in those boxes                                      */
-    int64_t lf_pairs;    /* (observer, source, image) pairs they sum per apply         */
+    int64_t lf_pairs;    /* (observer, source, image) pairs their exact kernel sums per
+                            apply (partners in the boxes with moments)                */
 } pim_info;
 
 /* Stages timed by the profiling ring (pim_set_profiling). */
@@ -150,11 +151,13 @@ typedef enum {
     PIM_STAGE_PERMUTE = 0,   /* regularise (Eq. neutral) and reorder the sources        */
     PIM_STAGE_SPREAD = 1,    /* near step 1: anterpolation onto the grid                */
     PIM_STAGE_FFT = 2,       /* near step 2: the five pruned FFT passes                 */
-    PIM_STAGE_GATHER = 3,    /* near steps 3-4: gather and correction                   */
+    PIM_STAGE_GATHER = 3,    /* near steps 3-4: gather and stored-list correction       */
     PIM_STAGE_FAR = 4,       /* far steps 1-3: projection, grid sum, interpolation
                                 (second stream; added to u after the gather)            */
     PIM_STAGE_APPLY = 5,     /* the whole apply, first to last launch                   */
-    PIM_NUM_STAGES = 6
+    PIM_STAGE_LF_EXACT = 6,  /* list-free boxes: exact kernel summed over their regions  */
+    PIM_STAGE_LF_GRID = 7,   /* list-free boxes: minus the regions' grid interaction    */
+    PIM_NUM_STAGES = 8
 } pim_stage;
 
 /* Fills *opt with the defaults documented above. */

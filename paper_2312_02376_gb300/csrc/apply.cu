@@ -1192,10 +1192,10 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             if (P->tune_ev[1]) PIM_CK(cudaEventRecord(P->tune_ev[1], sr));
         }
         PIM_CK(cudaGetLastError());
-        // list-free boxes: exact sum minus grid part, added to the gathered output
-        if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
         prof_mark(P, PIM_STAGE_GATHER, 1, sr);
         P->launches += N > 0 ? 1 : 0;
+        // list-free boxes: exact sum minus grid part, added to the gathered output
+        if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
         if (P->has_far) {
             PIM_CK(cudaStreamWaitEvent(sr, P->ev_join, 0));
             if (N > 0) {

@@ -50,11 +50,13 @@ constexpr int LF_OB = 8;        // observers per register group
 constexpr int LF_MAXOBS = 512;  // observers per pass over the region
 constexpr int LF_GNT = 512;     // threads of the grid-part kernel
 constexpr int LF_MAXNT = 8;     // polynomial terms
+constexpr int LF_MAXSEG = 512;  // region segments of a box staged in shared memory
 
 struct LfArgs {
     const int* lfslot;
     const int64_t* segptr;
     const int4* seg;
+    const int* lfself;
     const int* bstart;
     const int* blist;
     const int* dix;
@@ -75,6 +77,11 @@ struct LfArgs {
     long long nlf;
     int nrhs, r, real_out, sorted_out;
     int* status;
+};
+
+// an FP64 position padded to 32 bytes
+struct __align__(16) dpos4 {
+    double x, y, z, w;
 };
 
 __device__ __forceinline__ void box_xyz(int b, const int* nb, int* B) {
@@ -104,6 +111,39 @@ __device__ __forceinline__ void add_out(const LfArgs& a, void* out, long long m,
     }
 }
 
+// The region segments of list-free box j in shared memory (a box with more
+// segments reads them from global memory), with the first point of each:
+// returns the table and sets ns, and sp0 to the point table.
+__device__ __forceinline__ const int4* stage_segments(const LfArgs& a, int64_t g0, int64_t g1, int4* sSeg, int* sP0,
+                                                      int& ns, const int*& p0) {
+    ns = (int)(g1 - g0);
+    if (ns > LF_MAXSEG) {
+        p0 = nullptr;
+        return a.seg + g0;
+    }
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int4 sg = a.seg[g0 + i];
+        sSeg[i] = sg;
+        if (sP0) sP0[i] = a.bstart[sg.x];
+    }
+    p0 = sP0;
+    return sSeg;
+}
+
+// index of the last segment whose offset (point offset w, or slot offset
+// z >> 8) is <= f
+template <bool SLOTS>
+__device__ __forceinline__ int find_segment(const int4* t, int ns, int f) {
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int key = SLOTS ? (t[mid].z >> 8) : t[mid].w;
+        if (key <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Reduce-scatter of 16 values over the warp: afterwards lane l holds the
 // warp sum of value (l >> 1) & 15 (lanes 2v and 2v + 1 both hold value v).
 __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
@@ -121,19 +161,97 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
 }
 
 // ------------------------------ exact part --------------------------------
+// 1/sqrt(x) by the SFU, denormals flushed (PTX rsqrt.approx.ftz.f32, relative
+// error about 2^-23): one instruction per pair.
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// G0 of one pair times its source, added to (ar, ai): s = r^2, q the source
+// times its image phase.  NT > 0: cos(k r) / (4 pi) and -k sinc(k r) / (4 pi)
+// as polynomials in s (coefficients pc, ps); NT = 0: sincosf.  CHECK: the
+// pair may be the point itself (s = 0), which adds nothing.
+template <int MODE, int NT, bool CHECK>
+__device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float& ar, float& ai) {
+    float ri = rsqrt_sfu(s);
+    if (CHECK) ri = s > 0.f ? ri : 0.f;
+    float gr, gim;
+    if (NT > 0) {
+        float pcv = a.pc[NT - 1], psv = a.ps[NT - 1];
+#pragma unroll
+        for (int t = NT - 2; t >= 0; --t) {
+            pcv = fmaf(pcv, s, a.pc[t]);
+            psv = fmaf(psv, s, a.ps[t]);
+        }
+        gr = ri * pcv;
+        gim = CHECK ? (s > 0.f ? psv : 0.f) : psv;
+    } else {
+        float sn, cs;
+        sincosf((float)a.k * (s * ri), &sn, &cs);
+        const float s4 = ri * (float)(0.25 / PI);
+        gr = cs * s4;
+        gim = -sn * s4;
+    }
+    if (MODE == 1) gim = -gim;
+    ar = fmaf(gr, q.x, fmaf(-gim, q.y, ar));
+    ai = fmaf(gr, q.y, fmaf(gim, q.x, ai));
+}
+
+// The staged points [0, cnt) against the observers [0, no): warps split the
+// points, lanes take every 32nd of a warp's share, each lane sums LF_OB
+// observers at once; the sums are reduced over the warp and added to sAcc.
+template <int MODE, int NT, bool CHECK>
+__device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, const float2* sQ, const float4* sO,
+                                            float* sAcc, int no, int cnt, int warp, int lane) {
+    const int ngr = (no + LF_OB - 1) / LF_OB;
+    for (int gi = 0; gi < ngr; ++gi) {
+        float ox[LF_OB], oy[LF_OB], oz[LF_OB], ar[LF_OB], ai[LF_OB];
+#pragma unroll
+        for (int k = 0; k < LF_OB; ++k) {
+            const int i = gi * LF_OB + k;
+            const float4 O = i < no ? sO[i] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
+            ox[k] = O.x;
+            oy[k] = O.y;
+            oz[k] = O.z;
+            ar[k] = 0.f;
+            ai[k] = 0.f;
+        }
+        for (int s = warp * 32 + lane; s < cnt; s += LF_NT) {
+            const float4 X = sX[s];
+            const float2 q = sQ[s];
+#pragma unroll
+            for (int k = 0; k < LF_OB; ++k) {
+                const float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
+                g0_mac<MODE, NT, CHECK>(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), q, ar[k], ai[k]);
+            }
+        }
+        float v[2 * LF_OB];
+#pragma unroll
+        for (int k = 0; k < LF_OB; ++k) {
+            v[2 * k] = ar[k];
+            v[2 * k + 1] = ai[k];
+        }
+        const float sum = reduce_scatter16(v, lane);
+        const int vi = (lane >> 1) & 15;
+        const int i = gi * LF_OB + (vi >> 1);
+        if (!(lane & 1) && i < no) atomicAdd(&sAcc[2 * i + (vi & 1)], sum);
+    }
+}
+
 // One CTA per list-free box.  The region's points are staged in shared
 // memory LF_CH at a time, each as its position relative to A's centre (FP32,
 // physical units: integer box offset plus the box-centred local coordinate,
 // so that close pairs keep their relative precision) and its source
-// strength times the image phase.  Warps split the staged points, lanes take
-// every 32nd of a warp's share, and each lane sums LF_OB observers at once;
-// the observers' sums are reduced over the warp and added in shared memory.
+// strength times the image phase.  The points are taken in the order: A's
+// own points first (image 0; the only chunks that can hold the pair of a
+// point with itself, summed with the s > 0 test), then the rest of the
+// region's list (every other pair has s > 0: set-points rejects points that
+// coincide, or that FP32 coordinates cannot tell apart).
 //
-// MODE 0: forward, 1: adjoint (conj(G0)), 2: check only (flags points that
-// coincide modulo the lattice, or that FP32 coordinates cannot tell apart).
-// G0(r) = exp(-j k r)/(4 pi r) = [cos(k r) - j k sinc(k r)] / (4 pi r), with
-// cos and sinc as polynomials in s = r^2 of NT terms (Maclaurin series,
-// NT chosen on the host for the region's largest k r); NT = 0: sincosf.
+// MODE 0: forward, 1: adjoint (conj(G0)), 2: check only (flags pairs of
+// distinct points with s = 0).
 template <int MODE, int NT>
 __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __restrict__ qs, void* out) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -141,9 +259,10 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
     float2* sQ = (float2*)(sX + LF_CH);                  // LF_CH
     float4* sO = (float4*)(sQ + LF_CH);                  // LF_MAXOBS
     float* sAcc = (float*)(sO + LF_MAXOBS);              // 2 LF_MAXOBS
-    int* sIdx = (int*)(sAcc + 2 * LF_MAXOBS);            // LF_CH (check mode)
+    int4* sSeg = (int4*)(sAcc + 2 * LF_MAXOBS);          // LF_MAXSEG
+    int* sP0 = (int*)(sSeg + LF_MAXSEG);                 // LF_MAXSEG
+    int* sIdx = sP0 + LF_MAXSEG;                         // LF_CH (check mode)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = LF_NT / 32;
     for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
@@ -151,8 +270,16 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
         box_xyz(a.blist[sA], a.nb, A);
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
         if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
+        __syncthreads();
+        int ns;
+        const int* p0t;
+        const int4* tab = stage_segments(a, g0, g1, sSeg, sP0, ns, p0t);
         const int4 last = a.seg[g1 - 1];
         const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
+        // A's own points sit at [so, so + nA) of the region's list (so < 0:
+        // A has no moments, its pairs with itself are stored)
+        const int so = a.lfself[j];
+        const int nself = so >= 0 ? nA : 0;
         for (int o0 = 0; o0 < nA; o0 += LF_MAXOBS) {
             const int no = min(LF_MAXOBS, nA - o0);
             __syncthreads();
@@ -162,33 +289,36 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
                 sAcc[2 * i] = 0.f;
                 sAcc[2 * i + 1] = 0.f;
             }
-            for (int f0 = 0; f0 < total; f0 += LF_CH) {
-                const int cnt = min(LF_CH, total - f0);
+            // chunks of the reordered list: v < nself are A's points, the
+            // others the region's list without them
+            for (int v0 = 0; v0 < total; v0 += LF_CH) {
+                const bool own = v0 < nself;
+                const int cnt = own ? min(LF_CH, nself - v0) : min(LF_CH, total - v0);
                 __syncthreads();
-                // stage: warp w copies the segments w, w + NW, ... that meet [f0, f0 + cnt)
-                for (int64_t g = g0 + warp; g < g1; g += NW) {
-                    const int4 sg = a.seg[g];
-                    const int p0 = a.bstart[sg.x], len = a.bstart[sg.y] - p0;
-                    const int lo = max(sg.w, f0), hi = min(sg.w + len, f0 + cnt);
-                    if (lo >= hi) continue;
+                // stage: every thread finds the segment of each of its points
+                // (binary search) and loads it, the loads of all in flight
+#pragma unroll 4
+                for (int t = tid; t < cnt; t += LF_NT) {
+                    const int v = v0 + t;
+                    const int f = own ? so + v : (v - nself < so || so < 0 ? v - nself : v);
+                    const int gs = find_segment<false>(tab, ns, f);
+                    const int4 sg = tab[gs];
+                    const int nn = (p0t ? p0t[gs] : a.bstart[sg.x]) + (f - sg.w);
                     const int ii = sg.z & 255;
-                    const double2 phd = a.phase[ii];
-                    const float2 ph = make_float2((float)phd.x, (float)phd.y);
-                    for (int f = lo + lane; f < hi; f += 32) {
-                        const int nn = p0 + (f - sg.w);
-                        const float4 L = a.lfp[nn];
-                        int Bn[3];
-                        unpack3(__float_as_uint(L.w), Bn[0], Bn[1], Bn[2]);
-                        const float x = ((float)(Bn[0] + a.img[ii][0] * a.nL[0] - A[0]) + L.x) * a.hf[0];
-                        const float y = ((float)(Bn[1] + a.img[ii][1] * a.nL[1] - A[1]) + L.y) * a.hf[1];
-                        const float z = ((float)(Bn[2] + a.img[ii][2] * a.nL[2] - A[2]) + L.z) * a.hf[2];
-                        sX[f - f0] = make_float4(x, y, z, 0.f);
-                        if (MODE == 2) {
-                            sIdx[f - f0] = ii == a.self_img ? nn : -1;
-                        } else {
-                            const float2 q = qs[nn];
-                            sQ[f - f0] = make_float2(q.x * ph.x - q.y * ph.y, q.x * ph.y + q.y * ph.x);
-                        }
+                    const float4 L = a.lfp[nn];
+                    int Bn[3];
+                    unpack3(__float_as_uint(L.w), Bn[0], Bn[1], Bn[2]);
+                    const float x = ((float)(Bn[0] + a.img[ii][0] * a.nL[0] - A[0]) + L.x) * a.hf[0];
+                    const float y = ((float)(Bn[1] + a.img[ii][1] * a.nL[1] - A[1]) + L.y) * a.hf[1];
+                    const float z = ((float)(Bn[2] + a.img[ii][2] * a.nL[2] - A[2]) + L.z) * a.hf[2];
+                    sX[t] = make_float4(x, y, z, 0.f);
+                    if (MODE == 2) {
+                        sIdx[t] = ii == a.self_img ? nn : -1;
+                    } else {
+                        const double2 phd = a.phase[ii];
+                        const float2 ph = make_float2((float)phd.x, (float)phd.y);
+                        const float2 q = qs[nn];
+                        sQ[t] = make_float2(q.x * ph.x - q.y * ph.y, q.x * ph.y + q.y * ph.x);
                     }
                 }
                 __syncthreads();
@@ -200,64 +330,12 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
                         if (dx * dx + dy * dy + dz * dz == 0.f && sIdx[s] != m0 + o0 + i)
                             atomicOr(a.status, PIM_DEV_COINCIDENT);
                     }
-                    continue;
+                } else if (own) {
+                    exact_chunk<MODE, NT, true>(a, sX, sQ, sO, sAcc, no, cnt, warp, lane);
+                } else {
+                    exact_chunk<MODE, NT, false>(a, sX, sQ, sO, sAcc, no, cnt, warp, lane);
                 }
-                const int ngr = (no + LF_OB - 1) / LF_OB;
-                for (int gi = 0; gi < ngr; ++gi) {
-                    float ox[LF_OB], oy[LF_OB], oz[LF_OB], ar[LF_OB], ai[LF_OB];
-#pragma unroll
-                    for (int k = 0; k < LF_OB; ++k) {
-                        const int i = gi * LF_OB + k;
-                        const float4 O = i < no ? sO[i] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
-                        ox[k] = O.x;
-                        oy[k] = O.y;
-                        oz[k] = O.z;
-                        ar[k] = 0.f;
-                        ai[k] = 0.f;
-                    }
-                    for (int s = warp * 32 + lane; s < cnt; s += LF_NT) {
-                        const float4 X = sX[s];
-                        const float2 q = sQ[s];
-#pragma unroll
-                        for (int k = 0; k < LF_OB; ++k) {
-                            const float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const bool nz = r2 > 0.f;
-                            const float ri = nz ? rsqrtf(r2) : 0.f;
-                            float gr, gim;
-                            if (NT > 0) {
-                                float pcv = a.pc[NT - 1], psv = a.ps[NT - 1];
-#pragma unroll
-                                for (int t = NT - 2; t >= 0; --t) {
-                                    pcv = fmaf(pcv, r2, a.pc[t]);
-                                    psv = fmaf(psv, r2, a.ps[t]);
-                                }
-                                gr = ri * pcv;
-                                gim = nz ? psv : 0.f;
-                            } else {
-                                float sn, cs;
-                                const float rr = r2 * ri;
-                                sincosf((float)a.k * rr, &sn, &cs);
-                                const float s4 = ri * (float)(0.25 / PI);
-                                gr = cs * s4;
-                                gim = -sn * s4;
-                            }
-                            if (MODE == 1) gim = -gim;
-                            ar[k] = fmaf(gr, q.x, fmaf(-gim, q.y, ar[k]));
-                            ai[k] = fmaf(gr, q.y, fmaf(gim, q.x, ai[k]));
-                        }
-                    }
-                    float v[2 * LF_OB];
-#pragma unroll
-                    for (int k = 0; k < LF_OB; ++k) {
-                        v[2 * k] = ar[k];
-                        v[2 * k + 1] = ai[k];
-                    }
-                    const float sum = reduce_scatter16(v, lane);
-                    const int vi = (lane >> 1) & 15;
-                    const int i = gi * LF_OB + (vi >> 1);
-                    if (!(lane & 1) && i < no) atomicAdd(&sAcc[2 * i + (vi & 1)], sum);
-                }
+                if (own && v0 + cnt == nself) v0 = nself - LF_CH;  // the region's list starts its own chunk
             }
             __syncthreads();
             if (MODE != 2)
@@ -272,16 +350,21 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
 template <int MODE>
 __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* __restrict__ qs, void* out) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double4* sX = (double4*)smem;                        // LF_CH
+    dpos4* sX = (dpos4*)smem;                        // LF_CH
     double2* sQ = (double2*)(sX + LF_CH);                // LF_CH
     int* sIdx = (int*)(sQ + LF_CH);                      // LF_CH
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = LF_NT / 32;
+    int4* sSeg = (int4*)(sIdx + LF_CH);                  // LF_MAXSEG
+    int* sP0 = (int*)(sSeg + LF_MAXSEG);                 // LF_MAXSEG
+    const int tid = threadIdx.x;
     for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
         if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
+        __syncthreads();
+        int ns;
+        const int* p0t;
+        const int4* tab = stage_segments(a, g0, g1, sSeg, sP0, ns, p0t);
         const int4 last = a.seg[g1 - 1];
         const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
         // thread t sums observer t % nA over the staged points t / nA, + LF_NT / nA ...
@@ -297,26 +380,21 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
             for (int f0 = 0; f0 < total; f0 += LF_CH) {
                 const int cnt = min(LF_CH, total - f0);
                 __syncthreads();
-                for (int64_t g = g0 + warp; g < g1; g += NW) {
-                    const int4 sg = a.seg[g];
-                    const int p0 = a.bstart[sg.x], len = a.bstart[sg.y] - p0;
-                    const int lo = max(sg.w, f0), hi = min(sg.w + len, f0 + cnt);
-                    if (lo >= hi) continue;
+                for (int t = tid; t < cnt; t += LF_NT) {
+                    const int f = f0 + t;
+                    const int gs = find_segment<false>(tab, ns, f);
+                    const int4 sg = tab[gs];
+                    const int nn = (p0t ? p0t[gs] : a.bstart[sg.x]) + (f - sg.w);
                     const int ii = sg.z & 255;
-                    const double2 ph = a.phase[ii];
-                    for (int f = lo + lane; f < hi; f += 32) {
-                        const int nn = p0 + (f - sg.w);
-                        sX[f - f0] = make_double4(a.pos[3 * nn] + a.img[ii][0] * a.D[0],
-                                                  a.pos[3 * nn + 1] + a.img[ii][1] * a.D[1],
-                                                  a.pos[3 * nn + 2] + a.img[ii][2] * a.D[2], 0.0);
-                        sIdx[f - f0] = ii == a.self_img ? nn : -1;
-                        if (MODE != 2) sQ[f - f0] = cmul(qs[nn], ph);
-                    }
+                    sX[t] = dpos4{a.pos[3 * nn] + a.img[ii][0] * a.D[0], a.pos[3 * nn + 1] + a.img[ii][1] * a.D[1],
+                                 a.pos[3 * nn + 2] + a.img[ii][2] * a.D[2], 0.0};
+                    sIdx[t] = ii == a.self_img ? nn : -1;
+                    if (MODE != 2) sQ[t] = cmul(qs[nn], a.phase[ii]);
                 }
                 __syncthreads();
                 if (!act) continue;
                 for (int s = part; s < cnt; s += stride) {
-                    const double4 X = sX[s];
+                    const dpos4 X = sX[s];
                     const double dx = px - X.x, dy = py - X.y, dz = pz - X.z;
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 == 0.0) {
@@ -349,35 +427,48 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
 
 // ------------------------------ grid part ---------------------------------
 // One CTA per list-free box:
-//  1. the moments of the region's dense boxes, times their image phase, are
-//     added into the local grid Q_A (shared-memory atomics), work item =
-//     (region box, stencil row (jy, jz));
-//  2. V_A = g * Q_A at A's own (P+1)^3 stencil nodes: warps take the
-//     non-empty x-rows of Q_A, lane (ay, az) one output x-row; per input row
-//     the lane holds the g values of its x-offsets in registers and does
-//     (P+1) x EX complex multiply-adds;
-//  3. every point of A subtracts w_m . V_A from its output.
-// The kernel table g(|e|) is in shared memory (FP32) or read through the
-// cache (FP64).
+//  1. a table of the region's dense boxes in shared memory (moment index,
+//     position of the stencil in the local grid, image), LF_MAXSLOT boxes at
+//     a time;
+//  2. their moments, times the image phase, are added into the local grid
+//     Q_A (shared-memory atomics), work item = (region box, stencil row
+//     (jy, jz)); each x-row of Q_A records the x-range it received;
+//  3. V_A = g * Q_A at A's own (P+1)^3 stencil nodes: warps take the
+//     non-empty x-rows of Q_A, lane (ay, az) one output x-row; per block of 8
+//     input nodes inside the row's x-range the lane holds the g values of
+//     8 + P x-offsets in registers and does (P+1) x 8 complex multiply-adds;
+//     the warps' sums meet in shared memory (atomics);
+//  4. every point of A subtracts w_m . V_A from its output.
+// The kernel table g(|e|) ((H+1)^3 entries) sits in shared memory for FP32
+// plans: the lanes of a warp read 25 different rows of it, a few bank
+// conflicts there instead of as many cache lines through L1.
+constexpr int LF_MAXSLOT = 1024;
+
 template <typename T, int P, int EX, bool ADJ>
-__global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>* __restrict__ qs,
-                                                       const cplx<T>* __restrict__ mom,
+__global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>* __restrict__ mom,
                                                        const cplx<T>* __restrict__ gtab, void* out) {
     constexpr int NP = P + 1, RW = NP * NP, NW = LF_GNT / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     const int E = a.E, H1 = a.H + 1;
-    const int ncell = E * E * EX;
-    T* Qr = (T*)smem;
-    T* Qi = Qr + ncell;
-    cplx<T>* Vp = (cplx<T>*)(Qi + ncell);                   // NW x NP^3
-    int* rowflag = (int*)(Vp + NW * NP * NP * NP);           // E^2
-    int* rows = rowflag + E * E;                             // E^2
+    constexpr int XS = EX + 1;                               // row stride (odd: rows in different banks)
+    const int ncell = E * E * XS;
+    cplx<T>* Q = (cplx<T>*)smem;                             // E x E rows of XS
+    T* Vr = (T*)(Q + ncell);                                 // NP^3
+    T* Vi = Vr + NP * NP * NP;                               // NP^3
+    int2* slot = (int2*)(((uintptr_t)(Vi + NP * NP * NP) + 15) & ~(uintptr_t)15);  // LF_MAXSLOT
+    int* xlo = (int*)(slot + LF_MAXSLOT);                    // E^2
+    int* xhi = xlo + E * E;                                  // E^2
+    int* rows = xhi + E * E;                                 // E^2
     int* nrows = rows + E * E;                               // 1
     cplx<T>* gs = (cplx<T>*)(((uintptr_t)(nrows + 1) + 15) & ~(uintptr_t)15);  // H1^3 (FP32)
     const cplx<T>* gt = sizeof(T) == 4 ? gs : gtab;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (sizeof(T) == 4)
-        for (int i = tid; i < H1 * H1 * H1; i += LF_GNT) gs[i] = gtab[i];
+        for (int i = tid; i < H1 * H1 * H1; i += LF_GNT) {
+            cplx<T> g = gtab[i];
+            if (ADJ) g.y = -g.y;
+            gs[i] = g;
+        }
     for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
@@ -391,68 +482,74 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
         const int64_t g0 = a.segptr[j], g1 = a.segptr[j + 1];
         if (g1 == g0) continue;  // no dense box in the region (uniform over the CTA)
         __syncthreads();
-        for (int i = tid; i < ncell; i += LF_GNT) {
-            Qr[i] = T(0);
-            Qi[i] = T(0);
+        for (int i = tid; i < ncell; i += LF_GNT) Q[i] = mk<T>(T(0), T(0));
+        for (int i = tid; i < E * E; i += LF_GNT) {
+            xlo[i] = EX;
+            xhi[i] = -1;
         }
-        for (int i = tid; i < E * E; i += LF_GNT) rowflag[i] = 0;
-        __syncthreads();
-        // 1. local grid of the region's charges
+        for (int i = tid; i < NP * NP * NP; i += LF_GNT) {
+            Vr[i] = T(0);
+            Vi[i] = T(0);
+        }
         const int4 last = a.seg[g1 - 1];
         const int nslots = (last.z >> 8) + (last.y - last.x);
-        for (int w = tid; w < nslots * RW; w += LF_GNT) {
-            const int f = w / RW, rr = w - f * RW;
-            const int gy = rr % NP, gz = rr / NP;
-            int64_t lo = g0, hi = g1 - 1;  // last segment whose slot offset <= f
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if ((a.seg[mid].z >> 8) <= f) lo = mid;
-                else hi = mid - 1;
-            }
-            const int4 sg = a.seg[lo];
-            const int s = sg.x + (f - (sg.z >> 8));
-            const int ii = sg.z & 255;
-            int B[3], loc[3];
-            box_xyz(a.blist[s], a.nb, B);
-            bool ok = true;
+        for (int w0 = 0; w0 < nslots; w0 += LF_MAXSLOT) {
+            const int nw = min(LF_MAXSLOT, nslots - w0);
+            __syncthreads();
+            // 1. the window's dense boxes: warps over segments, lanes over slots
+            for (int64_t g = g0 + warp; g < g1; g += NW) {
+                const int4 sg = a.seg[g];
+                const int soff = sg.z >> 8, ii = sg.z & 255;
+                const int lo = max(sg.x, sg.x + (w0 - soff)), hi = min(sg.y, sg.x + (w0 + nw - soff));
+                for (int sl = lo + lane; sl < hi; sl += 32) {
+                    int B[3], loc[3];
+                    box_xyz(a.blist[sl], a.nb, B);
+                    bool ok = true;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                loc[d] = box_stencil(B[d], a.c, a.n[d], a.p) + a.img[ii][d] * a.nL[d] - org[d];
-                ok = ok && loc[d] >= 0 && loc[d] + P < E;
+                    for (int d = 0; d < 3; ++d) {
+                        loc[d] = box_stencil(B[d], a.c, a.n[d], a.p) + a.img[ii][d] * a.nL[d] - org[d];
+                        ok = ok && loc[d] >= 0 && loc[d] + P < E;
+                    }
+                    const int di = a.dix[sl];
+                    if (!ok || di < 0) atomicOr(a.status, PIM_DEV_BOUNDS);
+                    slot[soff + (sl - sg.x) - w0] =
+                        make_int2(ok ? di : -1, loc[0] | (loc[1] << 5) | (loc[2] << 10) | (ii << 15));
+                }
             }
-            if (!ok) {
-                atomicOr(a.status, PIM_DEV_BOUNDS);
-                continue;
-            }
-            // the segments hold dense boxes only: their moments, row (gy, gz)
-            const int di = a.dix[s];
-            if (di < 0) {
-                atomicOr(a.status, PIM_DEV_BOUNDS);
-                continue;
-            }
-            cplx<T> v[NP];
-            const cplx<T>* mr = mom + (((long long)di * NP + gz) * NP + gy) * NP;
+            __syncthreads();
+            // 2. their moments into the local grid (consecutive lanes take
+            // different boxes, so that their atomics fall in different banks)
+#pragma unroll 4
+            for (int w = tid; w < nw * RW; w += LF_GNT) {
+                const int rr = w / nw, f = w - rr * nw;
+                const int gy = rr % NP, gz = rr / NP;
+                const int2 e = slot[f];
+                if (e.x < 0) continue;
+                const int lx = e.y & 31, ly = (e.y >> 5) & 31, lz = (e.y >> 10) & 31, ii = e.y >> 15;
+                const cplx<T>* mr = mom + (((long long)e.x * NP + gz) * NP + gy) * NP;
+                cplx<T> v[NP];
 #pragma unroll
-            for (int jx = 0; jx < NP; ++jx) v[jx] = mr[jx];
-            const double2 phd = a.phase[ii];
-            const cplx<T> ph = mk<T>((T)phd.x, (T)phd.y);
-            const int row = (loc[2] + gz) * E + (loc[1] + gy);
-            T* qr = Qr + row * EX + loc[0];
-            T* qi = Qi + row * EX + loc[0];
+                for (int jx = 0; jx < NP; ++jx) v[jx] = mr[jx];
+                const double2 phd = a.phase[ii];
+                const cplx<T> ph = mk<T>((T)phd.x, (T)phd.y);
+                const int row = (lz + gz) * E + (ly + gy);
+                cplx<T>* qrow = Q + row * XS + lx;
 #pragma unroll
-            for (int jx = 0; jx < NP; ++jx) {
-                const cplx<T> x = cmul(v[jx], ph);
-                atomicAdd(qr + jx, x.x);
-                atomicAdd(qi + jx, x.y);
+                for (int jx = 0; jx < NP; ++jx) {
+                    const cplx<T> x = cmul(v[jx], ph);
+                    atomicAdd(&qrow[jx].x, x.x);
+                    atomicAdd(&qrow[jx].y, x.y);
+                }
+                atomicMin(&xlo[row], lx);
+                atomicMax(&xhi[row], lx + P);
             }
-            rowflag[row] = 1;
         }
         __syncthreads();
         // non-empty rows, in order
         if (warp == 0) {
             int base = 0;
             for (int r0 = 0; r0 < E * E; r0 += 32) {
-                const bool f = r0 + lane < E * E && rowflag[r0 + lane];
+                const bool f = r0 + lane < E * E && xhi[r0 + lane] >= 0;
                 const unsigned b = __ballot_sync(0xffffffffu, f);
                 if (f) rows[base + __popc(b & ((1u << lane) - 1u))] = r0 + lane;
                 base += __popc(b);
@@ -460,56 +557,51 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
             if (lane == 0) *nrows = base;
         }
         __syncthreads();
-        // 2. V_A = g * Q_A at A's stencil nodes
-        {
+        // 3. V_A = g * Q_A at A's stencil nodes
+        if (lane < RW) {
             cplx<T> acc[NP];
 #pragma unroll
             for (int jx = 0; jx < NP; ++jx) acc[jx] = mk<T>(T(0), T(0));
-            const int ay = lane % NP, az = lane / NP;
-            const int oy = X0[1] + ay, oz = X0[2] + az;
+            const int oy = X0[1] + lane % NP, oz = X0[2] + lane / NP;
             const int nr = *nrows;
-            if (lane < RW) {
-                for (int ri = warp; ri < nr; ri += NW) {
-                    const int row = rows[ri];
-                    const int cy = row % E, cz = row / E;
-                    const cplx<T>* grow = gt + ((long long)abs(oz - cz) * H1 + abs(oy - cy)) * H1;
-                    const T* qr = Qr + row * EX;
-                    const T* qi = Qi + row * EX;
-                    // input nodes cb..cb+7: output jx and input cb + i are
-                    // e = X0 + jx - cb - i apart, held as gb[jx - i + 7]
+            for (int ri = warp; ri < nr; ri += NW) {
+                const int row = rows[ri];
+                const int cy = row % E, cz = row / E;
+                const cplx<T>* grow = gt + ((long long)abs(oz - cz) * H1 + abs(oy - cy)) * H1;
+                const cplx<T>* qrow = Q + row * XS;
+                const int cend = xhi[row];
+                // input nodes cb..cb+7: output jx and input cb + i are
+                // e = X0 + jx - cb - i apart, held as gb[jx - i + 7]
 #pragma unroll 1
-                    for (int cb = 0; cb < EX; cb += 8) {
-                        cplx<T> gb[8 + P];
+                for (int cb = xlo[row] & ~7; cb <= cend; cb += 8) {
+                    cplx<T> gb[8 + P];
 #pragma unroll
-                        for (int k = 0; k < 8 + P; ++k) {
-                            gb[k] = grow[min(abs(X0[0] - cb - 7 + k), a.H)];
-                            if (ADJ) gb[k].y = -gb[k].y;
-                        }
+                    for (int k = 0; k < 8 + P; ++k) {
+                        gb[k] = grow[min(abs(X0[0] - cb - 7 + k), a.H)];
+                        if (ADJ && sizeof(T) == 8) gb[k].y = -gb[k].y;
+                    }
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const T xr = qr[cb + i], xi = qi[cb + i];
+                    for (int i = 0; i < 8; ++i) {
+                        const cplx<T> x = qrow[cb + i];
 #pragma unroll
-                            for (int jx = 0; jx < NP; ++jx) {
-                                const cplx<T> g = gb[jx - i + 7];
-                                acc[jx].x += g.x * xr - g.y * xi;
-                                acc[jx].y += g.x * xi + g.y * xr;
-                            }
+                        for (int jx = 0; jx < NP; ++jx) {
+                            const cplx<T> g = gb[jx - i + 7];
+                            acc[jx].x = fma(g.x, x.x, fma(-g.y, x.y, acc[jx].x));
+                            acc[jx].y = fma(g.x, x.y, fma(g.y, x.x, acc[jx].y));
                         }
                     }
                 }
-                (void)oy;
+            }
+            if (nr > warp) {
 #pragma unroll
-                for (int jx = 0; jx < NP; ++jx) Vp[warp * NP * NP * NP + lane * NP + jx] = acc[jx];
+                for (int jx = 0; jx < NP; ++jx) {
+                    atomicAdd(Vr + lane * NP + jx, acc[jx].x);
+                    atomicAdd(Vi + lane * NP + jx, acc[jx].y);
+                }
             }
         }
         __syncthreads();
-        for (int i = tid; i < NP * NP * NP; i += LF_GNT) {
-            cplx<T> t = Vp[i];
-            for (int w = 1; w < NW; ++w) t = cadd(t, Vp[w * NP * NP * NP + i]);
-            Vp[i] = t;
-        }
-        __syncthreads();
-        // 3. the grid part of every point of A
+        // 4. the grid part of every point of A
         for (int i = tid; i < nA; i += LF_GNT) {
             // V is re-read per point: hoisting its NP^3 values out of this
             // loop would not fit in registers
@@ -530,9 +622,9 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
                     cplx<T> r = mk<T>(T(0), T(0));
 #pragma unroll
                     for (int jx = 0; jx < NP; ++jx) {
-                        const cplx<T> vv = Vp[(jz * NP + jy) * NP + jx];
-                        r.x += wx[jx] * vv.x;
-                        r.y += wx[jx] * vv.y;
+                        const int v = (jz * NP + jy) * NP + jx;
+                        r.x += wx[jx] * Vr[v];
+                        r.y += wx[jx] * Vi[v];
                     }
                     const T w = wy[jy] * wz[jz];
                     gsum.x += w * r.x;
@@ -564,6 +656,7 @@ LfArgs lf_args(pim_plan P, const LfGeom& G) {
     a.lfslot = d.lfslot;
     a.segptr = d.segptr;
     a.seg = d.seg;
+    a.lfself = d.lfself;
     a.bstart = d.bstart;
     a.blist = d.blist;
     a.dix = d.dix;
@@ -610,18 +703,21 @@ LfArgs lf_args(pim_plan P, const LfGeom& G) {
     return a;
 }
 
-size_t lf_exact_smem(bool f64) {
-    if (f64) return LF_CH * (sizeof(double4) + sizeof(double2) + sizeof(int));
-    return LF_CH * (sizeof(float4) + sizeof(float2) + sizeof(int)) + LF_MAXOBS * (sizeof(float4) + 2 * sizeof(float));
+// shared memory of the exact-part kernels (the point indices only in check
+// mode, so that three FP32 CTAs fit an SM)
+size_t lf_exact_smem(bool f64, bool check) {
+    const size_t segs = LF_MAXSEG * (sizeof(int4) + sizeof(int));
+    if (f64) return LF_CH * (sizeof(dpos4) + sizeof(double2) + sizeof(int)) + segs;
+    return LF_CH * (sizeof(float4) + sizeof(float2) + (check ? sizeof(int) : 0)) +
+           LF_MAXOBS * (sizeof(float4) + 2 * sizeof(float)) + segs;
 }
 
 template <typename T, int P>
 size_t lf_grid_smem(const LfGeom& G) {
     constexpr int NP = P + 1;
-    const size_t base = 2 * sizeof(T) * (size_t)G.E * G.E * G.EX + sizeof(cplx<T>) * (LF_GNT / 32) * NP * NP * NP +
-                        sizeof(int) * (2 * (size_t)G.E * G.E + 1) + 16;
-    const size_t H1 = (size_t)G.H + 1;
-    return base + (sizeof(T) == 4 ? sizeof(cplx<T>) * H1 * H1 * H1 : 0);
+    const size_t H1 = G.H + 1;
+    return 2 * sizeof(T) * ((size_t)G.E * G.E * (G.EX + 1) + NP * NP * NP) + 32 + LF_MAXSLOT * sizeof(int2) +
+           sizeof(int) * (3 * (size_t)G.E * G.E + 1) + (sizeof(T) == 4 ? sizeof(cplx<T>) * H1 * H1 * H1 : 0);
 }
 
 template <typename K>
@@ -634,7 +730,7 @@ int lf_grid_blocks(long long nlf) { return (int)std::min<long long>(nlf, 152LL *
 
 template <int MODE>
 pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, void* dst, cudaStream_t s) {
-    const size_t sm = lf_exact_smem(false);
+    const size_t sm = lf_exact_smem(false, MODE == 2);
     const int nb = lf_grid_blocks(a.nlf);
     pim_status st;
 #define PIM_LF_EX(NTV)                                                                              \
@@ -653,7 +749,7 @@ pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, vo
 
 template <int MODE>
 pim_status launch_exact_f64(const LfArgs& a, const void* qs, void* dst, cudaStream_t s) {
-    const size_t sm = lf_exact_smem(true);
+    const size_t sm = lf_exact_smem(true, MODE == 2);
     pim_status st;
     if ((st = set_smem(lf_exact_f64<MODE>, sm)) != PIM_OK) return st;
     lf_exact_f64<MODE><<<lf_grid_blocks(a.nlf), LF_NT, sm, s>>>(a, (const double2*)qs, dst);
@@ -668,12 +764,12 @@ pim_status launch_grid(const LfGeom& G, const LfArgs& a, bool adj, const void* q
     pim_status st;
     if (adj) {
         if ((st = set_smem(lf_grid_kernel<T, P, EX, true>, sm)) != PIM_OK) return st;
-        lf_grid_kernel<T, P, EX, true><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(
-            a, (const cplx<T>*)qs, (const cplx<T>*)mom, (const cplx<T>*)gtab, dst);
+        lf_grid_kernel<T, P, EX, true><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(a, (const cplx<T>*)mom,
+                                                                                  (const cplx<T>*)gtab, dst);
     } else {
         if ((st = set_smem(lf_grid_kernel<T, P, EX, false>, sm)) != PIM_OK) return st;
-        lf_grid_kernel<T, P, EX, false><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(
-            a, (const cplx<T>*)qs, (const cplx<T>*)mom, (const cplx<T>*)gtab, dst);
+        lf_grid_kernel<T, P, EX, false><<<lf_grid_blocks(a.nlf), LF_GNT, sm, s>>>(a, (const cplx<T>*)mom,
+                                                                                   (const cplx<T>*)gtab, dst);
     }
     PIM_CK(cudaGetLastError());
     return PIM_OK;
@@ -725,8 +821,8 @@ LfGeom lf_geom(const pim_plan_s* P) {
         // the grid part's shared memory must fit one CTA
         const size_t NP = P->p + 1, H1 = G.H + 1;
         const size_t ts = P->prec == PIM_FP64 ? 8 : 4;
-        const size_t sm = 2 * ts * G.E * G.E * G.EX + 2 * ts * (LF_GNT / 32) * NP * NP * NP + 4 * (2 * G.E * G.E + 1) +
-                          16 + (ts == 4 ? 8 * H1 * H1 * H1 : 0);
+        const size_t sm = 2 * ts * ((size_t)G.E * G.E * (G.EX + 1) + NP * NP * NP) + 32 + 1024 * 8 +
+                          4 * (3 * (size_t)G.E * G.E + 1) + (ts == 4 ? 8 * H1 * H1 * H1 : 0);
         if (sm > 227 * 1024) G.EX = 0;
     }
     return G;
@@ -770,15 +866,15 @@ pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool
     a.real_out = P->real_data && !sorted_out ? 1 : 0;
     a.sorted_out = sorted_out ? 1 : 0;
     pim_status st;
-    if (P->prec == PIM_FP64) {
-        st = adj ? launch_exact_f64<1>(a, qs, dst, s) : launch_exact_f64<0>(a, qs, dst, s);
-        if (st != PIM_OK) return st;
-        st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
-    } else {
-        st = adj ? launch_exact_f32<1>(G, a, qs, dst, s) : launch_exact_f32<0>(G, a, qs, dst, s);
-        if (st != PIM_OK) return st;
-        st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
-    }
+    prof_mark(P, PIM_STAGE_LF_EXACT, 0, s);
+    if (P->prec == PIM_FP64) st = adj ? launch_exact_f64<1>(a, qs, dst, s) : launch_exact_f64<0>(a, qs, dst, s);
+    else st = adj ? launch_exact_f32<1>(G, a, qs, dst, s) : launch_exact_f32<0>(G, a, qs, dst, s);
+    if (st != PIM_OK) return st;
+    prof_mark(P, PIM_STAGE_LF_EXACT, 1, s);
+    prof_mark(P, PIM_STAGE_LF_GRID, 0, s);
+    if (P->prec == PIM_FP64) st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    else st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    prof_mark(P, PIM_STAGE_LF_GRID, 1, s);
     P->launches += 2;
     return st;
 }

@@ -196,6 +196,7 @@ struct PointsData {
     int64_t nlf = 0;              // list-free observer boxes
     int* lfslot = nullptr;        // nlf: slot of each
     int* lfmark = nullptr;        // nne: list-free index of each non-empty box, -1 if stored
+    int* lfself = nullptr;        // nlf: offset of the box's own points in its region list, -1 if absent
     int64_t* segptr = nullptr;    // nlf + 1: first region segment of each
     int4* seg = nullptr;          // nseg: (first slot, end slot, image | slot offset << 8, point offset)
     int64_t nseg = 0;

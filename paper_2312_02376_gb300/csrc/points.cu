@@ -347,18 +347,25 @@ __global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, i
 // box's first segment.  The points of the region's other boxes stay in the
 // stored rows of the box's points; sparse[j] receives their number.
 // seg == nullptr: counts only.
+// lfself[j] (fill pass): the offset of the box's own points in its region's
+// list (-1 if the box has no moments: then they are not in it).
 __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* bstart,
                               const int* dix, const int* lfslot, long long nlf, const int64_t* segptr, int* cnt,
-                              int* sparse, int4* seg) {
+                              int* sparse, int4* seg, int* lfself, unsigned long long* pairs) {
+    int self_img = -1;
+    for (int i = 0; i < a.nimg; ++i)
+        if (a.img[3 * i] == 0 && a.img[3 * i + 1] == 0 && a.img[3 * i + 2] == 0) self_img = i;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nlf; j += (long long)gridDim.x * blockDim.x) {
-        const int b = blist[lfslot[j]];
+        const int sA = lfslot[j];
+        const int b = blist[sA];
         const int B[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
-        int c = 0, soff = 0, ptoff = 0, nsp = 0;
+        int c = 0, soff = 0, ptoff = 0, nsp = 0, self = -1;
         const int64_t o = seg ? segptr[j] : 0;
         for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int, int) {
             int fs = -1, ls = -1;
             auto close = [&]() {
                 if (fs < 0) return;
+                if (ii == self_img && fs <= sA && sA <= ls) self = ptoff + (bstart[sA] - bstart[fs]);
                 if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
                 soff += ls + 1 - fs;
                 ptoff += bstart[ls + 1] - bstart[fs];
@@ -381,6 +388,9 @@ __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, 
         if (!seg) {
             cnt[j] = c;
             sparse[j] = nsp;
+        } else if (lfself) {
+            lfself[j] = self;
+            atomicAdd(pairs, (unsigned long long)(bstart[sA + 1] - bstart[sA]) * (unsigned long long)ptoff);
         }
     }
 }
@@ -835,7 +845,7 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         int* sparse = pos;    // reuse
         const unsigned nb = (unsigned)std::min<long long>((nlf + 127) / 128, 152 * 16);
         lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, nullptr,
-                                         cnt, sparse, nullptr);
+                                         cnt, sparse, nullptr, nullptr, nullptr);
         PIM_CK(cudaGetLastError());
         lf_rowlen_kernel<<<nb, 128, 0, s>>>(d.lfslot, nlf, d.bstart, sparse, rowlen);
         PIM_CK(cudaGetLastError());
@@ -845,14 +855,17 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         PIM_CK(cudaMemcpy(&nseg, d.segptr + nlf, sizeof(int64_t), cudaMemcpyDeviceToHost));
         if ((st = pim_alloc(P, (void**)&d.seg, (size_t)nseg * sizeof(int4))) != PIM_OK) return st;
         d.nseg = nseg;
+        if ((st = pim_alloc(P, (void**)&d.lfself, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
+        PIM_CK(cudaMemsetAsync(tot, 0, sizeof(unsigned long long), s));
         lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, d.segptr,
-                                         nullptr, nullptr, d.seg);
+                                         nullptr, nullptr, d.seg, d.lfself, tot);
         PIM_CK(cudaGetLastError());
         if ((st = pim_alloc(P, (void**)&d.lfp, (size_t)d.N * sizeof(float4))) != PIM_OK) return st;
         lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, d.N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
                                              nullptr, d.lfp);
         PIM_CK(cudaGetLastError());
         if ((st = lf_build_table(P, s)) != PIM_OK) return st;
+        PIM_CK(cudaMemcpy(ht, tot, sizeof(unsigned long long), cudaMemcpyDeviceToHost));  // the exact pairs
     }
     PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, flag, (size_t)nne * sizeof(int));
@@ -1016,6 +1029,7 @@ void points_free(pim_plan P) {
     pim_free(P, d.nbig, (size_t)std::max<int64_t>(1, d.N) * sizeof(int));
     pim_free(P, d.dix, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
     pim_free(P, d.lfslot, (size_t)d.nlf * sizeof(int));
+    pim_free(P, d.lfself, (size_t)d.nlf * sizeof(int));
     pim_free(P, d.lfmark, (size_t)(d.lfmark ? d.nne : 0) * sizeof(int));
     pim_free(P, d.segptr, (size_t)(d.nlf + 1) * sizeof(int64_t));
     pim_free(P, d.seg, (size_t)d.nseg * sizeof(int4));
