@@ -121,8 +121,10 @@ typedef struct {
                             the region's points minus the region's grid interaction,
                             formed from the box moments on a local grid -- and keeps
                             no stored entries.  The same operator as the stored list
-                            (to rounding).  -1: default (32768); 0: off (every
-                            correction stored).  Plans with with_gradient store every
+                            (to rounding).  -1: default (131072: per pair the list-free
+                            sum costs about a third of a stored entry's traffic, per
+                            box it adds a local convolution worth about 10^5 stored
+                            entries); 0: off (every correction stored).  Plans with with_gradient store every
                             correction (the gradient reads the stored derivatives); a
                             correction radius whose local grid exceeds 24 nodes per
                             axis (2b + 2 floor(p/2) + p + 3 > 24) also stores all.   */

@@ -70,15 +70,82 @@ def self_term(k, E):
     return 1j * k * special.erfc(1j * k / (2.0 * E)) / FOUR_PI - E * np.exp(k * k / (4.0 * E * E)) / (2.0 * np.pi * SQRT_PI)
 
 
-def _spatial_images(L, pdims, rcut):
-    rng = []
-    for d in range(3):
-        if d in pdims:
-            M = int(np.ceil(rcut / L[d])) + 1
-            rng.append(np.arange(-M, M + 1))
-        else:
-            rng.append(np.zeros(1, np.int64))
-    return np.stack(np.meshgrid(*rng, indexing="ij"), -1).reshape(-1, 3)
+def spatial_part(points, q, m, L, pdims, k, k0, E, rcut):
+    """The spatial half of Eq. 1 at point m: the sum over sources n and
+    lattice images i of exp(-j k0.(i o L)) f_E(|r_m - r_n - i o L|) q_n over
+    the pairs with |r_m - r_n - i o L| < rcut, the pair (n = m, i = 0)
+    excluded, plus the self term q_m lim [f_E - G0].  Each source is first
+    moved to its nearest image (i0 = round((r_m - r_n) / L) on the periodic
+    axes); the images within rcut are then i = i0 + j with
+    |j_d| <= ceil(rcut / L_d + 1/2).  pdims are the periodic axes (indices
+    into points' columns)."""
+    d0 = points[m] - points
+    i0 = np.zeros_like(d0)
+    for d in pdims:
+        i0[:, d] = np.round(d0[:, d] / L[d])
+    d0 = d0 - i0 * L
+    ph0 = np.exp(-1j * ((i0 * L) @ k0))
+    J = [int(np.ceil(rcut / L[d] + 0.5)) if d in pdims else 0 for d in range(3)]
+    acc = 0.0 + 0.0j
+    for jx in range(-J[0], J[0] + 1):
+        for jy in range(-J[1], J[1] + 1):
+            for jz in range(-J[2], J[2] + 1):
+                sh = np.array([jx, jy, jz]) * L
+                R = np.linalg.norm(d0 - sh, axis=1)
+                sel = R < rcut
+                if jx == 0 and jy == 0 and jz == 0:
+                    sel[m] = False
+                if not sel.any():
+                    continue
+                acc += np.exp(-1j * np.dot(k0, sh)) * np.sum(ph0[sel] * q[sel] * spatial_kernel(R[sel], k, E))
+    return acc + q[m] * self_term(k, E)
+
+
+def spectral_3d_setup(points, q, L, k, k0, E, Gc, chunk=2048):
+    """The 3D lattice spectral half, the part shared by all targets: the
+    wave vectors k_G = k0 + 2 pi (m_x / L_x, m_y / L_y, m_z / L_z) with
+    |k_G| <= Gc and their weights W(k_G) = f(k_G) T(k_G) / V, f =
+    exp((k^2 - |k_G|^2)/4E^2) / (|k_G|^2 - k^2), T(k_G) = sum_n q_n
+    exp(+j k_G.r_n) the structure factor (G = 0 dropped for k = k0 = 0)."""
+    V = np.prod(L)
+    ms = [np.arange(-int(np.ceil(Gc * L[d] / (2 * np.pi))) - 1, int(np.ceil(Gc * L[d] / (2 * np.pi))) + 2)
+          for d in range(3)]
+    kx = k0[0] + 2 * np.pi * ms[0] / L[0]
+    ky = k0[1] + 2 * np.pi * ms[1] / L[1]
+    kz = k0[2] + 2 * np.pi * ms[2] / L[2]
+    K2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.exp((k * k - K2) / (4 * E * E)) / (K2 - k * k)
+    if k == 0 and not np.any(k0 != 0):
+        f[np.abs(K2) == 0] = 0.0
+    f[np.abs(K2) ** 0.5 > Gc + 2 * np.pi / L.min()] = 0.0
+    # structure factor T(kG) = sum_n q_n exp(+j kG . r_n), separable in x, y, z
+    T = np.zeros(K2.shape, np.complex128)
+    for s0 in range(0, len(points), chunk):
+        s1 = min(len(points), s0 + chunk)
+        ex = np.exp(1j * np.outer(points[s0:s1, 0], kx))
+        ey = np.exp(1j * np.outer(points[s0:s1, 1], ky))
+        ez = np.exp(1j * np.outer(points[s0:s1, 2], kz))
+        qa = q[s0:s1, None] * ex
+        yz = (ey[:, :, None] * ez[:, None, :]).reshape(s1 - s0, -1)
+        T += (qa.T @ yz).reshape(K2.shape)
+    return kx, ky, kz, f * T / V
+
+
+def spectral_3d_at(setup, r):
+    """The 3D lattice spectral half at the point r: sum_G W(k_G) exp(-j k_G.r)."""
+    kx, ky, kz, W = setup
+    px = np.exp(-1j * kx * r[0])
+    py = np.exp(-1j * ky * r[1])
+    pz = np.exp(-1j * kz * r[2])
+    return np.einsum("abc,a,b,c->", W, px, py, pz)
+
+
+def splitting_cutoffs(k, E, tol=1e-15):
+    """(X, rcut, Gc): erfc(X) ~ tol, the spatial cutoff X / E and the
+    spectral one 2 E X + |k| + 1."""
+    X = np.sqrt(-np.log(tol)) + 0.5
+    return X, X / E, 2.0 * E * X + abs(k) + 1.0
 
 
 def potential(points, q, tgt, L, pdims, k, k0, E, tol=1e-15, chunk=2048):
@@ -94,55 +161,17 @@ def potential(points, q, tgt, L, pdims, k, k0, E, tol=1e-15, chunk=2048):
     order = pd + [d for d in range(3) if d not in pd]
     points, L, k0 = points[:, order], L[order], k0[order]
     pdc = tuple(range(len(pd)))
-    X = np.sqrt(-np.log(tol)) + 0.5           # erfc(X) ~ tol
-    rcut = X / E
+    X, rcut, Gc = splitting_cutoffs(k, E, tol)
     u = np.zeros(len(tgt), np.complex128)
     # ---------------- spatial part -----------------------------------
-    imgs = _spatial_images(L, pdc, rcut + np.linalg.norm(L[list(pdc)]))
     for t, m in enumerate(tgt):
-        acc = 0.0 + 0.0j
-        for i in imgs:
-            sh = i * L
-            d = points[m] - points - sh
-            R = np.linalg.norm(d, axis=1)
-            sel = R < rcut
-            if not i.any():
-                sel[m] = False
-            if not sel.any():
-                continue
-            ph = np.exp(-1j * np.dot(k0, sh))
-            acc += ph * np.sum(q[sel] * spatial_kernel(R[sel], k, E))
-        u[t] = acc + q[m] * self_term(k, E)
+        u[t] = spatial_part(points, q, m, L, pdc, k, k0, E, rcut)
     # ---------------- spectral part ----------------------------------
-    Gc = 2.0 * E * X + abs(k) + 1.0
     if len(pd) == 3:
         V = np.prod(L)
-        ms = [np.arange(-int(np.ceil(Gc * L[d] / (2 * np.pi))) - 1, int(np.ceil(Gc * L[d] / (2 * np.pi))) + 2) for d in range(3)]
-        kx = k0[0] + 2 * np.pi * ms[0] / L[0]
-        ky = k0[1] + 2 * np.pi * ms[1] / L[1]
-        kz = k0[2] + 2 * np.pi * ms[2] / L[2]
-        # structure factor T(kG) = sum_n q_n exp(+j kG . r_n), separable in x, y, z
-        ex = np.exp(1j * np.outer(points[:, 0], kx))
-        ey = np.exp(1j * np.outer(points[:, 1], ky))
-        ez = np.exp(1j * np.outer(points[:, 2], kz))
-        K2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
-        with np.errstate(divide="ignore", invalid="ignore"):
-            f = np.exp((k * k - K2) / (4 * E * E)) / (K2 - k * k)
-        if k == 0 and not np.any(k0 != 0):
-            f[np.abs(K2) == 0] = 0.0
-        f[np.abs(K2) ** 0.5 > Gc + 2 * np.pi / L.min()] = 0.0
-        T = np.zeros(K2.shape, np.complex128)
-        for s0 in range(0, len(points), chunk):
-            s1 = min(len(points), s0 + chunk)
-            qa = q[s0:s1, None] * ex[s0:s1]
-            yz = (ey[s0:s1, :, None] * ez[s0:s1, None, :]).reshape(s1 - s0, -1)
-            T += (qa.T @ yz).reshape(K2.shape)
-        W = f * T / V
+        setup = spectral_3d_setup(points, q, L, k, k0, E, Gc, chunk)
         for t, m in enumerate(tgt):
-            px = np.exp(-1j * kx * points[m, 0])
-            py = np.exp(-1j * ky * points[m, 1])
-            pz = np.exp(-1j * kz * points[m, 2])
-            u[t] += np.einsum("abc,a,b,c->", W, px, py, pz)
+            u[t] += spectral_3d_at(setup, points[m])
         if k == 0 and not np.any(k0 != 0):
             u += -np.sum(q) / (4 * E * E * V)
     elif len(pd) == 2:

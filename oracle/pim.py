@@ -445,22 +445,43 @@ def _lgf3_x(X, y, z, Lx, Ly, Lz):
     return greens.lgf3_canon(np.asarray(X), y, z, Lx, Ly, Lz)
 
 
+def far_sum(P, F, qg, adjoint=False, direct=None):
+    """Eq. 8: u(a) = sum_b F(a - b) q(b) over the far grid (observer nodes a,
+    source nodes b); adjoint: u(b) = sum_a conj(F(a - b)) q(a).  Summed
+    directly, one source node at a time (the shifted slice of the table F
+    over all a), for far grids up to 30000 nodes (direct = None) or when
+    direct is True; else as the linear convolution of F with q by a library
+    FFT convolution (scipy.signal.fftconvolve), sliced to the observer nodes."""
+    nf = tuple(int(v) for v in P.nf)
+    if direct is False or (direct is None and qg.size > 30000):
+        from scipy.signal import fftconvolve
+        Fk = np.conj(F[::-1, ::-1, ::-1]) if adjoint else F
+        full = fftconvolve(Fk, qg, mode="full")
+        return full[nf[0] - 1:2 * nf[0] - 1, nf[1] - 1:2 * nf[1] - 1, nf[2] - 1:2 * nf[2] - 1]
+    u = np.zeros(nf, np.complex128)
+    for b in zip(*np.nonzero(qg)):
+        sl = tuple(slice(nf[d] - 1 - b[d], 2 * nf[d] - 1 - b[d]) for d in range(3))
+        if adjoint:
+            # u(c) += conj(F(b - c)) q(b): the table reversed about b
+            rs = tuple(slice(nf[d] - 1 + b[d], b[d] - 1 if b[d] > 0 else None, -1) for d in range(3))
+            u += np.conj(F[rs]) * qg[b]
+        else:
+            u += F[sl] * qg[b]
+    return u
+
+
 def far_apply(P, F, ss, ws, so, wo, q):
     """Steps 1-3 of Sec. 3.2: project (Eq. projection), direct grid sum
     (Eq. 8), interpolate (Eq. interpolation)."""
     nf = tuple(P.nf)
     qg = spread(nf, ss, ws, P.pf, q)
-    A = far_matrix(P, F)
-    ug = (A @ qg.ravel()).reshape(nf)
-    return gather(ug, so, wo, P.pf)
+    return gather(far_sum(P, F, qg), so, wo, P.pf)
 
 
 def far_apply_adjoint(P, F, ss, ws, so, wo, v):
     nf = tuple(P.nf)
     vg = spread(nf, so, wo, P.pf, v)
-    A = far_matrix(P, F)
-    ug = (A.conj().T @ vg.ravel()).reshape(nf)
-    return gather(ug, ss, ws, P.pf)
+    return gather(far_sum(P, F, vg, adjoint=True), ss, ws, P.pf)
 
 
 def far_matrix(P, F):
@@ -549,8 +570,7 @@ class Plan:
         if len(P.pdims):
             nf = tuple(P.nf)
             qg = spread(nf, self.ss, self.ws, P.pf, q)
-            A = far_matrix(P, self.F)
-            ug = (A @ qg.ravel()).reshape(nf)
+            ug = far_sum(P, self.F, qg)
         return q, Q, ug
 
     def rows_from(self, state, rows):
@@ -613,9 +633,8 @@ class Plan:
         out = np.real(np.conj(g)[:, None] * obs) + np.real(q[:, None] * np.conj(src))
         if len(P.pdims):
             nf = tuple(P.nf)
-            A = far_matrix(P, self.F)
-            uf = (A @ spread(nf, self.ss, self.ws, P.pf, q).ravel()).reshape(nf)
-            vf = (A.conj().T @ spread(nf, self.so, self.wo, P.pf, g).ravel()).reshape(nf)
+            uf = far_sum(P, self.F, spread(nf, self.ss, self.ws, P.pf, q))
+            vf = far_sum(P, self.F, spread(nf, self.so, self.wo, P.pf, g), adjoint=True)
             obs_f = gather_grad(uf, self.so, self.wo, self.dwo, P.pf)
             src_f = gather_grad(vf, self.ss, self.ws, self.dws, P.pf)
             out += np.real(np.conj(g)[:, None] * obs_f) + np.real(q[:, None] * np.conj(src_f))

@@ -42,6 +42,15 @@ int far_stream_priority() {
     return greatest;
 }
 
+int lf_stream_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return least;
+}
+
 pim_status pim_alloc(pim_plan P, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return PIM_OK;
@@ -156,6 +165,7 @@ void pim_destroy(pim_plan P) {
         pim_free(P, P->qs, gq);
         pim_free(P, P->us, gq);
         pim_free(P, P->ufp, gq);
+        pim_free(P, P->ulf, P->ulf ? gq : 0);
         pim_free(P, P->hq, P->stage_bytes);
         pim_free(P, P->hu, P->stage_bytes);
     }
@@ -191,8 +201,11 @@ void pim_destroy(pim_plan P) {
     }
     if (P->s_far) cudaStreamDestroy(P->s_far);
     if (P->s_main) cudaStreamDestroy(P->s_main);
+    if (P->s_lf) cudaStreamDestroy(P->s_lf);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->ev_lf_fork) cudaEventDestroy(P->ev_lf_fork);
+    if (P->ev_lf_join) cudaEventDestroy(P->ev_lf_join);
     delete P;
 }
 
@@ -236,7 +249,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->autotune = o.autotune ? 1 : 0;
     P->with_gradient = o.with_gradient ? 1 : 0;
     P->force_variant = o.gather_variant;
-    P->lf_min_work = P->with_gradient ? 0 : (o.corr_listfree < 0 ? 32768 : o.corr_listfree);
+    P->lf_min_work = P->with_gradient ? 0 : (o.corr_listfree < 0 ? 131072 : o.corr_listfree);
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
@@ -319,10 +332,15 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     // the far zone's stream takes the highest priority: its short chain ends
     // with the far interpolation, which then runs ahead of the pending blocks
     // of the near gather instead of after them
+    // the list-free exact kernel's stream the lowest: its compute-bound blocks
+    // fill the SMs that the memory-bound near path leaves idle
     if (cudaStreamCreateWithPriority(&P->s_far, cudaStreamNonBlocking, far_stream_priority()) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&P->s_lf, cudaStreamNonBlocking, lf_stream_priority()) != cudaSuccess ||
         cudaStreamCreateWithFlags(&P->s_main, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_lf_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_lf_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         pim_set_error("stream or event creation failed");
         return fail(PIM_ERR_CUDA);
@@ -353,18 +371,18 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     if (P->has_far) {
         if ((st = build_far_table(P, s)) != PIM_OK) return fail(st);
         const long long Gf = (long long)P->nf[0] * P->nf[1] * P->nf[2];
-        if (Gf * 2 * (prec == PIM_FP64 ? 8 : 4) > 200 * 1024) {
-            pim_set_error("far grid too large for the shared-memory far spread");
-            return fail(PIM_ERR_UNSUPPORTED);
-        }
-        P->far_chunks = 304;
+        // far grids that do not fit in shared memory once per CTA are spread
+        // by z-windows (no per-CTA partial grids)
+        P->far_window = Gf * 2 * (prec == PIM_FP64 ? 8 : 4) > 200 * 1024;
+        P->far_chunks = P->far_window ? 0 : 304;
         if ((st = pim_alloc(P, (void**)&P->fA, Gf * sizeof(double2))) != PIM_OK) return fail(st);
         if ((st = pim_alloc(P, (void**)&P->fB, (long long)P->nf[2] * P->nf[1] * P->fg.L[0] * sizeof(double2))) != PIM_OK)
             return fail(st);
         if ((st = pim_alloc(P, (void**)&P->fC, (long long)P->nf[2] * P->fg.L[1] * P->fg.L[0] * sizeof(double2))) !=
             PIM_OK)
             return fail(st);
-        if ((st = pim_alloc(P, &P->fpart, (size_t)P->far_chunks * Gf * ge)) != PIM_OK) return fail(st);
+        if (!P->far_window && (st = pim_alloc(P, &P->fpart, (size_t)P->far_chunks * Gf * ge)) != PIM_OK)
+            return fail(st);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) {
         pim_set_error(cudaGetErrorString(cudaGetLastError()));
@@ -397,7 +415,8 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
         pim_free(P, P->qs, (size_t)P->pts.N * ge);
         pim_free(P, P->us, (size_t)P->pts.N * ge);
         pim_free(P, P->ufp, (size_t)P->pts.N * ge);
-        P->qs = P->us = P->ufp = nullptr;
+        pim_free(P, P->ulf, P->ulf ? (size_t)P->pts.N * ge : 0);
+        P->qs = P->us = P->ufp = P->ulf = nullptr;
         points_free(P);
     }
     const double* dx = xyz;
@@ -418,6 +437,7 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     if ((st = pim_alloc(P, &P->qs, (size_t)N * ge)) != PIM_OK) return st;
     if ((st = pim_alloc(P, &P->us, (size_t)N * ge)) != PIM_OK) return st;
     if (P->has_far && (st = pim_alloc(P, &P->ufp, (size_t)N * ge)) != PIM_OK) return st;
+    if (P->pts.nlf > 0 && (st = pim_alloc(P, &P->ulf, (size_t)N * ge)) != PIM_OK) return st;
     if (P->with_gradient && (st = alloc_grad_buffers(P)) != PIM_OK) return st;
     P->gather_variant = 0;
     if (P->force_variant >= 0) {

@@ -348,18 +348,44 @@ struct FarSpreadArgs {
 // while consecutive points share a stencil start, adding them to shared
 // memory when the start changes (the lanes of one flush write distinct
 // rows, so their atomics do not collide).
-template <typename T, int PF>
+//
+// WIN: for far grids too large for a copy per CTA.  The CTA's points (a run
+// of the box-sorted points, so a thin slab in z) have far stencils in a few
+// consecutive z planes; the CTA accumulates those planes in shared memory
+// and adds them to the FP64 far grid `grid` with atomics (a CTA whose planes
+// do not fit in maxplanes adds its sums to `grid` directly).
+template <typename T, int PF, bool WIN>
 __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const cplx<T>* __restrict__ qs,
-                                                         cplx<T>* part) {
+                                                         cplx<T>* part, double2* grid, int maxplanes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* acc = reinterpret_cast<T*>(smem_raw);
+    __shared__ int zr[2];
     constexpr int NP = PF + 1, KP = (NP * NP + 31) / 32;  // (jy, jz) rows per lane
     static_assert(3 * NP <= 32, "one lane per weight");
-    const int G = a.nf[0] * a.nf[1] * a.nf[2];
-    for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
-    __syncthreads();
+    const int plane = a.nf[0] * a.nf[1];
     const long long m0 = (long long)blockIdx.x * a.chunk;
     const long long m1 = min(a.N, m0 + a.chunk);
+    int G = a.nf[2] * plane, zoff = 0;
+    bool inshared = true;
+    if (WIN) {
+        if (threadIdx.x == 0) {
+            zr[0] = 1 << 30;
+            zr[1] = -1;
+        }
+        __syncthreads();
+        for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+            const int z = (int)((a.fst[m] >> 20) & 1023);
+            atomicMin(&zr[0], z);
+            atomicMax(&zr[1], z);
+        }
+        __syncthreads();
+        zoff = zr[0] * plane;
+        G = (zr[1] - zr[0] + PF + 1) * plane;
+        inshared = zr[1] >= zr[0] && zr[1] - zr[0] + PF + 1 <= maxplanes;
+    }
+    if (inshared)
+        for (int i = threadIdx.x; i < 2 * G; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const long long per = (m1 - m0 + nw - 1) / nw;
     const long long w0 = m0 + wid * per, w1 = min(m1, w0 + per);
@@ -384,8 +410,13 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
             if (act[k]) {
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    atomicAdd(acc + 2 * (base[k] + i), sum[k][i].x);
-                    atomicAdd(acc + 2 * (base[k] + i) + 1, sum[k][i].y);
+                    if (inshared) {
+                        atomicAdd(acc + 2 * (base[k] - zoff + i), sum[k][i].x);
+                        atomicAdd(acc + 2 * (base[k] - zoff + i) + 1, sum[k][i].y);
+                    } else {
+                        atomicAdd(&grid[base[k] + i].x, (double)sum[k][i].x);
+                        atomicAdd(&grid[base[k] + i].y, (double)sum[k][i].y);
+                    }
                 }
             }
     };
@@ -439,19 +470,30 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
     }
     if (cur != 0xffffffffu) flush();
     __syncthreads();
+    if (WIN) {
+        if (inshared)
+            for (int i = threadIdx.x; i < G; i += blockDim.x) {
+                const T re = acc[2 * i], im = acc[2 * i + 1];
+                if (re != T(0) || im != T(0)) {
+                    atomicAdd(&grid[zoff + i].x, (double)re);
+                    atomicAdd(&grid[zoff + i].y, (double)im);
+                }
+            }
+        return;
+    }
     cplx<T>* out = part + (long long)blockIdx.x * G;
     for (int i = threadIdx.x; i < G; i += blockDim.x) out[i] = mk<T>(acc[2 * i], acc[2 * i + 1]);
 }
 
-template <typename T>
-pim_status launch_far_spread(int pf, int grid, size_t sm, cudaStream_t s, const FarSpreadArgs& fa, const cplx<T>* qs,
-                             cplx<T>* part) {
-#define PIM_FAR_CASE(PFV)                                                                                  \
-    case PFV: {                                                                                            \
-        PIM_CK(cudaFuncSetAttribute(far_spread_kernel<T, PFV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    (int)sm));                                                             \
-        far_spread_kernel<T, PFV><<<grid, 256, sm, s>>>(fa, qs, part);                                     \
-        break;                                                                                             \
+template <typename T, bool WIN>
+pim_status launch_far_spread_k(int pf, int grid, size_t sm, cudaStream_t s, const FarSpreadArgs& fa,
+                               const cplx<T>* qs, cplx<T>* part, double2* out, int maxplanes) {
+#define PIM_FAR_CASE(PFV)                                                                                         \
+    case PFV: {                                                                                                   \
+        PIM_CK(cudaFuncSetAttribute(far_spread_kernel<T, PFV, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)sm));                                                                    \
+        far_spread_kernel<T, PFV, WIN><<<grid, 256, sm, s>>>(fa, qs, part, out, maxplanes);                       \
+        break;                                                                                                    \
     }
     switch (pf) {
         PIM_FAR_CASE(2)
@@ -463,6 +505,75 @@ pim_status launch_far_spread(int pf, int grid, size_t sm, cudaStream_t s, const 
     }
 #undef PIM_FAR_CASE
     PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+// qf[g] = sum over CTAs of the partials, in FP64, fixed order: one warp
+// per far node, lanes stride the partials, then a shuffle tree.
+template <typename T>
+__global__ void far_reduce_kernel(const cplx<T>* part, int nchunks, int G, double2* qf) {
+    const int lane = threadIdx.x & 31;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = w0; g < G; g += nw) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int c = lane; c < nchunks; c += 32) {
+            const cplx<T> v = part[(long long)c * G + g];
+            s.x += (double)v.x;
+            s.y += (double)v.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) qf[g] = s;
+    }
+}
+
+// The far grid charges (Eq. projection) of the sorted sources into the FP64
+// grid `out`: per-CTA partial grids in shared memory, reduced in a fixed
+// order (far grids up to 200 KB of plan-precision complex values), or
+// shared-memory z-windows added with FP64 atomics (larger far grids).
+template <typename T>
+pim_status far_spread_grid(pim_plan P, long long N, const uint32_t* fst, int toff, const cplx<T>* src,
+                           double2* out, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    const int G = P->nf[0] * P->nf[1] * P->nf[2];
+    FarSpreadArgs fa{};
+    for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
+    fa.pf = P->pf;
+    fa.N = N;
+    fa.fst = fst;
+    fa.ft = d.ft;
+    fa.ftd = d.ftd;
+    fa.toff = toff;
+    pim_status st;
+    if (!P->far_window) {
+        fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);
+        const size_t sm = 2 * sizeof(T) * G;
+        if (N > 0) {
+            if ((st = launch_far_spread_k<T, false>(P->pf, P->far_chunks, sm, s, fa, src, (cplx<T>*)P->fpart, nullptr,
+                                                    0)) != PIM_OK)
+                return st;
+        } else {
+            PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, s));
+        }
+        far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, s>>>((const cplx<T>*)P->fpart, P->far_chunks, G, out);
+        PIM_CK(cudaGetLastError());
+        P->launches += 2;
+        return PIM_OK;
+    }
+    PIM_CK(cudaMemsetAsync(out, 0, sizeof(double2) * G, s));
+    if (N == 0) return PIM_OK;
+    const int plane = P->nf[0] * P->nf[1];
+    const int maxplanes = (int)std::max<long long>(1, (200 * 1024) / (2 * sizeof(T) * (long long)plane));
+    const int nchunk = (int)std::max<long long>(1, std::min<long long>(152LL * 8, (N + 2047) / 2048));
+    fa.chunk = (int)((N + nchunk - 1) / nchunk);
+    const size_t sm = 2 * sizeof(T) * (size_t)maxplanes * plane;
+    if ((st = launch_far_spread_k<T, true>(P->pf, nchunk, sm, s, fa, src, nullptr, out, maxplanes)) != PIM_OK)
+        return st;
+    P->launches += 1;
     return PIM_OK;
 }
 
@@ -542,29 +653,6 @@ __global__ void far_add_kernel(GatherArgs a, const cplx<T>* __restrict__ ufp, vo
                 *u = mk<T>(u->x + f.x, u->y + f.y);
             }
         }
-    }
-}
-
-// qf[g] = sum over CTAs of the partials, in FP64, fixed order: one warp
-// per far node, lanes stride the partials, then a shuffle tree.
-template <typename T>
-__global__ void far_reduce_kernel(const cplx<T>* part, int nchunks, int G, double2* qf) {
-    const int lane = threadIdx.x & 31;
-    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long g = w0; g < G; g += nw) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int c = lane; c < nchunks; c += 32) {
-            const cplx<T> v = part[(long long)c * G + g];
-            s.x += (double)v.x;
-            s.y += (double)v.y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        }
-        if (lane == 0) qf[g] = s;
     }
 }
 
@@ -1089,27 +1177,9 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             PIM_CK(cudaEventRecord(P->ev_fork, sr));
             PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
             prof_mark(P, PIM_STAGE_FAR, 0, P->s_far);
-            FarSpreadArgs fa{};
-            for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
-            fa.pf = P->pf;
-            fa.N = N;
-            fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);
-            fa.fst = adj ? d.fo : d.fs;
-            fa.ft = d.ft;
-            fa.ftd = d.ftd;
-            fa.toff = adj ? 3 : 0;
             const int G = P->nf[0] * P->nf[1] * P->nf[2];
-            const size_t sm = 2 * sizeof(T) * G;
-            if (N > 0) {
-                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, P->s_far, fa, qs, (cplx<T>*)P->fpart)) !=
-                    PIM_OK)
-                    return st;
-            } else {
-                PIM_CK(cudaMemsetAsync(P->fpart, 0, sizeof(cplx<T>) * G * P->far_chunks, P->s_far));
-            }
-            far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks,
-                                                                             G, P->fA);
-            PIM_CK(cudaGetLastError());
+            if ((st = far_spread_grid<T>(P, N, adj ? d.fo : d.fs, adj ? 3 : 0, qs, P->fA, P->s_far)) != PIM_OK)
+                return st;
             if ((st = fft3_conv<double>(P, P->fg, P->fA, P->fB, P->fC, P->fspec, adj, P->s_far)) != PIM_OK) return st;
             if (sizeof(T) == 4) {
                 far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(P->fA, (cplx<T>*)P->fB, G);
@@ -1135,9 +1205,18 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
                 const cplx<T>* ufar = sizeof(T) == 4 ? (const cplx<T>*)P->fB : (const cplx<T>*)P->fA;
                 if ((st = launch_far_interp<T>(P->pf, N, P->s_far, fg, ufar, (cplx<T>*)P->ufp)) != PIM_OK) return st;
             }
-            P->launches += 2 + 5 + (sizeof(T) == 4 ? 1 : 0) + (N > 0 ? 1 : 0);
+            P->launches += 5 + (sizeof(T) == 4 ? 1 : 0) + (N > 0 ? 1 : 0);
             prof_mark(P, PIM_STAGE_FAR, 1, P->s_far);
             PIM_CK(cudaEventRecord(P->ev_join, P->s_far));
+        }
+        // list-free boxes, one right-hand side: their exact part on its own
+        // stream, while the spread, FFT and gather run
+        const bool lf_async = P->pts.nlf > 0 && P->ulf && nrhs == 1 && N > 0;
+        if (lf_async) {
+            PIM_CK(cudaEventRecord(P->ev_lf_fork, sr));
+            PIM_CK(cudaStreamWaitEvent(P->s_lf, P->ev_lf_fork, 0));
+            if ((st = lf_exact_async(P, qs, adj, P->s_lf)) != PIM_OK) return st;
+            PIM_CK(cudaEventRecord(P->ev_lf_join, P->s_lf));
         }
         // 3. near spread (two phases), 4. FFT convolution
         prof_mark(P, PIM_STAGE_SPREAD, 0, sr);
@@ -1195,7 +1274,12 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         prof_mark(P, PIM_STAGE_GATHER, 1, sr);
         P->launches += N > 0 ? 1 : 0;
         // list-free boxes: exact sum minus grid part, added to the gathered output
-        if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
+        if (lf_async) {
+            PIM_CK(cudaStreamWaitEvent(sr, P->ev_lf_join, 0));
+            if ((st = lf_grid_finish(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
+        } else if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) {
+            return st;
+        }
         if (P->has_far) {
             PIM_CK(cudaStreamWaitEvent(sr, P->ev_join, 0));
             if (N > 0) {
@@ -1308,21 +1392,10 @@ pim_status grad_typed(pim_plan P, const void* q, const void* g, double* grad, in
             PIM_CK(cudaEventRecord(P->ev_fork, s));
             PIM_CK(cudaStreamWaitEvent(P->s_far, P->ev_fork, 0));
             for (int side = 0; side < 2; ++side) {
-                FarSpreadArgs fa{};
-                for (int i = 0; i < 3; ++i) fa.nf[i] = P->nf[i];
-                fa.pf = P->pf;
-                fa.N = N;
-                fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);
-                fa.fst = side == 0 ? d.fs : d.fo;
-                fa.ft = d.ft;
-                fa.ftd = d.ftd;
-                fa.toff = side == 0 ? 0 : 3;
-                const size_t sm = 2 * sizeof(T) * G;
-                if ((st = launch_far_spread<T>(P->pf, P->far_chunks, sm, P->s_far, fa, side == 0 ? qs : gs,
-                                               (cplx<T>*)P->fpart)) != PIM_OK)
-                    return st;
                 double2* fq = side == 0 ? P->fA : P->fD;
-                far_reduce_kernel<T><<<(G * 32 + 255) / 256, 256, 0, P->s_far>>>((const cplx<T>*)P->fpart, P->far_chunks, G, fq);
+                if ((st = far_spread_grid<T>(P, N, side == 0 ? d.fs : d.fo, side == 0 ? 0 : 3, side == 0 ? qs : gs, fq,
+                                             P->s_far)) != PIM_OK)
+                    return st;
                 if ((st = fft3_conv<double>(P, P->fg, fq, P->fB, P->fC, P->fspec, side == 1, P->s_far)) != PIM_OK) return st;
                 far_convert_kernel<T><<<(G + 255) / 256, 256, 0, P->s_far>>>(fq, (cplx<T>*)(side == 0 ? P->fU : P->fV), G);
                 PIM_CK(cudaGetLastError());

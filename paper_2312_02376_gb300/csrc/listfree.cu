@@ -46,8 +46,7 @@ using namespace pim_k;
 constexpr double PI = 3.141592653589793238462643383279502884;
 constexpr int LF_NT = 256;      // threads of the exact-part kernel
 constexpr int LF_CH = 2048;     // region points staged per chunk
-constexpr int LF_OB = 8;        // observers per register group
-constexpr int LF_MAXOBS = 512;  // observers per pass over the region
+constexpr int LF_MAXOBS = 256;  // observers per pass over the region
 constexpr int LF_GNT = 512;     // threads of the grid-part kernel
 constexpr int LF_MAXNT = 8;     // polynomial terms
 constexpr int LF_MAXSEG = 512;  // region segments of a box staged in shared memory
@@ -57,6 +56,8 @@ struct LfArgs {
     const int64_t* segptr;
     const int4* seg;
     const int* lfself;
+    const int* lfnear;
+    const float4* lfl;
     const int* bstart;
     const int* blist;
     const int* dix;
@@ -77,6 +78,8 @@ struct LfArgs {
     long long nlf;
     int nrhs, r, real_out, sorted_out;
     int* status;
+    void* ulf;              // exact part: stored here (sorted order) instead of added to the output;
+                            // grid part: added to the output with it
 };
 
 // an FP64 position padded to 32 bytes
@@ -144,11 +147,13 @@ __device__ __forceinline__ int find_segment(const int4* t, int ns, int f) {
     return lo;
 }
 
-// Reduce-scatter of 16 values over the warp: afterwards lane l holds the
-// warp sum of value (l >> 1) & 15 (lanes 2v and 2v + 1 both hold value v).
-__device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
+// Reduce-scatter of NV values (8 or 16) over the warp: afterwards lane l
+// holds the warp sum of value l >> (5 - log2 NV) (the 32 / NV lanes of a
+// group all hold it).
+template <int NV>
+__device__ __forceinline__ float reduce_scatter(float* v, int lane) {
 #pragma unroll
-    for (int o = 16, h = 8; o >= 2; o >>= 1, h >>= 1) {
+    for (int o = 16, h = NV / 2; h >= 1; o >>= 1, h >>= 1) {
         const bool up = lane & o;
 #pragma unroll
         for (int i = 0; i < h; ++i) {
@@ -157,7 +162,10 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    float r = v[0];
+#pragma unroll
+    for (int o = 16 / NV; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
 }
 
 // ------------------------------ exact part --------------------------------
@@ -202,28 +210,52 @@ __device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float
 // The staged points [0, cnt) against the observers [0, no): warps split the
 // points, lanes take every 32nd of a warp's share, each lane sums LF_OB
 // observers at once; the sums are reduced over the warp and added to sAcc.
-template <int MODE, int NT, bool CHECK>
+// PREC: points and observers as double-float coordinates in grid steps
+// relative to A's centre (heads sX, sO; tails sX + LF_CH / 2, sOl), their
+// differences formed exactly before they are scaled by h; otherwise FP32
+// positions in physical units (sX; observers sO scaled by h).
+template <int MODE, int NT, bool CHECK, bool PREC, int LF_OB>
 __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, const float2* sQ, const float4* sO,
-                                            float* sAcc, int no, int cnt, int warp, int lane) {
+                                            const float4* sOl, float* sAcc, int no, int cnt, int warp, int lane) {
+    constexpr int NV = 2 * LF_OB, SH = NV == 16 ? 1 : 2;   // lane >> SH: the value a lane holds
     const int ngr = (no + LF_OB - 1) / LF_OB;
+    const float4* sXl = sX + LF_CH / 2;
     for (int gi = 0; gi < ngr; ++gi) {
-        float ox[LF_OB], oy[LF_OB], oz[LF_OB], ar[LF_OB], ai[LF_OB];
+        float ox[LF_OB], oy[LF_OB], oz[LF_OB], olx[LF_OB], oly[LF_OB], olz[LF_OB], ar[LF_OB], ai[LF_OB];
 #pragma unroll
         for (int k = 0; k < LF_OB; ++k) {
             const int i = gi * LF_OB + k;
             const float4 O = i < no ? sO[i] : make_float4(1e3f, 1e3f, 1e3f, 0.f);
-            ox[k] = O.x;
-            oy[k] = O.y;
-            oz[k] = O.z;
+            if (PREC) {
+                const float4 Ol = i < no ? sOl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                ox[k] = O.x;
+                oy[k] = O.y;
+                oz[k] = O.z;
+                olx[k] = Ol.x;
+                oly[k] = Ol.y;
+                olz[k] = Ol.z;
+            } else {
+                ox[k] = O.x * a.hf[0];
+                oy[k] = O.y * a.hf[1];
+                oz[k] = O.z * a.hf[2];
+            }
             ar[k] = 0.f;
             ai[k] = 0.f;
         }
         for (int s = warp * 32 + lane; s < cnt; s += LF_NT) {
             const float4 X = sX[s];
             const float2 q = sQ[s];
+            float4 Xl;
+            if (PREC) Xl = sXl[s];
 #pragma unroll
             for (int k = 0; k < LF_OB; ++k) {
-                const float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
+                float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
+                if (PREC) {
+                    // heads of close points differ exactly; add the tails' difference
+                    dx = (dx + (olx[k] - Xl.x)) * a.hf[0];
+                    dy = (dy + (oly[k] - Xl.y)) * a.hf[1];
+                    dz = (dz + (olz[k] - Xl.z)) * a.hf[2];
+                }
                 g0_mac<MODE, NT, CHECK>(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), q, ar[k], ai[k]);
             }
         }
@@ -233,32 +265,34 @@ __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, c
             v[2 * k] = ar[k];
             v[2 * k + 1] = ai[k];
         }
-        const float sum = reduce_scatter16(v, lane);
-        const int vi = (lane >> 1) & 15;
+        const float sum = reduce_scatter<NV>(v, lane);
+        const int vi = lane >> SH;
         const int i = gi * LF_OB + (vi >> 1);
-        if (!(lane & 1) && i < no) atomicAdd(&sAcc[2 * i + (vi & 1)], sum);
+        if (!(lane & ((1 << SH) - 1)) && i < no) atomicAdd(&sAcc[2 * i + (vi & 1)], sum);
     }
 }
 
 // One CTA per list-free box.  The region's points are staged in shared
-// memory LF_CH at a time, each as its position relative to A's centre (FP32,
-// physical units: integer box offset plus the box-centred local coordinate,
-// so that close pairs keep their relative precision) and its source
-// strength times the image phase.  The points are taken in the order: A's
-// own points first (image 0; the only chunks that can hold the pair of a
-// point with itself, summed with the s > 0 test), then the rest of the
-// region's list (every other pair has s > 0: set-points rejects points that
-// coincide, or that FP32 coordinates cannot tell apart).
+// memory, LF_CH at a time (LF_CH / 2 for the double-float chunks), with their
+// source strengths times the image phase, in the order: A's own points
+// (image 0; the only chunks that can hold the pair of a point with itself,
+// summed with the s > 0 test), the other points of the 27 boxes around A
+// (pairs as close as the points come: double-float coordinates in grid steps
+// relative to A's centre, the integer box offset and the box-centred
+// coordinate added exactly), then the rest of the region (at least one box
+// apart: FP32 positions in physical units).  Every pair but a point's own
+// has s > 0: set-points rejects points that coincide.
 //
 // MODE 0: forward, 1: adjoint (conj(G0)), 2: check only (flags pairs of
 // distinct points with s = 0).
 template <int MODE, int NT>
-__global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __restrict__ qs, void* out) {
+__global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2* __restrict__ qs, void* out) {
     extern __shared__ __align__(16) unsigned char smem[];
     float4* sX = (float4*)smem;                          // LF_CH
     float2* sQ = (float2*)(sX + LF_CH);                  // LF_CH
-    float4* sO = (float4*)(sQ + LF_CH);                  // LF_MAXOBS
-    float* sAcc = (float*)(sO + LF_MAXOBS);              // 2 LF_MAXOBS
+    float4* sO = (float4*)(sQ + LF_CH);                  // LF_MAXOBS: heads, grid steps
+    float4* sOl = sO + LF_MAXOBS;                        // LF_MAXOBS: tails
+    float* sAcc = (float*)(sOl + LF_MAXOBS);             // 2 LF_MAXOBS
     int4* sSeg = (int4*)(sAcc + 2 * LF_MAXOBS);          // LF_MAXSEG
     int* sP0 = (int*)(sSeg + LF_MAXSEG);                 // LF_MAXSEG
     int* sIdx = sP0 + LF_MAXSEG;                         // LF_CH (check mode)
@@ -276,31 +310,36 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
         const int4* tab = stage_segments(a, g0, g1, sSeg, sP0, ns, p0t);
         const int4 last = a.seg[g1 - 1];
         const int total = last.w + (a.bstart[last.y] - a.bstart[last.x]);
-        // A's own points sit at [so, so + nA) of the region's list (so < 0:
-        // A has no moments, its pairs with itself are stored)
-        const int so = a.lfself[j];
+        // the region's list: [0, nnear) the 27 boxes around A, with A's own
+        // points at [so, so + nA) (so < 0: A has no moments, its pairs with
+        // itself are stored); taken as [A's points][the rest of the 27
+        // boxes][the others]
+        const int so = a.lfself[j], nnear = a.lfnear[j];
         const int nself = so >= 0 ? nA : 0;
         for (int o0 = 0; o0 < nA; o0 += LF_MAXOBS) {
             const int no = min(LF_MAXOBS, nA - o0);
             __syncthreads();
             for (int i = tid; i < no; i += LF_NT) {
                 const float4 L = a.lfp[m0 + o0 + i];
-                sO[i] = make_float4(L.x * a.hf[0], L.y * a.hf[1], L.z * a.hf[2], 0.f);
+                sO[i] = make_float4(L.x, L.y, L.z, 0.f);
+                sOl[i] = a.lfl[m0 + o0 + i];
                 sAcc[2 * i] = 0.f;
                 sAcc[2 * i + 1] = 0.f;
             }
-            // chunks of the reordered list: v < nself are A's points, the
-            // others the region's list without them
-            for (int v0 = 0; v0 < total; v0 += LF_CH) {
-                const bool own = v0 < nself;
-                const int cnt = own ? min(LF_CH, nself - v0) : min(LF_CH, total - v0);
+            int v0 = 0;
+            while (v0 < total) {
+                const bool own = v0 < nself, prec = v0 < nnear;
+                const int vend = own ? nself : (prec ? nnear : total);
+                const int cnt = min(prec ? LF_CH / 2 : LF_CH, vend - v0);
                 __syncthreads();
                 // stage: every thread finds the segment of each of its points
                 // (binary search) and loads it, the loads of all in flight
 #pragma unroll 4
                 for (int t = tid; t < cnt; t += LF_NT) {
                     const int v = v0 + t;
-                    const int f = own ? so + v : (v - nself < so || so < 0 ? v - nself : v);
+                    int f = v;
+                    if (own) f = so + v;
+                    else if (prec && so >= 0) f = v - nself < so ? v - nself : v;
                     const int gs = find_segment<false>(tab, ns, f);
                     const int4 sg = tab[gs];
                     const int nn = (p0t ? p0t[gs] : a.bstart[sg.x]) + (f - sg.w);
@@ -308,10 +347,19 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
                     const float4 L = a.lfp[nn];
                     int Bn[3];
                     unpack3(__float_as_uint(L.w), Bn[0], Bn[1], Bn[2]);
-                    const float x = ((float)(Bn[0] + a.img[ii][0] * a.nL[0] - A[0]) + L.x) * a.hf[0];
-                    const float y = ((float)(Bn[1] + a.img[ii][1] * a.nL[1] - A[1]) + L.y) * a.hf[1];
-                    const float z = ((float)(Bn[2] + a.img[ii][2] * a.nL[2] - A[2]) + L.z) * a.hf[2];
-                    sX[t] = make_float4(x, y, z, 0.f);
+                    const float bx = (float)(Bn[0] + a.img[ii][0] * a.nL[0] - A[0]);
+                    const float by = (float)(Bn[1] + a.img[ii][1] * a.nL[1] - A[1]);
+                    const float bz = (float)(Bn[2] + a.img[ii][2] * a.nL[2] - A[2]);
+                    if (prec) {
+                        // integer offset + head exactly: s + e (|offset| >= |head| or offset 0)
+                        const float4 Ll = a.lfl[nn];
+                        const float sx = bx + L.x, sy = by + L.y, sz = bz + L.z;
+                        sX[t] = make_float4(sx, sy, sz, 0.f);
+                        sX[LF_CH / 2 + t] = make_float4((L.x - (sx - bx)) + Ll.x, (L.y - (sy - by)) + Ll.y,
+                                                        (L.z - (sz - bz)) + Ll.z, 0.f);
+                    } else {
+                        sX[t] = make_float4((bx + L.x) * a.hf[0], (by + L.y) * a.hf[1], (bz + L.z) * a.hf[2], 0.f);
+                    }
                     if (MODE == 2) {
                         sIdx[t] = ii == a.self_img ? nn : -1;
                     } else {
@@ -326,21 +374,36 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f32(LfArgs a, const float2* __
                     for (int w = tid; w < no * cnt; w += LF_NT) {
                         const int i = w / cnt, s = w - i * cnt;
                         const float4 O = sO[i], X = sX[s];
-                        const float dx = O.x - X.x, dy = O.y - X.y, dz = O.z - X.z;
+                        float dx = O.x - X.x, dy = O.y - X.y, dz = O.z - X.z;
+                        if (prec) {
+                            const float4 Ol = sOl[i], Xl = sX[LF_CH / 2 + s];
+                            dx += Ol.x - Xl.x;
+                            dy += Ol.y - Xl.y;
+                            dz += Ol.z - Xl.z;
+                        } else {
+                            dx = O.x * a.hf[0] - X.x;
+                            dy = O.y * a.hf[1] - X.y;
+                            dz = O.z * a.hf[2] - X.z;
+                        }
                         if (dx * dx + dy * dy + dz * dz == 0.f && sIdx[s] != m0 + o0 + i)
                             atomicOr(a.status, PIM_DEV_COINCIDENT);
                     }
                 } else if (own) {
-                    exact_chunk<MODE, NT, true>(a, sX, sQ, sO, sAcc, no, cnt, warp, lane);
+                    exact_chunk<MODE, NT, true, true, 4>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
+                } else if (prec) {
+                    exact_chunk<MODE, NT, false, true, 4>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
                 } else {
-                    exact_chunk<MODE, NT, false>(a, sX, sQ, sO, sAcc, no, cnt, warp, lane);
+                    exact_chunk<MODE, NT, false, false, 8>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
                 }
-                if (own && v0 + cnt == nself) v0 = nself - LF_CH;  // the region's list starts its own chunk
+                v0 += cnt;
             }
             __syncthreads();
             if (MODE != 2)
-                for (int i = tid; i < no; i += LF_NT)
-                    add_out<float>(a, out, m0 + o0 + i, make_float2(sAcc[2 * i], sAcc[2 * i + 1]));
+                for (int i = tid; i < no; i += LF_NT) {
+                    const float2 v = make_float2(sAcc[2 * i], sAcc[2 * i + 1]);
+                    if (a.ulf) ((float2*)a.ulf)[m0 + o0 + i] = v;
+                    else add_out<float>(a, out, m0 + o0 + i, v);
+                }
         }
     }
 }
@@ -418,7 +481,8 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
                 if (tid < no) {
                     double2 t = make_double2(0.0, 0.0);
                     for (int k = 0; k < stride; ++k) t = cadd(t, sQ[k * no + tid]);
-                    add_out<double>(a, out, m0 + o0 + tid, t);
+                    if (a.ulf) ((double2*)a.ulf)[m0 + o0 + tid] = t;
+                    else add_out<double>(a, out, m0 + o0 + tid, t);
                 }
             }
         }
@@ -630,7 +694,9 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
                     gsum.x += w * r.x;
                     gsum.y += w * r.y;
                 }
-            add_out<T>(a, out, m, mk<T>(-gsum.x, -gsum.y));
+            cplx<T> v = mk<T>(-gsum.x, -gsum.y);
+            if (a.ulf) v = cadd(v, ((const cplx<T>*)a.ulf)[m]);
+            add_out<T>(a, out, m, v);
         }
     }
 }
@@ -657,6 +723,8 @@ LfArgs lf_args(pim_plan P, const LfGeom& G) {
     a.segptr = d.segptr;
     a.seg = d.seg;
     a.lfself = d.lfself;
+    a.lfnear = d.lfnear;
+    a.lfl = d.lfl;
     a.bstart = d.bstart;
     a.blist = d.blist;
     a.dix = d.dix;
@@ -709,7 +777,7 @@ size_t lf_exact_smem(bool f64, bool check) {
     const size_t segs = LF_MAXSEG * (sizeof(int4) + sizeof(int));
     if (f64) return LF_CH * (sizeof(dpos4) + sizeof(double2) + sizeof(int)) + segs;
     return LF_CH * (sizeof(float4) + sizeof(float2) + (check ? sizeof(int) : 0)) +
-           LF_MAXOBS * (sizeof(float4) + 2 * sizeof(float)) + segs;
+           LF_MAXOBS * (2 * sizeof(float4) + 2 * sizeof(float)) + segs;
 }
 
 template <typename T, int P>
@@ -851,6 +919,44 @@ pim_status lf_check(pim_plan P, cudaStream_t s) {
     const LfArgs a = lf_args(P, G);
     if (P->prec == PIM_FP64) return launch_exact_f64<2>(a, nullptr, nullptr, s);
     return launch_exact_f32<2>(G, a, nullptr, nullptr, s);
+}
+
+// The list-free boxes' exact part into P->ulf (sorted order), on stream s:
+// it reads only the sorted sources, so it runs while the spread, FFT and
+// gather of the same apply run on the main stream.
+pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) {
+    if (P->pts.nlf == 0) return PIM_OK;
+    const LfGeom G = lf_geom(P);
+    LfArgs a = lf_args(P, G);
+    a.ulf = P->ulf;
+    pim_status st;
+    prof_mark(P, PIM_STAGE_LF_EXACT, 0, s);
+    if (P->prec == PIM_FP64) st = adj ? launch_exact_f64<1>(a, qs, nullptr, s) : launch_exact_f64<0>(a, qs, nullptr, s);
+    else st = adj ? launch_exact_f32<1>(G, a, qs, nullptr, s) : launch_exact_f32<0>(G, a, qs, nullptr, s);
+    prof_mark(P, PIM_STAGE_LF_EXACT, 1, s);
+    P->launches += 1;
+    return st;
+}
+
+// After lf_exact_async and the gather: dst += ulf - the grid part, for the
+// points of the list-free boxes.
+pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
+                          cudaStream_t s) {
+    if (P->pts.nlf == 0) return PIM_OK;
+    const LfGeom G = lf_geom(P);
+    LfArgs a = lf_args(P, G);
+    a.nrhs = nrhs;
+    a.r = r;
+    a.real_out = P->real_data && !sorted_out ? 1 : 0;
+    a.sorted_out = sorted_out ? 1 : 0;
+    a.ulf = P->ulf;
+    pim_status st;
+    prof_mark(P, PIM_STAGE_LF_GRID, 0, s);
+    if (P->prec == PIM_FP64) st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    else st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    prof_mark(P, PIM_STAGE_LF_GRID, 1, s);
+    P->launches += 1;
+    return st;
 }
 
 // Adds the list-free boxes' corrections to the apply's output: the exact

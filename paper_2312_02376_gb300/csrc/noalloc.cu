@@ -155,11 +155,14 @@ extern "C" pim_status pim_apply_noalloc(pim_plan P, const void* q, void* u, int 
         P->ufp = ptrs[10];
     }
     const bool no_multi = P->no_multi;
+    void* ulf = P->ulf;
     P->no_multi = true;  // the multi-RHS path would allocate its source buffer
     P->keep_off = true;  // the grid potentials live in the borrowed scratch
+    P->ulf = nullptr;    // list-free boxes: the exact and grid parts added in turn, no buffer
     const pim_status st = apply_run(P, q, u, nrhs, adjoint != 0, (cudaStream_t)stream);
     P->no_multi = no_multi;
     P->keep_off = false;
+    P->ulf = ulf;
     P->qs = save[0];
     P->us = save[1];
     P->gA = save[2];

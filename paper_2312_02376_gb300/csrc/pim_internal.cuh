@@ -197,6 +197,8 @@ struct PointsData {
     int* lfslot = nullptr;        // nlf: slot of each
     int* lfmark = nullptr;        // nne: list-free index of each non-empty box, -1 if stored
     int* lfself = nullptr;        // nlf: offset of the box's own points in its region list, -1 if absent
+    int* lfnear = nullptr;        // nlf: points of the 27 surrounding boxes, first in the region list
+    float4* lfl = nullptr;        // N: FP32 rounding of the rest of the box-centred coordinates
     int64_t* segptr = nullptr;    // nlf + 1: first region segment of each
     int4* seg = nullptr;          // nseg: (first slot, end slot, image | slot offset << 8, point offset)
     int64_t nseg = 0;
@@ -244,6 +246,7 @@ struct pim_plan_s {
     double2* fC = nullptr;        // [nfz][Ly][Lx]
     void* fpart = nullptr;        // far spread partials [nchunk][nf^3] complex<T>
     int far_chunks = 0;
+    bool far_window = false;      // far grid spread by z-windows (too large for per-CTA partials)
     // twiddles (cos, sin of 2 pi j / L) per padded length, FP32 and FP64 copies
     float2* tw32 = nullptr;       // concatenated tables, offsets per power of two
     double2* tw64 = nullptr;
@@ -292,6 +295,11 @@ struct pim_plan_s {
     cudaStream_t s_main = nullptr;  // the plan's own stream inside a batched graph
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // list-free boxes: their exact part runs on its own low-priority stream,
+    // concurrently with the spread, FFT and gather, into ulf (sorted order)
+    cudaStream_t s_lf = nullptr;
+    cudaEvent_t ev_lf_fork = nullptr, ev_lf_join = nullptr;
+    void* ulf = nullptr;            // N x complex<T> (plans with list-free boxes)
     double plan_ms = 0, points_ms = 0;
     // extra lanes of a multi-RHS apply: right-hand side r runs its per-RHS
     // stages on lane r % nlanes, each lane with its own scratch and streams
@@ -358,6 +366,10 @@ void lanes_free(pim_plan P);
 // listfree.cu
 pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
                     cudaStream_t s);
+pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s);
+pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
+                          cudaStream_t s);
+int lf_stream_priority();  // the device's lowest stream priority
 pim_status lf_check(pim_plan P, cudaStream_t s);
 pim_status lf_build_table(pim_plan P, cudaStream_t s);
 

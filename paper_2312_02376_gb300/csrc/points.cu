@@ -344,14 +344,16 @@ __global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, i
 // Region segments of every list-free box: runs of consecutive dense boxes
 // (boxes with moments) inside one (image, box row) span, as (first slot, end
 // slot, image | slot offset << 8, point offset), the offsets counted from the
-// box's first segment.  The points of the region's other boxes stay in the
-// stored rows of the box's points; sparse[j] receives their number.
-// seg == nullptr: counts only.
-// lfself[j] (fill pass): the offset of the box's own points in its region's
-// list (-1 if the box has no moments: then they are not in it).
+// box's first segment.  The segments of the 27 boxes around the box (box
+// offsets -1..1 on every axis after the image shift) come first: lfnear[j]
+// receives the number of their points (the exact kernel sums these pairs
+// with double-float coordinates).  The points of the region's other boxes
+// stay in the stored rows of the box's points; sparse[j] receives their
+// number; lfself[j] the offset of the box's own points in the list (-1 if
+// the box has no moments: then they are not in it).  seg == nullptr: counts.
 __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* bstart,
                               const int* dix, const int* lfslot, long long nlf, const int64_t* segptr, int* cnt,
-                              int* sparse, int4* seg, int* lfself, unsigned long long* pairs) {
+                              int* sparse, int4* seg, int* lfself, int* lfnear, unsigned long long* pairs) {
     int self_img = -1;
     for (int i = 0; i < a.nimg; ++i)
         if (a.img[3 * i] == 0 && a.img[3 * i + 1] == 0 && a.img[3 * i + 2] == 0) self_img = i;
@@ -359,37 +361,51 @@ __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, 
         const int sA = lfslot[j];
         const int b = blist[sA];
         const int B[3] = {b % a.nb[0], (b / a.nb[0]) % a.nb[1], b / (a.nb[0] * a.nb[1])};
-        int c = 0, soff = 0, ptoff = 0, nsp = 0, self = -1;
+        int c = 0, soff = 0, ptoff = 0, nsp = 0, self = -1, nnear = 0;
         const int64_t o = seg ? segptr[j] : 0;
-        for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int, int) {
-            int fs = -1, ls = -1;
-            auto close = [&]() {
-                if (fs < 0) return;
-                if (ii == self_img && fs <= sA && sA <= ls) self = ptoff + (bstart[sA] - bstart[fs]);
-                if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
-                soff += ls + 1 - fs;
-                ptoff += bstart[ls + 1] - bstart[fs];
-                ++c;
-                fs = ls = -1;
-            };
-            for (int x = x0; x <= x1; ++x) {
-                const int sl = bslot[row + x];
-                if (sl < 0) continue;
-                if (dix[sl] >= 0) {
-                    if (fs < 0) fs = sl;
-                    ls = sl;
-                } else {
-                    close();
-                    nsp += bstart[sl + 1] - bstart[sl];
+        for (int pass = 0; pass < 2; ++pass) {
+            for_each_region_span(a, box_ptr, B, [&](int ii, long long row, int x0, int x1, int, int) {
+                // offsets of the row from the image-shifted box
+                const int by = (int)((row / a.nb[0]) % a.nb[1]), bz = (int)(row / ((long long)a.nb[0] * a.nb[1]));
+                const int cx = B[0] - a.img[3 * ii] * a.nL[0];
+                const bool nrow = abs(B[1] - a.img[3 * ii + 1] * a.nL[1] - by) <= 1 &&
+                                  abs(B[2] - a.img[3 * ii + 2] * a.nL[2] - bz) <= 1;
+                int fs = -1, ls = -1;
+                auto close = [&]() {
+                    if (fs < 0) return;
+                    if (ii == self_img && fs <= sA && sA <= ls) self = ptoff + (bstart[sA] - bstart[fs]);
+                    if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
+                    soff += ls + 1 - fs;
+                    ptoff += bstart[ls + 1] - bstart[fs];
+                    ++c;
+                    fs = ls = -1;
+                };
+                for (int x = x0; x <= x1; ++x) {
+                    const bool near = nrow && abs(x - cx) <= 1;
+                    const int sl = bslot[row + x];
+                    if (near != (pass == 0)) {
+                        close();  // a box of the other pass breaks the run
+                        continue;
+                    }
+                    if (sl < 0) continue;
+                    if (dix[sl] >= 0) {
+                        if (fs < 0) fs = sl;
+                        ls = sl;
+                    } else {
+                        close();
+                        nsp += bstart[sl + 1] - bstart[sl];
+                    }
                 }
-            }
-            close();
-        });
+                close();
+            });
+            if (pass == 0) nnear = ptoff;
+        }
         if (!seg) {
             cnt[j] = c;
             sparse[j] = nsp;
         } else if (lfself) {
             lfself[j] = self;
+            lfnear[j] = nnear;
             atomicAdd(pairs, (unsigned long long)(bstart[sA + 1] - bstart[sA]) * (unsigned long long)ptoff);
         }
     }
@@ -403,23 +419,27 @@ __global__ void lf_rowlen_kernel(const int* lfslot, long long nlf, const int* bs
     }
 }
 
-// Box-centred local coordinates u - (B + 1/2 for odd p) in grid steps, FP32,
-// and the packed box (its bits in w).  old != nullptr keeps the boxes of an
-// earlier call (frozen topology).
+// Box-centred local coordinates u - (B + 1/2 for odd p) in grid steps as an
+// FP32 head (lfp, with the packed box's bits in w) and the FP32 rounding of
+// the rest (lfl).  old != nullptr keeps the boxes of an earlier call (frozen
+// topology).
 __global__ void lf_point_kernel(const double* pos, long long N, double h0, double h1, double h2, int nb0, int nb1,
-                                int nb2, int p, const float4* old, float4* lfp) {
+                                int nb2, int p, const float4* old, float4* lfp, float4* lfl) {
     const double h[3] = {h0, h1, h2};
     const int nb[3] = {nb0, nb1, nb2};
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
         int B[3];
         if (old) unpack3(__float_as_uint(old[m].w), B[0], B[1], B[2]);
-        float c[3];
+        float c[3], cl[3];
         for (int d = 0; d < 3; ++d) {
             const double u = pos[3 * m + d] / h[d];
             if (!old) B[d] = box_of(u, nb[d], p);
-            c[d] = (float)(u - (B[d] + ((p & 1) ? 0.5 : 0.0)));
+            const double cd = u - (B[d] + ((p & 1) ? 0.5 : 0.0));
+            c[d] = (float)cd;
+            cl[d] = (float)(cd - (double)c[d]);
         }
         lfp[m] = make_float4(c[0], c[1], c[2], __uint_as_float(pack3(B[0], B[1], B[2])));
+        lfl[m] = make_float4(cl[0], cl[1], cl[2], 0.f);
     }
 }
 
@@ -845,7 +865,7 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         int* sparse = pos;    // reuse
         const unsigned nb = (unsigned)std::min<long long>((nlf + 127) / 128, 152 * 16);
         lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, nullptr,
-                                         cnt, sparse, nullptr, nullptr, nullptr);
+                                         cnt, sparse, nullptr, nullptr, nullptr, nullptr);
         PIM_CK(cudaGetLastError());
         lf_rowlen_kernel<<<nb, 128, 0, s>>>(d.lfslot, nlf, d.bstart, sparse, rowlen);
         PIM_CK(cudaGetLastError());
@@ -856,13 +876,15 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         if ((st = pim_alloc(P, (void**)&d.seg, (size_t)nseg * sizeof(int4))) != PIM_OK) return st;
         d.nseg = nseg;
         if ((st = pim_alloc(P, (void**)&d.lfself, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.lfnear, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
         PIM_CK(cudaMemsetAsync(tot, 0, sizeof(unsigned long long), s));
         lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, d.segptr,
-                                         nullptr, nullptr, d.seg, d.lfself, tot);
+                                         nullptr, nullptr, d.seg, d.lfself, d.lfnear, tot);
         PIM_CK(cudaGetLastError());
         if ((st = pim_alloc(P, (void**)&d.lfp, (size_t)d.N * sizeof(float4))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.lfl, (size_t)d.N * sizeof(float4))) != PIM_OK) return st;
         lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, d.N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
-                                             nullptr, d.lfp);
+                                             nullptr, d.lfp, d.lfl);
         PIM_CK(cudaGetLastError());
         if ((st = lf_build_table(P, s)) != PIM_OK) return st;
         PIM_CK(cudaMemcpy(ht, tot, sizeof(unsigned long long), cudaMemcpyDeviceToHost));  // the exact pairs
@@ -945,7 +967,7 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
                                                  d.ftd, P->dstatus);
     if (N > 0 && d.lfp)
         lf_point_kernel<<<1024, 256, 0, s>>>(d.pos, N, P->h[0], P->h[1], P->h[2], P->nb[0], P->nb[1], P->nb[2], P->p,
-                                             d.lfp, d.lfp);
+                                             d.lfp, d.lfp, d.lfl);
     PIM_CK(cudaGetLastError());
     int hstat = 0;
     PIM_CK(cudaMemcpyAsync(&hstat, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1030,6 +1052,8 @@ void points_free(pim_plan P) {
     pim_free(P, d.dix, (size_t)std::max<int64_t>(1, d.nne) * sizeof(int));
     pim_free(P, d.lfslot, (size_t)d.nlf * sizeof(int));
     pim_free(P, d.lfself, (size_t)d.nlf * sizeof(int));
+    pim_free(P, d.lfnear, (size_t)d.nlf * sizeof(int));
+    pim_free(P, d.lfl, d.lfl ? N * sizeof(float4) : 0);
     pim_free(P, d.lfmark, (size_t)(d.lfmark ? d.nne : 0) * sizeof(int));
     pim_free(P, d.segptr, (size_t)(d.nlf + 1) * sizeof(int64_t));
     pim_free(P, d.seg, (size_t)d.nseg * sizeof(int4));

@@ -25,7 +25,8 @@ for them.  Each workload below is named by what it is.
                     their mean, grid 256^3, p = 4, FP32 bulk; energy gradient.
   helmholtz3d_16m   3D-periodic Helmholtz with Bloch phase, k = 2 pi 2,
                     k0 = (0.2k, 0.2k, 0), N = 1.6e7 (3/4 uniform, 1/4 on 8
-                    spheres of radius 0.05), grid 512^3, p = 4.
+                    spheres of radius 0.05), grid 512^3, p = 4, far grid
+                    51^3 (ceil(4 k D), the library's default rule).
 
 "Twins" are the same recipes at a smaller N and grid (for tests whose
 oracle must finish in seconds).
@@ -143,7 +144,7 @@ def coulomb3d_big(N=1_000_000, n=256, index=3, salt=0, b=5, nf=10):
                     (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp32", N, 1, pts, q.astype(np.float32))
 
 
-def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=20):
+def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=51):
     rng = _rng(index, salt)
     nu = (3 * N) // 4
     uni = rng.random((nu, 3))

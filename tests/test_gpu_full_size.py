@@ -124,22 +124,89 @@ def test_helmholtz1d_batch_largest_set_rows():
     pl.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
-def test_helmholtz3d_spheres_recipe_rows(precision, tol):
-    # the 3D-periodic Helmholtz + Bloch recipe (3/4 uniform, 1/4 on 8 small
-    # spheres, k = 2 pi 2, k0 = (0.2k, 0.2k, 0)) at N = 40000 on a 48^3 grid:
-    # sampled rows against the oracle (at the full size of 1.6e7 points the
-    # correction list does not fit in device memory)
-    W = inputs.helmholtz3d(N=40000, n=48, nf=12)
-    pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=precision, b=W.b, nf=W.nf,
-                  pf=W.pf)
-    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
-    dt = torch.complex128 if precision == "fp64" else torch.complex64
-    u = pl.apply(torch.tensor(W.q, dtype=dt, device="cuda")).cpu().numpy()
+@pytest.fixture(scope="module")
+def helmholtz3d_twin():
+    """The 3D-periodic Helmholtz + Bloch recipe (3/4 uniform, 1/4 on 8 spheres
+    of radius 0.05, k = 2 pi 2, k0 = (0.2k, 0.2k, 0)) at N = 2.5e5 on a 128^3
+    grid, and the oracle's rows at 32 points: 16 uniform, 16 on the spheres."""
+    W = inputs.helmholtz3d(N=250_000, n=128)
     P = opim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b, nf=W.nf, pf=W.pf)
     o = opim.Plan(P, W.points)
-    rows = np.concatenate([np.random.default_rng(7).choice(30000, 4, replace=False),
-                           30000 + np.random.default_rng(8).choice(10000, 4, replace=False)])
-    ue = o.apply_rows(W.q.astype(np.complex128), rows)
+    nu = (3 * W.N) // 4
+    rng = np.random.default_rng(17)
+    rows = np.concatenate([rng.choice(nu, 16, replace=False), nu + rng.choice(W.N - nu, 16, replace=False)])
+    q = W.q.astype(np.complex128)
+    return W, rows, o.apply_rows(q, rows)
+
+
+@pytest.mark.parametrize("listfree", [None, 8192])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_helmholtz3d_twin_rows(helmholtz3d_twin, precision, tol, listfree):
+    """Rows of the 128^3 twin against the oracle, with the library's default
+    split of the correction (every box stored at this size) and with the
+    sphere boxes' corrections list-free."""
+    W, rows, ue = helmholtz3d_twin
+    pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=precision, b=W.b, nf=W.nf,
+                  pf=W.pf, listfree=listfree)
+    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    if listfree:
+        assert pl.info().lf_pairs > 0
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    u = pl.apply(torch.tensor(W.q, dtype=dt, device="cuda")).cpu().numpy()
+    assert pl.device_status() == pim.PIM_OK
     assert rel(u[rows], ue) < tol, rel(u[rows], ue)
     pl.close()
+
+
+@pytest.fixture(scope="module")
+def helmholtz3d_16m():
+    """The 3D Helmholtz + Bloch workload at full size (N = 1.6e7, 512^3), FP32
+    bulk with the library's defaults: the launch configuration bench.py times."""
+    W = inputs.helmholtz3d()
+    pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
+                  pf=W.pf)
+    pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    q = torch.tensor(W.q, device="cuda")
+    u = pl.apply(q)
+    yield W, pl, q, u
+    pl.close()
+
+
+def test_helmholtz3d_16m_rows_vs_ewald(helmholtz3d_16m):
+    """32 rows (16 uniform, 16 on the spheres) of the full-size run against
+    the Ewald ground truth, within the method error stated at p = 4."""
+    W, pl, q, u = helmholtz3d_16m
+    info = pl.info()
+    assert info.lf_pairs > 0 and info.nnz > 0
+    rows, ue = read_rows("helmholtz3d_16m_ewald_rows.txt")
+    assert rel(u.cpu().numpy()[rows], ue) < METHOD_TOL, rel(u.cpu().numpy()[rows], ue)
+
+
+def test_helmholtz3d_16m_fp32_vs_fp64_all_points(helmholtz3d_16m):
+    """The FP32-bulk apply and adjoint against the FP64 GPU apply (itself
+    equal to the oracle to 1e-12 on the twins) at every one of the 1.6e7
+    points."""
+    W, pl, q, u = helmholtz3d_16m
+    w = pl.apply_adjoint(q)
+    p64 = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp64", b=W.b, nf=W.nf,
+                   pf=W.pf)
+    p64.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+    q64 = q.to(torch.complex128)
+    u64 = p64.apply(q64)
+    w64 = p64.apply_adjoint(q64)
+    assert p64.device_status() == pim.PIM_OK and pl.device_status() == pim.PIM_OK
+    eu = (torch.linalg.norm(u.to(torch.complex128) - u64) / torch.linalg.norm(u64)).item()
+    ew = (torch.linalg.norm(w.to(torch.complex128) - w64) / torch.linalg.norm(w64)).item()
+    p64.close()
+    assert eu < FP32_TOL and ew < FP32_TOL, (eu, ew)
+
+
+def test_helmholtz3d_16m_adjoint_identity(helmholtz3d_16m):
+    """<g, A q> = <A^H g, q> at full size (complex inner products in FP64)."""
+    W, pl, q, u = helmholtz3d_16m
+    rng = np.random.default_rng(12)
+    g = torch.tensor((rng.standard_normal(W.N) + 1j * rng.standard_normal(W.N)) * np.sqrt(0.5), dtype=torch.complex64,
+                     device="cuda")
+    a = torch.vdot(g.to(torch.complex128), u.to(torch.complex128)).item()
+    b = torch.vdot(pl.apply_adjoint(g).to(torch.complex128), q.to(torch.complex128)).item()
+    assert abs(a - b) < 1e-5 * abs(a), (a, b)

@@ -371,3 +371,21 @@ def test_full_size_helmholtz2d_rows_vs_ewald_golden():
     P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b, nf=W.nf, pf=W.pf)
     u = pim.Plan(P, W.points).apply_rows(W.q.astype(np.complex128), rows)
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 5e-5
+
+
+def test_far_sum_equals_the_dense_operator():
+    """Eq. 8 as the oracle sums it (directly, and by FFT convolution for large
+    far grids) equals the dense matrix A[a, b] = F(a - b) applied to the
+    source-grid charges, forward and adjoint."""
+    rng = np.random.default_rng(4)
+    P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=5.0, k0=(0.7, -0.3, 0), n=(9, 9, 5), nf=(7, 6, 5), pf=3)
+    nf = tuple(int(v) for v in P.nf)
+    F = rng.standard_normal(tuple(2 * v - 1 for v in nf)) + 1j * rng.standard_normal(tuple(2 * v - 1 for v in nf))
+    qg = rng.standard_normal(nf) + 1j * rng.standard_normal(nf)
+    A = pim.far_matrix(P, F)
+    u = (A @ qg.ravel()).reshape(nf)
+    w = (A.conj().T @ qg.ravel()).reshape(nf)
+    for direct in (True, False):
+        assert np.abs(pim.far_sum(P, F, qg, direct=direct) - u).max() < 1e-12 * np.abs(u).max()
+        assert np.abs(pim.far_sum(P, F, qg, adjoint=True, direct=direct) - w).max() < 1e-12 * np.abs(w).max()
+
