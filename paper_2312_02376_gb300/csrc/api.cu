@@ -195,6 +195,7 @@ void pim_destroy(pim_plan P) {
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
     pim_free(P, P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES);
     pim_free(P, P->dstatus, sizeof(int));
+    pim_free(P, P->lfnext, sizeof(unsigned long long) * (pim_plan_s::RHS_LANES + 1));
     if (P->prof_ev) {
         for (int i = 0; i < pim_plan_s::PROF_RING * PIM_NUM_STAGES * 2; ++i) cudaEventDestroy(P->prof_ev[i]);
         delete[] P->prof_ev;
@@ -346,6 +347,8 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
         return fail(PIM_ERR_CUDA);
     }
     if ((st = pim_alloc(P, (void**)&P->dstatus, sizeof(int))) != PIM_OK) return fail(st);
+    if ((st = pim_alloc(P, (void**)&P->lfnext, sizeof(unsigned long long) * (pim_plan_s::RHS_LANES + 1))) != PIM_OK)
+        return fail(st);
     if ((st = pim_alloc(P, (void**)&P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS))) != PIM_OK) return fail(st);
     if ((st = pim_alloc(P, (void**)&P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES)) != PIM_OK)
         return fail(st);

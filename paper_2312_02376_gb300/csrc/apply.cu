@@ -1277,7 +1277,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         if (lf_async) {
             PIM_CK(cudaStreamWaitEvent(sr, P->ev_lf_join, 0));
             if ((st = lf_grid_finish(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
-        } else if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) {
+        } else if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr, lk)) != PIM_OK) {
             return st;
         }
         if (P->has_far) {

@@ -78,6 +78,7 @@ struct LfArgs {
     long long nlf;
     int nrhs, r, real_out, sorted_out;
     int* status;
+    unsigned long long* next;   // box counter of the exact-part kernel
     void* ulf;              // exact part: stored here (sorted order) instead of added to the output;
                             // grid part: added to the output with it
 };
@@ -296,8 +297,17 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
     int4* sSeg = (int4*)(sAcc + 2 * LF_MAXOBS);          // LF_MAXSEG
     int* sP0 = (int*)(sSeg + LF_MAXSEG);                 // LF_MAXSEG
     int* sIdx = sP0 + LF_MAXSEG;                         // LF_CH (check mode)
+    __shared__ long long sj;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
+    // boxes are taken from a counter (zero at launch): the CTAs stay resident
+    // (a set number per SM, leaving room for concurrent kernels) and the
+    // boxes' uneven costs balance out
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sj = (long long)atomicAdd(a.next, 1ULL);
+        __syncthreads();
+        const long long j = sj;
+        if (j >= a.nlf) break;
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
         int A[3];
@@ -768,6 +778,7 @@ LfArgs lf_args(pim_plan P, const LfGeom& G) {
     }
     a.nlf = d.nlf;
     a.status = P->dstatus;
+    a.next = P->lfnext;
     return a;
 }
 
@@ -796,10 +807,16 @@ pim_status set_smem(K kern, size_t bytes) {
 
 int lf_grid_blocks(long long nlf) { return (int)std::min<long long>(nlf, 152LL * 64); }
 
+// resident CTAs of the exact-part kernel per SM: alone, as many as fit; on
+// its own stream next to the spread, FFT and gather, one
+constexpr int LF_CTAS_ALONE = 3, LF_CTAS_SHARED = 3;
+
 template <int MODE>
-pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, void* dst, cudaStream_t s) {
+pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, void* dst, cudaStream_t s,
+                            int ctas_per_sm = LF_CTAS_ALONE) {
     const size_t sm = lf_exact_smem(false, MODE == 2);
-    const int nb = lf_grid_blocks(a.nlf);
+    const int nb = (int)std::min<long long>(a.nlf, 152LL * ctas_per_sm);
+    PIM_CK(cudaMemsetAsync(a.next, 0, sizeof(unsigned long long), s));
     pim_status st;
 #define PIM_LF_EX(NTV)                                                                              \
     do {                                                                                            \
@@ -929,10 +946,13 @@ pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) 
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
     a.ulf = P->ulf;
+    a.next = P->lfnext + pim_plan_s::RHS_LANES;  // its own box counter
     pim_status st;
     prof_mark(P, PIM_STAGE_LF_EXACT, 0, s);
     if (P->prec == PIM_FP64) st = adj ? launch_exact_f64<1>(a, qs, nullptr, s) : launch_exact_f64<0>(a, qs, nullptr, s);
-    else st = adj ? launch_exact_f32<1>(G, a, qs, nullptr, s) : launch_exact_f32<0>(G, a, qs, nullptr, s);
+    else
+        st = adj ? launch_exact_f32<1>(G, a, qs, nullptr, s, LF_CTAS_SHARED)
+                 : launch_exact_f32<0>(G, a, qs, nullptr, s, LF_CTAS_SHARED);
     prof_mark(P, PIM_STAGE_LF_EXACT, 1, s);
     P->launches += 1;
     return st;
@@ -963,10 +983,11 @@ pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r
 // part, then minus the grid part (both read-modify-write dst after the
 // gather has written it).  qs: sorted sources of right-hand side r.
 pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
-                    cudaStream_t s) {
+                    cudaStream_t s, int lane) {
     if (P->pts.nlf == 0) return PIM_OK;
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
+    a.next = P->lfnext + lane;  // the right-hand-side lanes run at once: a box counter each
     a.nrhs = nrhs;
     a.r = r;
     a.real_out = P->real_data && !sorted_out ? 1 : 0;

@@ -300,6 +300,7 @@ struct pim_plan_s {
     cudaStream_t s_lf = nullptr;
     cudaEvent_t ev_lf_fork = nullptr, ev_lf_join = nullptr;
     void* ulf = nullptr;            // N x complex<T> (plans with list-free boxes)
+    unsigned long long* lfnext = nullptr;  // box counters of the exact-part kernel: one per lane, + async
     double plan_ms = 0, points_ms = 0;
     // extra lanes of a multi-RHS apply: right-hand side r runs its per-RHS
     // stages on lane r % nlanes, each lane with its own scratch and streams
@@ -365,7 +366,7 @@ void lanes_free(pim_plan P);
 
 // listfree.cu
 pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
-                    cudaStream_t s);
+                    cudaStream_t s, int lane = 0);
 pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s);
 pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
                           cudaStream_t s);
