@@ -496,8 +496,8 @@ def run_batch(args):
     plans, qs, us, ws = [], [], [], []
     t0 = time.perf_counter()
     for W in sets:
-        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, pf=W.pf,
-                      corr_mode=pim.PIM_CORR_COMPACT)
+        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
+                      pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT)
         pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
         plans.append(pl)
         qs.append(torch.tensor(W.q, device="cuda"))
@@ -532,7 +532,8 @@ def run_batch(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
            "data": "synthetic",
            "config": {"workload": "helmholtz1d_batch", "sets": len(sets), "N_total": NT, "nrhs": R,
-                      "nnz_total": int(nnz), "corr_radius_steps": sets[0].b, "set_points_s": round(t_plan, 1),
+                      "nnz_total": int(nnz), "corr_radius_steps": sets[0].b, "far_grid": list(sets[0].nf),
+                      "set_points_s": round(t_plan, 1),
                       "graph": "one captured graph per direction, replayed"},
            "clocks": clocks}
     for pl in plans:

@@ -20,7 +20,9 @@ for them.  Each workload below is named by what it is.
   helmholtz1d_batch 16 sets, 1D-periodic along z Helmholtz, cell
                     1 x 0.25 x 0.25, k = 2 pi 0.5, N log-uniform in
                     [1e4, 5e5] (half uniform, half in 8 Gaussian clusters of
-                    sigma 0.02), 64 complex64 right-hand sides.
+                    sigma 0.02), 64 complex64 right-hand sides; grid step
+                    half the mean point spacing, correction radius 5 steps,
+                    far grid 20 x 10 x 10.
   coulomb3d_1m      3D static Coulomb, N = 10^6 uniform, charges N(0,1) minus
                     their mean, grid 256^3, p = 4, FP32 bulk; energy gradient.
   helmholtz3d_16m   3D-periodic Helmholtz with Bloch phase, k = 2 pi 2,
@@ -95,12 +97,18 @@ def helmholtz2d(N=262144, n=(128, 128, 64), index=1, salt=0, b=4, nf=(21, 21, 11
                     tuple(n), 4, 1, b, tuple(nf), 4, "fp32", N, 1, pts, q.astype(np.complex64))
 
 
-def helmholtz1d_set(N, index=2, salt=0, b=2, nrhs=64, rng=None):
+def helmholtz1d_set(N, index=2, salt=0, b=5, nrhs=64, rng=None, refine=2, nf=(20, 10, 10)):
     """One point set of the batched 1D-periodic Helmholtz workload: cell
     1 x 0.25 x 0.25, periodic along z (L_z = 0.25), k = 2 pi 0.5, no phase
     shift; half the points uniform, half in 8 Gaussian clusters (sigma 0.02,
     centres uniform, wrapped along z, redrawn if outside the cell in x or y);
-    grid step (V/N)^(1/3) (about one point per node); nrhs CN(0,1) sources."""
+    grid step (V/N)^(1/3) / refine (refine = 2: about eight nodes per point)
+    and correction radius b = 5 steps, which meet the 1e-4 target against the
+    1D-lattice Ewald sum (one node per point needs b = 5 on that grid, a
+    correction list about eight times longer); far grid 20 x 10 x 10 (the
+    length-1 open axis needs 20 nodes: with 13, ceil(4 k D), the far-zone
+    interpolation alone leaves 1.9e-4 on the 2.9e5-point set); nrhs CN(0,1)
+    sources."""
     rng = rng if rng is not None else _rng(index, salt)
     D = np.array([1.0, 0.25, 0.25])
     nu = N // 2
@@ -119,15 +127,15 @@ def helmholtz1d_set(N, index=2, salt=0, b=2, nrhs=64, rng=None):
         pts[:, 2] = np.mod(pts[:, 2], D[2])
         cl.append(pts)
     pts = np.concatenate([uni] + cl)
-    h = (np.prod(D) / N) ** (1.0 / 3.0)
+    h = (np.prod(D) / N) ** (1.0 / 3.0) / refine
     n = tuple(int(max(5, round(D[d] / h) + 1)) for d in range(3))
     q = _cn(rng, (N, nrhs)).astype(np.complex64)
     k = 2 * np.pi * 0.5
     return Workload("helmholtz1d_%d" % N, tuple(D), (2,), k, (0.0, 0.0, 0.0), n, 4, 1, b,
-                    (0, 0, 0), 4, "fp32", N, nrhs, pts, q)
+                    tuple(nf), 4, "fp32", N, nrhs, pts, q)
 
 
-def helmholtz1d_batch(nsets=16, Nmin=10_000, Nmax=500_000, index=2, salt=0, b=2, nrhs=64):
+def helmholtz1d_batch(nsets=16, Nmin=10_000, Nmax=500_000, index=2, salt=0, b=5, nrhs=64):
     """The batched workload: nsets point sets with N log-uniform in
     [Nmin, Nmax] (helmholtz1d_set each)."""
     rng = _rng(index, salt)

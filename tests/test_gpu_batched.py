@@ -98,3 +98,59 @@ def test_batched_graph_equals_single_applies(precision, tol):
     assert rel(us[1], plans[1].apply(qs[1])) < tol
     for pl in plans:
         pl.close()
+
+
+@pytest.fixture(scope="module")
+def helmholtz1d_batch_run():
+    """The batched 1D-periodic Helmholtz workload (16 sets, 64 right-hand
+    sides, FP32 bulk) through one batched graph, as bench.py runs it."""
+    sets = inputs.helmholtz1d_batch()
+    plans, qs, us = [], [], []
+    for W in sets:
+        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
+                      pf=W.pf)
+        pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
+        plans.append(pl)
+        qs.append(torch.tensor(W.q, device="cuda"))
+        us.append(torch.empty_like(qs[-1]))
+    stream = torch.cuda.Stream()
+    pim.pim_apply_batched(plans, qs, us, sets[0].nrhs, adjoint=False, stream=stream)
+    stream.synchronize()
+    out = [u.cpu().numpy() for u in us]
+    infos = [pl.info() for pl in plans]
+    for pl in plans:
+        pl.close()
+    return sets, out, infos
+
+
+def test_helmholtz1d_batch_graph_vs_ewald_rows(helmholtz1d_batch_run):
+    """Rows of the smallest and the largest set, first and last right-hand
+    side, of the batched graph's output against the committed 1D-lattice
+    Ewald ground truth, within the stated method error (1e-4 at p = 4)."""
+    import os
+    sets, out, _ = helmholtz1d_batch_run
+    d = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                "helmholtz1d_batch_ewald_rows.txt"), comments="#")
+    for si in np.unique(d[:, 0].astype(int)):
+        for r in np.unique(d[d[:, 0] == si, 1].astype(int)):
+            sel = (d[:, 0] == si) & (d[:, 1] == r)
+            rows = d[sel, 2].astype(np.int64)
+            ref = d[sel, 3] + 1j * d[sel, 4]
+            e = rel(out[si][rows, r], ref)
+            assert e < 1e-4, (si, r, e)
+
+
+def test_helmholtz1d_batch_graph_vs_oracle_rows(helmholtz1d_batch_run):
+    """The batched graph's output of the smallest and the largest set against
+    the FP64 oracle's rows (FP32 bar), first and last right-hand side."""
+    sets, out, infos = helmholtz1d_batch_run
+    Ns = [W.N for W in sets]
+    for si in (int(np.argmin(Ns)), int(np.argmax(Ns))):
+        W = sets[si]
+        P = opim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=W.p, layers=W.layers, b=W.b,
+                        nf=tuple(infos[si].nf), pf=W.pf)
+        o = opim.Plan(P, W.points)
+        rows = np.random.default_rng(31 + si).choice(W.N, 6, replace=False)
+        for r in (0, W.nrhs - 1):
+            ue = o.apply_rows(W.q[:, r].astype(np.complex128), rows)
+            assert rel(out[si][rows, r], ue) < 2e-5, (si, r, rel(out[si][rows, r], ue))

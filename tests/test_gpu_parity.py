@@ -248,11 +248,11 @@ def test_full_size_coulomb3d_4k_fp64():
 
 def test_full_size_helmholtz2d_262k_sampled_rows():
     # 2D-periodic Helmholtz + Bloch, N = 262144, grid 128 x 128 x 64, FP32 bulk:
-    # sampled rows of the oracle (which the oracle computes one by one)
+    # 256 sampled rows of the oracle (which the oracle computes one by one)
     W = inputs.helmholtz2d(nf=(21, 21, 11))
     pl = gpu_plan(W, "fp32")
     u = pl.apply(torch.tensor(W.q, device="cuda")).cpu().numpy()
-    rows = np.random.default_rng(5).choice(W.N, 12, replace=False)
+    rows = np.random.default_rng(5).choice(W.N, 256, replace=False)
     o = oracle_plan(W)
     ue = o.apply_rows(W.q.astype(np.complex128), rows)
     assert rel(u[rows], ue) < FP32_TOL

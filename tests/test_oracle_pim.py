@@ -202,19 +202,19 @@ def test_npsp3d_vs_ewald_within_method_error():
 
 def test_helmholtz1d_vs_1d_ewald_error_falls_with_correction_radius():
     # The batched 1D-periodic workload's recipe (smallest of its sets, p = 4,
-    # one grid node per point): sampled rows of the operator against the
-    # 1D-lattice Ewald ground truth.  The method error falls with the
-    # correction radius b (about 2e-3, 5e-4, 1e-4, 1e-5 at b = 2..5) and is
-    # below 1e-4 at b = p + 1 = 5, the default.
+    # grid step half the mean point spacing): sampled rows of the operator
+    # against the 1D-lattice Ewald ground truth.  The method error falls with
+    # the correction radius b and is below 1e-4 at the recipe's b = 5 (7e-5;
+    # on a grid with one node per point b = 5 is needed as well, with a
+    # correction list about eight times longer).
     pytest.importorskip("mpmath")
     W = inputs.helmholtz1d_set(11294, rng=np.random.default_rng(17))
     q = (W.q[:, 0] if W.q.ndim == 2 else W.q).astype(complex)
     rows = np.random.default_rng(3).choice(W.N, 12, replace=False)
     ref = ewald.potential(W.points, q, rows, W.D, W.pdims, W.k, W.k0, 2.0)
-    nf = tuple(max(10, int(np.ceil(4.0 * W.k * W.D[d]))) for d in range(3))
     err = []
     for b in (2, 3, 5):
-        P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=4, layers=1, b=b, nf=nf, pf=4)
+        P = pim.Params(D=W.D, pdims=W.pdims, k=W.k, k0=W.k0, n=W.n, p=4, layers=1, b=b, nf=W.nf, pf=4)
         u = pim.Plan(P, W.points).apply_rows(q, rows)
         err.append(np.linalg.norm(u - ref) / np.linalg.norm(ref))
     assert err[0] > err[1] > err[2], err
