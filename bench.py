@@ -206,6 +206,98 @@ def profile_traffic():
     return None
 
 
+def nextpow2(x):
+    v = 1
+    while v < x:
+        v *= 2
+    return v
+
+
+def fft_geometry(W):
+    """Padded FFT lengths (the next power of two >= 2 n - 1 per axis, every
+    axis zero-padded) and the stored spectrum's extent (L/2 + 1 along the
+    axes where the near kernel is even: open, or periodic without a phase
+    shift; L otherwise)."""
+    L = [nextpow2(2 * n - 1) for n in W.n]
+    S = [L[d] // 2 + 1 if (d not in W.pdims or W.k0[d] == 0) else L[d] for d in range(3)]
+    return L, S
+
+
+def stage_bytes(W, info, fp64=False, nbig=0):
+    """Algorithmic HBM bytes of one apply's main-stream stages (one right-hand
+    side): what each stage must read and write at least once.
+      permute         q in, permutation, sorted sources out
+      spread          per point stencil start, local coordinates and sorted
+                      source; the near grid written once (box moments, which
+                      stay in L2, not counted)
+      fft             the five passes: x (n0 n1 n2 in, L0 n1 n2 out), y (L0 n1 n2
+                      in, L0 L1 n2 out), z with the spectrum (L0 L1 n2 in and
+                      out, the stored spectrum in), inverse y and inverse x (the
+                      mirror images of y and x)
+      gather_correct  gather_bytes()"""
+    c, r = (16, 8) if fp64 else (8, 4)
+    N = W.N
+    G = int(np.prod(W.n))
+    (L0, L1, _), S = fft_geometry(W)
+    n0, n1, n2 = W.n
+    xb = (n0 * n1 * n2 + L0 * n1 * n2) * c
+    yb = (L0 * n1 * n2 + L0 * L1 * n2) * c
+    zb = (2 * L0 * L1 * n2 + int(np.prod(S))) * c
+    return {"permute": N * (2 * c + 4), "spread": N * (4 + 3 * r + c) + G * c, "fft": 2 * xb + 2 * yb + zb,
+            "gather_correct": gather_bytes(info, N, G, int(np.prod(W.nf)), fp64, nbig)}
+
+
+def hbm_table(W, info, per, peak, fp64=False, nbig=0):
+    """Per stage and for the whole apply: algorithmic bytes over the CUDA-event
+    time, as a fraction of the measured HBM peak.  The whole-apply figure
+    divides the main-stream stages' bytes by the apply's duration (every
+    stage included, the list-free ones and the far part's join too)."""
+    sb = stage_bytes(W, info, fp64, nbig)
+    out = {}
+    for k, b in sb.items():
+        ms = per.get(k, 0.0)
+        if ms > 0:
+            out[k] = {"bytes": int(b), "ms": round(ms, 4), "GBs": round(b / (ms * 1e-3) / 1e9, 1),
+                      "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4)}
+    tot = sum(sb.values())
+    ams = per.get("apply", 0.0)
+    if ams > 0:
+        out["whole_apply"] = {"bytes": int(tot), "ms": round(ams, 4), "GBs": round(tot / (ams * 1e-3) / 1e9, 1),
+                              "frac": round(tot / (ams * 1e-3) / 1e9 / peak, 4)}
+    return out
+
+
+def cufft_comparison(W, fp64, ours_fft_ms, reps=10):
+    """cuFFT (torch.fft) on the same padded grid: forward 3D transform, the
+    product with a stored spectrum of the full padded size, inverse 3D
+    transform, timed with CUDA events on the current stream.  cuFFT
+    transforms every padded line (no pruning of the zero half on input or of
+    the discarded half on output), so this is the unpruned convolution the
+    library's five passes replace."""
+    import torch
+    L, _ = fft_geometry(W)
+    dt = torch.complex128 if fp64 else torch.complex64
+    shape = (L[2], L[1], L[0])
+    x = torch.zeros(shape, dtype=dt, device="cuda")
+    x[: W.n[2], : W.n[1], : W.n[0]] = 1.0
+    spec = torch.ones(shape, dtype=dt, device="cuda")
+    ts = []
+    for it in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y = torch.fft.ifftn(torch.fft.fftn(x) * spec)
+        e1.record()
+        e1.synchronize()
+        if it >= 2:
+            ts.append(e0.elapsed_time(e1))
+    del x, spec, y
+    torch.cuda.empty_cache()
+    ms = float(np.mean(ts))
+    return {"padded_grid": [L[0], L[1], L[2]], "cufft_fwd_mul_inv_ms": round(ms, 4),
+            "library_fft_stage_ms": round(ours_fft_ms, 4), "speedup": round(ms / ours_fft_ms, 2),
+            "note": "torch.fft.fftn / ifftn (cuFFT), unpruned; timed after the bench's timed region"}
+
+
 # algorithmic FP32 operations of one exact-kernel pair (list-free boxes): the
 # difference vector (3), its square norm (5), 1/r (1), the cos and sinc
 # polynomials in r^2 (2 x 2 (NT - 1)), their product with 1/r (1) and the
@@ -350,6 +442,7 @@ def run_gpu(args):
         # the dominant kernel of the two modelled ones first
         rooflines.sort(key=lambda r: -r["kernel_ms"])
         apply_ms = per["apply"]
+        stages_hbm = hbm_table(W, info, per, peak, fp64, nbig)
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -372,6 +465,7 @@ def run_gpu(args):
             "roofline": rooflines[0],
             "roofline_other": rooflines[1:],
             "stages_ms_per_apply": {k: round(v, 4) for k, v in per.items()},
+            "stages_hbm_per_apply": stages_hbm,
             "apply_ms": round(apply_ms, 4),
             "e2e": {"value": round(e2e_val, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * W.N * elem,
                     "d2h_bytes_per_step": 2 * W.N * elem},
@@ -379,6 +473,8 @@ def run_gpu(args):
             "clocks": clocks,
         }
     plan.close()
+    if rank == 0 and args.cufft:
+        result["cufft_comparison"] = cufft_comparison(W, fp64, per["fft"])
     return rank, world, result
 
 
@@ -484,23 +580,36 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def corr_multi_bytes(info, N, nrhs, fp64=False, nbig=0):
+    """Algorithmic bytes of one multi-RHS correction launch: the list once
+    (value and column per entry, the bf16 tails of the double-float entries),
+    per point its row pointer, row split and permutation; the sorted sources
+    of all right-hand sides read once and the output read and written once."""
+    c = 16 if fp64 else 8
+    per_nnz = VALUE_BYTES[int(info.corr_mode)] + 4
+    return info.nnz * per_nnz + 4 * nbig + (N + 1) * 8 + N * 8 + 3 * N * nrhs * c
+
+
 def run_batch(args):
-    """16 point sets x 64 right-hand sides, one captured graph per direction."""
+    """16 point sets x 64 right-hand sides, one captured graph per direction.
+    --precision fp64: the plain FP64 apply of the same sets (FP64 plans and
+    correction values, each set applied in turn through pim_apply, no graph)."""
     import torch
 
     import __graft_entry__ as g
     g.build()
     from paper_2312_02376_gb300 import inputs, pim
     torch.cuda.set_device(0)
+    fp64 = args.precision == "fp64"
     sets = inputs.helmholtz1d_batch()
     plans, qs, us, ws = [], [], [], []
     t0 = time.perf_counter()
     for W in sets:
-        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
-                      pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT)
+        pl = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=args.precision, b=W.b,
+                      nf=W.nf, pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_COMPACT)
         pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
         plans.append(pl)
-        qs.append(torch.tensor(W.q, device="cuda"))
+        qs.append(torch.tensor(W.q, dtype=torch.complex128 if fp64 else torch.complex64, device="cuda"))
         us.append(torch.empty_like(qs[-1]))
         ws.append(torch.empty_like(qs[-1]))
     t_plan = time.perf_counter() - t0
@@ -508,8 +617,14 @@ def run_batch(args):
     R = sets[0].nrhs
 
     def step():
-        pim.pim_apply_batched(plans, qs, us, R, False, stream)
-        pim.pim_apply_batched(plans, us, ws, R, True, stream)
+        if fp64:
+            for pl, q, u, w in zip(plans, qs, us, ws):
+                pim.pim_apply(pl._h, q, u, R, stream)
+            for pl, q, u, w in zip(plans, qs, us, ws):
+                pim.pim_apply_adjoint(pl._h, u, w, R, stream)
+        else:
+            pim.pim_apply_batched(plans, qs, us, R, False, stream)
+            pim.pim_apply_batched(plans, us, ws, R, True, stream)
 
     for _ in range(args.warmup):
         step()
@@ -527,73 +642,278 @@ def run_batch(args):
     ms = float(np.mean(times))
     NT = sum(W.N for W in sets)
     nnz = sum(pl.info().nnz for pl in plans)
-    out = {"metric": METRIC, "value": round(2.0 * NT * R / (ms * 1e-3) / 1e6, 3), "unit": "Mpts/s (x RHS)",
+
+    # kernels per step: the graph replays the launches of one direct forward
+    # and one direct adjoint call per set (the same capture), counted by the plans
+    l0 = sum(pl.info().launches for pl in plans)
+    with torch.cuda.stream(stream):
+        for pl, q, u, w in zip(plans, qs, us, ws):
+            pim.pim_apply(pl._h, q, u, R, stream)
+            pim.pim_apply_adjoint(pl._h, u, w, R, stream)
+    stream.synchronize()
+    launches = sum(pl.info().launches for pl in plans) - l0
+
+    # stage times of direct calls (one forward and one adjoint per set), for
+    # the multi-RHS correction's roofline and the per-RHS near paths' share
+    peak, peak_kind = measured_peaks()
+    stage_tot = {}
+    corr_bytes = 0
+    for pl, q, u, w, W in zip(plans, qs, us, ws, sets):
+        pl.set_profiling(True)
+        pim.pim_apply(pl._h, q, u, R, stream)
+        pim.pim_apply_adjoint(pl._h, u, w, R, stream)
+        st, _ = pl.stage_times()
+        pl.set_profiling(False)
+        for k, v in st.items():
+            stage_tot[k] = stage_tot.get(k, 0.0) + v
+        info = pl.info()
+        nbig = int(pl.debug(7).astype(np.int64).sum()) if int(info.corr_mode) == 3 else 0
+        corr_bytes += 2 * corr_multi_bytes(info, W.N, R, fp64, nbig)
+    cm_ms = stage_tot.get("corr_multi", 0.0)
+    roofline = {"bound": "hbm", "kernel": "corr_multi_kernel (stored-list correction of all 64 right-hand sides, "
+                                          "one launch per set and direction)",
+                "achieved": round(corr_bytes / (cm_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(corr_bytes / (cm_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_step": int(corr_bytes), "kernel_ms_per_step": round(cm_ms, 3),
+                "note": "launches timed with CUDA events in direct (ungraphed) calls of the same plans"}
+
+    # end to end: every set's sources copied in from pinned host memory, both
+    # graphs, the adjoint's output copied back, inside the timed region
+    qh = [q.cpu().pin_memory() for q in qs]
+    wh = [torch.empty_like(h).pin_memory() for h in qh]
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for h, q in zip(qh, qs):
+                q.copy_(h, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            for h, w in zip(wh, ws):
+                h.copy_(w, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * float(np.mean(e2e_t))
+    io_bytes = sum(h.numel() * h.element_size() for h in qh)
+    unit = "Mpts/s (x RHS)"
+    out = {"metric": METRIC, "value": round(2.0 * NT * R / (ms * 1e-3) / 1e6, 3), "unit": unit,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
-           "data": "synthetic",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c128" if fp64 else "c64+f64", "data": "synthetic",
            "config": {"workload": "helmholtz1d_batch", "sets": len(sets), "N_total": NT, "nrhs": R,
                       "nnz_total": int(nnz), "corr_radius_steps": sets[0].b, "far_grid": list(sets[0].nf),
                       "set_points_s": round(t_plan, 1),
-                      "graph": "one captured graph per direction, replayed"},
+                      "form": ("plain FP64: FP64 plans and correction values, pim_apply per set, no graph" if fp64
+                               else "FP32 bulk, compact correction rows; one captured graph per direction, "
+                                    "replayed"),
+                      "l2": "inputs larger than L2 (64 right-hand sides of 1.6e6 points, 0.8 GB per direction)"},
+           "roofline": roofline,
+           "stage_ms_per_step_direct": {k: round(v, 3) for k, v in stage_tot.items()},
+           "e2e": {"value": round(2.0 * NT * R / (e2e_ms * 1e-3) / 1e6, 3), "unit": unit,
+                   "h2d_bytes_per_step": int(io_bytes), "d2h_bytes_per_step": int(io_bytes)},
+           "gpu_launches": int(launches) * args.steps,
            "clocks": clocks}
     for pl in plans:
         pl.close()
     return out
 
 
+def grad_bytes(info, N, G, fp64=False, nbig=0):
+    """Algorithmic bytes of one position-gradient launch on the kept grid
+    potentials: per entry the column and the three derivative values (FP64
+    or double-float: 48 B; compact rows: the 24 B of FP32 heads, 24 B more for
+    the leading entries summed in double-float); per point the stencil start,
+    local coordinates, permutation, q, g and the FP64 gradient out; the near
+    grid potentials of q and g once (the far ones are small)."""
+    c, r = (16, 8) if fp64 else (8, 4)
+    compact = int(info.corr_mode) == 3
+    per_nnz = 4 + (24 if compact else 48)
+    return info.nnz * per_nnz + 24 * nbig + (N + 1) * 8 + N * (4 + 3 * r + 4 + 2 * c + 24) + 2 * G * c
+
+
 def run_coulomb_grad(args):
     """Differentiated 3D Coulomb, N = 1e6, 256^3, FP32 bulk: forward,
-    adjoint and position gradient per step."""
+    adjoint and position gradient per step (the gradient on the grid
+    potentials the two applies kept).  --precision fp64: the plain FP64
+    form (FP64 plan and values; the full pim_position_grad, which recomputes
+    both grid potentials)."""
     import torch
 
     import __graft_entry__ as g
     g.build()
     from paper_2312_02376_gb300 import inputs, pim
     torch.cuda.set_device(0)
+    fp64 = args.precision == "fp64"
     W = inputs.coulomb3d_big()
     t0 = time.perf_counter()
-    pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b, nf=W.nf,
-                  pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT, with_gradient=True)
+    pl = pim.Plan(W.D, W.pdims, 0.0, W.k0, W.n, p=W.p, layers=W.layers, precision=args.precision, b=W.b, nf=W.nf,
+                  pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_COMPACT, with_gradient=True)
     pl.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     t_plan = time.perf_counter() - t0
-    q = torch.tensor(W.q, device="cuda")
+    rdt = torch.float64 if fp64 else torch.float32
+    q = torch.tensor(W.q, dtype=rdt, device="cuda")
     u = torch.empty_like(q)
     w = torch.empty_like(q)
     gx = torch.empty((W.N, 3), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    gev = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+    gms = []
 
-    def step():
+    def step(timed_grad=False):
         pim.pim_apply(pl._h, q, u, 1, stream)
         pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
-        pim.pim_position_grad_reuse(pl._h, q, u, gx, stream)
+        if timed_grad:
+            gev[0].record(stream)
+        if fp64:
+            pim.pim_position_grad(pl._h, q, u, gx, 1, stream)
+        else:
+            pim.pim_position_grad_reuse(pl._h, q, u, gx, stream)
+        if timed_grad:
+            gev[1].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    launches0 = pl.info().launches
     pl.set_profiling(True)
     clk = ClockSampler(0)
     times = []
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        step(timed_grad=True)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+        gms.append(gev[0].elapsed_time(gev[1]))
     clocks = clk.stop()
     stage_ms, nap = pl.stage_times()
+    pl.set_profiling(False)
+    launches = pl.info().launches - launches0
     ms = float(np.mean(times))
+    info = pl.info()
+    per = {k: v / max(1, nap) for k, v in stage_ms.items()}
+    peak, peak_kind = measured_peaks()
+    nbig = int(pl.debug(7).astype(np.int64).sum()) if int(info.corr_mode) == 3 else 0
+    G = int(np.prod(W.n))
+    gb = gather_bytes(info, W.N, G, int(np.prod(W.nf)), fp64, nbig)
+    grb = grad_bytes(info, W.N, G, fp64, nbig)
+    g_ms = float(np.mean(gms))
+    rooflines = [
+        {"bound": "hbm", "kernel": "gather_kernel (near gather + stored-list correction), per apply",
+         "achieved": round(gb / (per["gather_correct"] * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(gb / (per["gather_correct"] * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+         "traffic": None, "algorithmic_bytes_per_launch": int(gb), "kernel_ms": round(per["gather_correct"], 4)},
+        {"bound": "hbm", "kernel": ("position gradient, full (recomputes both grid potentials)" if fp64 else
+                                    "grad_kernel (position gradient on the kept grid potentials)"),
+         "achieved": round(grb / (g_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(grb / (g_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind, "traffic": None,
+         "algorithmic_bytes_per_launch": int(grb), "kernel_ms": round(g_ms, 4)}]
+    rooflines.sort(key=lambda r: -r["kernel_ms"])
+
+    # end to end: q in from pinned host memory, the step, u and the gradient out
+    qh = q.cpu().pin_memory()
+    uh = torch.empty_like(qh).pin_memory()
+    gh = torch.empty((W.N, 3), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        q.copy_(qh, non_blocking=True)
+        step()
+        uh.copy_(u, non_blocking=True)
+        gh.copy_(gx, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * float(np.mean(e2e_t))
+    rb = q.element_size()
     out = {"metric": METRIC, "value": round(2.0 * W.N / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": "coulomb3d_1m", "N": W.N, "grid": list(W.n), "nnz": int(pl.info().nnz),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32+f64", "data": "synthetic",
+           "config": {"workload": "coulomb3d_1m", "N": W.N, "grid": list(W.n), "nnz": int(info.nnz),
                       "corr_radius_steps": W.b,
-                      "step": "forward + adjoint + position gradient (on the grid potentials the two applies kept)",
-                      "set_points_s": round(t_plan, 1)},
-           "stages_ms_per_apply": {k: round(v / max(1, nap), 4) for k, v in stage_ms.items()},
+                      "step": ("forward + adjoint + full position gradient (plain FP64)" if fp64 else
+                               "forward + adjoint + position gradient (on the grid potentials the two applies "
+                               "kept)"),
+                      "set_points_s": round(t_plan, 1),
+                      "l2": "inputs, list and grids larger than L2"},
+           "roofline": rooflines[0], "roofline_other": rooflines[1:],
+           "stages_ms_per_apply": {k: round(v, 4) for k, v in per.items()},
+           "grad_ms": round(g_ms, 4),
+           "e2e": {"value": round(2.0 * W.N / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                   "h2d_bytes_per_step": W.N * rb, "d2h_bytes_per_step": W.N * rb + W.N * 24},
+           "gpu_launches": int(launches),
            "clocks": clocks}
     pl.close()
     return out
+
+
+def run_timing_report(args):
+    """Pre-processing against execution, and the cost of periodicity (the
+    paper's Sec. 4.2 comparison): for the 2D-periodic 262k workload and the
+    3D-periodic 16M workload, the wall time of pim_plan_create and
+    pim_set_points and the CUDA-event time of a forward and an adjoint apply;
+    then the same points and grid with no periodic axis and no phase shift
+    (no far zone, one image), the apply's time and the periodic overhead
+    t_periodic / t_open - 1."""
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2312_02376_gb300 import pim
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name in ("helmholtz2d_262k", "helmholtz3d_16m"):
+        W = workload(name)
+        res = {"workload": name, "N": W.N, "grid": list(W.n)}
+        for label, pdims, k0 in (("periodic", W.pdims, W.k0), ("open", (), (0.0, 0.0, 0.0))):
+            t0 = time.perf_counter()
+            pl = pim.Plan(W.D, pdims, W.k, k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b,
+                          nf=W.nf if pdims else None, pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT)
+            torch.cuda.synchronize()
+            t_create = time.perf_counter() - t0
+            xyz = torch.tensor(W.points, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pl.set_points(xyz)
+            torch.cuda.synchronize()
+            t_points = time.perf_counter() - t0
+            q = torch.tensor(W.q, dtype=torch.complex64, device="cuda")
+            u = torch.empty_like(q)
+            w = torch.empty_like(q)
+            for _ in range(3):
+                pim.pim_apply(pl._h, q, u, 1, stream)
+                pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
+            ts = []
+            for _ in range(max(3, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pim.pim_apply(pl._h, q, u, 1, stream)
+                pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            info = pl.info()
+            res[label] = {"plan_create_s": round(t_create, 3), "plan_ms_library": round(info.plan_ms, 1),
+                          "set_points_s": round(t_points, 3), "points_ms_library": round(info.points_ms, 1),
+                          "apply_fwd_adj_ms": round(float(np.mean(ts)), 3), "nnz": int(info.nnz),
+                          "listfree_pairs": int(info.lf_pairs)}
+            pl.close()
+            del xyz, q, u, w
+            torch.cuda.empty_cache()
+        res["periodic_overhead"] = round(res["periodic"]["apply_fwd_adj_ms"] / res["open"]["apply_fwd_adj_ms"] - 1, 4)
+        rows.append(res)
+    return {"report": "pre-processing vs execution; periodic vs open", "rows": rows}
 
 
 def main():
@@ -613,6 +933,11 @@ def main():
                     help="pim_options.corr_listfree (default: the library's; 0 stores every correction)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="fp64: the plain FP64 apply of the same workload, for comparison with the FP32-bulk path")
+    ap.add_argument("--cufft", action="store_true",
+                    help="also time cuFFT (torch.fft) on the same padded grid after the timed region")
+    ap.add_argument("--report", default=None, choices=["timing"],
+                    help="timing: plan and set-points times beside the apply, and the periodic overhead "
+                         "(2D 262k and 3D 16M workloads); prints its own JSON line")
     ap.add_argument("--corr-radius", type=int, default=None,
                     help="override the correction radius of the helmholtz2d workloads (for profiler captures "
                          "of the stages that do not depend on it; the line then states the radius used)")
@@ -620,6 +945,9 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.report == "timing":
+        print(json.dumps(run_timing_report(args)))
         return
     if args.workload == "helmholtz1d_batch":
         print(json.dumps(run_batch(args)))

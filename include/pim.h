@@ -159,7 +159,10 @@ typedef enum {
     PIM_STAGE_APPLY = 5,     /* the whole apply, first to last launch                   */
     PIM_STAGE_LF_EXACT = 6,  /* list-free boxes: exact kernel summed over their regions  */
     PIM_STAGE_LF_GRID = 7,   /* list-free boxes: minus the regions' grid interaction    */
-    PIM_NUM_STAGES = 8
+    PIM_STAGE_CORR_MULTI = 8,/* several right-hand sides: the one stored-list correction
+                                launch for all of them (recorded in the ring slot of the
+                                call's last right-hand side)                            */
+    PIM_NUM_STAGES = 9
 } pim_stage;
 
 /* Fills *opt with the defaults documented above. */

@@ -73,7 +73,7 @@ void prof_mark(pim_plan P, int stage, int which, cudaStream_t s) {
     if (!P->prof_on || P->prof_next >= pim_plan_s::PROF_RING) return;
     const int slot = P->prof_next;
     cudaEventRecord(P->prof_ev[(slot * PIM_NUM_STAGES + stage) * 2 + which], s);
-    if (which == 1) P->prof_mask[slot] |= (unsigned char)(1u << stage);
+    if (which == 1) P->prof_mask[slot] |= (unsigned short)(1u << stage);
 }
 
 void pim_free(pim_plan P, void* ptr, size_t bytes) {
@@ -665,7 +665,7 @@ pim_status pim_stage_times(pim_plan P, double* ms, int n, int64_t* count) {
 
 const char* pim_stage_name(int stage) {
     static const char* names[PIM_NUM_STAGES] = {"permute", "spread", "fft", "gather_correct", "far", "apply",
-                                                "lf_exact", "lf_grid"};
+                                                "lf_exact", "lf_grid", "corr_multi"};
     return stage >= 0 && stage < PIM_NUM_STAGES ? names[stage] : nullptr;
 }
 

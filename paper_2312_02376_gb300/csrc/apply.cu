@@ -1133,6 +1133,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
     const bool keep = P->with_gradient && nrhs == 1 && !multi && !P->keep_off && P->gD;
     const int kept = P->pot_valid;
     P->pot_valid = 0;  // until this apply has been issued in full
+    const int prof_slot0 = P->prof_next;  // ring slot of this call's first right-hand side
     if (K > 1) {
         if ((st = lanes_prepare(P, K)) != PIM_OK) return st;
         PIM_CK(cudaEventRecord(P->lane_fork, s));
@@ -1331,6 +1332,10 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ca.phasedf = P->dphasedf;
         const int cm = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
         const unsigned nb = (unsigned)((N * 32 + 255) / 256);
+        // timed in the ring slot of the last right-hand side, if this call recorded any
+        const bool prof_corr = P->prof_on && P->prof_next > prof_slot0;
+        if (prof_corr) --P->prof_next;
+        prof_mark(P, PIM_STAGE_CORR_MULTI, 0, s);
 #define PIM_CM_LAUNCH(CMV)                                                                                   \
     do {                                                                                                     \
         if (nrhs <= 32) corr_multi_kernel<T, CMV, 1><<<nb, 256, 0, s>>>(ca, qsall, u);                      \
@@ -1343,6 +1348,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         else PIM_CM_LAUNCH(PIM_CORR_FP64);
 #undef PIM_CM_LAUNCH
         PIM_CK(cudaGetLastError());
+        prof_mark(P, PIM_STAGE_CORR_MULTI, 1, s);
+        if (prof_corr) ++P->prof_next;
         P->launches += 2;
     }
     if (keep) P->pot_valid = kept | (adj ? 2 : 1);

@@ -268,7 +268,7 @@ struct pim_plan_s {
     bool prof_on = false;
     int prof_next = 0;             // applies recorded since the reset
     cudaEvent_t* prof_ev = nullptr;  // [PROF_RING][PIM_NUM_STAGES][2]
-    unsigned char prof_mask[512];    // stages recorded per ring slot
+    unsigned short prof_mask[512];   // stages recorded per ring slot (bit per stage)
     int64_t launches = 0;
     int gather_variant = 0;       // launch shape of the gather kernel (autotuned)
     int force_variant = -1;       // >= 0: launch shape fixed by the options
