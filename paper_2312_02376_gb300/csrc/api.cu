@@ -206,6 +206,7 @@ void pim_destroy(pim_plan P) {
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     if (P->ev_lf_fork) cudaEventDestroy(P->ev_lf_fork);
+    if (P->ev_lf_mom) cudaEventDestroy(P->ev_lf_mom);
     if (P->ev_lf_join) cudaEventDestroy(P->ev_lf_join);
     delete P;
 }
@@ -341,6 +342,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
         cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_lf_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_lf_mom, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_lf_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         pim_set_error("stream or event creation failed");

@@ -1217,12 +1217,18 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
             PIM_CK(cudaEventRecord(P->ev_lf_fork, sr));
             PIM_CK(cudaStreamWaitEvent(P->s_lf, P->ev_lf_fork, 0));
             if ((st = lf_exact_async(P, qs, adj, P->s_lf)) != PIM_OK) return st;
-            PIM_CK(cudaEventRecord(P->ev_lf_join, P->s_lf));
         }
         // 3. near spread (two phases), 4. FFT convolution
         prof_mark(P, PIM_STAGE_SPREAD, 0, sr);
         if ((st = spread_two_phase<T, PP>(P, qs, gN, sr)) != PIM_OK) return st;
         prof_mark(P, PIM_STAGE_SPREAD, 1, sr);
+        // the list-free boxes' grid part needs the box moments of the spread
+        if (lf_async) {
+            PIM_CK(cudaEventRecord(P->ev_lf_mom, sr));
+            PIM_CK(cudaStreamWaitEvent(P->s_lf, P->ev_lf_mom, 0));
+            if ((st = lf_grid_async(P, qs, adj, P->s_lf)) != PIM_OK) return st;
+            PIM_CK(cudaEventRecord(P->ev_lf_join, P->s_lf));
+        }
         prof_mark(P, PIM_STAGE_FFT, 0, sr);
         if ((st = fft3_conv<T>(P, P->ng, gN, (cplx<T>*)P->gB, (cplx<T>*)P->gC, (const cplx<T>*)P->spec, adj, sr)) != PIM_OK)
             return st;
@@ -1277,7 +1283,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         // list-free boxes: exact sum minus grid part, added to the gathered output
         if (lf_async) {
             PIM_CK(cudaStreamWaitEvent(sr, P->ev_lf_join, 0));
-            if ((st = lf_grid_finish(P, qs, dst, nrhs, r, adj, post_mean, sr)) != PIM_OK) return st;
+            if ((st = lf_add(P, dst, post_mean, sr)) != PIM_OK) return st;
         } else if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr, lk)) != PIM_OK) {
             return st;
         }

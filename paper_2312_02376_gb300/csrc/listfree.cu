@@ -711,6 +711,23 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
     }
 }
 
+// out += ulf for the points of the list-free boxes (one warp per box), after
+// the grid part has been subtracted from ulf on the list-free stream; boxes
+// whose region holds no dense box are skipped, as both list-free kernels skip
+// them (their ulf entries are not written)
+template <typename T>
+__global__ void lf_add_kernel(LfArgs a, const cplx<T>* __restrict__ ulf, void* out) {
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long j = w0; j < a.nlf; j += nw) {
+        if (a.segptr[j + 1] == a.segptr[j]) continue;  // no dense box in its region: nothing was summed
+        const int sA = a.lfslot[j];
+        const int m0 = a.bstart[sA], m1 = a.bstart[sA + 1];
+        for (int m = m0 + lane; m < m1; m += 32) add_out<T>(a, out, m, ulf[m]);
+    }
+}
+
 // g(|e|) on the offsets 0..H per axis: G0(|e o h|), g(0) = 0 (the grid
 // kernel of the near table at zero offset)
 template <typename T>
@@ -958,25 +975,38 @@ pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) 
     return st;
 }
 
-// After lf_exact_async and the gather: dst += ulf - the grid part, for the
-// points of the list-free boxes.
-pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
-                          cudaStream_t s) {
+// After lf_exact_async on the same stream and the spread of the same apply
+// (the box moments): ulf -= the grid part, so that the whole list-free
+// correction is formed off the main stream while the FFT and gather run.
+pim_status lf_grid_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) {
     if (P->pts.nlf == 0) return PIM_OK;
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
-    a.nrhs = nrhs;
-    a.r = r;
-    a.real_out = P->real_data && !sorted_out ? 1 : 0;
-    a.sorted_out = sorted_out ? 1 : 0;
-    a.ulf = P->ulf;
+    a.sorted_out = 1;  // into ulf, sorted order
     pim_status st;
     prof_mark(P, PIM_STAGE_LF_GRID, 0, s);
-    if (P->prec == PIM_FP64) st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
-    else st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, dst, s);
+    if (P->prec == PIM_FP64) st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, P->ulf, s);
+    else st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, P->ulf, s);
     prof_mark(P, PIM_STAGE_LF_GRID, 1, s);
     P->launches += 1;
     return st;
+}
+
+// After lf_grid_async and the gather: dst += ulf for the list-free points.
+pim_status lf_add(pim_plan P, void* dst, bool sorted_out, cudaStream_t s) {
+    if (P->pts.nlf == 0) return PIM_OK;
+    const LfGeom G = lf_geom(P);
+    LfArgs a = lf_args(P, G);
+    a.nrhs = 1;  // the concurrent form serves single right-hand sides
+    a.r = 0;
+    a.real_out = P->real_data && !sorted_out ? 1 : 0;
+    a.sorted_out = sorted_out ? 1 : 0;
+    const unsigned nb = (unsigned)std::min<long long>((P->pts.nlf + 7) / 8, 152 * 16);
+    if (P->prec == PIM_FP64) lf_add_kernel<double><<<nb, 256, 0, s>>>(a, (const double2*)P->ulf, dst);
+    else lf_add_kernel<float><<<nb, 256, 0, s>>>(a, (const float2*)P->ulf, dst);
+    PIM_CK(cudaGetLastError());
+    P->launches += 1;
+    return PIM_OK;
 }
 
 // Adds the list-free boxes' corrections to the apply's output: the exact

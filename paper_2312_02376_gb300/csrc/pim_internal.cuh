@@ -295,10 +295,12 @@ struct pim_plan_s {
     cudaStream_t s_main = nullptr;  // the plan's own stream inside a batched graph
     cudaStream_t s_far = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // list-free boxes: their exact part runs on its own low-priority stream,
-    // concurrently with the spread, FFT and gather, into ulf (sorted order)
+    // list-free boxes (one right-hand side): their exact part, then their grid
+    // part once the spread has formed the box moments, run on their own
+    // low-priority stream into ulf (sorted order), concurrently with the
+    // spread, FFT and gather; ulf is added to the output after the gather
     cudaStream_t s_lf = nullptr;
-    cudaEvent_t ev_lf_fork = nullptr, ev_lf_join = nullptr;
+    cudaEvent_t ev_lf_fork = nullptr, ev_lf_mom = nullptr, ev_lf_join = nullptr;
     void* ulf = nullptr;            // N x complex<T> (plans with list-free boxes)
     unsigned long long* lfnext = nullptr;  // box counters of the exact-part kernel: one per lane, + async
     double plan_ms = 0, points_ms = 0;
@@ -368,8 +370,8 @@ void lanes_free(pim_plan P);
 pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
                     cudaStream_t s, int lane = 0);
 pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s);
-pim_status lf_grid_finish(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,
-                          cudaStream_t s);
+pim_status lf_grid_async(pim_plan P, const void* qs, bool adj, cudaStream_t s);
+pim_status lf_add(pim_plan P, void* dst, bool sorted_out, cudaStream_t s);
 int lf_stream_priority();  // the device's lowest stream priority
 pim_status lf_check(pim_plan P, cudaStream_t s);
 pim_status lf_build_table(pim_plan P, cudaStream_t s);

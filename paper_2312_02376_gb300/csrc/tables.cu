@@ -126,6 +126,10 @@ struct FarArgs {
     int nimg;
     const int* img;
     const double2* phase;
+    // 3D lattice, Eq. pgf_3: bit c set when axis c may serve as the series'
+    // image axis (no Floquet mode of the other two axes has k_z = 0); each
+    // entry takes the allowed axis along which its terms decay fastest
+    int zaxes;
 };
 
 constexpr int FAR_NT = 128;
@@ -229,31 +233,60 @@ __global__ void __launch_bounds__(FAR_NT) far_table_kernel(FarArgs a, double2* o
         }
     } else {
         // ------------------------- Eq. pgf_2 / pgf_3 -----------------------
-        const double dlen = a.npd == 2 ? fabs(z) : fmin(fabs(z), Lz - fabs(z));
-        const int M = mode_window(a.k0c[0], Lx, dlen, a.k);
-        const int N = mode_window(a.k0c[1], Ly, dlen, a.k);
+        // For the 3D lattice the sum is the same whichever axis plays z: the
+        // modes needed grow as Lx Ly / dlen^2 (dlen the distance to the
+        // nearest image plane along z), so the axis with the largest
+        // Lz dlen^2 is taken (among those allowed by a.zaxes).
+        double xs = x, ys = y, zs = z, Lxs = Lx, Lys = Ly, Lzs = Lz;
+        double k0x = a.k0c[0], k0y = a.k0c[1], k0z = a.k0c[2];
+        if (a.npd == 3) {
+            int cz = 2;
+            double best = -1.0;
+            for (int c = 0; c < 3; ++c) {
+                if (!(a.zaxes & (1 << c))) continue;
+                const double dl = fmin(fabs(r[c]), a.Lc[c] - fabs(r[c]));
+                const double score = a.Lc[c] * dl * dl;
+                if (score > best) {
+                    best = score;
+                    cz = c;
+                }
+            }
+            const int c1 = cz == 0 ? 1 : 0, c2 = cz == 2 ? 1 : 2;  // the other two, in order
+            xs = r[c1];
+            ys = r[c2];
+            zs = r[cz];
+            Lxs = a.Lc[c1];
+            Lys = a.Lc[c2];
+            Lzs = a.Lc[cz];
+            k0x = a.k0c[c1];
+            k0y = a.k0c[c2];
+            k0z = a.k0c[cz];
+        }
+        const double dlen = a.npd == 2 ? fabs(zs) : fmin(fabs(zs), Lzs - fabs(zs));
+        const int M = mode_window(k0x, Lxs, dlen, a.k);
+        const int N = mode_window(k0y, Lys, dlen, a.k);
         const int W = 2 * N + 1;
         const long long nm = (long long)(2 * M + 1) * W;
-        const double A = Lx * Ly;
+        const double A = Lxs * Lys;
         for (long long t = tid; t < nm; t += FAR_NT) {
             const int m = (int)(t / W) - M, n = (int)(t % W) - N;
-            const double kx = a.k0c[0] + 2.0 * PI * m / Lx;
-            const double ky = a.k0c[1] + 2.0 * PI * n / Ly;
+            const double kx = k0x + 2.0 * PI * m / Lxs;
+            const double ky = k0y + 2.0 * PI * n / Lys;
             const double2 kz = kz_branch(a.k * a.k - kx * kx - ky * ky);
-            double2 zf = cexp_mj(kz, fabs(z));
+            double2 zf = cexp_mj(kz, fabs(zs));
             if (a.npd == 3) {
                 // z-image factor of Eq. pgf_3; numerators with their exponents
                 // combined: e^{-j kz (Lz + z)} e^{j kz0 Lz}, e^{-j kz (Lz - z)} e^{-j kz0 Lz}
-                const double2 km = make_double2(kz.x - a.k0c[2], kz.y), kp = make_double2(kz.x + a.k0c[2], kz.y);
-                const double2 em = cexp_mj(km, Lz), ep = cexp_mj(kp, Lz);
+                const double2 km = make_double2(kz.x - k0z, kz.y), kp = make_double2(kz.x + k0z, kz.y);
+                const double2 em = cexp_mj(km, Lzs), ep = cexp_mj(kp, Lzs);
                 const double2 one = make_double2(1.0, 0.0);
-                const double2 t2 = cdiv(cmul(cexp_mj(kz, Lz + z), cexpj(a.k0c[2] * Lz)), csub(one, em));
-                const double2 t3 = cdiv(cmul(cexp_mj(kz, Lz - z), cexpj(-a.k0c[2] * Lz)), csub(one, ep));
+                const double2 t2 = cdiv(cmul(cexp_mj(kz, Lzs + zs), cexpj(k0z * Lzs)), csub(one, em));
+                const double2 t3 = cdiv(cmul(cexp_mj(kz, Lzs - zs), cexpj(-k0z * Lzs)), csub(one, ep));
                 zf = cadd(zf, cadd(t2, t3));
             }
             // / (2 j kz A)
             const double2 den = make_double2(-2.0 * kz.y * A, 2.0 * kz.x * A);
-            acc = cadd(acc, cmul(cexpj(-(kx * x + ky * y)), cdiv(zf, den)));
+            acc = cadd(acc, cmul(cexpj(-(kx * xs + ky * ys)), cdiv(zf, den)));
         }
     }
     red[tid] = acc;
@@ -428,6 +461,16 @@ pim_status build_far_table(pim_plan P, cudaStream_t s) {
         pim_set_error("Rayleigh-Wood anomaly: a Floquet mode has k_z (or k_rho) = 0 for these k, k0, L");
         return PIM_ERR_ANOMALY;
     }
+    // 3D lattice: the axes that may serve as the series' z axis (z itself
+    // always can, having passed the check above)
+    a.zaxes = 1 << 2;
+    if (P->npd == 3)
+        for (int c = 0; c < 2; ++c) {
+            const int c1 = c == 0 ? 1 : 0, c2 = 2;
+            const double Lr[3] = {a.Lc[c1], a.Lc[c2], a.Lc[c]};
+            const double kr[3] = {a.k0c[c1], a.k0c[c2], a.k0c[c]};
+            if (!wood_anomaly(P, Lr, kr)) a.zaxes |= 1 << c;
+        }
     pim_status st;
     int* dimg = nullptr;
     double2* dph = nullptr;
