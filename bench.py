@@ -70,6 +70,8 @@ def workload(name=WORKLOAD):
         return inputs.helmholtz3d()
     if name == "helmholtz3d_4m":    # the same recipe on 256^3: the same points per box on the spheres
         return inputs.helmholtz3d(N=4_000_000, n=256)
+    if name == "helmholtz3d_spheres_1m":  # the sphere points alone on 256^3: the same points per sphere box
+        return inputs.helmholtz3d(N=1_000_000, n=256, uniform=0.0)
     if name == "helmholtz3d_250k":  # the same recipe on 128^3
         return inputs.helmholtz3d(N=250_000, n=128)
     if name == "helmholtz2d_65k":   # the same recipe at a quarter of the points and half the grid per axis
@@ -924,10 +926,12 @@ def main():
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "helmholtz3d_4m", "helmholtz3d_250k", "helmholtz2d_262k", "helmholtz2d_65k",
+                    choices=[WORKLOAD, "helmholtz3d_4m", "helmholtz3d_spheres_1m", "helmholtz3d_250k", "helmholtz2d_262k",
+                             "helmholtz2d_65k",
                              "helmholtz1d_batch", "coulomb3d_1m"],
                     help="helmholtz3d_4m / _250k, helmholtz2d_65k: the same recipes, smaller, for profiler "
-                         "captures; helmholtz1d_batch: 16 sets x 64 right-hand sides, batched graph; "
+                         "captures; helmholtz3d_spheres_1m: the sphere points alone on 256^3 (list-free kernel "
+                         "captures); helmholtz1d_batch: 16 sets x 64 right-hand sides, batched graph; "
                          "coulomb3d_1m: forward + adjoint + position gradient")
     ap.add_argument("--listfree", type=int, default=None,
                     help="pim_options.corr_listfree (default: the library's; 0 stores every correction)")

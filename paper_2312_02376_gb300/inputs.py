@@ -152,9 +152,11 @@ def coulomb3d_big(N=1_000_000, n=256, index=3, salt=0, b=5, nf=10):
                     (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp32", N, 1, pts, q.astype(np.float32))
 
 
-def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=51):
+def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=51, uniform=0.75):
+    """The 3D-periodic Helmholtz + Bloch recipe; `uniform` is the fraction
+    of uniform points (the rest on the 8 spheres)."""
     rng = _rng(index, salt)
-    nu = (3 * N) // 4
+    nu = int(round(uniform * N))
     uni = rng.random((nu, 3))
     rest = N - nu
     centres = 0.05 + 0.9 * rng.random((8, 3))
