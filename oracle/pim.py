@@ -242,8 +242,10 @@ def in_region(P, dB):
 
 
 def correction_pairs(P, B, rows=None):
-    """All (m, n, image) with |B(m) - B(n) - i o (n-1)|_inf <= b (Sec. 3.3 step 4
-    with the single-extra-image rule).  Returns arrays m, n, image index."""
+    """All (m, n, image) whose boxes B(m) and B(n) + i o (n-1) lie in each
+    other's error-correction region (in_region: minimum box distance at most
+    b steps, or Chebyshev distance for region "cube"; Sec. 3.3 step 4 with the
+    single-extra-image rule).  Returns arrays m, n, image index."""
     rows = np.arange(len(B)) if rows is None else np.asarray(rows)
     I = P.images()
     M, Nn, Ii = [], [], []
