@@ -127,7 +127,18 @@ typedef struct {
                             entries); 0: off (every correction stored).  Plans with with_gradient store every
                             correction (the gradient reads the stored derivatives); a
                             correction radius whose local grid exceeds 24 nodes per
-                            axis (2b + 2 floor(p/2) + p + 3 > 24) also stores all.   */
+                            axis (2b + 2 floor(p/2) + p + 3 > 24) also stores all;
+                            and so does a complex wavenumber (k_imag != 0).          */
+    double k_imag;       /* imaginary part of k (Sec. 2: a lossy medium has Im k < 0;
+                            must be <= 0 and finite); default 0                        */
+    double k0_imag[3];   /* imaginary parts of the phase shift (k_x0, k_y0, k_z0), 0 on
+                            non-periodic axes; default 0.  With k_imag or k0_imag
+                            nonzero the far series are summed in complex arithmetic;
+                            the 1D series then evaluates H0^(2) of complex arguments
+                            and returns PIM_ERR_UNSUPPORTED for an argument z = krho rho
+                            of modulus 6..20 within 0.17 rad of the real axis (a weakly
+                            lossy propagating mode); with_gradient plans must have
+                            real k and k0 (PIM_ERR_UNSUPPORTED)                      */
 } pim_options;
 
 typedef struct {
@@ -189,9 +200,10 @@ const char* pim_last_error(void);
  *                  period is L_d = D_d.
  *   periodic_mask  bit d set: periodic along axis d (0 = free space, near
  *                  zone only).
- *   k              wavenumber (k_0 of the paper), real, >= 0.
- *   k0             phase shift per axis (k_x0, k_y0, k_z0), real; must be 0 on
- *                  non-periodic axes.
+ *   k              wavenumber (k_0 of the paper), real part, >= 0; its
+ *                  imaginary part (a lossy medium, Sec. 2) is opt->k_imag.
+ *   k0             phase shift per axis (k_x0, k_y0, k_z0), real parts; must be 0
+ *                  on non-periodic axes; imaginary parts in opt->k0_imag.
  *   h              grid spacing per axis: D_d / h_d must be an integer; the
  *                  grid has n_d = D_d / h_d + 1 nodes spanning [0, D_d].
  *   p              near Lagrange degree (p+1 nodes per axis), 2..4.

@@ -135,6 +135,8 @@ void pim_options_default(pim_options* o) {
     o->corr_split = 10;
     o->gather_variant = -1;
     o->corr_listfree = -1;
+    o->k_imag = 0.0;
+    for (int d = 0; d < 3; ++d) o->k0_imag[d] = 0.0;
 }
 
 const char* pim_status_string(pim_status s) {
@@ -193,7 +195,7 @@ void pim_destroy(pim_plan P) {
     pim_free(P, P->tw32, 2048 * sizeof(float2));
     pim_free(P, P->tw64, 2048 * sizeof(double2));
     pim_free(P, P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS));
-    pim_free(P, P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES);
+    pim_free(P, P->dphase, 2 * (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES);
     pim_free(P, P->dstatus, sizeof(int));
     pim_free(P, P->lfnext, sizeof(unsigned long long) * (pim_plan_s::RHS_LANES + 1));
     if (P->prof_ev) {
@@ -237,6 +239,16 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
         pim_set_error("interpolation degree p must be 2, 3 or 4 on the GPU path");
         return PIM_ERR_UNSUPPORTED;
     }
+    const bool cplx = o.k_imag != 0.0 || o.k0_imag[0] != 0.0 || o.k0_imag[1] != 0.0 || o.k0_imag[2] != 0.0;
+    if (!(o.k_imag <= 0.0) || !std::isfinite(o.k0_imag[0]) || !std::isfinite(o.k0_imag[1]) ||
+        !std::isfinite(o.k0_imag[2])) {
+        pim_set_error("Im k must be <= 0 (a lossy medium) and the phase shift finite");
+        return PIM_ERR_ARG;
+    }
+    if (cplx && o.with_gradient) {
+        pim_set_error("the position gradient needs a real k and k0");
+        return PIM_ERR_UNSUPPORTED;
+    }
     pim_plan P = new pim_plan_s();
     auto fail = [&](pim_status st) {
         pim_destroy(P);
@@ -244,6 +256,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     };
     P->pmask = pmask;
     P->k = k;
+    P->ki = o.k_imag;
     P->p = p;
     P->layers = near_layers;
     P->prec = prec;
@@ -251,20 +264,22 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->autotune = o.autotune ? 1 : 0;
     P->with_gradient = o.with_gradient ? 1 : 0;
     P->force_variant = o.gather_variant;
-    P->lf_min_work = P->with_gradient ? 0 : (o.corr_listfree < 0 ? 131072 : o.corr_listfree);
+    // the list-free kernels' polynomials in r^2 assume a real k
+    P->lf_min_work = P->with_gradient || o.k_imag != 0.0 ? 0 : (o.corr_listfree < 0 ? 131072 : o.corr_listfree);
     P->neutral_tol = o.neutral_tol > 0 ? o.neutral_tol : 1e-6;
     P->series_tol = o.series_tol > 0 ? o.series_tol : 1e-16;
     P->npd = 0;
     for (int d = 0; d < 3; ++d) {
         P->D[d] = lattice[4 * d];
         P->k0[d] = k0[d];
+        P->k0i[d] = o.k0_imag[d];
         if (!(P->D[d] > 0.0) || !std::isfinite(P->D[d]) || !(h[d] > 0.0) || !std::isfinite(k0[d])) {
             pim_set_error("cell extents and grid spacings must be positive and finite");
             return fail(PIM_ERR_ARG);
         }
         const bool per = (pmask >> d) & 1u;
         if (per) P->npd++;
-        if (!per && k0[d] != 0.0) {
+        if (!per && (k0[d] != 0.0 || o.k0_imag[d] != 0.0)) {
             pim_set_error("phase shift on a non-periodic axis");
             return fail(PIM_ERR_ARG);
         }
@@ -282,8 +297,9 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
             return fail(PIM_ERR_ARG);
         }
     }
-    P->npsp = P->npd > 0 && k == 0.0 && k0[0] == 0.0 && k0[1] == 0.0 && k0[2] == 0.0;
-    P->real_data = k == 0.0 && k0[0] == 0.0 && k0[1] == 0.0 && k0[2] == 0.0;
+    const bool k_zero = k == 0.0 && k0[0] == 0.0 && k0[1] == 0.0 && k0[2] == 0.0 && !cplx;
+    P->npsp = P->npd > 0 && k_zero;
+    P->real_data = k_zero;
     P->b = o.corr_radius >= 0 ? o.corr_radius : p + 1;
     P->cube = o.corr_cube ? 1 : 0;
     P->corr_mode = prec == PIM_FP64 ? PIM_CORR_FP64 : o.corr_mode;
@@ -309,8 +325,14 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
             for (int ix = -lx; ix <= lx; ++ix) {
                 int* v = P->img[P->nimg];
                 v[0] = ix; v[1] = iy; v[2] = iz;
+                // exp(-j k0.a), k0 = k0 + j k0i: modulus exp(k0i.a), angle -k0.a
                 const double th = -(k0[0] * ix * P->D[0] + k0[1] * iy * P->D[1] + k0[2] * iz * P->D[2]);
-                P->phase[P->nimg] = make_double2(std::cos(th), std::sin(th));
+                const double lm = o.k0_imag[0] * ix * P->D[0] + o.k0_imag[1] * iy * P->D[1] +
+                                  o.k0_imag[2] * iz * P->D[2];
+                const double mag = lm != 0.0 ? std::exp(lm) : 1.0;
+                P->phase[P->nimg] = make_double2(mag * std::cos(th), mag * std::sin(th));
+                // the adjoint's phase exp(-j conj(k0).a): modulus exp(-k0i.a)
+                P->phase_adj[P->nimg] = make_double2(std::cos(th) / mag, std::sin(th) / mag);
                 P->nimg++;
             }
     if (P->nimg > (1 << (32 - PIM_COL_BITS))) return fail(PIM_ERR_UNSUPPORTED);
@@ -318,7 +340,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->has_far = P->npd > 0;
     P->pf = o.far_p >= 0 ? o.far_p : p;
     for (int d = 0; d < 3; ++d) {
-        P->nf[d] = o.far_n[d] > 0 ? o.far_n[d] : std::max(10, (int)std::ceil(4.0 * k * P->D[d]));
+        P->nf[d] = o.far_n[d] > 0 ? o.far_n[d] : std::max(10, (int)std::ceil(4.0 * std::hypot(k, P->ki) * P->D[d]));
         P->df[d] = P->D[d] / P->nf[d];
         if (P->has_far && (P->nf[d] < P->pf + 1 || P->nf[d] > 512)) {
             pim_set_error("far grid must have p_f+1 .. 512 nodes per axis");
@@ -352,17 +374,25 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     if ((st = pim_alloc(P, (void**)&P->lfnext, sizeof(unsigned long long) * (pim_plan_s::RHS_LANES + 1))) != PIM_OK)
         return fail(st);
     if ((st = pim_alloc(P, (void**)&P->dsum, sizeof(double) * (4 + 3 * PIM_RED_BLOCKS))) != PIM_OK) return fail(st);
-    if ((st = pim_alloc(P, (void**)&P->dphase, (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES)) != PIM_OK)
+    if ((st = pim_alloc(P, (void**)&P->dphase, 2 * (sizeof(double2) + sizeof(float4)) * PIM_MAX_IMAGES)) != PIM_OK)
         return fail(st);
     P->dphasedf = reinterpret_cast<float4*>(P->dphase + PIM_MAX_IMAGES);
-    float4 phdf[PIM_MAX_IMAGES];
+    P->dphase_adj = reinterpret_cast<double2*>(P->dphasedf + PIM_MAX_IMAGES);
+    P->dphasedf_adj = reinterpret_cast<float4*>(P->dphase_adj + PIM_MAX_IMAGES);
+    float4 phdf[PIM_MAX_IMAGES], phdfa[PIM_MAX_IMAGES];
+    auto split = [](double2 v) {
+        const float rh = (float)v.x, ih = (float)v.y;
+        return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    };
     for (int i = 0; i < P->nimg; ++i) {
-        const float rh = (float)P->phase[i].x, ih = (float)P->phase[i].y;
-        phdf[i] = make_float4(rh, (float)(P->phase[i].x - (double)rh), ih, (float)(P->phase[i].y - (double)ih));
+        phdf[i] = split(P->phase[i]);
+        phdfa[i] = split(P->phase_adj[i]);
     }
     if (cudaMemset(P->dstatus, 0, sizeof(int)) != cudaSuccess ||
         cudaMemcpy(P->dphase, P->phase, sizeof(double2) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(P->dphasedf, phdf, sizeof(float4) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(P->dphasedf, phdf, sizeof(float4) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->dphase_adj, P->phase_adj, sizeof(double2) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P->dphasedf_adj, phdfa, sizeof(float4) * P->nimg, cudaMemcpyHostToDevice) != cudaSuccess) {
         pim_set_error("initial copies failed");
         return fail(PIM_ERR_CUDA);
     }

@@ -1265,8 +1265,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ga.valf = d.valf;
         ga.valt = d.valt;
         ga.nbig = d.nbig;
-        ga.phase = P->dphase;
-        ga.phasedf = P->dphasedf;
+        ga.phase = adj ? P->dphase_adj : P->dphase;
+        ga.phasedf = adj ? P->dphasedf_adj : P->dphasedf;
         void* dst = post_mean ? P->us : u;
         const long long threads = N * 32;
         prof_mark(P, PIM_STAGE_GATHER, 0, sr);
@@ -1334,8 +1334,8 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         ca.valf = d.valf;
         ca.valt = d.valt;
         ca.nbig = d.nbig;
-        ca.phase = P->dphase;
-        ca.phasedf = P->dphasedf;
+        ca.phase = adj ? P->dphase_adj : P->dphase;
+        ca.phasedf = adj ? P->dphasedf_adj : P->dphasedf;
         const int cm = sizeof(T) == 8 ? PIM_CORR_FP64 : P->corr_mode;
         const unsigned nb = (unsigned)((N * 32 + 255) / 256);
         // timed in the ring slot of the last right-hand side, if this call recorded any

@@ -962,6 +962,7 @@ pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) 
     if (P->pts.nlf == 0) return PIM_OK;
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
+    if (adj) a.phase = P->dphase_adj;
     a.ulf = P->ulf;
     a.next = P->lfnext + pim_plan_s::RHS_LANES;  // its own box counter
     pim_status st;
@@ -982,6 +983,7 @@ pim_status lf_grid_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) {
     if (P->pts.nlf == 0) return PIM_OK;
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
+    if (adj) a.phase = P->dphase_adj;
     a.sorted_out = 1;  // into ulf, sorted order
     pim_status st;
     prof_mark(P, PIM_STAGE_LF_GRID, 0, s);
@@ -1017,6 +1019,7 @@ pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool
     if (P->pts.nlf == 0) return PIM_OK;
     const LfGeom G = lf_geom(P);
     LfArgs a = lf_args(P, G);
+    if (adj) a.phase = P->dphase_adj;
     a.next = P->lfnext + lane;  // the right-hand-side lanes run at once: a box counter each
     a.nrhs = nrhs;
     a.r = r;

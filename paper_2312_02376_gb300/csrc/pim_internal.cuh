@@ -220,6 +220,7 @@ LfGeom lf_geom(const pim_plan_s* P);
 struct pim_plan_s {
     // geometry and method parameters
     double D[3], h[3], k, k0[3], df[3];
+    double ki = 0.0, k0i[3] = {0.0, 0.0, 0.0};  // imaginary parts of k and k0
     unsigned pmask = 0;
     int npd = 0;                  // number of periodic axes
     int n[3], nb[3], p, layers, b, cube, nf[3], pf, prec, corr_mode;
@@ -230,6 +231,7 @@ struct pim_plan_s {
     int nimg = 0;
     int img[PIM_MAX_IMAGES][3];
     double2 phase[PIM_MAX_IMAGES];    // exp(-j k0.(i o L))
+    double2 phase_adj[PIM_MAX_IMAGES];  // exp(-j conj(k0).(i o L)) (the adjoint's)
     // near spectrum and work grids
     FftGeom ng;
     void* spec = nullptr;         // [Lz][Ly][Lx] complex<T>, scaled by 1/(Lx Ly Lz)
@@ -262,6 +264,10 @@ struct pim_plan_s {
     double* dsum = nullptr;       // FP64 scratch: [0..1] mean, [4..) reduction partials
     double2* dphase = nullptr;    // device copy of phase[], followed by its double-float split
     float4* dphasedf = nullptr;   // (re hi, re lo, im hi, im lo), inside the dphase allocation
+    // the adjoint's image phases exp(-j conj(k0).(i o L)) (equal to phase[] for
+    // a real k0), same layout, inside the same allocation
+    double2* dphase_adj = nullptr;
+    float4* dphasedf_adj = nullptr;
     int* dstatus = nullptr;
     // profiling ring (pim_set_profiling)
     static constexpr int PROF_RING = 512;

@@ -13,10 +13,12 @@ namespace {
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 
-__device__ __forceinline__ double2 G0(double R, double k) {
+// exp(-j k R) / (4 pi R), k = k + j ki
+__device__ __forceinline__ double2 G0(double R, double k, double ki) {
     double s, c;
     sincos(k * R, &s, &c);
-    const double a = 1.0 / (4.0 * PI * R);
+    double a = 1.0 / (4.0 * PI * R);
+    if (ki != 0.0) a *= exp(ki * R);
     return make_double2(c * a, -s * a);
 }
 
@@ -456,7 +458,7 @@ __global__ void pair_count_kernel(const double* pos, long long N, const double* 
 
 struct FillArgs {
     PairArgs pa;
-    double h[3], D[3], k;
+    double h[3], D[3], k, ki;
     int p, R, W, self_img;
     const double2* gtab;   // g(e), e in [-R, R]^3, x fastest
     int corr_mode;
@@ -567,10 +569,10 @@ __device__ double2 corr_value(const FillArgs& a, const double* pos, const uint32
             return make_double2(0.0, 0.0);
         }
         const double R = sqrt(r2);
-        exact = G0(R, a.k);
+        exact = G0(R, a.k, a.ki);
         if (GRAD) {
             // grad G0(R) = G0(R) (-jk - 1/R) r / R
-            const double2 f = cmul(exact, make_double2(-1.0 / R, -a.k));
+            const double2 f = cmul(exact, make_double2(-1.0 / R + a.ki, -a.k));
             for (int d = 0; d < 3; ++d) dex[d] = make_double2(f.x * r[d] / R, f.y * r[d] / R);
         }
     }
@@ -788,13 +790,13 @@ __global__ void point_update_kernel(const double* xyz, const int* perm, long lon
     }
 }
 
-__global__ void gtab_kernel(double2* gtab, int R, double h0, double h1, double h2, double k) {
+__global__ void gtab_kernel(double2* gtab, int R, double h0, double h1, double h2, double k, double ki) {
     const int W = 2 * R + 1;
     const long long tot = (long long)W * W * W;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(e % W) - R, y = (int)((e / W) % W) - R, z = (int)(e / ((long long)W * W)) - R;
         const double r = sqrt((x * h0) * (x * h0) + (y * h1) * (y * h1) + (z * h2) * (z * h2));
-        gtab[e] = r > 0.0 ? G0(r, k) : make_double2(0.0, 0.0);
+        gtab[e] = r > 0.0 ? G0(r, k, ki) : make_double2(0.0, 0.0);
     }
 }
 
@@ -822,6 +824,7 @@ FillArgs fill_args(pim_plan P, const PairArgs& pr) {
     fa.pa = pr;
     for (int i = 0; i < 3; ++i) { fa.h[i] = P->h[i]; fa.D[i] = P->D[i]; }
     fa.k = P->k;
+    fa.ki = P->ki;
     fa.p = P->p;
     fa.R = P->b + 2 + 2 * P->p;
     fa.W = 2 * fa.R + 1;
@@ -991,7 +994,7 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
     double2* gtab = nullptr;
     const size_t gsz = (size_t)fa.W * fa.W * fa.W * sizeof(double2);
     if ((st = pim_alloc(P, (void**)&gtab, gsz)) != PIM_OK) return st;
-    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k);
+    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k, P->ki);
     fa.gtab = gtab;
     if (N > 0 && d.nnz > 0)
         pair_refill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.row_ptr, d.col, d.val, d.valdf,
@@ -1211,7 +1214,7 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     double2* gtab = nullptr;
     const size_t gsz = (size_t)fa.W * fa.W * fa.W * sizeof(double2);
     if ((st = pim_alloc(P, (void**)&gtab, gsz)) != PIM_OK) return st;
-    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k);
+    gtab_kernel<<<256, 256, 0, s>>>(gtab, fa.R, P->h[0], P->h[1], P->h[2], P->k, P->ki);
     fa.gtab = gtab;
     if (N > 0 && nnz > 0)
         pair_fill_kernel<<<152 * 16, 256, 0, s>>>(d.pos, d.ns, d.ntd, N, fa, d.box_ptr, d.bslot, d.bstart, d.dix,

@@ -2,6 +2,7 @@
 // far-zone table G_far = G^p - G_near on the shifted far grids (Sec. 3.2).
 // Everything here is FP64.
 #include <cmath>
+#include <complex>
 #include <vector>
 
 #include "pim_internal.cuh"
@@ -11,11 +12,12 @@ namespace {
 constexpr double PI = 3.141592653589793238462643383279502884;
 constexpr double EULER_GAMMA = 0.57721566490153286060651209008240243;
 
-// exp(-j k R) / (4 pi R)
-__device__ __forceinline__ double2 G0(double R, double k) {
+// exp(-j k R) / (4 pi R), k = k + j ki (ki <= 0: a lossy medium)
+__device__ __forceinline__ double2 G0(double R, double k, double ki) {
     double s, c;
     sincos(k * R, &s, &c);
-    const double a = 1.0 / (4.0 * PI * R);
+    double a = 1.0 / (4.0 * PI * R);
+    if (ki != 0.0) a *= exp(ki * R);
     return make_double2(c * a, -s * a);
 }
 
@@ -26,7 +28,7 @@ __device__ __forceinline__ double2 G0(double R, double k) {
 // ---------------------------------------------------------------------------
 struct NearArgs {
     int n[3], L[3];
-    double h[3], k;
+    double h[3], k, ki;
     int nimg;
     const int* img;          // nimg x 3
     const double2* phase;    // nimg
@@ -53,7 +55,7 @@ __global__ void near_table_kernel(NearArgs a, double2* out) {
                     r2 += x * x;
                 }
                 if (r2 == 0.0) continue;  // g(0) = 0
-                acc = cadd(acc, cmul(a.phase[i], G0(sqrt(r2), a.k)));
+                acc = cadd(acc, cmul(a.phase[i], G0(sqrt(r2), a.k, a.ki)));
             }
         }
         out[e] = acc;
@@ -130,6 +132,11 @@ struct FarArgs {
     // image axis (no Floquet mode of the other two axes has k_z = 0); each
     // entry takes the allowed axis along which its terms decay fastest
     int zaxes;
+    // complex k (ki) or phase shift (k0ci): the series in complex arithmetic
+    int cplx;
+    double ki;
+    double k0ci[3];
+    int* bad;            // set when a Hankel-function argument is outside the evaluated regimes
 };
 
 constexpr int FAR_NT = 128;
@@ -157,6 +164,96 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 // kz = sqrt(r) with Im <= 0 for real r (positive root for r > 0)
 __device__ __forceinline__ double2 kz_branch(double r) {
     return r >= 0.0 ? make_double2(sqrt(r), 0.0) : make_double2(0.0, -sqrt(-r));
+}
+
+// principal square root, then the branch with Im <= 0 (Sec. 2 after Eq. pgf;
+// for a positive real radicand the positive root)
+__device__ __forceinline__ double2 csqrt_branch(double2 w) {
+    const double r = hypot(w.x, w.y);
+    if (r == 0.0) return make_double2(0.0, 0.0);
+    const double t = sqrt(0.5 * (r + fabs(w.x)));
+    double2 v = w.x >= 0.0 ? make_double2(t, w.y / (2.0 * t)) : make_double2(fabs(w.y) / (2.0 * t), copysign(t, w.y));
+    if (v.y > 0.0) v = make_double2(-v.x, -v.y);
+    return v;
+}
+
+__device__ __forceinline__ double2 cexp_c(double2 z) {  // exp(z)
+    const double m = exp(z.x);
+    double s, c;
+    sincos(z.y, &s, &c);
+    return make_double2(m * c, m * s);
+}
+
+// K0(w) for complex w with Re w >= 0, w != 0 (the 1D series with complex k
+// or k0: H0^(2)(z) = (2j/pi) K0(j z)).  Three methods, each within about
+// 1e-13 relative where it is used (checked against an independent library
+// on a grid of |w| <= 40, |arg w| <= pi/2):
+//  |w| >= 20: the asymptotic series sqrt(pi/2w) e^-w sum_k c_k w^-k,
+//    c_k = c_{k-1} (-(2k-1)^2) / (8k) (A&S 9.7.2), summed to its smallest term;
+//  |w| <= 2, and |w| <= 6 within 0.17 rad of the imaginary axis: the power
+//    series of A&S 9.6.13 with 9.6.12 (complex logarithm); near the real axis
+//    K0 ~ e^-|w| while the terms grow like e^|w|, so it is not used there;
+//  |arg w| <= 1.4: the trapezoidal rule on K0(w) = int_0^inf exp(-w cosh t) dt,
+//    whose integrand is analytic and decaying in the strip |Im t| < d,
+//    d = pi/2 - |arg w| (Trefethen & Weideman, SIAM Rev. 56 (2014)): on the
+//    line Im t = s = d/2 it is at most exp(-|w| cos(|arg w| + s)), so the step
+//    h = 2 pi s / (42 + |w| (cos|arg w| - cos(|arg w| + s))) keeps the error
+//    below e^-42 relative to K0 ~ exp(-|w| cos arg w).
+// Other arguments (modulus 6..20 within 0.17 rad of the imaginary axis:
+// weakly lossy propagating modes far from the axis) set *bad and return 0.
+__device__ double2 bessel_k0c(double2 w, int* bad) {
+    const double aw = hypot(w.x, w.y), th = atan2(w.y, w.x);
+    if (aw >= 20.0) {
+        const double2 iw = cdiv(make_double2(1.0, 0.0), w);
+        double2 term = make_double2(1.0, 0.0), sum = term;
+        double last = 1.0;
+        for (int k = 1; k < 60; ++k) {
+            const double f = -(2.0 * k - 1.0) * (2.0 * k - 1.0) / (8.0 * k);
+            term = cmul(term, iw);
+            term.x *= f;
+            term.y *= f;
+            const double mt = hypot(term.x, term.y);
+            if (mt > last) break;  // the smallest term has been passed
+            sum = cadd(sum, term);
+            last = mt;
+            if (mt < 1e-17) break;
+        }
+        const double2 pre = csqrt_branch(cdiv(make_double2(0.5 * PI, 0.0), w));
+        // the principal root (Re w >= 0): undo the Im <= 0 choice when it flipped
+        const double2 root = pre.x < 0.0 ? make_double2(-pre.x, -pre.y) : pre;
+        return cmul(cmul(root, cexp_c(make_double2(-w.x, -w.y))), sum);
+    }
+    if (aw <= 2.0 || (aw <= 6.0 && fabs(th) > 1.4)) {
+        const double2 y = make_double2(0.25 * (w.x * w.x - w.y * w.y), 0.5 * w.x * w.y);
+        double2 t = make_double2(1.0, 0.0), I = t, S = make_double2(0.0, 0.0);
+        double H = 0.0;
+        for (int k = 1; k < 80; ++k) {
+            t = cmul(t, y);
+            t.x /= (double)k * (double)k;
+            t.y /= (double)k * (double)k;
+            H += 1.0 / k;
+            I = cadd(I, t);
+            S = cadd(S, make_double2(t.x * H, t.y * H));
+            if (k > 8 && hypot(t.x, t.y) < 1e-18 * hypot(I.x, I.y)) break;
+        }
+        const double2 lg = make_double2(log(0.5 * aw) + EULER_GAMMA, th);  // log(w/2) + gamma
+        return csub(S, cmul(lg, I));
+    }
+    if (fabs(th) <= 1.4) {
+        const double at = fabs(th), sd = 0.5 * (0.5 * PI - at);
+        const double h = fmin(0.1, 2.0 * PI * sd / (42.0 + aw * (cos(at) - cos(at + sd))));
+        double2 sum = cexp_c(make_double2(-w.x, -w.y));
+        sum.x *= 0.5;
+        sum.y *= 0.5;
+        for (int k = 1; k < 20000; ++k) {
+            const double c = cosh(k * h);
+            sum = cadd(sum, cexp_c(make_double2(-w.x * c, -w.y * c)));
+            if (w.x * (c - 1.0) > 44.0) break;
+        }
+        return make_double2(h * sum.x, h * sum.y);
+    }
+    atomicOr(bad, 1);
+    return make_double2(0.0, 0.0);
 }
 
 __device__ int mode_window(double kc, double Lc, double decay_len, double k) {
@@ -212,6 +309,21 @@ __global__ void __launch_bounds__(FAR_NT) far_table_kernel(FarArgs a, double2* o
         } else {
             if (tid == 0) fixed.x = -log(hypot(y, z)) / (2.0 * PI * Lx);
         }
+    } else if (a.npd == 1 && a.cplx) {
+        // ---------------- Eq. pgf_1, complex k or k0 -----------------------
+        // exp(-j kx x) H0^(2)(krho rho) / (4 j Lx) = exp(-j kx x) K0(j krho rho) / (2 pi Lx)
+        const double rho = hypot(y, z);
+        const int M = mode_window(hypot(a.k0c[0], a.k0ci[0]), Lx, rho, hypot(a.k, a.ki));
+        const double2 kk = make_double2(a.k * a.k - a.ki * a.ki, 2.0 * a.k * a.ki);
+        for (int t = tid; t < 2 * M + 1; t += FAR_NT) {
+            const int m = t - M;
+            const double2 kx = make_double2(a.k0c[0] + 2.0 * PI * m / Lx, a.k0ci[0]);
+            const double2 krho = csqrt_branch(csub(kk, cmul(kx, kx)));
+            const double2 w = make_double2(-krho.y * rho, krho.x * rho);  // j krho rho
+            const double2 k0v = bessel_k0c(w, a.bad);
+            const double2 h = make_double2(k0v.x / (2.0 * PI * Lx), k0v.y / (2.0 * PI * Lx));
+            acc = cadd(acc, cmul(cexp_mj(kx, x), h));
+        }
     } else if (a.npd == 1) {
         // ------------------------- Eq. pgf_1 -------------------------------
         const double rho = hypot(y, z);
@@ -239,6 +351,7 @@ __global__ void __launch_bounds__(FAR_NT) far_table_kernel(FarArgs a, double2* o
         // Lz dlen^2 is taken (among those allowed by a.zaxes).
         double xs = x, ys = y, zs = z, Lxs = Lx, Lys = Ly, Lzs = Lz;
         double k0x = a.k0c[0], k0y = a.k0c[1], k0z = a.k0c[2];
+        double k0xi = a.k0ci[0], k0yi = a.k0ci[1], k0zi = a.k0ci[2];
         if (a.npd == 3) {
             int cz = 2;
             double best = -1.0;
@@ -261,13 +374,40 @@ __global__ void __launch_bounds__(FAR_NT) far_table_kernel(FarArgs a, double2* o
             k0x = a.k0c[c1];
             k0y = a.k0c[c2];
             k0z = a.k0c[cz];
+            k0xi = a.k0ci[c1];
+            k0yi = a.k0ci[c2];
+            k0zi = a.k0ci[cz];
         }
         const double dlen = a.npd == 2 ? fabs(zs) : fmin(fabs(zs), Lzs - fabs(zs));
-        const int M = mode_window(k0x, Lxs, dlen, a.k);
-        const int N = mode_window(k0y, Lys, dlen, a.k);
+        const double kabs = a.cplx ? hypot(a.k, a.ki) : a.k;
+        const int M = mode_window(a.cplx ? hypot(k0x, k0xi) : k0x, Lxs, dlen, kabs);
+        const int N = mode_window(a.cplx ? hypot(k0y, k0yi) : k0y, Lys, dlen, kabs);
         const int W = 2 * N + 1;
         const long long nm = (long long)(2 * M + 1) * W;
         const double A = Lxs * Lys;
+        if (a.cplx) {
+            // the same series in complex arithmetic: kx, ky carry the phase
+            // shift's imaginary parts, kz = (k^2 - kx^2 - ky^2)^(1/2) with Im <= 0
+            const double2 kk = make_double2(a.k * a.k - a.ki * a.ki, 2.0 * a.k * a.ki);
+            const double2 kz0 = make_double2(k0z, k0zi), mkz0 = make_double2(-k0z, -k0zi);
+            const double2 one = make_double2(1.0, 0.0);
+            for (long long t = tid; t < nm; t += FAR_NT) {
+                const int m = (int)(t / W) - M, n = (int)(t % W) - N;
+                const double2 kx = make_double2(k0x + 2.0 * PI * m / Lxs, k0xi);
+                const double2 ky = make_double2(k0y + 2.0 * PI * n / Lys, k0yi);
+                const double2 kz = csqrt_branch(csub(csub(kk, cmul(kx, kx)), cmul(ky, ky)));
+                double2 zf = cexp_mj(kz, fabs(zs));
+                if (a.npd == 3) {
+                    const double2 em = cexp_mj(csub(kz, kz0), Lzs), ep = cexp_mj(cadd(kz, kz0), Lzs);
+                    const double2 t2 = cdiv(cmul(cexp_mj(kz, Lzs + zs), cexp_mj(mkz0, Lzs)), csub(one, em));
+                    const double2 t3 = cdiv(cmul(cexp_mj(kz, Lzs - zs), cexp_mj(kz0, Lzs)), csub(one, ep));
+                    zf = cadd(zf, cadd(t2, t3));
+                }
+                const double2 den = make_double2(-2.0 * kz.y * A, 2.0 * kz.x * A);
+                const double2 ph = cexp_mj(make_double2(kx.x * xs + ky.x * ys, kx.y * xs + ky.y * ys), 1.0);
+                acc = cadd(acc, cmul(ph, cdiv(zf, den)));
+            }
+        } else
         for (long long t = tid; t < nm; t += FAR_NT) {
             const int m = (int)(t / W) - M, n = (int)(t % W) - N;
             const double kx = k0x + 2.0 * PI * m / Lxs;
@@ -304,7 +444,7 @@ __global__ void __launch_bounds__(FAR_NT) far_table_kernel(FarArgs a, double2* o
                 const double q = r[d] - a.img[3 * i + d] * a.D[d];
                 r2 += q * q;
             }
-            v = csub(v, cmul(a.phase[i], G0(sqrt(r2), a.k)));
+            v = csub(v, cmul(a.phase[i], G0(sqrt(r2), a.k, a.ki)));
         }
         out[e] = v;
     }
@@ -366,6 +506,7 @@ pim_status build_near_spectrum(pim_plan P, cudaStream_t s) {
     NearArgs a{};
     for (int d = 0; d < 3; ++d) { a.n[d] = g.n[d]; a.L[d] = g.L[d]; a.h[d] = P->h[d]; }
     a.k = P->k;
+    a.ki = P->ki;
     a.nimg = P->nimg;
     a.img = dimg;
     a.phase = dph;
@@ -379,7 +520,7 @@ pim_status build_near_spectrum(pim_plan P, cudaStream_t s) {
     // and so is its spectrum: keep frequencies 0..L/2 of those axes
     g.fold = 0;
     for (int d = 0; d < 3; ++d) {
-        const bool even = !((P->pmask >> d) & 1u) || P->k0[d] == 0.0;
+        const bool even = !((P->pmask >> d) & 1u) || (P->k0[d] == 0.0 && P->k0i[d] == 0.0);
         if (even) g.fold |= 1 << d;
         g.S[d] = even ? g.L[d] / 2 + 1 : g.L[d];
     }
@@ -397,6 +538,41 @@ pim_status build_near_spectrum(pim_plan P, cudaStream_t s) {
     pim_free(P, dimg, sizeof(int) * 3 * P->nimg);
     pim_free(P, dph, sizeof(double2) * P->nimg);
     return PIM_OK;
+}
+
+// The anomaly check with complex k or phase shift: a Floquet mode whose
+// k_z^2 (k_rho^2) vanishes, or a vanishing denominator of Eq. pgf_3's z-image
+// factor, in complex arithmetic.
+static bool wood_anomaly_c(pim_plan P, const double* Lc, const double* k0r, const double* k0i) {
+    using C = std::complex<double>;
+    const C k(P->k, P->ki), kk = k * k;
+    const C k0[3] = {C(k0r[0], k0i[0]), C(k0r[1], k0i[1]), C(k0r[2], k0i[2])};
+    double scale = std::norm(k);
+    for (int d = 0; d < P->npd && d < 2; ++d) scale = fmax(scale, pow(2.0 * PI / Lc[d], 2));
+    const int M = (int)ceil((std::abs(k) + std::abs(k0[0])) * Lc[0] / (2.0 * PI)) + 2;
+    if (P->npd == 1) {
+        for (int m = -M; m <= M; ++m) {
+            const C kx = k0[0] + 2.0 * PI * m / Lc[0];
+            if (std::abs(kk - kx * kx) <= 1e-8 * scale) return true;
+        }
+        return false;
+    }
+    const int N = (int)ceil((std::abs(k) + std::abs(k0[1])) * Lc[1] / (2.0 * PI)) + 2;
+    for (int m = -M; m <= M; ++m)
+        for (int n = -N; n <= N; ++n) {
+            const C kx = k0[0] + 2.0 * PI * m / Lc[0], ky = k0[1] + 2.0 * PI * n / Lc[1];
+            const C r = kk - kx * kx - ky * ky;
+            if (std::abs(r) <= 1e-8 * scale) return true;
+            if (P->npd == 3) {
+                C kz = std::sqrt(r);
+                if (kz.imag() > 0.0) kz = -kz;
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    const C e = std::exp(C(0.0, -1.0) * (kz + (double)sgn * k0[2]) * Lc[2]);
+                    if (std::abs(1.0 - e) < 1e-9) return true;
+                }
+            }
+        }
+    return false;
 }
 
 // Rayleigh-Wood anomaly check (Sec. 2 after Eq. pgf): a Floquet mode with
@@ -452,12 +628,18 @@ pim_status build_far_table(pim_plan P, cudaStream_t s) {
         a.df[d] = P->df[d];
         a.Lc[d] = P->D[a.perm[d]];
         a.k0c[d] = P->k0[a.perm[d]];
+        a.k0ci[d] = P->k0i[a.perm[d]];
         a.D[d] = P->D[d];
     }
     a.npd = P->npd;
     a.k = P->k;
+    a.ki = P->ki;
+    a.cplx = (P->ki != 0.0 || a.k0ci[0] != 0.0 || a.k0ci[1] != 0.0 || a.k0ci[2] != 0.0) ? 1 : 0;
     a.npsp = P->npsp ? 1 : 0;
-    if (wood_anomaly(P, a.Lc, a.k0c)) {
+    auto anomaly = [&](const double* Lc, const double* kr, const double* ki) {
+        return a.cplx ? wood_anomaly_c(P, Lc, kr, ki) : wood_anomaly(P, Lc, kr);
+    };
+    if (anomaly(a.Lc, a.k0c, a.k0ci)) {
         pim_set_error("Rayleigh-Wood anomaly: a Floquet mode has k_z (or k_rho) = 0 for these k, k0, L");
         return PIM_ERR_ANOMALY;
     }
@@ -469,7 +651,8 @@ pim_status build_far_table(pim_plan P, cudaStream_t s) {
             const int c1 = c == 0 ? 1 : 0, c2 = 2;
             const double Lr[3] = {a.Lc[c1], a.Lc[c2], a.Lc[c]};
             const double kr[3] = {a.k0c[c1], a.k0c[c2], a.k0c[c]};
-            if (!wood_anomaly(P, Lr, kr)) a.zaxes |= 1 << c;
+            const double kim[3] = {a.k0ci[c1], a.k0ci[c2], a.k0ci[c]};
+            if (!anomaly(Lr, kr, kim)) a.zaxes |= 1 << c;
         }
     pim_status st;
     int* dimg = nullptr;
@@ -481,10 +664,22 @@ pim_status build_far_table(pim_plan P, cudaStream_t s) {
     a.nimg = P->nimg;
     a.img = dimg;
     a.phase = dph;
+    a.bad = P->dstatus;  // zero at plan creation
     const int ntab = (2 * P->nf[0] - 1) * (2 * P->nf[1] - 1) * (2 * P->nf[2] - 1);
     if ((st = pim_alloc(P, (void**)&P->ftab, sizeof(double2) * ntab)) != PIM_OK) return st;
     far_table_kernel<<<ntab, FAR_NT, 0, s>>>(a, P->ftab);
     PIM_CK(cudaGetLastError());
+    if (a.cplx && P->npd == 1) {
+        int bad = 0;
+        PIM_CK(cudaMemcpyAsync(&bad, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PIM_CK(cudaStreamSynchronize(s));
+        PIM_CK(cudaMemsetAsync(P->dstatus, 0, sizeof(int), s));
+        if (bad) {
+            pim_set_error("1D series with complex k or k0: a Hankel-function argument of modulus between 6 and "
+                          "20 lies within 0.17 rad of the real axis (a weakly lossy propagating mode); not supported");
+            return PIM_ERR_UNSUPPORTED;
+        }
+    }
     // far spectrum for the grid sum of Eq. 8 by zero-padded FFT
     FftGeom& g = P->fg;
     for (int d = 0; d < 3; ++d) {

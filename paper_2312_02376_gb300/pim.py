@@ -33,7 +33,8 @@ class pim_options(ctypes.Structure):
                 ("corr_cube", ctypes.c_int), ("corr_mode", ctypes.c_int),
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
                 ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int), ("corr_split", ctypes.c_int),
-                ("gather_variant", ctypes.c_int), ("corr_listfree", ctypes.c_int)]
+                ("gather_variant", ctypes.c_int), ("corr_listfree", ctypes.c_int), ("k_imag", ctypes.c_double),
+                ("k0_imag", ctypes.c_double * 3)]
 
 
 class pim_info(ctypes.Structure):
@@ -248,7 +249,7 @@ class Plan:
     D          cell extents (D_x, D_y, D_z); the lattice is diag(D)
     pdims      periodic axes, e.g. (0, 1)
     k, k0      wavenumber and phase-shift vector (the paper's k_0 and
-               k_x0, k_y0, k_z0)
+               k_x0, k_y0, k_z0); complex values allowed (Im k <= 0)
     n          near grid nodes per axis (h = D / (n - 1))
     p          near Lagrange degree; layers = near-image layers i_d
     precision  "fp64" or "fp32"
@@ -261,10 +262,14 @@ class Plan:
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
         self.pdims = tuple(pdims)
-        self.k = float(k)
-        self.k0 = np.asarray(k0, np.float64)
+        self.k = complex(k) if np.iscomplexobj(k) and complex(k).imag != 0 else float(np.real(k))
+        k0c = np.asarray(k0, np.complex128)
+        self.k0 = k0c if np.any(k0c.imag != 0) else k0c.real.copy()
         self.precision = precision
         opt = pim_options_default()
+        opt.k_imag = float(np.imag(self.k))
+        for d in range(3):
+            opt.k0_imag[d] = float(k0c[d].imag)
         if b is not None:
             opt.corr_radius = int(b)
         if nf is not None:
@@ -290,8 +295,9 @@ class Plan:
         mask = sum(1 << d for d in self.pdims)
         h = self.D / (self.n - 1)
         prec = PIM_FP64 if precision == "fp64" else PIM_FP32_MIXED
-        self.real = self.k == 0.0 and not np.any(self.k0 != 0)
-        self._h = pim_plan_create(np.diag(self.D), mask, self.k, self.k0, h, p, layers, prec, opt, stream)
+        self.real = self.k == 0 and not np.any(self.k0 != 0)
+        self._h = pim_plan_create(np.diag(self.D), mask, float(np.real(self.k)), np.real(k0c), h, p, layers, prec, opt,
+                                  stream)
         self.N = 0
 
     def set_points(self, xyz):

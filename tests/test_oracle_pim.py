@@ -96,13 +96,24 @@ def test_apply_rows_equals_apply():
     assert np.allclose(pl.apply_rows(W.q, rows), u[rows], rtol=1e-12, atol=1e-12 * np.abs(u).max())
 
 
-@pytest.mark.parametrize("case", ["helmholtz2d", "npsp3d", "helmholtz1d"])
+@pytest.mark.parametrize("case", ["helmholtz2d", "npsp3d", "helmholtz1d", "lossy2d", "lossy1d", "lossy3d"])
 def test_adjoint_is_conjugate_transpose(case):
+    # the lossy cases have complex k and complex phase shifts (Sec. 2): the
+    # image phases then have modulus != 1 and the adjoint's differ from them
     rng = np.random.default_rng(5)
     N = 30
     if case == "helmholtz2d":
         P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=4.0, k0=(1.2, 0.4, 0.0), n=(8, 8, 6), p=3, layers=1, b=2,
                        nf=(6, 6, 5), pf=3)
+    elif case == "lossy2d":
+        P = pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=4.0 - 0.6j, k0=(1.2 - 0.3j, 0.4 + 0.2j, 0.0), n=(8, 8, 6), p=3,
+                       layers=1, b=2, nf=(6, 6, 5), pf=3)
+    elif case == "lossy1d":
+        P = pim.Params(D=(0.5, 0.5, 1.0), pdims=(2,), k=3.0 - 0.4j, k0=(0, 0, 0.8 - 0.2j), n=(6, 6, 8), p=2, layers=1,
+                       b=2, nf=(5, 5, 6), pf=2)
+    elif case == "lossy3d":
+        P = pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=3.0 - 0.5j, k0=(1.0 - 0.2j, 0.5 + 0.1j, -0.3j), n=(8, 8, 8),
+                       p=2, layers=1, b=2, nf=(5, 5, 5), pf=2)
     elif case == "helmholtz1d":
         P = pim.Params(D=(0.5, 0.5, 1.0), pdims=(2,), k=3.0, k0=(0, 0, 0.0), n=(6, 6, 8), p=2, layers=1, b=2,
                        nf=(5, 5, 6), pf=2)
@@ -389,3 +400,32 @@ def test_far_sum_equals_the_dense_operator():
         assert np.abs(pim.far_sum(P, F, qg, direct=direct) - u).max() < 1e-12 * np.abs(u).max()
         assert np.abs(pim.far_sum(P, F, qg, adjoint=True, direct=direct) - w).max() < 1e-12 * np.abs(w).max()
 
+
+
+def test_lossy_operator_vs_direct_lattice_sum():
+    """A lossy wavenumber with a complex phase shift (2D lattice): the image
+    sum of Eq. 2 converges absolutely, so the operator's rows can be checked
+    against the lattice summed directly (the n = m, image-0 term left out,
+    reading of Eq. 5), within the method error at p = 4."""
+    rng = np.random.default_rng(23)
+    N = 60
+    D = np.array([1.0, 1.0, 0.5])
+    k = 2 * np.pi * 0.8 - 1.0j
+    k0 = np.array([1.0 - 0.3j, 0.5 + 0.2j, 0.0])
+    P = pim.Params(D=tuple(D), pdims=(0, 1), k=k, k0=tuple(k0), n=(17, 17, 9), p=4, layers=1, b=4, nf=(12, 12, 8),
+                   pf=4)
+    pts = rng.random((N, 3)) * D
+    q = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * np.sqrt(0.5)
+    u = pim.Plan(P, pts).apply(q)
+    # net decay of an image term: exp(Im k |iL|) |exp(-j k0.iL)| <= exp(-(1.0 - 0.3 sqrt 2)|i|)
+    I = 40
+    ref = np.zeros(N, complex)
+    d = pts[:, None, :] - pts[None, :, :]
+    for ix in range(-I, I + 1):
+        for iy in range(-I, I + 1):
+            sh = np.array([ix, iy, 0.0]) * D
+            R = np.linalg.norm(d - sh, axis=-1)
+            if ix == 0 and iy == 0:
+                np.fill_diagonal(R, np.inf)
+            ref += np.exp(-1j * np.dot(k0, sh)) * (np.exp(-1j * k * R) / (4 * np.pi * R)) @ q
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-3
