@@ -290,6 +290,35 @@ pim_status pim_position_grad(pim_plan plan, const void* q, const void* g, double
 pim_status pim_position_grad_reuse(pim_plan plan, const void* q, const void* g, double* grad_xyz, void* stream);
 
 /*
+ * pim_set_points_observers -- sources and observer points apart from them
+ * (the paper's accuracy test, Sec. 4.1, evaluates the potential at points
+ * that carry no source).  N sources, then M >= 1 observers, each N x 3 / M x 3
+ * FP64 (device or host), form the plan's point set in that order (an
+ * observer is a point of zero strength); everything pim_set_points does is
+ * done for the N + M points, and pim_apply / pim_apply_adjoint act on all of
+ * them.  An observer that coincides with a source modulo the lattice is
+ * rejected like two coinciding points (PIM_ERR_ARG).  A later pim_set_points
+ * drops the observers.
+ */
+pim_status pim_set_points_observers(pim_plan plan, int64_t N, const double* xyz, int64_t M, const double* obs_xyz);
+
+/*
+ * pim_apply_observers -- the potentials at the M observers due to the N
+ * sources (Eq. 1 with r_m an observer): u_obs = rows of A at the observers
+ * applied to [q; 0].  q [N][nrhs], u_obs [M][nrhs], the plan's data type,
+ * device or host (host copies synchronise).  In the neutral static case the
+ * regularisation of Eq. neutral removes the mean of q over the sources, and
+ * the neutrality test is on q (PIM_ERR_NOT_NEUTRAL via
+ * pim_last_device_status).  PIM_ERR_STATE without observers.
+ *
+ * pim_apply_observers_adjoint -- the adjoint of that map: w [N][nrhs] from
+ * v [M][nrhs] (the source rows of A^H applied to [0; v]; in the neutral
+ * static case projected on the sources' neutral subspace).
+ */
+pim_status pim_apply_observers(pim_plan plan, const void* q, void* u_obs, int nrhs, void* stream);
+pim_status pim_apply_observers_adjoint(pim_plan plan, const void* v_obs, void* w, int nrhs, void* stream);
+
+/*
  * pim_update_positions -- moves the points of the last pim_set_points to new
  * positions (N x 3 FP64, caller order, device or host) while keeping the
  * discrete structure: the box order, every stencil start, the box of every

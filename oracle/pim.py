@@ -652,3 +652,34 @@ class Plan:
             out[:, d] += np.bincount(m, weights=t1[:, d] + t2[:, d], minlength=len(q))
         return out
 
+
+
+# ---------------------------------------------------------------------------
+# observer points apart from the sources (Sec. 4.1's accuracy test: the
+# potential evaluated at points that carry no source)
+# ---------------------------------------------------------------------------
+def apply_observers(P, src, obs, q):
+    """u at the observers obs (M, 3) due to strengths q at the sources src
+    (N, 3): Eq. 1 with r_m an observer.  The operator of the point set
+    [src; obs] in which the observers carry zero strength, read at the
+    observers' rows.  Neutral static case: Eq. neutral holds for q over the
+    sources, whose residual mean is removed there only."""
+    src = np.asarray(src, np.float64)
+    obs = np.asarray(obs, np.float64)
+    q = np.asarray(q, np.complex128)
+    if P.npsp:
+        if abs(np.sum(q)) > P.neutral_tol * np.sum(np.abs(q)):
+            raise ValueError("charges are not neutral (Eq. neutral)")
+        q = q - np.mean(q)
+    full = np.concatenate([q, np.zeros(len(obs), np.complex128)])
+    return Plan(P, np.vstack([src, obs])).apply(full)[len(src):]
+
+
+def apply_observers_adjoint(P, src, obs, v):
+    """The adjoint of apply_observers: strengths at the sources from values v
+    at the observers (the source rows of A^H applied to [0; v]), projected on
+    the sources' neutral subspace in the neutral static case."""
+    src = np.asarray(src, np.float64)
+    full = np.concatenate([np.zeros(len(src), np.complex128), np.asarray(v, np.complex128)])
+    w = Plan(P, np.vstack([src, np.asarray(obs, np.float64)])).apply_adjoint(full)[:len(src)]
+    return w - np.mean(w) if P.npsp else w

@@ -17,7 +17,8 @@ LIB = os.path.join(OUT, "libpim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-UNITS = ["api.cu", "fft.cu", "tables.cu", "points.cu", "apply.cu", "listfree.cu", "noalloc.cu", "batch.cu"]
+UNITS = ["api.cu", "fft.cu", "tables.cu", "points.cu", "apply.cu", "listfree.cu", "noalloc.cu", "batch.cu",
+         "observers.cu"]
 
 
 def nvcc():

@@ -161,6 +161,7 @@ void pim_destroy(pim_plan P) {
     cudaDeviceSynchronize();
     batch_forget(P);
     lanes_free(P);
+    observers_free(P);
     if (P->lane_fork) cudaEventDestroy(P->lane_fork);
     {
         const size_t gq = grid_elem(P) * (size_t)P->pts.N;
@@ -441,6 +442,9 @@ pim_status pim_set_points(pim_plan P, int64_t N, const double* xyz) {
     cudaDeviceSynchronize();
     batch_forget(P);
     lanes_free(P);  // their sizes depend on the points
+    observers_free(P);
+    P->nsrc = N;    // pim_set_points_observers sets the split after this call
+    P->nobs = 0;
     const size_t ge = grid_elem(P);
     if (P->pts.N > 0 || P->pts.box_ptr) {
         free_grad_buffers(P);

@@ -309,6 +309,14 @@ struct pim_plan_s {
     cudaEvent_t ev_lf_fork = nullptr, ev_lf_mom = nullptr, ev_lf_join = nullptr;
     void* ulf = nullptr;            // N x complex<T> (plans with list-free boxes)
     unsigned long long* lfnext = nullptr;  // box counters of the exact-part kernel: one per lane, + async
+    // observer points (pim_set_points_observers): the last nobs of the point
+    // set; sources [0, nsrc); padded right-hand sides and results, per-RHS means
+    int64_t nsrc = 0, nobs = 0;
+    void* obs_q = nullptr;
+    void* obs_u = nullptr;
+    size_t obs_bytes = 0;
+    double* obs_means = nullptr;
+    int obs_nmeans = 0;
     double plan_ms = 0, points_ms = 0;
     // extra lanes of a multi-RHS apply: right-hand side r runs its per-RHS
     // stages on lane r % nlanes, each lane with its own scratch and streams
@@ -371,6 +379,9 @@ pim_status alloc_grad_buffers(pim_plan P);
 pim_status apply_prepare(pim_plan P, int nrhs, bool adjoint);
 pim_status lanes_prepare(pim_plan P, int nlanes);
 void lanes_free(pim_plan P);
+
+// observers.cu
+void observers_free(pim_plan P);
 
 // listfree.cu
 pim_status lf_apply(pim_plan P, const void* qs, void* dst, int nrhs, int r, bool adj, bool sorted_out,

@@ -170,6 +170,33 @@ def helmholtz3d(N=16_000_000, n=512, index=4, salt=0, b=5, nf=51, uniform=0.75):
                     (n, n, n), 4, 1, b, (nf, nf, nf), 4, "fp32", N, 1, pts, q.astype(np.complex64))
 
 
+def coax(nt1=64, nt2=128, nz=16, L=1.0, W=5.0, r1=1.0, r2=2.0, nobs=8, r_out=2.3):
+    """A coaxial line, periodic along z with period L (Sec. 4's 1D-periodic
+    neutral coax): charges on regular lattices on two cylinders about the
+    axis of a W x W x L cell, nt1 x nz points of total charge +1 at radius
+    r1 and nt2 x nz points of total charge -1 at radius r2 (equal charge
+    per point on each cylinder, so the set is exactly neutral).  Observers:
+    nobs points on the axis and nobs points at radius r_out outside the outer
+    cylinder (angles 2 pi j / nobs), at heights (j + 1/4) L / nobs.  Returns
+    (sources (N, 3), strengths (N,), observers (2 nobs, 3))."""
+    c = np.array([0.5 * W, 0.5 * W])
+
+    def cylinder(r, nt, charge):
+        th = (np.arange(nt) + 0.5) * 2.0 * np.pi / nt
+        z = (np.arange(nz) + 0.5) * L / nz
+        T, Z = np.meshgrid(th, z, indexing="ij")
+        pts = np.stack([c[0] + r * np.cos(T).ravel(), c[1] + r * np.sin(T).ravel(), Z.ravel()], axis=1)
+        return pts, np.full(len(pts), charge / len(pts))
+
+    p1, q1 = cylinder(r1, nt1, 1.0)
+    p2, q2 = cylinder(r2, nt2, -1.0)
+    zo = (np.arange(nobs) + 0.25) * L / nobs
+    ang = np.arange(nobs) * 2.0 * np.pi / nobs
+    axis = np.stack([np.full(nobs, c[0]), np.full(nobs, c[1]), zo], axis=1)
+    out = np.stack([c[0] + r_out * np.cos(ang), c[1] + r_out * np.sin(ang), zo], axis=1)
+    return np.vstack([p1, p2]), np.concatenate([q1, q2]), np.vstack([axis, out])
+
+
 def random_case(N, D, pdims, k, k0, n, p=4, layers=1, b=5, nf=(10, 10, 10), pf=4, seed=0,
                 complex_q=True, neutral=False, precision="fp64", nrhs=1):
     """A small uniform case with arbitrary parameters (for parity tests)."""

@@ -23,7 +23,7 @@ PIM_CORR_FP64, PIM_CORR_DOUBLE_FLOAT, PIM_CORR_FP32, PIM_CORR_COMPACT = 0, 1, 2,
 EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_plan_create", "pim_set_points",
            "pim_apply", "pim_apply_adjoint", "pim_last_device_status", "pim_plan_info", "pim_set_profiling",
            "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_position_grad_reuse", "pim_update_positions",
-           "pim_apply_noalloc",
+           "pim_apply_noalloc", "pim_set_points_observers", "pim_apply_observers", "pim_apply_observers_adjoint",
            "pim_apply_batched", "pim_debug_copy", "pim_destroy"]
 STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply", "lf_exact", "lf_grid", "corr_multi"]
 
@@ -101,6 +101,12 @@ def load(path=LIB_PATH):
     lib.pim_position_grad_reuse.restype = i32
     lib.pim_update_positions.argtypes = [vp, vp]
     lib.pim_update_positions.restype = i32
+    lib.pim_set_points_observers.argtypes = [vp, i64, vp, i64, vp]
+    lib.pim_set_points_observers.restype = i32
+    lib.pim_apply_observers.argtypes = [vp, vp, vp, i32, vp]
+    lib.pim_apply_observers.restype = i32
+    lib.pim_apply_observers_adjoint.argtypes = [vp, vp, vp, i32, vp]
+    lib.pim_apply_observers_adjoint.restype = i32
     lib.pim_apply_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32, vp]
     lib.pim_apply_batched.restype = i32
     lib.pim_apply_noalloc.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -211,6 +217,20 @@ def pim_position_grad_reuse(plan, q, g, grad_xyz, stream=None):
            "pim_position_grad_reuse")
 
 
+def pim_set_points_observers(plan, N, xyz, M, obs):
+    _check(load().pim_set_points_observers(plan, ctypes.c_int64(int(N)), _ptr(xyz), ctypes.c_int64(int(M)), _ptr(obs)),
+           "pim_set_points_observers")
+
+
+def pim_apply_observers(plan, q, u, nrhs=1, stream=None):
+    _check(load().pim_apply_observers(plan, _ptr(q), _ptr(u), int(nrhs), _stream_ptr(stream)), "pim_apply_observers")
+
+
+def pim_apply_observers_adjoint(plan, v, w, nrhs=1, stream=None):
+    _check(load().pim_apply_observers_adjoint(plan, _ptr(v), _ptr(w), int(nrhs), _stream_ptr(stream)),
+           "pim_apply_observers_adjoint")
+
+
 def pim_update_positions(plan, xyz):
     _check(load().pim_update_positions(plan, _ptr(xyz)), "pim_update_positions")
 
@@ -304,6 +324,28 @@ class Plan:
         """xyz: (N, 3) float64 positions (torch tensor on the GPU or numpy)."""
         self.N = int(xyz.shape[0])
         pim_set_points(self._h, self.N, xyz)
+
+    def set_points_observers(self, xyz, obs):
+        """N sources xyz (N, 3) and M observers obs (M, 3), float64 (torch on
+        the GPU or numpy): one point set, sources first."""
+        self.N_src, self.M_obs = int(xyz.shape[0]), int(obs.shape[0])
+        self.N = self.N_src + self.M_obs
+        pim_set_points_observers(self._h, self.N_src, xyz, self.M_obs, obs)
+
+    def apply_observers(self, q, stream=None, adjoint=False):
+        """Potentials at the observers from source strengths q ([N] or
+        [N, nrhs]); adjoint=True maps observer values ([M] or [M, nrhs]) to
+        the sources."""
+        nrhs = 1 if q.ndim == 1 else int(q.shape[1])
+        rows = self.N_src if adjoint else self.M_obs
+        shape = (rows,) if q.ndim == 1 else (rows, nrhs)
+        if hasattr(q, "data_ptr") and not isinstance(q, np.ndarray):
+            import torch
+            out = torch.empty(shape, dtype=q.dtype, device=q.device)
+        else:
+            out = np.empty(shape, q.dtype)
+        (pim_apply_observers_adjoint if adjoint else pim_apply_observers)(self._h, q, out, nrhs, stream)
+        return out
 
     def dtype_np(self):
         if self.real:

@@ -429,3 +429,62 @@ def test_lossy_operator_vs_direct_lattice_sum():
                 np.fill_diagonal(R, np.inf)
             ref += np.exp(-1j * np.dot(k0, sh)) * (np.exp(-1j * k * R) / (4 * np.pi * R)) @ q
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-3
+
+
+def test_observers_vs_ewald_same_error_as_the_sources_rows():
+    """Potentials at observer points apart from the sources (Sec. 4.1's
+    accuracy test) against the Ewald sum at those points: the method error
+    there is that of the sources' own rows (both fall with the grid step)."""
+    rng = np.random.default_rng(1)
+    N, M = 400, 24
+    D = np.array([1.0, 1.0, 1.0])
+    k, k0 = 2 * np.pi * 0.7, np.array([0.9, 0.5, 0.0])
+    src, obs = rng.random((N, 3)), rng.random((M, 3))
+    q = (rng.standard_normal(N) + 1j * rng.standard_normal(N)) * np.sqrt(0.5)
+    P = pim.Params(D=tuple(D), pdims=(0, 1, 2), k=k, k0=tuple(k0), n=(33, 33, 33), p=4, layers=1, b=5,
+                   nf=(16, 16, 16), pf=4)
+    u = pim.apply_observers(P, src, obs, q)
+    ref = ewald.potential(np.vstack([src, obs]), np.concatenate([q, np.zeros(M)]), np.arange(N, N + M), D,
+                          (0, 1, 2), k, k0, 3.0)
+    us = pim.Plan(P, src).apply_rows(q, np.arange(M))
+    ref_s = ewald.potential(src, q, np.arange(M), D, (0, 1, 2), k, k0, 3.0)
+    e_obs = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    e_src = np.linalg.norm(us - ref_s) / np.linalg.norm(ref_s)
+    assert e_obs < 3e-4 and e_obs < 1.5 * e_src, (e_obs, e_src)
+
+
+def test_observers_adjoint_is_conjugate_transpose():
+    rng = np.random.default_rng(4)
+    N, M = 25, 7
+    for P in (pim.Params(D=(1, 1, 0.5), pdims=(0, 1), k=4.0 - 0.3j, k0=(1.2 - 0.2j, 0.4, 0.0), n=(8, 8, 6), p=3,
+                         layers=1, b=2, nf=(6, 6, 5), pf=3),
+              pim.Params(D=(1, 1, 1), pdims=(0, 1, 2), k=0.0, k0=(0, 0, 0), n=(8, 8, 8), p=2, layers=1, b=2,
+                         nf=(5, 5, 5), pf=2)):
+        src, obs = rng.random((N, 3)) * P.D, rng.random((M, 3)) * P.D
+        E = np.eye(N)
+        if P.npsp:
+            A = np.array([pim.apply_observers(P, src, obs, E[:, j] - 1.0 / N) for j in range(N)]).T
+            proj = np.eye(N) - 1.0 / N
+        else:
+            A = np.array([pim.apply_observers(P, src, obs, E[:, j]) for j in range(N)]).T
+            proj = np.eye(N)
+        AH = np.array([pim.apply_observers_adjoint(P, src, obs, np.eye(M)[:, j]) for j in range(M)]).T
+        assert np.allclose(AH, proj @ A.conj().T, atol=1e-12 * np.abs(A).max())
+
+
+def test_coax_neutral_static_axis_is_flat_at_the_coax_voltage():
+    """The 1D-periodic neutral coax (inner radius 1, charge +1 per period;
+    outer radius 2, charge -1): the potential is constant on the axis and
+    outside the outer cylinder, and their difference is the coax voltage
+    ln(r2/r1) / (2 pi) per unit charge per period (the exact values for
+    uniformly charged cylinders, which the regular lattices of charges
+    reproduce to exponentially small ripple at these distances)."""
+    src, q, obs = inputs.coax()
+    P = pim.Params(D=(5.0, 5.0, 1.0), pdims=(2,), k=0.0, k0=(0, 0, 0), n=(51, 51, 11), p=4, layers=1, b=5,
+                   nf=(24, 24, 10), pf=4)
+    u = pim.apply_observers(P, src, obs, q).real
+    ua, uo = u[:8], u[8:]
+    dv = ua.mean() - uo.mean()
+    exact = np.log(2.0) / (2 * np.pi)
+    assert np.ptp(ua) < 2e-5 * dv and np.ptp(uo) < 2e-5 * dv, (np.ptp(ua) / dv, np.ptp(uo) / dv)
+    assert abs(dv - exact) < 1e-5 * exact, (dv, exact)
