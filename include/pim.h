@@ -63,8 +63,9 @@ typedef enum {
     PIM_ERR_STATE = 6,        /* apply before pim_set_points */
     PIM_ERR_OOM = 7,          /* device allocation failed or mem_cap exceeded */
     PIM_ERR_CUDA = 8,         /* a CUDA runtime call failed */
-    PIM_ERR_TIMEOUT = 9,      /* a bounded device wait ran out (reserved: no kernel of this
-                                 version waits on another)                                */
+    PIM_ERR_TIMEOUT = 9,      /* a bounded device wait ran out (the tensor-core kernel's
+                                 waits for its own matrix products; reported by
+                                 pim_last_device_status)                                  */
     PIM_ERR_DEVICE = 10       /* a device-side bounds check tripped */
 } pim_status;
 
@@ -139,6 +140,11 @@ typedef struct {
                             of modulus 6..20 within 0.17 rad of the real axis (a weakly
                             lossy propagating mode); with_gradient plans must have
                             real k and k0 (PIM_ERR_UNSUPPORTED)                      */
+    int lf_tensor_cores; /* 1 (default): in FP32 plans the grid part of the list-free
+                            correction for the boxes whose stencils are not clamped
+                            at a face of the grid runs as one matrix product on the
+                            tensor cores (TF32 operands split in hi and lo parts,
+                            FP32 accuracy; one right-hand side); 0: CUDA cores       */
 } pim_options;
 
 typedef struct {
@@ -157,6 +163,7 @@ typedef struct {
     int64_t lf_points;   /* points in those boxes                                      */
     int64_t lf_pairs;    /* (observer, source, image) pairs their exact kernel sums per
                             apply (partners in the boxes with moments)                */
+    int64_t lf_tc_boxes; /* list-free boxes whose grid part runs on the tensor cores  */
 } pim_info;
 
 /* Stages timed by the profiling ring (pim_set_profiling). */

@@ -135,6 +135,7 @@ void pim_options_default(pim_options* o) {
     o->corr_split = 10;
     o->gather_variant = -1;
     o->corr_listfree = -1;
+    o->lf_tensor_cores = 1;
     o->k_imag = 0.0;
     for (int d = 0; d < 3; ++d) o->k0_imag[d] = 0.0;
 }
@@ -264,6 +265,7 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned pmas
     P->mem_cap = o.mem_cap;
     P->autotune = o.autotune ? 1 : 0;
     P->with_gradient = o.with_gradient ? 1 : 0;
+    P->lf_tc = o.lf_tensor_cores ? 1 : 0;
     P->force_variant = o.gather_variant;
     // the list-free kernels' polynomials in r^2 assume a real k
     P->lf_min_work = P->with_gradient || o.k_imag != 0.0 ? 0 : (o.corr_listfree < 0 ? 131072 : o.corr_listfree);
@@ -636,6 +638,10 @@ pim_status pim_last_device_status(pim_plan P) {
     PIM_CK(cudaMemcpy(&h, P->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
     PIM_CK(cudaMemset(P->dstatus, 0, sizeof(int)));
     if (h & PIM_DEV_NOT_NEUTRAL) return PIM_ERR_NOT_NEUTRAL;
+    if (h & PIM_DEV_TIMEOUT) {
+        pim_set_error("a bounded wait of the tensor-core kernel ran out");
+        return PIM_ERR_TIMEOUT;
+    }
     if (h) return PIM_ERR_DEVICE;
     return PIM_OK;
 }
@@ -665,6 +671,7 @@ pim_status pim_plan_info(pim_plan P, pim_info* info) {
     info->lf_boxes = P->pts.nlf;
     info->lf_points = P->pts.lf_points;
     info->lf_pairs = P->pts.lf_pairs;
+    info->lf_tc_boxes = P->pts.ntc;
     return PIM_OK;
 }
 

@@ -1213,17 +1213,22 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         // list-free boxes, one right-hand side: their exact part on its own
         // stream, while the spread, FFT and gather run
         const bool lf_async = P->pts.nlf > 0 && P->ulf && nrhs == 1 && N > 0;
+        // with the tensor-core form the grid part runs on this stream after the
+        // gather: it moves the local grids through HBM, and beside the gather
+        // and FFT it would slow them by more than it takes alone
+        const bool grid_main = lf_async && P->pts.ntc > 0;
         if (lf_async) {
             PIM_CK(cudaEventRecord(P->ev_lf_fork, sr));
             PIM_CK(cudaStreamWaitEvent(P->s_lf, P->ev_lf_fork, 0));
             if ((st = lf_exact_async(P, qs, adj, P->s_lf)) != PIM_OK) return st;
+            if (grid_main) PIM_CK(cudaEventRecord(P->ev_lf_join, P->s_lf));
         }
         // 3. near spread (two phases), 4. FFT convolution
         prof_mark(P, PIM_STAGE_SPREAD, 0, sr);
         if ((st = spread_two_phase<T, PP>(P, qs, gN, sr)) != PIM_OK) return st;
         prof_mark(P, PIM_STAGE_SPREAD, 1, sr);
         // the list-free boxes' grid part needs the box moments of the spread
-        if (lf_async) {
+        if (lf_async && !grid_main) {
             PIM_CK(cudaEventRecord(P->ev_lf_mom, sr));
             PIM_CK(cudaStreamWaitEvent(P->s_lf, P->ev_lf_mom, 0));
             if ((st = lf_grid_async(P, qs, adj, P->s_lf)) != PIM_OK) return st;
@@ -1283,6 +1288,7 @@ pim_status run_typed(pim_plan P, const void* q, void* u, int nrhs, bool adj, cud
         // list-free boxes: exact sum minus grid part, added to the gathered output
         if (lf_async) {
             PIM_CK(cudaStreamWaitEvent(sr, P->ev_lf_join, 0));
+            if (grid_main && (st = lf_grid_async(P, qs, adj, sr)) != PIM_OK) return st;
             if ((st = lf_add(P, dst, post_mean, sr)) != PIM_OK) return st;
         } else if (N > 0 && (st = lf_apply(P, qs, dst, nrhs, r, adj, post_mean, sr, lk)) != PIM_OK) {
             return st;

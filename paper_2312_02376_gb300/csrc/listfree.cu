@@ -81,6 +81,14 @@ struct LfArgs {
     unsigned long long* next;   // box counter of the exact-part kernel
     void* ulf;              // exact part: stored here (sorted order) instead of added to the output;
                             // grid part: added to the output with it
+    // grid part on the tensor cores: the boxes it handles (tcmask, by list-free
+    // index) are skipped by lf_grid_kernel; in its Q-output form the kernel
+    // takes the boxes tcl[0, tcrows) and writes their local grids as rows of
+    // tcKP-padded FP32 [Re Q | Im Q] to the kernel's out
+    const unsigned char* tcmask;
+    const int* tcl;
+    long long tcrows;
+    int tcKP;
 };
 
 // an FP64 position padded to 32 bytes
@@ -96,6 +104,14 @@ __device__ __forceinline__ void box_xyz(int b, const int* nb, int* B) {
 
 // stencil start of box B along one axis: clamp(B - c, 0, n - 1 - p)
 __device__ __forceinline__ int box_stencil(int B, int c, int n, int p) { return min(max(B - c, 0), n - 1 - p); }
+
+// x rounded to TF32 (10 explicit mantissa bits, to nearest, ties away), held in
+// an FP32 register with the low 13 bits zero
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 // dst[m] += v in the layout of the apply's output (caller order with the
 // right-hand-side stride, real or complex, or the sorted scratch)
@@ -518,7 +534,8 @@ __global__ void __launch_bounds__(LF_NT) lf_exact_f64(LfArgs a, const double2* _
 // conflicts there instead of as many cache lines through L1.
 constexpr int LF_MAXSLOT = 1024;
 
-template <typename T, int P, int EX, bool ADJ>
+// OUTQ: the Q-output form (steps 1 and 2 only; tensor-core path).
+template <typename T, int P, int EX, bool ADJ, bool OUTQ = false>
 __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>* __restrict__ mom,
                                                        const cplx<T>* __restrict__ gtab, void* out) {
     constexpr int NP = P + 1, RW = NP * NP, NW = LF_GNT / 32;
@@ -537,13 +554,16 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
     cplx<T>* gs = (cplx<T>*)(((uintptr_t)(nrows + 1) + 15) & ~(uintptr_t)15);  // H1^3 (FP32)
     const cplx<T>* gt = sizeof(T) == 4 ? gs : gtab;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (sizeof(T) == 4)
+    if (sizeof(T) == 4 && !OUTQ)
         for (int i = tid; i < H1 * H1 * H1; i += LF_GNT) {
             cplx<T> g = gtab[i];
             if (ADJ) g.y = -g.y;
             gs[i] = g;
         }
-    for (long long j = blockIdx.x; j < a.nlf; j += gridDim.x) {
+    const long long nbox = OUTQ ? a.tcrows : a.nlf;
+    for (long long jj = blockIdx.x; jj < nbox; jj += gridDim.x) {
+        const long long j = OUTQ ? (long long)a.tcl[jj] : jj;
+        if (!OUTQ && a.tcmask && a.tcmask[j]) continue;  // on the tensor cores
         const int sA = a.lfslot[j];
         const int m0 = a.bstart[sA], nA = a.bstart[sA + 1] - m0;
         int A[3], org[3], X0[3];
@@ -619,6 +639,23 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
             }
         }
         __syncthreads();
+        if (OUTQ) {
+            // the local grid as one FP32 row [Re Q | Im Q] (local node
+            // (z E + y) E + x, zero beyond E^3)
+            float* bq = (float*)out + (size_t)jj * 2 * a.tcKP;
+            const int E3 = E * E * E;
+            for (int i = tid; i < a.tcKP; i += LF_GNT) {
+                float re = 0.f, im = 0.f;
+                if (i < E3) {
+                    const cplx<T> v = Q[(i / E) * XS + i % E];
+                    re = (float)v.x;
+                    im = (float)v.y;
+                }
+                bq[i] = re;
+                bq[a.tcKP + i] = im;
+            }
+            continue;
+        }
         // non-empty rows, in order
         if (warp == 0) {
             int base = 0;
@@ -708,6 +745,293 @@ __global__ void __launch_bounds__(LF_GNT) lf_grid_kernel(LfArgs a, const cplx<T>
             if (a.ulf) v = cadd(v, ((const cplx<T>*)a.ulf)[m]);
             add_out<T>(a, out, m, v);
         }
+    }
+}
+
+// ------------------- grid part on the tensor cores -------------------------
+// For a box A whose stencil is not clamped at a face of the grid, step 3 of the
+// grid part, V_A(s) = sum_nu g(X0 + s - nu) Q_A(nu), uses the same operator for
+// every box (X0 = R + c on every axis): one product V = G Q over all such boxes,
+// G the 125 x E^3 complex Toeplitz block written in real form as the 256 x 2KP
+// matrix [[Re g, -Im g], [Im g, Re g]] (rows: Re V at s, Im V at 128 + s;
+// columns [Re Q | Im Q], each padded to KP), Q one row per box.  It runs as a
+// tcgen05 kind::tf32 GEMM (accumulators in tensor memory) with each FP32
+// operand split into TF32 hi and lo parts, hi.hi + hi.lo + lo.hi (FP32
+// accuracy: the dropped lo.lo term is 2^-22 relative).  A CTA takes 128
+// boxes (two M = 128 accumulators of 128 columns), K in chunks of 32 staged in
+// shared memory in the 128-byte-swizzled K-major layout, two stages: the
+// threads load chunk k + 1 while the MMAs of chunk k run.
+constexpr int TC_M = 256, TC_N = 128, TC_K = 32, TC_NT = 128;
+constexpr int TC_ABYTES = TC_M * TC_K * 4, TC_BBYTES = TC_N * TC_K * 4;
+constexpr int TC_STAGE = 2 * TC_ABYTES + 2 * TC_BBYTES;
+constexpr size_t TC_SMEM = 2 * (size_t)TC_STAGE + 1024 + 64;
+constexpr long long TC_BATCH = 32768;  // boxes per batch (their Q rows: 32768 x 2KP x 8 bytes)
+
+__device__ __forceinline__ uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading byte offset 16
+// (unused by the swizzled K-major layout), stride byte offset 1024 (8 rows of
+// 128 bytes), descriptor version 1, 128-byte swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// bounded wait for the completion of phase `parity` of an mbarrier
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes 0 fills zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t tc_sw(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// C[n][m] = sum_k A[m][k] B[n][k] (A: 256 x K, B: N x K, both K-major, each as
+// TF32 hi and lo arrays; K a multiple of 32).  On a wait that runs out the
+// CTA sets PIM_DEV_TIMEOUT and writes nothing.
+__global__ void __launch_bounds__(TC_NT, 1) lf_tc_gemm_kernel(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                             const float* __restrict__ Bq, int K, long long N,
+                                                             float* __restrict__ C, int* status) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = (uint64_t*)(sm + 2 * TC_STAGE);
+    uint32_t* holder = (uint32_t*)(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long n0 = (long long)blockIdx.x * TC_N;
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_saddr(bars + st)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(tc_saddr(holder)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *holder;
+    // D F32, A and B TF32, both K-major, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const int nk = K / TC_K;
+    uint32_t used[2] = {0, 0};
+    bool ok = true;
+    // chunk kc into stage st: the operator's hi and lo parts by 16-byte
+    // asynchronous copies into the swizzled layout (one commit group per
+    // chunk); the FP32 Q rows through registers (all of a thread's loads in
+    // flight at once), split into TF32 hi and lo parts on the way (rows past N
+    // zero)
+    constexpr int BPT = TC_N * 8 / TC_NT;  // 16-byte pieces of B per thread and chunk
+    auto load_chunk = [&](int kc, int st) {
+        unsigned char* sA = sm + st * TC_STAGE;
+        unsigned char* sAl = sA + TC_ABYTES;
+        unsigned char* sB = sA + 2 * TC_ABYTES;
+        unsigned char* sBl = sB + TC_BBYTES;
+        const size_t k0 = (size_t)kc * TC_K;
+        for (int e = tid; e < TC_M * 8; e += TC_NT) {
+            const int r = e >> 3, c = e & 7;
+            cp_async16(tc_saddr(sA + tc_sw(r, c)), Ah + (size_t)r * K + k0 + 4 * c, 16);
+            cp_async16(tc_saddr(sAl + tc_sw(r, c)), Al + (size_t)r * K + k0 + 4 * c, 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        float4 v[BPT];
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int e = tid + i * TC_NT, r = e >> 3, c = e & 7;
+            const long long n = n0 + r;
+            v[i] = n < N ? __ldcs((const float4*)(Bq + (size_t)n * K + k0) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int e = tid + i * TC_NT, r = e >> 3, c = e & 7;
+            const float4 h = make_float4(tf32_rna(v[i].x), tf32_rna(v[i].y), tf32_rna(v[i].z), tf32_rna(v[i].w));
+            const float4 l = make_float4(tf32_rna(v[i].x - h.x), tf32_rna(v[i].y - h.y), tf32_rna(v[i].z - h.z),
+                                         tf32_rna(v[i].w - h.w));
+            *(float4*)(sB + tc_sw(r, c)) = h;
+            *(float4*)(sBl + tc_sw(r, c)) = l;
+        }
+    };
+    if (nk > 0) load_chunk(0, 0);
+    for (int kc = 0; kc < nk && ok; ++kc) {
+        const int st = kc & 1;
+        // the copies of chunk kc (the only group in flight) are in shared
+        // memory; make them visible to the tensor cores
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char* sA = sm + st * TC_STAGE;
+            unsigned char* sAl = sA + TC_ABYTES;
+            unsigned char* sB = sA + 2 * TC_ABYTES;
+            unsigned char* sBl = sB + TC_BBYTES;
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t d = tmem + h * TC_N;
+                for (int kk = 0; kk < TC_K / 8; ++kk) {
+                    const uint32_t ao = h * 128 * 128 + kk * 32, bo = kk * 32;
+                    tc_mma(d, tc_desc(tc_saddr(sA) + ao), tc_desc(tc_saddr(sB) + bo), idesc, kc > 0 || kk > 0);
+                    tc_mma(d, tc_desc(tc_saddr(sA) + ao), tc_desc(tc_saddr(sBl) + bo), idesc, 1);
+                    tc_mma(d, tc_desc(tc_saddr(sAl) + ao), tc_desc(tc_saddr(sB) + bo), idesc, 1);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(tc_saddr(bars + st)));
+        }
+        if (kc + 1 < nk) {
+            // the other stage is free once the MMAs of chunk kc - 1 are done;
+            // its copies for chunk kc + 1 then overlap the MMAs of chunk kc
+            const int sn = st ^ 1;
+            if (kc >= 1) {
+                if (!tc_wait(tc_saddr(bars + sn), used[sn] & 1)) ok = false;
+                used[sn]++;
+            }
+            if (ok) load_chunk(kc + 1, sn);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last commit of each stage (every earlier one has been waited for)
+    for (int st = 0; st < 2 && ok; ++st) {
+        const int issued = nk > st ? (nk - st + 1) / 2 : 0;
+        if ((int)used[st] < issued) {
+            if (!tc_wait(tc_saddr(bars + st), used[st] & 1)) ok = false;
+            used[st]++;
+        }
+    }
+    if (!ok) {
+        // a wait ran out: wait (bounded) for what was issued, so that the
+        // tensor memory is no longer written, then free it
+        for (int st = 0; st < 2; ++st) {
+            const int issued = nk > st ? (nk - st + 1) / 2 : 0;
+            while ((int)used[st] < issued && tc_wait(tc_saddr(bars + st), used[st] & 1)) used[st]++;
+        }
+        if (tid == 0) atomicOr(status, PIM_DEV_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        for (int h = 0; h < 2; ++h)
+            for (int j = 0; j < TC_N / 16; ++j) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + h * TC_N + j * 16;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                               "=r"(v[15])
+                             : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                const int m = h * 128 + warp * 32 + lane;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const long long n = n0 + j * 16 + i;
+                    if (n < N) C[(size_t)n * TC_M + m] = __uint_as_float(v[i]);
+                }
+            }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem));
+}
+
+// The operator of the tensor-core grid part, forward and adjoint (conj g),
+// each as TF32 hi and lo parts, from G0 evaluated in FP64.
+__global__ void lf_tc_table_kernel(float* Afh, float* Afl, float* Aah, float* Aal, int E, int KP, int X0, int NP, double h0,
+                                   double h1, double h2, double k) {
+    const long long K2 = 2LL * KP, tot = (long long)TC_M * K2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e / K2), col = (int)(e % K2);
+        const int hh = m / 128, sn = m % 128, part = col / KP, nu = col % KP;
+        double gr = 0.0, gi = 0.0;
+        if (sn < NP * NP * NP && nu < E * E * E) {
+            const int ex = X0 + sn % NP - nu % E, ey = X0 + (sn / NP) % NP - (nu / E) % E,
+                      ez = X0 + sn / (NP * NP) - nu / (E * E);
+            const double r = sqrt((ex * h0) * (ex * h0) + (ey * h1) * (ey * h1) + (ez * h2) * (ez * h2));
+            if (r > 0.0) {
+                double sv, cv;
+                sincos(k * r, &sv, &cv);
+                gr = cv / (4.0 * PI * r);
+                gi = -sv / (4.0 * PI * r);
+            }
+        }
+        const double vf = hh == 0 ? (part == 0 ? gr : -gi) : (part == 0 ? gi : gr);
+        const double va = hh == 0 ? (part == 0 ? gr : gi) : (part == 0 ? -gi : gr);  // conj g
+        const float fh = tf32_rna((float)vf), ah = tf32_rna((float)va);
+        Afh[e] = fh;
+        Afl[e] = tf32_rna((float)(vf - (double)fh));
+        Aah[e] = ah;
+        Aal[e] = tf32_rna((float)(va - (double)ah));
+    }
+}
+
+// Step 4 for the tensor-core boxes: every point of box tcl[row] subtracts
+// w_m . V (V = C[row][0..NP^3) + j C[row][128..]), one warp per box.
+template <int P>
+__global__ void lf_tc_interp_kernel(LfArgs a, const int* __restrict__ tcl, long long rows, const float* __restrict__ C,
+                                    void* out) {
+    constexpr int NP = P + 1;
+    __shared__ float sV[8][TC_M];  // the box's products, one slot per warp (blocks of 256 threads)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* V = sV[wib];
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = w0; row < rows; row += nw) {
+        const int sA = a.lfslot[tcl[row]];
+        const int m0 = a.bstart[sA], m1 = a.bstart[sA + 1];
+        __syncwarp();
+        for (int i = lane; i < TC_M; i += 32) V[i] = __ldg(C + (size_t)row * TC_M + i);
+        __syncwarp();
+        for (int m = m0 + lane; m < m1; m += 32) {
+            float wx[NP], wy[NP], wz[NP];
+            lagrange_w<float, P>(a.nt[3 * (long long)m], wx);
+            lagrange_w<float, P>(a.nt[3 * (long long)m + 1], wy);
+            lagrange_w<float, P>(a.nt[3 * (long long)m + 2], wz);
+            float gr = 0.f, gi = 0.f;
+#pragma unroll 1
+            for (int jz = 0; jz < NP; ++jz)
+#pragma unroll
+                for (int jy = 0; jy < NP; ++jy) {
+                    float rr = 0.f, ri = 0.f;
+#pragma unroll
+                    for (int jx = 0; jx < NP; ++jx) {
+                        const int v = (jz * NP + jy) * NP + jx;
+                        rr += wx[jx] * V[v];
+                        ri += wx[jx] * V[128 + v];
+                    }
+                    const float w = wy[jy] * wz[jz];
+                    gr += w * rr;
+                    gi += w * ri;
+                }
+            add_out<float>(a, out, m, make_float2(-gr, -gi));
+        }
+    }
+}
+
+// interior list-free boxes with a region: flag and list them
+__global__ void lf_tc_list_kernel(const int* lfslot, const int* blist, const int64_t* segptr, long long nlf, int nb0, int nb1,
+                                  int n0, int n1, int n2, int c, int p, int X0, int R, unsigned char* mask, int* list,
+                                  int* count) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nlf; j += (long long)gridDim.x * blockDim.x) {
+        const int b = blist[lfslot[j]];
+        const int A[3] = {b % nb0, (b / nb0) % nb1, b / (nb0 * nb1)};
+        const int n[3] = {n0, n1, n2};
+        bool in = segptr[j + 1] > segptr[j];
+        for (int d = 0; d < 3; ++d) in = in && (min(max(A[d] - c, 0), n[d] - 1 - p) - (A[d] - R - 2 * c) == X0);
+        mask[j] = in ? 1 : 0;
+        if (in) list[atomicAdd(count, 1)] = (int)j;
     }
 }
 
@@ -894,7 +1218,124 @@ pim_status launch_grid_t(const LfGeom& G, const LfArgs& a, bool adj, const void*
     }
 }
 
+// the Q-output form of the grid kernel for `rows` boxes (FP32 plans)
+template <int P, int EX>
+pim_status launch_grid_q(const LfGeom& G, const LfArgs& a, bool adj, const void* mom, float* outh, long long rows,
+                         cudaStream_t s) {
+    // no kernel table in this form: two CTAs per SM where the full form has one
+    const size_t H1 = G.H + 1;
+    const size_t sm = lf_grid_smem<float, P>(G) - sizeof(float2) * H1 * H1 * H1;
+    const int nb = (int)std::min<long long>(rows, 152LL * 64);
+    pim_status st;
+    if (adj) {
+        if ((st = set_smem(lf_grid_kernel<float, P, EX, true, true>, sm)) != PIM_OK) return st;
+        lf_grid_kernel<float, P, EX, true, true><<<nb, LF_GNT, sm, s>>>(a, (const float2*)mom, nullptr, outh);
+    } else {
+        if ((st = set_smem(lf_grid_kernel<float, P, EX, false, true>, sm)) != PIM_OK) return st;
+        lf_grid_kernel<float, P, EX, false, true><<<nb, LF_GNT, sm, s>>>(a, (const float2*)mom, nullptr, outh);
+    }
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
+
+template <int P>
+pim_status launch_grid_q_p(const LfGeom& G, const LfArgs& a, bool adj, const void* mom, float* outh, long long rows,
+                           cudaStream_t s) {
+    if (G.EX == 16) return launch_grid_q<P, 16>(G, a, adj, mom, outh, rows, s);
+    return launch_grid_q<P, 24>(G, a, adj, mom, outh, rows, s);
+}
+
+// The tensor-core form of the grid part for the interior boxes, batch by
+// batch: their local grids (Q rows), the product with the operator, and
+// step 4 (out -= w . V, out in the layout LfArgs a describes).
+pim_status lf_tc_run(pim_plan P, const LfGeom& G, const LfArgs& a, bool adj, void* out, cudaStream_t s) {
+    const PointsData& d = P->pts;
+    const long long K2 = 2LL * d.tcKP;
+    const float* Ah = d.tcA + (adj ? 2 : 0) * (size_t)TC_M * K2;
+    const float* Al = Ah + (size_t)TC_M * K2;
+    float* Bq = d.tcB;
+    pim_status st;
+    if ((st = set_smem(lf_tc_gemm_kernel, TC_SMEM)) != PIM_OK) return st;
+    for (long long b0 = 0; b0 < d.ntc; b0 += d.tcbatch) {
+        const long long rows = std::min<long long>(d.tcbatch, d.ntc - b0);
+        LfArgs q = a;
+        q.tcl = d.tcl + b0;
+        q.tcrows = rows;
+        q.tcKP = d.tcKP;
+        switch (P->p) {
+            case 2: st = launch_grid_q_p<2>(G, q, adj, d.mom, Bq, rows, s); break;
+            case 3: st = launch_grid_q_p<3>(G, q, adj, d.mom, Bq, rows, s); break;
+            default: st = launch_grid_q_p<4>(G, q, adj, d.mom, Bq, rows, s); break;
+        }
+        if (st != PIM_OK) return st;
+        lf_tc_gemm_kernel<<<(unsigned)((rows + TC_N - 1) / TC_N), TC_NT, TC_SMEM, s>>>(Ah, Al, Bq, (int)K2, rows, d.tcC,
+                                                                                        a.status);
+        PIM_CK(cudaGetLastError());
+        const unsigned nb = (unsigned)std::min<long long>((rows + 7) / 8, 152 * 16);
+        switch (P->p) {
+            case 2: lf_tc_interp_kernel<2><<<nb, 256, 0, s>>>(a, d.tcl + b0, rows, d.tcC, out); break;
+            case 3: lf_tc_interp_kernel<3><<<nb, 256, 0, s>>>(a, d.tcl + b0, rows, d.tcC, out); break;
+            default: lf_tc_interp_kernel<4><<<nb, 256, 0, s>>>(a, d.tcl + b0, rows, d.tcC, out); break;
+        }
+        PIM_CK(cudaGetLastError());
+        P->launches += 3;
+    }
+    return PIM_OK;
+}
+
 }  // namespace
+
+void lf_tc_free(pim_plan P) {
+    PointsData& d = P->pts;
+    const size_t K2 = 2 * (size_t)d.tcKP;
+    pim_free(P, d.tcmask, d.tcmask ? (size_t)d.nlf : 0);
+    pim_free(P, d.tcl, d.tcl ? (size_t)d.nlf * sizeof(int) : 0);
+    pim_free(P, d.tcA, d.tcA ? 4 * (size_t)TC_M * K2 * sizeof(float) : 0);
+    pim_free(P, d.tcB, d.tcB ? (size_t)d.tcbatch * K2 * sizeof(float) : 0);
+    pim_free(P, d.tcC, d.tcC ? (size_t)d.tcbatch * TC_M * sizeof(float) : 0);
+    d.tcmask = nullptr;
+    d.tcl = nullptr;
+    d.tcA = d.tcB = d.tcC = nullptr;
+    d.ntc = 0;
+    d.tcKP = 0;
+    d.tcbatch = 0;
+}
+
+// The interior list-free boxes of an FP32 plan and the tables of their
+// tensor-core grid part (after the list-free tables are built and nlf set).
+pim_status lf_tc_prepare(pim_plan P, cudaStream_t s) {
+    PointsData& d = P->pts;
+    lf_tc_free(P);
+    const LfGeom G = lf_geom(P);
+    if (!P->lf_tc || P->prec != PIM_FP32_MIXED || d.nlf == 0 || G.EX == 0 || P->p < 2 || P->p > 4) return PIM_OK;
+    pim_status st;
+    int* cnt = nullptr;
+    if ((st = pim_alloc(P, (void**)&d.tcmask, (size_t)d.nlf)) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.tcl, (size_t)d.nlf * sizeof(int))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&cnt, sizeof(int))) != PIM_OK) return st;
+    PIM_CK(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+    const unsigned nb = (unsigned)std::min<long long>((d.nlf + 255) / 256, 152 * 16);
+    lf_tc_list_kernel<<<nb, 256, 0, s>>>(d.lfslot, d.blist, d.segptr, d.nlf, P->nb[0], P->nb[1], P->n[0], P->n[1], P->n[2],
+                                         G.c, P->p, G.R + G.c, G.R, d.tcmask, d.tcl, cnt);
+    PIM_CK(cudaGetLastError());
+    int ntc = 0;
+    PIM_CK(cudaMemcpyAsync(&ntc, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIM_CK(cudaStreamSynchronize(s));
+    pim_free(P, cnt, sizeof(int));
+    d.ntc = ntc;
+    if (ntc == 0) return PIM_OK;
+    d.tcKP = (G.E * G.E * G.E + TC_K - 1) / TC_K * TC_K;
+    const size_t K2 = 2 * (size_t)d.tcKP;
+    d.tcbatch = std::min<long long>((ntc + TC_N - 1) / TC_N * TC_N, TC_BATCH);
+    if ((st = pim_alloc(P, (void**)&d.tcA, 4 * (size_t)TC_M * K2 * sizeof(float))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.tcB, (size_t)d.tcbatch * K2 * sizeof(float))) != PIM_OK) return st;
+    if ((st = pim_alloc(P, (void**)&d.tcC, (size_t)d.tcbatch * TC_M * sizeof(float))) != PIM_OK) return st;
+    const size_t A1 = (size_t)TC_M * K2;
+    lf_tc_table_kernel<<<1024, 256, 0, s>>>(d.tcA, d.tcA + A1, d.tcA + 2 * A1, d.tcA + 3 * A1, G.E, d.tcKP, G.R + G.c,
+                                            P->p + 1, P->h[0], P->h[1], P->h[2], P->k);
+    PIM_CK(cudaGetLastError());
+    return PIM_OK;
+}
 
 LfGeom lf_geom(const pim_plan_s* P) {
     LfGeom G{};
@@ -987,6 +1428,11 @@ pim_status lf_grid_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) {
     a.sorted_out = 1;  // into ulf, sorted order
     pim_status st;
     prof_mark(P, PIM_STAGE_LF_GRID, 0, s);
+    if (P->pts.ntc > 0) {
+        // the interior boxes on the tensor cores, the others below
+        if ((st = lf_tc_run(P, G, a, adj, P->ulf, s)) != PIM_OK) return st;
+        a.tcmask = P->pts.tcmask;
+    }
     if (P->prec == PIM_FP64) st = launch_grid_t<double>(G, a, adj, qs, P->pts.mom, P->pts.lfg, P->ulf, s);
     else st = launch_grid_t<float>(G, a, adj, qs, P->pts.mom, P->pts.lfg, P->ulf, s);
     prof_mark(P, PIM_STAGE_LF_GRID, 1, s);

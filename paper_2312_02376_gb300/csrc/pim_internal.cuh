@@ -36,7 +36,7 @@ __host__ __device__ constexpr bool corr_df(int mode) {
 }
 
 // device-side status flags (bit set)
-enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2, PIM_DEV_COINCIDENT = 4 };
+enum { PIM_DEV_NOT_NEUTRAL = 1, PIM_DEV_BOUNDS = 2, PIM_DEV_COINCIDENT = 4, PIM_DEV_TIMEOUT = 8 };
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -204,6 +204,15 @@ struct PointsData {
     int64_t nseg = 0;
     float4* lfp = nullptr;        // N: box-centred local coordinates (grid steps) and the packed box (w bits)
     void* lfg = nullptr;          // (H+1)^3 grid kernel g(|e|) on the offsets of the local grid, plan precision
+    // grid part on the tensor cores (FP32 plans): the interior list-free boxes
+    unsigned char* tcmask = nullptr;  // nlf: 1 if box j is handled there
+    int* tcl = nullptr;               // ntc list-free indices
+    int64_t ntc = 0;
+    int tcKP = 0;                     // E^3 padded to a multiple of 32
+    long long tcbatch = 0;            // boxes per batch
+    float* tcA = nullptr;             // forward hi, lo, adjoint hi, lo: 4 x 256 x 2 tcKP
+    float* tcB = nullptr;             // a batch's FP32 Q rows, tcbatch x 2 tcKP
+    float* tcC = nullptr;             // tcbatch x 256 products
     int64_t lf_points = 0;        // points in list-free boxes
     int64_t lf_pairs = 0;         // (observer, source, image) pairs their correction sums per apply
 };
@@ -291,6 +300,7 @@ struct pim_plan_s {
     bool no_multi = false;        // keep the fused per-RHS path (set by pim_apply_noalloc)
     int autotune = 1;
     int with_gradient = 0;
+    int lf_tc = 1;                // list-free grid part on the tensor cores where it applies
     int lf_min_work = 0;          // list-free boxes: n_box x region points >= this (0: off)
     void* gD = nullptr;           // second full grid (adjoint potential of the gradient)
     void* gsrt = nullptr;         // sorted upstream gradient g, complex<T>, N
@@ -392,6 +402,8 @@ pim_status lf_add(pim_plan P, void* dst, bool sorted_out, cudaStream_t s);
 int lf_stream_priority();  // the device's lowest stream priority
 pim_status lf_check(pim_plan P, cudaStream_t s);
 pim_status lf_build_table(pim_plan P, cudaStream_t s);
+pim_status lf_tc_prepare(pim_plan P, cudaStream_t s);  // after the list-free tables and nlf
+void lf_tc_free(pim_plan P);
 
 // batch.cu
 void batch_forget(pim_plan P);

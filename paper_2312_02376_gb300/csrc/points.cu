@@ -899,6 +899,7 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
     d.nlf = nlf;
     d.lf_pairs = (int64_t)ht[0];
     d.lf_points = (int64_t)ht[1];
+    if (nlf > 0 && (st = lf_tc_prepare(P, s)) != PIM_OK) return st;
     return PIM_OK;
 }
 
@@ -1017,6 +1018,7 @@ pim_status points_update(pim_plan P, const double* xyz, cudaStream_t s) {
 }
 
 void points_free(pim_plan P) {
+    lf_tc_free(P);
     PointsData& d = P->pts;
     const size_t N = (size_t)d.N;
     pim_free(P, d.perm, N * sizeof(int));

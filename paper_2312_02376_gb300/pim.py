@@ -34,7 +34,7 @@ class pim_options(ctypes.Structure):
                 ("neutral_tol", ctypes.c_double), ("series_tol", ctypes.c_double), ("mem_cap", ctypes.c_size_t),
                 ("autotune", ctypes.c_int), ("with_gradient", ctypes.c_int), ("corr_split", ctypes.c_int),
                 ("gather_variant", ctypes.c_int), ("corr_listfree", ctypes.c_int), ("k_imag", ctypes.c_double),
-                ("k0_imag", ctypes.c_double * 3)]
+                ("k0_imag", ctypes.c_double * 3), ("lf_tensor_cores", ctypes.c_int)]
 
 
 class pim_info(ctypes.Structure):
@@ -44,7 +44,7 @@ class pim_info(ctypes.Structure):
                 ("nnz", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_ms", ctypes.c_double),
                 ("points_ms", ctypes.c_double), ("launches", ctypes.c_int64), ("gather_variant", ctypes.c_int),
                 ("gather_variants", ctypes.c_int), ("lf_boxes", ctypes.c_int64), ("lf_points", ctypes.c_int64),
-                ("lf_pairs", ctypes.c_int64)]
+                ("lf_pairs", ctypes.c_int64), ("lf_tc_boxes", ctypes.c_int64)]
 
 
 class PimError(RuntimeError):
@@ -277,7 +277,8 @@ class Plan:
     """
 
     def __init__(self, D, pdims, k, k0, n, p=4, layers=1, precision="fp32", b=None, nf=None, pf=None,
-                 corr_mode=None, cube=False, listfree=None, neutral_tol=None, mem_cap=0, autotune=None,
+                 corr_mode=None, cube=False, listfree=None, lf_tensor_cores=None, neutral_tol=None, mem_cap=0,
+                 autotune=None,
                  with_gradient=False, gather_variant=None, corr_split=None, stream=None):
         self.D = np.asarray(D, np.float64)
         self.n = np.asarray(n, np.int64)
@@ -301,6 +302,8 @@ class Plan:
             opt.corr_mode = int(corr_mode)
         if listfree is not None:
             opt.corr_listfree = int(listfree)
+        if lf_tensor_cores is not None:
+            opt.lf_tensor_cores = 1 if lf_tensor_cores else 0
         if neutral_tol is not None:
             opt.neutral_tol = float(neutral_tol)
         opt.corr_cube = 1 if cube else 0

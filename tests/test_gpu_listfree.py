@@ -208,3 +208,21 @@ def test_listfree_rejects_coincident_points():
             pl.set_points(torch.tensor(pts, dtype=torch.float64, device="cuda"))
         assert e.value.status == pim.PIM_ERR_ARG
         pl.close()
+
+
+@pytest.mark.parametrize("name", ["helmholtz3d_bloch", "npsp3d", "helmholtz2d_bloch", "p2_helmholtz3d"])
+def test_fp32_grid_part_on_tensor_cores_equals_cuda_cores(name, cache):
+    """The interior boxes' grid part as one TF32-split matrix product on the
+    tensor cores against the CUDA-core kernel, forward and adjoint: the same
+    sums in FP32 (bar 2e-6)."""
+    W, _, _ = oracle_results(name, cache)
+    a = gpu_plan(W, "fp32", listfree=1)
+    b = gpu_plan(W, "fp32", listfree=1, lf_tensor_cores=False)
+    assert a.info().lf_tc_boxes > 0 and b.info().lf_tc_boxes == 0
+    q = to_dev(W.q, "fp32", is_real(W))
+    ua, ub = a.apply(q).cpu().numpy(), b.apply(q).cpu().numpy()
+    wa, wb = a.apply_adjoint(q).cpu().numpy(), b.apply_adjoint(q).cpu().numpy()
+    assert a.device_status() == pim.PIM_OK
+    assert rel(ua, ub) < 2e-6 and rel(wa, wb) < 2e-6, (rel(ua, ub), rel(wa, wb))
+    a.close()
+    b.close()
