@@ -322,6 +322,37 @@ def lf_nterm(W):
     return 0
 
 
+def tc_roofline(W, info, ms):
+    """The list-free grid part's matrix product on the tensor cores: executed
+    TF32 operations per launch (three products, hi.hi + hi.lo + lo.hi, of the
+    256 x 2 KP operator by 2 KP x boxes: 6 x 256 x 2 KP per box; KP = E^3
+    padded to 32, E = 2 (b + 1) + 2 floor(p/2) + p + 1) against the TF32 peak
+    derived from the measured sustained bf16 GEMM rate x the nominal
+    TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); also the useful complex work
+    (125 x E^3 complex multiply-adds, 8 operations each, per box)."""
+    E = 2 * (W.b + 1) + 2 * (W.p // 2) + W.p + 1
+    KP = (E ** 3 + 31) // 32 * 32
+    boxes = int(info.lf_tc_boxes)
+    fl = 6.0 * 256 * 2 * KP * boxes
+    useful = 8.0 * (W.p + 1) ** 3 * E ** 3 * boxes
+    pk = measured_peaks_all()
+    peak = pk.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+    ach = fl / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "lf_tc_gemm_kernel (list-free grid part: tcgen05 kind::tf32, 3 TF32 products "
+                                        "per FP32 product)",
+            "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+            "peak_kind": "measured sustained bf16 x 1.1/2.25 (nominal TF32 / bf16)", "traffic": None,
+            "executed_flops_per_launch": fl, "useful_complex_flops_per_launch": useful, "boxes": boxes,
+            "kernel_ms": round(ms, 4)}
+
+
+def measured_peaks_all():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def fp32_alu_peak():
     """FP32 FLOP/s of the chip's CUDA cores: 152 SMs x 128 FP32 lanes x 2 (FMA)
     x the maximum SM clock (2070 MHz)."""
@@ -441,7 +472,9 @@ def run_gpu(args):
                               "traffic": None, "algorithmic_flops_per_launch": fl,
                               "pairs_per_launch": int(info.lf_pairs), "flops_per_pair": lf_pair_flops(nt if nt else 8),
                               "kernel_ms": round(x_ms, 4)})
-        # the dominant kernel of the two modelled ones first
+        if int(getattr(info, "lf_tc_boxes", 0)) > 0 and per.get("lf_tc_gemm", 0) > 0:
+            rooflines.append(tc_roofline(W, info, per["lf_tc_gemm"]))
+        # the dominant kernel of the modelled ones first
         rooflines.sort(key=lambda r: -r["kernel_ms"])
         apply_ms = per["apply"]
         stages_hbm = hbm_table(W, info, per, peak, fp64, nbig)

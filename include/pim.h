@@ -180,7 +180,9 @@ typedef enum {
     PIM_STAGE_CORR_MULTI = 8,/* several right-hand sides: the one stored-list correction
                                 launch for all of them (recorded in the ring slot of the
                                 call's last right-hand side)                            */
-    PIM_NUM_STAGES = 9
+    PIM_STAGE_LF_TC_GEMM = 9,/* list-free grid part on the tensor cores: the matrix
+                                product(s) alone (first to last batch)                  */
+    PIM_NUM_STAGES = 10
 } pim_stage;
 
 /* Fills *opt with the defaults documented above. */

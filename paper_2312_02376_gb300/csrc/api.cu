@@ -708,7 +708,7 @@ pim_status pim_stage_times(pim_plan P, double* ms, int n, int64_t* count) {
 
 const char* pim_stage_name(int stage) {
     static const char* names[PIM_NUM_STAGES] = {"permute", "spread", "fft", "gather_correct", "far", "apply",
-                                                "lf_exact", "lf_grid", "corr_multi"};
+                                                "lf_exact", "lf_grid", "corr_multi", "lf_tc_gemm"};
     return stage >= 0 && stage < PIM_NUM_STAGES ? names[stage] : nullptr;
 }
 

@@ -765,7 +765,7 @@ constexpr int TC_M = 256, TC_N = 128, TC_K = 32, TC_NT = 128;
 constexpr int TC_ABYTES = TC_M * TC_K * 4, TC_BBYTES = TC_N * TC_K * 4;
 constexpr int TC_STAGE = 2 * TC_ABYTES + 2 * TC_BBYTES;
 constexpr size_t TC_SMEM = 2 * (size_t)TC_STAGE + 1024 + 64;
-constexpr long long TC_BATCH = 32768;  // boxes per batch (their Q rows: 32768 x 2KP x 8 bytes)
+constexpr long long TC_BATCH = 131072;  // boxes per batch (their FP32 Q rows: 131072 x 2KP x 4 bytes)
 
 __device__ __forceinline__ uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -1268,9 +1268,11 @@ pim_status lf_tc_run(pim_plan P, const LfGeom& G, const LfArgs& a, bool adj, voi
             default: st = launch_grid_q_p<4>(G, q, adj, d.mom, Bq, rows, s); break;
         }
         if (st != PIM_OK) return st;
+        if (b0 == 0) prof_mark(P, PIM_STAGE_LF_TC_GEMM, 0, s);
         lf_tc_gemm_kernel<<<(unsigned)((rows + TC_N - 1) / TC_N), TC_NT, TC_SMEM, s>>>(Ah, Al, Bq, (int)K2, rows, d.tcC,
                                                                                         a.status);
         PIM_CK(cudaGetLastError());
+        if (b0 + rows >= d.ntc) prof_mark(P, PIM_STAGE_LF_TC_GEMM, 1, s);
         const unsigned nb = (unsigned)std::min<long long>((rows + 7) / 8, 152 * 16);
         switch (P->p) {
             case 2: lf_tc_interp_kernel<2><<<nb, 256, 0, s>>>(a, d.tcl + b0, rows, d.tcC, out); break;

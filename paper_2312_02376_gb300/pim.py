@@ -25,7 +25,8 @@ EXPORTS = ["pim_options_default", "pim_status_string", "pim_last_error", "pim_pl
            "pim_stage_times", "pim_stage_name", "pim_position_grad", "pim_position_grad_reuse", "pim_update_positions",
            "pim_apply_noalloc", "pim_set_points_observers", "pim_apply_observers", "pim_apply_observers_adjoint",
            "pim_apply_batched", "pim_debug_copy", "pim_destroy"]
-STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply", "lf_exact", "lf_grid", "corr_multi"]
+STAGES = ["permute", "spread", "fft", "gather_correct", "far", "apply", "lf_exact", "lf_grid", "corr_multi",
+          "lf_tc_gemm"]
 
 
 class pim_options(ctypes.Structure):
