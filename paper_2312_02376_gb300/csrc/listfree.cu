@@ -199,10 +199,9 @@ __device__ __forceinline__ float rsqrt_sfu(float x) {
 // as polynomials in s (coefficients pc, ps); NT = 0: sincosf.  CHECK: the
 // pair may be the point itself (s = 0), which adds nothing.
 template <int MODE, int NT, bool CHECK>
-__device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float& ar, float& ai) {
+__device__ __forceinline__ void g0_val(const LfArgs& a, float s, float& gr, float& gim) {
     float ri = rsqrt_sfu(s);
     if (CHECK) ri = s > 0.f ? ri : 0.f;
-    float gr, gim;
     if (NT > 0) {
         float pcv = a.pc[NT - 1], psv = a.ps[NT - 1];
 #pragma unroll
@@ -220,6 +219,12 @@ __device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float
         gim = -sn * s4;
     }
     if (MODE == 1) gim = -gim;
+}
+
+template <int MODE, int NT, bool CHECK>
+__device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float& ar, float& ai) {
+    float gr, gim;
+    g0_val<MODE, NT, CHECK>(a, s, gr, gim);
     ar = fmaf(gr, q.x, fmaf(-gim, q.y, ar));
     ai = fmaf(gr, q.y, fmaf(gim, q.x, ai));
 }
@@ -231,12 +236,16 @@ __device__ __forceinline__ void g0_mac(const LfArgs& a, float s, float2 q, float
 // relative to A's centre (heads sX, sO; tails sX + LF_CH / 2, sOl), their
 // differences formed exactly before they are scaled by h; otherwise FP32
 // positions in physical units (sX; observers sO scaled by h).
-template <int MODE, int NT, bool CHECK, bool PREC, int LF_OB>
+// REV (far chunks of the symmetric form): each source's sum over the
+// observers of K q_obs (K = G0, conj for MODE 1) is also formed, per source in
+// sRev[s] (each source belongs to one thread for all observer groups).
+template <int MODE, int NT, bool CHECK, bool PREC, int LF_OB, int CH, bool REV>
 __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, const float2* sQ, const float4* sO,
-                                            const float4* sOl, float* sAcc, int no, int cnt, int warp, int lane) {
+                                            const float4* sOl, float* sAcc, int no, int cnt, int warp, int lane,
+                                            const float2* sOq, float2* sRev) {
     constexpr int NV = 2 * LF_OB, SH = NV == 16 ? 1 : 2;   // lane >> SH: the value a lane holds
     const int ngr = (no + LF_OB - 1) / LF_OB;
-    const float4* sXl = sX + LF_CH / 2;
+    const float4* sXl = sX + CH / 2;
     for (int gi = 0; gi < ngr; ++gi) {
         float ox[LF_OB], oy[LF_OB], oz[LF_OB], olx[LF_OB], oly[LF_OB], olz[LF_OB], ar[LF_OB], ai[LF_OB];
 #pragma unroll
@@ -259,11 +268,20 @@ __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, c
             ar[k] = 0.f;
             ai[k] = 0.f;
         }
+        float2 oq[REV ? LF_OB : 1];
+        if (REV) {
+#pragma unroll
+            for (int k = 0; k < LF_OB; ++k) {
+                const int i = gi * LF_OB + k;
+                oq[k] = i < no ? sOq[i] : make_float2(0.f, 0.f);
+            }
+        }
         for (int s = warp * 32 + lane; s < cnt; s += LF_NT) {
             const float4 X = sX[s];
             const float2 q = sQ[s];
             float4 Xl;
             if (PREC) Xl = sXl[s];
+            float rr = 0.f, rim = 0.f;
 #pragma unroll
             for (int k = 0; k < LF_OB; ++k) {
                 float dx = ox[k] - X.x, dy = oy[k] - X.y, dz = oz[k] - X.z;
@@ -273,7 +291,22 @@ __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, c
                     dy = (dy + (oly[k] - Xl.y)) * a.hf[1];
                     dz = (dz + (olz[k] - Xl.z)) * a.hf[2];
                 }
-                g0_mac<MODE, NT, CHECK>(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), q, ar[k], ai[k]);
+                if (REV) {
+                    float gr, gim;
+                    g0_val<MODE, NT, CHECK>(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), gr, gim);
+                    ar[k] = fmaf(gr, q.x, fmaf(-gim, q.y, ar[k]));
+                    ai[k] = fmaf(gr, q.y, fmaf(gim, q.x, ai[k]));
+                    rr = fmaf(gr, oq[k].x, fmaf(-gim, oq[k].y, rr));
+                    rim = fmaf(gr, oq[k].y, fmaf(gim, oq[k].x, rim));
+                } else {
+                    g0_mac<MODE, NT, CHECK>(a, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), q, ar[k], ai[k]);
+                }
+            }
+            if (REV) {
+                float2 t = sRev[s];
+                t.x += rr;
+                t.y += rim;
+                sRev[s] = t;
             }
         }
         float v[2 * LF_OB];
@@ -302,17 +335,27 @@ __device__ __forceinline__ void exact_chunk(const LfArgs& a, const float4* sX, c
 //
 // MODE 0: forward, 1: adjoint (conj(G0)), 2: check only (flags pairs of
 // distinct points with s = 0).
-template <int MODE, int NT>
+//
+// SYM (one right-hand side, the exact list with flagged segments): beyond the
+// 27 boxes a flagged partner box is list-free and keeps no segment of this
+// box, so this CTA sums each such pair once for both: K times the source into
+// the observer's sum, K times the observer's strength into the source's
+// (with the phase of the mirrored image), added to ulf by atomics; ulf is zero
+// at launch.  Chunks of 1280 points keep three CTAs per SM.
+template <int MODE, int NT, bool SYM = false>
 __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2* __restrict__ qs, void* out) {
+    constexpr int CH = SYM ? 1280 : LF_CH;
     extern __shared__ __align__(16) unsigned char smem[];
-    float4* sX = (float4*)smem;                          // LF_CH
-    float2* sQ = (float2*)(sX + LF_CH);                  // LF_CH
-    float4* sO = (float4*)(sQ + LF_CH);                  // LF_MAXOBS: heads, grid steps
+    float4* sX = (float4*)smem;                          // CH
+    float2* sQ = (float2*)(sX + CH);                     // CH
+    float4* sO = (float4*)(sQ + CH);                     // LF_MAXOBS: heads, grid steps
     float4* sOl = sO + LF_MAXOBS;                        // LF_MAXOBS: tails
     float* sAcc = (float*)(sOl + LF_MAXOBS);             // 2 LF_MAXOBS
     int4* sSeg = (int4*)(sAcc + 2 * LF_MAXOBS);          // LF_MAXSEG
     int* sP0 = (int*)(sSeg + LF_MAXSEG);                 // LF_MAXSEG
-    int* sIdx = sP0 + LF_MAXSEG;                         // LF_CH (check mode)
+    int* sIdx = sP0 + LF_MAXSEG;                         // CH (check mode; SYM: image << 25 | point, or ~0)
+    float2* sRev = (float2*)(sIdx + CH);                 // CH (SYM)
+    float2* sOq = sRev + CH;                             // LF_MAXOBS (SYM): the observers' strengths
     __shared__ long long sj;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // boxes are taken from a counter (zero at launch): the CTAs stay resident
@@ -351,12 +394,13 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
                 sOl[i] = a.lfl[m0 + o0 + i];
                 sAcc[2 * i] = 0.f;
                 sAcc[2 * i + 1] = 0.f;
+                if (SYM) sOq[i] = qs[m0 + o0 + i];
             }
             int v0 = 0;
             while (v0 < total) {
                 const bool own = v0 < nself, prec = v0 < nnear;
                 const int vend = own ? nself : (prec ? nnear : total);
-                const int cnt = min(prec ? LF_CH / 2 : LF_CH, vend - v0);
+                const int cnt = min(prec ? CH / 2 : CH, vend - v0);
                 __syncthreads();
                 // stage: every thread finds the segment of each of its points
                 // (binary search) and loads it, the loads of all in flight
@@ -369,7 +413,7 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
                     const int gs = find_segment<false>(tab, ns, f);
                     const int4 sg = tab[gs];
                     const int nn = (p0t ? p0t[gs] : a.bstart[sg.x]) + (f - sg.w);
-                    const int ii = sg.z & 255;
+                    const int ii = sg.z & 127;
                     const float4 L = a.lfp[nn];
                     int Bn[3];
                     unpack3(__float_as_uint(L.w), Bn[0], Bn[1], Bn[2]);
@@ -381,10 +425,14 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
                         const float4 Ll = a.lfl[nn];
                         const float sx = bx + L.x, sy = by + L.y, sz = bz + L.z;
                         sX[t] = make_float4(sx, sy, sz, 0.f);
-                        sX[LF_CH / 2 + t] = make_float4((L.x - (sx - bx)) + Ll.x, (L.y - (sy - by)) + Ll.y,
-                                                        (L.z - (sz - bz)) + Ll.z, 0.f);
+                        sX[CH / 2 + t] = make_float4((L.x - (sx - bx)) + Ll.x, (L.y - (sy - by)) + Ll.y,
+                                                     (L.z - (sz - bz)) + Ll.z, 0.f);
                     } else {
                         sX[t] = make_float4((bx + L.x) * a.hf[0], (by + L.y) * a.hf[1], (bz + L.z) * a.hf[2], 0.f);
+                        if (SYM) {
+                            ((unsigned*)sIdx)[t] = (sg.z & 128) ? ((unsigned)ii << 25) | (unsigned)nn : 0xFFFFFFFFu;
+                            sRev[t] = make_float2(0.f, 0.f);
+                        }
                     }
                     if (MODE == 2) {
                         sIdx[t] = ii == a.self_img ? nn : -1;
@@ -402,7 +450,7 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
                         const float4 O = sO[i], X = sX[s];
                         float dx = O.x - X.x, dy = O.y - X.y, dz = O.z - X.z;
                         if (prec) {
-                            const float4 Ol = sOl[i], Xl = sX[LF_CH / 2 + s];
+                            const float4 Ol = sOl[i], Xl = sX[CH / 2 + s];
                             dx += Ol.x - Xl.x;
                             dy += Ol.y - Xl.y;
                             dz += Ol.z - Xl.z;
@@ -415,11 +463,29 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
                             atomicOr(a.status, PIM_DEV_COINCIDENT);
                     }
                 } else if (own) {
-                    exact_chunk<MODE, NT, true, true, 4>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
+                    exact_chunk<MODE, NT, true, true, 4, CH, false>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane, sOq,
+                                                                    sRev);
                 } else if (prec) {
-                    exact_chunk<MODE, NT, false, true, 4>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
+                    exact_chunk<MODE, NT, false, true, 4, CH, false>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane, sOq,
+                                                                     sRev);
                 } else {
-                    exact_chunk<MODE, NT, false, false, 8>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane);
+                    exact_chunk<MODE, NT, false, false, 8, CH, SYM>(a, sX, sQ, sO, sOl, sAcc, no, cnt, warp, lane, sOq,
+                                                                    sRev);
+                    if (SYM) {
+                        // the sources' sums, with the phase of the mirrored image,
+                        // into their own outputs (other CTAs add to them as well)
+                        __syncthreads();
+                        for (int t = tid; t < cnt; t += LF_NT) {
+                            const unsigned code = ((const unsigned*)sIdx)[t];
+                            if (code == 0xFFFFFFFFu) continue;
+                            const int nn = (int)(code & 0x1FFFFFFu), ii = (int)(code >> 25);
+                            const double2 phd = a.phase[a.nimg - 1 - ii];
+                            const float2 S = sRev[t];
+                            const float px = (float)phd.x, py = (float)phd.y;
+                            atomicAdd((float*)a.ulf + 2 * (long long)nn, px * S.x - py * S.y);
+                            atomicAdd((float*)a.ulf + 2 * (long long)nn + 1, px * S.y + py * S.x);
+                        }
+                    }
                 }
                 v0 += cnt;
             }
@@ -427,8 +493,14 @@ __global__ void __launch_bounds__(LF_NT, 3) lf_exact_f32(LfArgs a, const float2*
             if (MODE != 2)
                 for (int i = tid; i < no; i += LF_NT) {
                     const float2 v = make_float2(sAcc[2 * i], sAcc[2 * i + 1]);
-                    if (a.ulf) ((float2*)a.ulf)[m0 + o0 + i] = v;
-                    else add_out<float>(a, out, m0 + o0 + i, v);
+                    if (SYM) {
+                        atomicAdd((float*)a.ulf + 2 * (long long)(m0 + o0 + i), v.x);
+                        atomicAdd((float*)a.ulf + 2 * (long long)(m0 + o0 + i) + 1, v.y);
+                    } else if (a.ulf) {
+                        ((float2*)a.ulf)[m0 + o0 + i] = v;
+                    } else {
+                        add_out<float>(a, out, m0 + o0 + i, v);
+                    }
                 }
         }
     }
@@ -1125,9 +1197,12 @@ LfArgs lf_args(pim_plan P, const LfGeom& G) {
 
 // shared memory of the exact-part kernels (the point indices only in check
 // mode, so that three FP32 CTAs fit an SM)
-size_t lf_exact_smem(bool f64, bool check) {
+size_t lf_exact_smem(bool f64, bool check, bool sym = false) {
     const size_t segs = LF_MAXSEG * (sizeof(int4) + sizeof(int));
     if (f64) return LF_CH * (sizeof(dpos4) + sizeof(double2) + sizeof(int)) + segs;
+    if (sym)
+        return 1280 * (sizeof(float4) + sizeof(float2) + sizeof(int) + sizeof(float2)) +
+               LF_MAXOBS * (2 * sizeof(float4) + 2 * sizeof(float) + sizeof(float2)) + segs;
     return LF_CH * (sizeof(float4) + sizeof(float2) + (check ? sizeof(int) : 0)) +
            LF_MAXOBS * (2 * sizeof(float4) + 2 * sizeof(float)) + segs;
 }
@@ -1154,15 +1229,20 @@ constexpr int LF_CTAS_ALONE = 3, LF_CTAS_SHARED = 3;
 
 template <int MODE>
 pim_status launch_exact_f32(const LfGeom& G, const LfArgs& a, const void* qs, void* dst, cudaStream_t s,
-                            int ctas_per_sm = LF_CTAS_ALONE) {
-    const size_t sm = lf_exact_smem(false, MODE == 2);
+                            int ctas_per_sm = LF_CTAS_ALONE, bool sym = false) {
+    const size_t sm = lf_exact_smem(false, MODE == 2, sym && MODE != 2);
     const int nb = (int)std::min<long long>(a.nlf, 152LL * ctas_per_sm);
     PIM_CK(cudaMemsetAsync(a.next, 0, sizeof(unsigned long long), s));
     pim_status st;
 #define PIM_LF_EX(NTV)                                                                              \
     do {                                                                                            \
-        if ((st = set_smem(lf_exact_f32<MODE, NTV>, sm)) != PIM_OK) return st;                      \
-        lf_exact_f32<MODE, NTV><<<nb, LF_NT, sm, s>>>(a, (const float2*)qs, dst);                   \
+        if (sym && MODE != 2) {                                                                     \
+            if ((st = set_smem(lf_exact_f32<MODE, NTV, true>, sm)) != PIM_OK) return st;            \
+            lf_exact_f32<MODE, NTV, true><<<nb, LF_NT, sm, s>>>(a, (const float2*)qs, dst);         \
+        } else {                                                                                    \
+            if ((st = set_smem(lf_exact_f32<MODE, NTV>, sm)) != PIM_OK) return st;                  \
+            lf_exact_f32<MODE, NTV><<<nb, LF_NT, sm, s>>>(a, (const float2*)qs, dst);               \
+        }                                                                                           \
     } while (0)
     if (MODE == 2 || G.nterm == 0) PIM_LF_EX(0);
     else if (G.nterm <= 4) PIM_LF_EX(4);
@@ -1410,10 +1490,17 @@ pim_status lf_exact_async(pim_plan P, const void* qs, bool adj, cudaStream_t s) 
     a.next = P->lfnext + pim_plan_s::RHS_LANES;  // its own box counter
     pim_status st;
     prof_mark(P, PIM_STAGE_LF_EXACT, 0, s);
+    const bool sym = P->prec != PIM_FP64 && P->pts.xseg;
+    if (sym) {
+        // the pairs of two list-free boxes once for both (atomics into a zero ulf)
+        a.seg = P->pts.xseg;
+        a.segptr = P->pts.xsegptr;
+        PIM_CK(cudaMemsetAsync(P->ulf, 0, (size_t)P->pts.N * sizeof(float2), s));
+    }
     if (P->prec == PIM_FP64) st = adj ? launch_exact_f64<1>(a, qs, nullptr, s) : launch_exact_f64<0>(a, qs, nullptr, s);
     else
-        st = adj ? launch_exact_f32<1>(G, a, qs, nullptr, s, LF_CTAS_SHARED)
-                 : launch_exact_f32<0>(G, a, qs, nullptr, s, LF_CTAS_SHARED);
+        st = adj ? launch_exact_f32<1>(G, a, qs, nullptr, s, LF_CTAS_SHARED, sym)
+                 : launch_exact_f32<0>(G, a, qs, nullptr, s, LF_CTAS_SHARED, sym);
     prof_mark(P, PIM_STAGE_LF_EXACT, 1, s);
     P->launches += 1;
     return st;

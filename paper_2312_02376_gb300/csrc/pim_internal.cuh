@@ -204,6 +204,12 @@ struct PointsData {
     int64_t nseg = 0;
     float4* lfp = nullptr;        // N: box-centred local coordinates (grid steps) and the packed box (w bits)
     void* lfg = nullptr;          // (H+1)^3 grid kernel g(|e|) on the offsets of the local grid, plan precision
+    // the exact kernel's list in FP32 plans: segments as seg, with the pairs of
+    // two list-free boxes (beyond the 27 boxes) kept by the box of lower slot
+    // only, flagged 128 in the image byte (summed there for both boxes)
+    int64_t* xsegptr = nullptr;       // nlf + 1
+    int4* xseg = nullptr;
+    int64_t nxseg = 0;
     // grid part on the tensor cores (FP32 plans): the interior list-free boxes
     unsigned char* tcmask = nullptr;  // nlf: 1 if box j is handled there
     int* tcl = nullptr;               // ntc list-free indices

@@ -353,9 +353,14 @@ __global__ void lf_list_kernel(const int* flag, const int* pos, long long nne, i
 // stay in the stored rows of the box's points; sparse[j] receives their
 // number; lfself[j] the offset of the box's own points in the list (-1 if
 // the box has no moments: then they are not in it).  seg == nullptr: counts.
+// sym (the exact kernel's list, FP32 plans): beyond the 27 boxes, a partner
+// that is itself list-free, of a box with moments, is kept only by the box
+// of the lower slot, whose segment carries the flag 128 in its image byte
+// (the exact kernel then sums the pairs for both boxes); the other box drops it.
 __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, const int* blist, const int* bstart,
                               const int* dix, const int* lfslot, long long nlf, const int64_t* segptr, int* cnt,
-                              int* sparse, int4* seg, int* lfself, int* lfnear, unsigned long long* pairs) {
+                              int* sparse, int4* seg, int* lfself, int* lfnear, unsigned long long* pairs,
+                              const int* lfmark = nullptr, int sym = 0) {
     int self_img = -1;
     for (int i = 0; i < a.nimg; ++i)
         if (a.img[3 * i] == 0 && a.img[3 * i + 1] == 0 && a.img[3 * i + 2] == 0) self_img = i;
@@ -372,16 +377,17 @@ __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, 
                 const int cx = B[0] - a.img[3 * ii] * a.nL[0];
                 const bool nrow = abs(B[1] - a.img[3 * ii + 1] * a.nL[1] - by) <= 1 &&
                                   abs(B[2] - a.img[3 * ii + 2] * a.nL[2] - bz) <= 1;
-                int fs = -1, ls = -1;
+                int fs = -1, ls = -1, two = 0;
                 auto close = [&]() {
                     if (fs < 0) return;
                     if (ii == self_img && fs <= sA && sA <= ls) self = ptoff + (bstart[sA] - bstart[fs]);
-                    if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (soff << 8), ptoff);
+                    if (seg) seg[o + c] = make_int4(fs, ls + 1, ii | (two << 7) | (soff << 8), ptoff);
                     soff += ls + 1 - fs;
                     ptoff += bstart[ls + 1] - bstart[fs];
                     ++c;
                     fs = ls = -1;
                 };
+                const bool asym = sym && pass == 1 && dix[sA] >= 0;
                 for (int x = x0; x <= x1; ++x) {
                     const bool near = nrow && abs(x - cx) <= 1;
                     const int sl = bslot[row + x];
@@ -391,6 +397,19 @@ __global__ void lf_seg_kernel(PairArgs a, const int* box_ptr, const int* bslot, 
                     }
                     if (sl < 0) continue;
                     if (dix[sl] >= 0) {
+                        // (the box itself under another image stays one-way:
+                        // both images of the pair are in its own list)
+                        if (asym && lfmark[sl] >= 0 && sl != sA) {
+                            if (sl < sA) {  // summed by that box for both
+                                close();
+                                continue;
+                            }
+                            if (fs >= 0 && !two) close();
+                            two = 1;
+                        } else if (two) {
+                            close();
+                            two = 0;
+                        }
                         if (fs < 0) fs = sl;
                         ls = sl;
                     } else {
@@ -891,6 +910,26 @@ static pim_status lf_classify(pim_plan P, int* rowlen, const PairArgs& pr, cudaS
         PIM_CK(cudaGetLastError());
         if ((st = lf_build_table(P, s)) != PIM_OK) return st;
         PIM_CK(cudaMemcpy(ht, tot, sizeof(unsigned long long), cudaMemcpyDeviceToHost));  // the exact pairs
+        if (P->prec == PIM_FP32_MIXED) {
+            // the exact kernel's list with the pairs of two list-free boxes once
+            int* xcnt = nullptr;
+            if ((st = pim_alloc(P, (void**)&xcnt, (size_t)nlf * sizeof(int))) != PIM_OK) return st;
+            lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, nullptr,
+                                             xcnt, sparse, nullptr, nullptr, nullptr, nullptr, d.lfmark, 1);
+            PIM_CK(cudaGetLastError());
+            if ((st = pim_alloc(P, (void**)&d.xsegptr, (size_t)(nlf + 1) * sizeof(int64_t))) != PIM_OK) return st;
+            if ((st = scan<int64_t>(P, xcnt, d.xsegptr, nlf, s)) != PIM_OK) return st;
+            int64_t nx = 0;
+            PIM_CK(cudaMemcpy(&nx, d.xsegptr + nlf, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            if ((st = pim_alloc(P, (void**)&d.xseg, (size_t)std::max<int64_t>(nx, 1) * sizeof(int4))) != PIM_OK)
+                return st;
+            d.nxseg = nx;
+            lf_seg_kernel<<<nb, 128, 0, s>>>(pr, d.box_ptr, d.bslot, d.blist, d.bstart, d.dix, d.lfslot, nlf, d.xsegptr,
+                                             nullptr, nullptr, d.xseg, nullptr, nullptr, nullptr, d.lfmark, 1);
+            PIM_CK(cudaGetLastError());
+            PIM_CK(cudaStreamSynchronize(s));
+            pim_free(P, xcnt, (size_t)nlf * sizeof(int));
+        }
     }
     PIM_CK(cudaStreamSynchronize(s));
     pim_free(P, flag, (size_t)nne * sizeof(int));
@@ -1062,6 +1101,11 @@ void points_free(pim_plan P) {
     pim_free(P, d.lfmark, (size_t)(d.lfmark ? d.nne : 0) * sizeof(int));
     pim_free(P, d.segptr, (size_t)(d.nlf + 1) * sizeof(int64_t));
     pim_free(P, d.seg, (size_t)d.nseg * sizeof(int4));
+    pim_free(P, d.xsegptr, d.xsegptr ? (size_t)(d.nlf + 1) * sizeof(int64_t) : 0);
+    pim_free(P, d.xseg, d.xseg ? (size_t)std::max<int64_t>(d.nxseg, 1) * sizeof(int4) : 0);
+    d.xsegptr = nullptr;
+    d.xseg = nullptr;
+    d.nxseg = 0;
     pim_free(P, d.lfp, N * sizeof(float4));
     if (d.lfg) {
         const LfGeom G = lf_geom(P);
