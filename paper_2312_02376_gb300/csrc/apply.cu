@@ -340,6 +340,7 @@ struct FarSpreadArgs {
     const float* ft;       // local coordinates (stride 6, offset toff)
     const double* ftd;
     int toff;
+    const int* fperm;      // the points in order of their stencil start on that grid (or null: box order)
 };
 
 // Per-CTA partial far-grid charges (Eq. projection) in shared memory.  Each
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
         }
         __syncthreads();
         for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-            const int z = (int)((a.fst[m] >> 20) & 1023);
+            const int z = (int)((a.fst[a.fperm ? a.fperm[m] : m] >> 20) & 1023);
             atomicMin(&zr[0], z);
             atomicMax(&zr[1], z);
         }
@@ -427,11 +428,12 @@ __global__ void __launch_bounds__(256) far_spread_kernel(FarSpreadArgs a, const 
         T tl[3] = {T(0), T(0), T(0)};
         cplx<T> ql = mk<T>(T(0), T(0));
         if (lane < cnt) {
-            sl = a.fst[ml];
+            const long long mm = a.fperm ? (long long)a.fperm[ml] : ml;
+            sl = a.fst[mm];
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-                tl[d] = sizeof(T) == 8 ? (T)a.ftd[6 * ml + a.toff + d] : (T)a.ft[6 * ml + a.toff + d];
-            ql = qs[ml];
+                tl[d] = sizeof(T) == 8 ? (T)a.ftd[6 * mm + a.toff + d] : (T)a.ft[6 * mm + a.toff + d];
+            ql = qs[mm];
         }
         for (int j = 0; j < cnt; ++j) {
             const uint32_t sm = __shfl_sync(0xffffffffu, sl, j);
@@ -548,6 +550,7 @@ pim_status far_spread_grid(pim_plan P, long long N, const uint32_t* fst, int tof
     fa.ft = d.ft;
     fa.ftd = d.ftd;
     fa.toff = toff;
+    fa.fperm = fst == d.fs ? d.fperm_s : (fst == d.fo ? d.fperm_o : nullptr);
     pim_status st;
     if (!P->far_window) {
         fa.chunk = (int)((N + P->far_chunks - 1) / P->far_chunks);

@@ -161,6 +161,11 @@ struct PointsData {
     double* ntd = nullptr;        // near local coordinates (FP64), 3N
     uint32_t* fs = nullptr;       // far source-grid stencil starts, packed
     uint32_t* fo = nullptr;       // far observer-grid stencil starts, packed
+    // the points (box order indices) sorted by their far stencil start on the
+    // source and on the observer grid, for the far spread: runs of points that
+    // share a stencil are summed in registers before one shared-memory addition
+    int* fperm_s = nullptr;
+    int* fperm_o = nullptr;
     float* ft = nullptr;          // far local coordinates, source grid then observer grid (6N)
     double* ftd = nullptr;        // same in FP64 (FP64 plans)
     int* box_ptr = nullptr;       // nboxes + 1

@@ -7,6 +7,8 @@
 
 #include <cuda_bf16.h>
 
+#include <cub/device/device_radix_sort.cuh>
+
 #include "pim_internal.cuh"
 
 namespace {
@@ -819,6 +821,16 @@ __global__ void gtab_kernel(double2* gtab, int R, double h0, double h1, double h
     }
 }
 
+// far cell (stencil start, x fastest) of every point and its index
+__global__ void far_key_kernel(const uint32_t* fst, long long N, int nf0, int nf1, int* key, int* idx) {
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < N; m += (long long)gridDim.x * blockDim.x) {
+        const uint32_t v = fst[m];
+        const int x = (int)(v & 1023u), y = (int)((v >> 10) & 1023u), z = (int)((v >> 20) & 1023u);
+        key[m] = (z * nf1 + y) * nf0 + x;
+        idx[m] = (int)m;
+    }
+}
+
 template <typename OutT>
 pim_status scan(pim_plan P, const int* in, OutT* out, long long n, cudaStream_t s) {
     const long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -1067,6 +1079,9 @@ void points_free(pim_plan P) {
     pim_free(P, d.ntd, 3 * N * sizeof(double));
     pim_free(P, d.fs, N * sizeof(uint32_t));
     pim_free(P, d.fo, N * sizeof(uint32_t));
+    pim_free(P, d.fperm_s, d.fperm_s ? N * sizeof(int) : 0);
+    pim_free(P, d.fperm_o, d.fperm_o ? N * sizeof(int) : 0);
+    d.fperm_s = d.fperm_o = nullptr;
     pim_free(P, d.ft, 6 * N * sizeof(float));
     pim_free(P, d.ftd, 6 * N * sizeof(double));
     const size_t nboxes = (size_t)P->nb[0] * P->nb[1] * P->nb[2];
@@ -1222,6 +1237,35 @@ pim_status points_build(pim_plan P, int64_t N, const double* xyz, cudaStream_t s
     if (N > 0)
         point_data_kernel<<<1024, 256, 0, s>>>(xyz, d.perm, N, pa, d.pos, d.ns, d.nt, d.ntd, d.fs, d.fo, d.ft, d.ftd);
     PIM_CK(cudaGetLastError());
+    if (P->has_far && N > 0) {
+        // the far spread's point orders: by stencil start on each far grid
+        // (a stable sort: points of one stencil stay in box order)
+        int *kin = nullptr, *kout = nullptr, *vin = nullptr;
+        void* tmp = nullptr;
+        size_t tb = 0;
+        const int cells = P->nf[0] * P->nf[1] * P->nf[2];
+        int bits = 1;
+        while ((1 << bits) < cells) ++bits;
+        if ((st = pim_alloc(P, (void**)&d.fperm_s, N * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&d.fperm_o, N * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&kin, N * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&kout, N * sizeof(int))) != PIM_OK) return st;
+        if ((st = pim_alloc(P, (void**)&vin, N * sizeof(int))) != PIM_OK) return st;
+        PIM_CK(cub::DeviceRadixSort::SortPairs(nullptr, tb, kin, kout, vin, d.fperm_s, (int)N, 0, bits, s));
+        if ((st = pim_alloc(P, &tmp, tb)) != PIM_OK) return st;
+        for (int side = 0; side < 2; ++side) {
+            far_key_kernel<<<1024, 256, 0, s>>>(side == 0 ? d.fs : d.fo, N, P->nf[0], P->nf[1], kin, vin);
+            PIM_CK(cudaGetLastError());
+            size_t t2 = tb;
+            PIM_CK(cub::DeviceRadixSort::SortPairs(tmp, t2, kin, kout, vin, side == 0 ? d.fperm_s : d.fperm_o, (int)N, 0,
+                                                   bits, s));
+        }
+        PIM_CK(cudaStreamSynchronize(s));
+        pim_free(P, tmp, tb);
+        pim_free(P, kin, N * sizeof(int));
+        pim_free(P, kout, N * sizeof(int));
+        pim_free(P, vin, N * sizeof(int));
+    }
     // near-pair list
     int* dimg = nullptr;
     if ((st = pim_alloc(P, (void**)&dimg, sizeof(int) * 3 * P->nimg)) != PIM_OK) return st;
