@@ -34,7 +34,8 @@
  *     returns after the result has been copied back).
  *   - Threading: a plan is not thread safe.  All device work of a call is
  *     ordered on the stream passed to that call (0 = the legacy default
- *     stream); the plan's internal second stream is joined back to it.
+ *     stream); the plan's internal streams (far zone, list-free correction)
+ *     fork from it and are joined back to it.
  *
  * Errors are returned as pim_status codes; no call aborts the process, and
  * no device fault is used for control flow.  Device-side conditions (a
@@ -56,7 +57,9 @@ typedef struct pim_plan_s* pim_plan;
 typedef enum {
     PIM_OK = 0,
     PIM_ERR_ARG = 1,          /* invalid argument (null pointer, size, grid) */
-    PIM_ERR_UNSUPPORTED = 2,  /* non-rectangular lattice, complex k or k0, p out of range */
+    PIM_ERR_UNSUPPORTED = 2,  /* non-rectangular lattice, p out of range, a complex k or k0
+                                 with with_gradient, a 1D complex series outside its
+                                 evaluated regimes (k0_imag)                             */
     PIM_ERR_ANOMALY = 3,      /* Rayleigh-Wood anomaly: k_z or k_rho of a Floquet mode ~ 0 (Sec. 2) */
     PIM_ERR_NOT_NEUTRAL = 4,  /* k = k0 = 0 and |sum q| > neutral_tol * sum |q| (Eq. neutral) */
     PIM_ERR_OUT_OF_CELL = 5,  /* a point outside the closed cell [0, D] */
@@ -233,7 +236,9 @@ pim_status pim_plan_create(pim_plan* out, const double lattice[9], unsigned peri
  * bins the points into the grid's boxes (counting sort), stores their
  * stencils and interpolation coordinates, and builds the near-pair
  * correction list of Sec. 3.3 step 4 (Eq. er, single-extra-image rule) with
- * its values exp(-j k0.(i o L)) [G0(r_m - r_n - i o L) - G_grid] in FP64.
+ * its values exp(-j k0.(i o L)) [G0(r_m - r_n - i o L) - G_grid] in FP64;
+ * for the boxes corrected list-free (opt.corr_listfree) it builds their
+ * region tables instead of stored entries.
  *
  *   xyz   N x 3 row-major FP64 positions, device or host pointer; copied.
  *         Every point must lie in the closed cell [0, D] (else
