@@ -920,14 +920,33 @@ def run_coulomb_grad(args):
     return out
 
 
+TIMING_WORKLOADS = ("coulomb3d_4k", "helmholtz2d_262k", "helmholtz1d_batch", "coulomb3d_1m", "helmholtz3d_16m")
+
+
+def timing_sets(name):
+    """The point sets of a workload for the timing report, and whether its
+    plans store the position derivatives (the differentiated 3D Coulomb)."""
+    from paper_2312_02376_gb300 import inputs
+    if name == "coulomb3d_4k":
+        return [inputs.coulomb3d()], False
+    if name == "helmholtz1d_batch":
+        return inputs.helmholtz1d_batch(), False
+    if name == "coulomb3d_1m":
+        return [inputs.coulomb3d_big()], True
+    return [workload(name)], False
+
+
 def run_timing_report(args):
     """Pre-processing against execution, and the cost of periodicity (the
-    paper's Sec. 4.2 comparison): for the 2D-periodic 262k workload and the
-    3D-periodic 16M workload, the wall time of pim_plan_create and
-    pim_set_points and the CUDA-event time of a forward and an adjoint apply;
-    then the same points and grid with no periodic axis and no phase shift
-    (no far zone, one image), the apply's time and the periodic overhead
-    t_periodic / t_open - 1."""
+    paper's Sec. 4.2 comparison), for each workload named in
+    --timing-workloads: the wall time of pim_plan_create and pim_set_points
+    and the CUDA-event time of a forward and an adjoint apply (all right-hand
+    sides; summed over the point sets of the batched workload, applied one
+    set at a time); then the same points and grid with no periodic axis and
+    no phase shift (no far zone, one image), the apply's time and the
+    periodic overhead t_periodic / t_open - 1.  Each workload in its own
+    precision (FP64 for the 4096-point Coulomb set); real data where k and
+    k0 vanish."""
     import torch
 
     import __graft_entry__ as g
@@ -935,46 +954,70 @@ def run_timing_report(args):
     from paper_2312_02376_gb300 import pim
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    names = [x for x in args.timing_workloads.split(",") if x]
     rows = []
-    for name in ("helmholtz2d_262k", "helmholtz3d_16m"):
-        W = workload(name)
-        res = {"workload": name, "N": W.N, "grid": list(W.n)}
-        for label, pdims, k0 in (("periodic", W.pdims, W.k0), ("open", (), (0.0, 0.0, 0.0))):
-            t0 = time.perf_counter()
-            pl = pim.Plan(W.D, pdims, W.k, k0, W.n, p=W.p, layers=W.layers, precision="fp32", b=W.b,
-                          nf=W.nf if pdims else None, pf=W.pf, corr_mode=pim.PIM_CORR_COMPACT)
-            torch.cuda.synchronize()
-            t_create = time.perf_counter() - t0
-            xyz = torch.tensor(W.points, dtype=torch.float64, device="cuda")
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pl.set_points(xyz)
-            torch.cuda.synchronize()
-            t_points = time.perf_counter() - t0
-            q = torch.tensor(W.q, dtype=torch.complex64, device="cuda")
-            u = torch.empty_like(q)
-            w = torch.empty_like(q)
-            for _ in range(3):
-                pim.pim_apply(pl._h, q, u, 1, stream)
-                pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
-            ts = []
-            for _ in range(max(3, args.steps)):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                pim.pim_apply(pl._h, q, u, 1, stream)
-                pim.pim_apply_adjoint(pl._h, u, w, 1, stream)
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            info = pl.info()
-            res[label] = {"plan_create_s": round(t_create, 3), "plan_ms_library": round(info.plan_ms, 1),
-                          "set_points_s": round(t_points, 3), "points_ms_library": round(info.points_ms, 1),
-                          "apply_fwd_adj_ms": round(float(np.mean(ts)), 3), "nnz": int(info.nnz),
-                          "listfree_pairs": int(info.lf_pairs)}
-            pl.close()
-            del xyz, q, u, w
+    for name in names:
+        sets, grad = timing_sets(name)
+        res = {"workload": name, "N": int(sum(W.N for W in sets)), "sets": len(sets), "nrhs": sets[0].nrhs,
+               "precision": sets[0].precision, "grid": list(sets[0].n) if len(sets) == 1 else None}
+        try:
+            for label in ("periodic", "open"):
+                tot = {"plan_create_s": 0.0, "plan_ms_library": 0.0, "set_points_s": 0.0, "points_ms_library": 0.0,
+                       "apply_fwd_adj_ms": 0.0, "nnz": 0, "listfree_pairs": 0}
+                for W in sets:
+                    pdims, k0 = (W.pdims, W.k0) if label == "periodic" else ((), (0.0, 0.0, 0.0))
+                    fp64 = W.precision == "fp64"
+                    real = W.k == 0 and not any(k0)
+                    t0 = time.perf_counter()
+                    pl = pim.Plan(W.D, pdims, W.k, k0, W.n, p=W.p, layers=W.layers, precision=W.precision, b=W.b,
+                                  nf=W.nf if pdims else None, pf=W.pf,
+                                  corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_COMPACT, with_gradient=grad)
+                    torch.cuda.synchronize()
+                    t_create = time.perf_counter() - t0
+                    xyz = torch.tensor(W.points, dtype=torch.float64, device="cuda")
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    pl.set_points(xyz)
+                    torch.cuda.synchronize()
+                    t_points = time.perf_counter() - t0
+                    if real:
+                        q = torch.tensor(np.real(W.q), dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+                    else:
+                        q = torch.tensor(W.q, dtype=torch.complex128 if fp64 else torch.complex64, device="cuda")
+                    R = 1 if q.dim() == 1 else int(q.shape[1])
+                    u = torch.empty_like(q)
+                    w = torch.empty_like(q)
+                    for _ in range(3):
+                        pim.pim_apply(pl._h, q, u, R, stream)
+                        pim.pim_apply_adjoint(pl._h, u, w, R, stream)
+                    ts = []
+                    for _ in range(max(3, args.steps)):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        pim.pim_apply(pl._h, q, u, R, stream)
+                        pim.pim_apply_adjoint(pl._h, u, w, R, stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    if pl.device_status() != pim.PIM_OK:
+                        raise RuntimeError("device status %d" % pl.device_status())
+                    info = pl.info()
+                    tot["plan_create_s"] += t_create
+                    tot["plan_ms_library"] += info.plan_ms
+                    tot["set_points_s"] += t_points
+                    tot["points_ms_library"] += info.points_ms
+                    tot["apply_fwd_adj_ms"] += float(np.mean(ts))
+                    tot["nnz"] += int(info.nnz)
+                    tot["listfree_pairs"] += int(info.lf_pairs)
+                    pl.close()
+                    del xyz, q, u, w
+                    torch.cuda.empty_cache()
+                res[label] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tot.items()}
+            res["periodic_overhead"] = round(res["periodic"]["apply_fwd_adj_ms"] / res["open"]["apply_fwd_adj_ms"] - 1,
+                                             4)
+        except Exception as e:  # one workload's failure is reported in its row; the others still run
+            res["error"] = "%s: %s" % (type(e).__name__, e)
             torch.cuda.empty_cache()
-        res["periodic_overhead"] = round(res["periodic"]["apply_fwd_adj_ms"] / res["open"]["apply_fwd_adj_ms"] - 1, 4)
         rows.append(res)
     return {"report": "pre-processing vs execution; periodic vs open", "rows": rows}
 
@@ -1001,8 +1044,10 @@ def main():
     ap.add_argument("--cufft", action="store_true",
                     help="also time cuFFT (torch.fft) on the same padded grid after the timed region")
     ap.add_argument("--report", default=None, choices=["timing"],
-                    help="timing: plan and set-points times beside the apply, and the periodic overhead "
-                         "(2D 262k and 3D 16M workloads); prints its own JSON line")
+                    help="timing: plan and set-points times beside the apply, and the periodic overhead, "
+                         "for the workloads of --timing-workloads; prints its own JSON line")
+    ap.add_argument("--timing-workloads", default=",".join(TIMING_WORKLOADS),
+                    help="comma-separated workloads of --report timing (default: all five)")
     ap.add_argument("--corr-radius", type=int, default=None,
                     help="override the correction radius of the helmholtz2d workloads (for profiler captures "
                          "of the stages that do not depend on it; the line then states the radius used)")
