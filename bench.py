@@ -167,6 +167,14 @@ class ClockSampler:
 
 
 VALUE_BYTES = {0: 16, 1: 16, 2: 8, 3: 8}   # per correction value, by pim_corr_mode
+CORR_MODES = {"fp64": 0, "double_float": 1, "fp32": 2, "compact": 3}
+CORR_TEXT = {
+    0: "stored correction values FP64, summed in FP64",
+    1: "stored correction values FP64 split into two FP32 words per component, summed in double-float",
+    2: "stored correction values rounded to complex64 after the FP64 cancellation, summed in FP32",
+    3: "stored correction values computed in FP64, per row the entries above 2^-10 of its largest as FP32 "
+       "head + bf16 tail summed in double-float, the rest complex64 summed in FP32",
+}
 
 
 def gather_bytes(info, N, G, nf3, fp64=False, nbig=0):
@@ -402,9 +410,9 @@ def run_gpu(args):
         W.b = args.corr_radius
     fp64 = args.precision == "fp64"
     cdt = torch.complex128 if fp64 else torch.complex64
+    cmode = pim.PIM_CORR_FP64 if fp64 else CORR_MODES[args.corr_mode or "compact"]
     plan = pim.Plan(W.D, W.pdims, W.k, W.k0, W.n, p=W.p, layers=W.layers, precision=args.precision, b=W.b,
-                    nf=W.nf, pf=W.pf, corr_mode=pim.PIM_CORR_FP64 if fp64 else pim.PIM_CORR_COMPACT,
-                    listfree=args.listfree)
+                    nf=W.nf, pf=W.pf, corr_mode=cmode, listfree=args.listfree)
     t0 = time.perf_counter()
     plan.set_points(torch.tensor(W.points, dtype=torch.float64, device="cuda"))
     t_points = time.perf_counter() - t0
@@ -484,7 +492,8 @@ def run_gpu(args):
         hbm = {"bound": "hbm", "kernel": "gather_kernel (near gather + stored-list correction)",
                "achieved": round(gb / (g_ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                "frac": round(gb / (g_ms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind,
-               "traffic": None if fp64 or args.workload != "helmholtz2d_262k" else profile_traffic(),
+               "traffic": None if fp64 or args.workload != "helmholtz2d_262k" or int(info.corr_mode) != 3
+               else profile_traffic(),
                "algorithmic_bytes_per_launch": gb, "kernel_ms": round(g_ms, 4)}
         rooflines = [hbm]
         if info.lf_pairs > 0 and not fp64:
@@ -517,9 +526,8 @@ def run_gpu(args):
                        "listfree_pairs": int(info.lf_pairs),
                        "precision": "FP64 throughout" if fp64 else
                                     "complex64 bulk (spread, FFT, gather, list-free exact and grid sums in FP32), "
-                                    "FP64 far series and far grid sum; stored correction values computed in FP64, "
-                                    "per row the entries above 2^-10 of its largest as FP32 head + bf16 tail "
-                                    "summed in double-float, the rest complex64 summed in FP32",
+                                    "FP64 far series and far grid sum; " + CORR_TEXT[int(info.corr_mode)],
+                       "corr_mode": [k for k, v in CORR_MODES.items() if v == int(info.corr_mode)][0],
                        "rel_l2_vs_ewald_ground_truth": err_truth,
                        "ground_truth_rows": None if rows is None else int(len(rows)),
                        "set_points_s": round(t_points, 1),
@@ -1048,6 +1056,9 @@ def main():
                          "for the workloads of --timing-workloads; prints its own JSON line")
     ap.add_argument("--timing-workloads", default=",".join(TIMING_WORKLOADS),
                     help="comma-separated workloads of --report timing (default: all five)")
+    ap.add_argument("--corr-mode", default=None, choices=list(CORR_MODES),
+                    help="pim_corr_mode of the FP32 plan's stored correction values (default compact); fp64, "
+                         "double_float and fp32 for comparison with the default")
     ap.add_argument("--corr-radius", type=int, default=None,
                     help="override the correction radius of the helmholtz2d workloads (for profiler captures "
                          "of the stages that do not depend on it; the line then states the radius used)")
