@@ -97,3 +97,12 @@ def test_tensor_core_product_operations():
 
 def test_fp32_alu_peak():
     assert bench.fp32_alu_peak() == pytest.approx(152 * 128 * 2 * 2.07e9)
+
+
+def test_correction_modes_match_the_library():
+    from paper_2312_02376_gb300 import pim
+    assert bench.CORR_MODES == {"fp64": pim.PIM_CORR_FP64, "double_float": pim.PIM_CORR_DOUBLE_FLOAT,
+                                "fp32": pim.PIM_CORR_FP32, "compact": pim.PIM_CORR_COMPACT}
+    assert set(bench.CORR_TEXT) == set(bench.CORR_MODES.values()) == set(bench.VALUE_BYTES)
+    # FP64 values: 16 B per complex value, the double-float split too; complex64 and compact heads 8 B
+    assert bench.VALUE_BYTES == {0: 16, 1: 16, 2: 8, 3: 8}
